@@ -1,0 +1,270 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle runs.
+
+This module holds none of the method's arithmetic: it only builds problem
+statements -- grid sizes, material constants, boundary kinds and values, and
+the initial displacement u0 and velocity v0 fields -- from fixed seeds.  Both
+the CUDA library and the CPU oracle consume what it produces.
+
+Geometry conventions (node placement of Sec. 7, probe points at half-spacing
+offsets): along a bounded axis node k sits at (k + 1/2) dX, with walls at 0 and
+n dX; along a periodic axis node k sits at k dX.
+
+Workloads named after the paper's setting:
+  * shear_wave      -- periodic square body, transverse standing wave
+                       u_x = A sin(2 pi y / L) (64 x 64, lambda 0.5, mu 0.3).
+  * clamped_body    -- rectangular body, x- edge clamped (Dirichlet u* = 0),
+                       other edges traction-free, initial transverse velocity
+                       v_y = v_max x / L (4096 x 2048 and 8192 x 8192 variants).
+  * body_batch      -- many independent bodies with seeded sizes, materials,
+                       boundary sets and low-mode initial displacements.
+  * serving_trace   -- Poisson arrivals of bodies like body_batch's.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+PERIODIC, DIRICHLET, NEUMANN = 0, 1, 2
+EDGE_NAMES = ("x-", "x+", "y-", "y+")
+
+
+@dataclasses.dataclass
+class Edge:
+    kind: int
+    value: tuple = (0.0, 0.0)   # Dirichlet: u* at t=0; Neumann: T0
+    rate: tuple = (0.0, 0.0)    # Dirichlet: v*;        Neumann: T1
+    times: tuple = (0.0, 0.0, math.inf)  # Neumann: t_on, t_ramp, t_off
+
+    def as_dict(self) -> dict:
+        return {"kind": self.kind, "value": self.value, "rate": self.rate, "times": self.times}
+
+
+@dataclasses.dataclass
+class Problem:
+    nx: int
+    ny: int
+    lam: float
+    mu: float
+    rho0: float = 1.0
+    omega: float = 1.0
+    dX: float = 1.0
+    body: tuple = (0.0, 0.0)
+    edges: List[Edge] = dataclasses.field(default_factory=list)
+    u0: Optional[np.ndarray] = None   # [ny][nx][2] float64
+    v0: Optional[np.ndarray] = None   # [ny][nx][2] float64
+    name: str = ""
+
+    @property
+    def nodes(self) -> int:
+        return self.nx * self.ny
+
+    def edge_dicts(self) -> list:
+        return [e.as_dict() for e in self.edges]
+
+    def periodic(self, axis: int) -> bool:
+        return self.edges[2 * axis].kind == PERIODIC
+
+
+def lame_from_nu(mu: float, nu: float) -> float:
+    """Plane-strain Lame lambda from shear modulus and Poisson ratio."""
+    return 2.0 * mu * nu / (1.0 - 2.0 * nu)
+
+
+def node_coords(n: int, dX: float, periodic: bool) -> np.ndarray:
+    k = np.arange(n, dtype=np.float64)
+    return (k if periodic else k + 0.5) * dX
+
+
+def all_periodic() -> List[Edge]:
+    return [Edge(PERIODIC) for _ in range(4)]
+
+
+def clamped_free_edges() -> List[Edge]:
+    """x- clamped (u* = 0, v* = 0); x+, y-, y+ traction-free."""
+    return [Edge(DIRICHLET), Edge(NEUMANN), Edge(NEUMANN), Edge(NEUMANN)]
+
+
+# ----------------------------------------------------------------- workloads
+
+def shear_wave(n: int = 64, amp: float = 0.01, lam: float = 0.5, mu: float = 0.3,
+               rho0: float = 1.0, omega: float = 1.0, dX: float = 1.0) -> Problem:
+    """Periodic n x n body, u_x = amp sin(2 pi y / (n dX)), v = 0."""
+    y = node_coords(n, dX, True)
+    u0 = np.zeros((n, n, 2))
+    u0[:, :, 0] = amp * np.sin(2.0 * np.pi * y / (n * dX))[:, None]
+    return Problem(nx=n, ny=n, lam=lam, mu=mu, rho0=rho0, omega=omega, dX=dX,
+                   edges=all_periodic(), u0=u0, v0=np.zeros_like(u0), name=f"shear_wave_{n}")
+
+
+def longitudinal_wave(n: int = 64, amp: float = 1e-6, lam: float = 0.5, mu: float = 0.3,
+                      rho0: float = 1.0, omega: float = 1.0, dX: float = 1.0) -> Problem:
+    """Periodic n x n body, u_y = amp sin(2 pi y / (n dX)) (a P-wave)."""
+    y = node_coords(n, dX, True)
+    u0 = np.zeros((n, n, 2))
+    u0[:, :, 1] = amp * np.sin(2.0 * np.pi * y / (n * dX))[:, None]
+    return Problem(nx=n, ny=n, lam=lam, mu=mu, rho0=rho0, omega=omega, dX=dX,
+                   edges=all_periodic(), u0=u0, v0=np.zeros_like(u0), name=f"p_wave_{n}")
+
+
+def clamped_body(nx: int = 4096, ny: int = 2048, mu: float = 0.3, nu: float = 0.3,
+                 vmax: float = 0.05, rho0: float = 1.0, omega: float = 1.0,
+                 dX: float = 1.0) -> Problem:
+    """Left edge clamped, other edges traction-free, v_y = vmax x / L."""
+    x = node_coords(nx, dX, False)
+    L = nx * dX
+    v0 = np.zeros((ny, nx, 2))
+    v0[:, :, 1] = (vmax * x / L)[None, :]
+    return Problem(nx=nx, ny=ny, lam=lame_from_nu(mu, nu), mu=mu, rho0=rho0, omega=omega,
+                   dX=dX, edges=clamped_free_edges(), u0=np.zeros_like(v0), v0=v0,
+                   name=f"clamped_{nx}x{ny}")
+
+
+def smooth_random(nx: int, ny: int, edges: List[Edge], seed: int, amp: float = 0.02,
+                  vamp: float = 0.01, lam: float = 0.45, mu: float = 0.3, rho0: float = 1.0,
+                  omega: float = 1.0, dX: float = 1.0, modes: int = 3) -> Problem:
+    """Sum of a few seeded low Fourier modes in u0 and v0 (for parity tests)."""
+    rng = np.random.default_rng(seed)
+    px = edges[0].kind == PERIODIC
+    py = edges[2].kind == PERIODIC
+    x = node_coords(nx, dX, px)
+    y = node_coords(ny, dX, py)
+    Lx, Ly = nx * dX, ny * dX
+    X, Y = np.meshgrid(x, y)
+    u0 = np.zeros((ny, nx, 2))
+    v0 = np.zeros((ny, nx, 2))
+    for field, a in ((u0, amp), (v0, vamp)):
+        for comp in range(2):
+            for _ in range(modes):
+                kx = rng.integers(0, 3)
+                ky = rng.integers(0, 3)
+                ph = rng.uniform(0, 2 * np.pi, size=2)
+                c = rng.uniform(-1, 1) * a / modes
+                field[:, :, comp] += c * np.sin(2 * np.pi * kx * X / Lx + ph[0]) * np.cos(
+                    2 * np.pi * ky * Y / Ly + ph[1])
+    return Problem(nx=nx, ny=ny, lam=lam, mu=mu, rho0=rho0, omega=omega, dX=dX,
+                   edges=edges, u0=u0, v0=v0, name=f"smooth_{nx}x{ny}_s{seed}")
+
+
+def affine_patch(nx: int, ny: int, H0, edges_kind: int = NEUMANN, lam: float = 1.0,
+                 mu: float = 1.0, rho0: float = 1.0, omega: float = 1.0, dX: float = 1.0,
+                 tractions=None) -> Problem:
+    """u0 = H0 X (X node positions from the body centre), v0 = 0.
+
+    tractions: four (T_x, T_y) pairs for Neumann edges (x-, x+, y-, y+)."""
+    H0 = np.asarray(H0, dtype=np.float64).reshape(2, 2)
+    x = node_coords(nx, dX, False) - 0.5 * nx * dX
+    y = node_coords(ny, dX, False) - 0.5 * ny * dX
+    X, Y = np.meshgrid(x, y)
+    u0 = np.zeros((ny, nx, 2))
+    u0[:, :, 0] = H0[0, 0] * X + H0[0, 1] * Y
+    u0[:, :, 1] = H0[1, 0] * X + H0[1, 1] * Y
+    edges = []
+    for k in range(4):
+        T = tuple(tractions[k]) if tractions is not None else (0.0, 0.0)
+        edges.append(Edge(edges_kind, value=T, rate=T))
+    return Problem(nx=nx, ny=ny, lam=lam, mu=mu, rho0=rho0, omega=omega, dX=dX,
+                   edges=edges, u0=u0, v0=np.zeros_like(u0), name="affine_patch")
+
+
+def uniform_motion(nx: int, ny: int, v, lam: float = 0.5, mu: float = 0.3, rho0: float = 1.0,
+                   omega: float = 1.0, dX: float = 1.0) -> Problem:
+    """v0 = v everywhere, all four edges Dirichlet moving with v* = v."""
+    v = tuple(float(a) for a in v)
+    v0 = np.zeros((ny, nx, 2))
+    v0[:, :, 0], v0[:, :, 1] = v
+    edges = [Edge(DIRICHLET, value=(0.0, 0.0), rate=v) for _ in range(4)]
+    return Problem(nx=nx, ny=ny, lam=lam, mu=mu, rho0=rho0, omega=omega, dX=dX,
+                   edges=edges, u0=np.zeros_like(v0), v0=v0, name="uniform_motion")
+
+
+def tension_block(n: int = 40, T1: float = 1.0, lam: float = 1.0, mu: float = 1.0,
+                  t_ramp: float = 1.0) -> Problem:
+    """Square block of side l = 1 (dX = 1/n), traction ramped on y+ (Sec. 7).
+
+    The y- edge is clamped; x edges are traction-free."""
+    dX = 1.0 / n
+    edges = [Edge(NEUMANN), Edge(NEUMANN), Edge(DIRICHLET),
+             Edge(NEUMANN, value=(0.0, 0.0), rate=(0.0, T1), times=(0.0, t_ramp, math.inf))]
+    z = np.zeros((n, n, 2))
+    return Problem(nx=n, ny=n, lam=lam, mu=mu, dX=dX, edges=edges, u0=z, v0=z.copy(),
+                   name=f"tension_{n}")
+
+
+# ----------------------------------------------------------------- batches
+
+@dataclasses.dataclass
+class BatchSpec:
+    problems: List[Problem]
+    steps: List[int]
+
+
+def random_body(rng: np.random.Generator, side_lo: int, side_hi: int, dX: float = 1.0,
+                omega: float = 1.0) -> Problem:
+    """One body: sides U{lo..hi}, mu log-U[0.05, 0.4], nu U[0.2, 0.45],
+    periodic or clamped (50/50), low-mode initial displacement of amplitude
+    up to 0.1 L, zero velocity."""
+    nx = int(rng.integers(side_lo, side_hi + 1))
+    ny = int(rng.integers(side_lo, side_hi + 1))
+    mu = float(math.exp(rng.uniform(math.log(0.05), math.log(0.4))))
+    nu = float(rng.uniform(0.2, 0.45))
+    periodic = bool(rng.integers(0, 2) == 0)
+    A_frac = float(rng.uniform(0.0, 0.1))
+    theta = float(rng.uniform(0.0, 2 * np.pi))
+    phase = float(rng.uniform(0.0, 2 * np.pi))
+    axis = int(rng.integers(0, 2))
+    edges = all_periodic() if periodic else clamped_free_edges()
+    x = node_coords(nx, dX, periodic)
+    y = node_coords(ny, dX, periodic)
+    X, Y = np.meshgrid(x, y)
+    Lx, Ly = nx * dX, ny * dX
+    if periodic:
+        L = Ly if axis == 0 else Lx
+        m = np.sin(2 * np.pi * Y / Ly + phase) if axis == 0 else np.sin(2 * np.pi * X / Lx + phase)
+    else:
+        L = Lx
+        m = np.sin(np.pi * X / (2 * Lx))
+    A = A_frac * L
+    u0 = np.zeros((ny, nx, 2))
+    u0[:, :, 0] = A * math.cos(theta) * m
+    u0[:, :, 1] = A * math.sin(theta) * m
+    return Problem(nx=nx, ny=ny, lam=lame_from_nu(mu, nu), mu=mu, omega=omega, dX=dX,
+                   edges=edges, u0=u0, v0=np.zeros_like(u0),
+                   name=f"body_{nx}x{ny}_{'per' if periodic else 'clamp'}")
+
+
+def body_batch(count: int = 256, seed: int = 20220825, side_lo: int = 64, side_hi: int = 1024,
+               steps: int = 2000) -> BatchSpec:
+    rng = np.random.default_rng(seed)
+    probs = [random_body(rng, side_lo, side_hi) for _ in range(count)]
+    return BatchSpec(problems=probs, steps=[steps] * count)
+
+
+@dataclasses.dataclass
+class Request:
+    arrival: float
+    problem: Problem
+    steps: int
+
+
+def serving_trace(rate: float = 200.0, duration: float = 60.0, seed: int = 7,
+                  side_lo: int = 128, side_hi: int = 2048, steps_lo: int = 500,
+                  steps_hi: int = 20000, max_requests: Optional[int] = None,
+                  lazy_fields: bool = True) -> List[Request]:
+    """Poisson arrivals; each request a body as in body_batch with a
+    log-uniform step count."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out: List[Request] = []
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t >= duration:
+            break
+        prob = random_body(rng, side_lo, side_hi)
+        steps = int(round(math.exp(rng.uniform(math.log(steps_lo), math.log(steps_hi)))))
+        out.append(Request(arrival=t, problem=prob, steps=steps))
+        if max_requests is not None and len(out) >= max_requests:
+            break
+    return out

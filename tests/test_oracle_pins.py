@@ -1,0 +1,347 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: moment
+identities of the D2Q9 equilibrium (Sec. 5), the derivative of the neo-Hooke
+energy of Sec. 7, objectivity, the printed time steps of Sec. 7, conservation,
+an exact large-amplitude shear-wave solution, second-order convergence, the
+linear-elastic P-wave speed, and patch tests in which the exact solution is
+static or uniform.  The D2Q9 lattice used to take moments below is the
+textbook one, typed here independently of the oracle.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_13769_gb300 import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+# textbook D2Q9: rest, 4 axis, 4 diagonal links; weights 4/9, 1/9, 1/36
+E = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]], float)
+WT = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def _moments(f, c):
+    C = c * E
+    m0 = f.sum()
+    m1 = C.T @ f
+    m2 = np.einsum("i,ia,ib->ab", f, C, C)
+    m3 = np.einsum("i,ia,ib,ig->abg", f, C, C, C)
+    return m0, m1, m2, m3
+
+
+def _rot(a):
+    return np.array([[math.cos(a), -math.sin(a)], [math.sin(a), math.cos(a)]])
+
+
+# ------------------------------------------------------------ lattice, f^eq, psi
+
+@pytest.mark.parametrize("mu", [0.05, 0.3, 1.0, 4.0])
+def test_feq_moment_identities(mu):
+    """Sec. 5: f^eq reproduces r, j, Pbar and Qbar = C_s^2 (j d + j d + j d)."""
+    rng = np.random.default_rng(1)
+    dt, c, cs2 = oracle.time_step(1.0, mu, 1.0)
+    assert math.isclose(cs2, c * c / 3, rel_tol=1e-14)
+    for _ in range(20):
+        r = rng.normal()
+        j = rng.normal(size=2)
+        A = rng.normal(size=(2, 2))
+        Pb = A + A.T
+        f = oracle.feq(c, cs2, r, j, Pb)
+        m0, m1, m2, m3 = _moments(f, c)
+        scale = 1 + abs(r) + np.abs(Pb).max() + np.abs(j).max() * c
+        assert abs(m0 - r) < 1e-13 * scale
+        np.testing.assert_allclose(m1, j, atol=1e-13 * scale)
+        np.testing.assert_allclose(m2, Pb, atol=1e-13 * scale * c * c)
+        d = np.eye(2)
+        Q = cs2 * (np.einsum("a,bg->abg", j, d) + np.einsum("b,ag->abg", j, d) + np.einsum("g,ab->abg", j, d))
+        np.testing.assert_allclose(m3, Q, atol=1e-12 * scale * c ** 3)
+
+
+def test_lattice_weights_and_opposites():
+    Cv, w, opp = oracle.lattice(2.0)
+    np.testing.assert_allclose(Cv, 2.0 * E)
+    np.testing.assert_allclose(w, WT, rtol=0, atol=1e-16)
+    for i in range(9):
+        np.testing.assert_allclose(E[opp[i]], -E[i])
+
+
+def test_psi_moments():
+    """Eq. (source): psi has zero mass, first moment 1S, zero second moment."""
+    rng = np.random.default_rng(2)
+    for mu in (0.1, 0.3, 2.0):
+        dt, c, cs2 = oracle.time_step(1.0, mu, 1.0)
+        S = rng.normal(size=2)
+        p = oracle.psi(c, cs2, S)
+        m0, m1, m2, _ = _moments(p, c)
+        assert abs(m0) < 1e-14
+        np.testing.assert_allclose(m1, S, atol=1e-13)
+        np.testing.assert_allclose(m2, 0, atol=1e-13 * c * c)
+
+
+def test_printed_time_steps():
+    """Sec. 7 prints dt for two lattice spacings (golden fixture)."""
+    with open(os.path.join(HERE, "golden", "paper_time_steps.json")) as fh:
+        gold = json.load(fh)
+    for case in gold["cases"]:
+        dt, c, cs2 = oracle.time_step(case["dX"], case["mu"], case["rho0"])
+        assert float(f"{dt:.{case['digits']}g}") == case["dt_printed"], (dt, case)
+
+
+# ------------------------------------------------------------ constitutive law
+
+def _num_dW(H, lam, mu, h=1e-6):
+    g = np.zeros(4)
+    Hf = np.asarray(H, float).ravel()
+    for k in range(4):
+        e = np.zeros(4)
+        e[k] = h
+        g[k] = (oracle.strain_energy(Hf + e, lam, mu) - oracle.strain_energy(Hf - e, lam, mu)) / (2 * h)
+    return g.reshape(2, 2)
+
+
+@pytest.mark.parametrize("lam,mu", [(1.0, 1.0), (0.45, 0.3), (2.7, 0.3)])
+def test_piola_is_energy_derivative(lam, mu):
+    """Sec. 7: P = dW/dF, checked against a central difference of W."""
+    rng = np.random.default_rng(3)
+    for _ in range(25):
+        H = rng.uniform(-0.3, 0.3, size=(2, 2))
+        P, J = oracle.piola(H, lam, mu)
+        assert J > 0
+        np.testing.assert_allclose(P, _num_dW(H, lam, mu), atol=1e-8)
+        assert math.isclose(J, np.linalg.det(np.eye(2) + H), rel_tol=1e-13)
+
+
+def test_piola_rest_rotation_objectivity():
+    """P(I) = 0, P(R) = 0, P(QF) = Q P(F), W(R) = 0."""
+    lam, mu = 0.45, 0.3
+    P, J = oracle.piola(np.zeros((2, 2)), lam, mu)
+    assert np.abs(P).max() == 0.0 and J == 1.0
+    rng = np.random.default_rng(4)
+    for a in (0.1, 0.5, 1.3, 3.0):
+        R = _rot(a)
+        P, J = oracle.piola(R - np.eye(2), lam, mu)
+        assert np.abs(P).max() < 1e-14
+        assert abs(oracle.strain_energy(R - np.eye(2), lam, mu)) < 1e-14
+        H = rng.uniform(-0.2, 0.2, size=(2, 2))
+        F = np.eye(2) + H
+        PF, _ = oracle.piola(H, lam, mu)
+        PQF, _ = oracle.piola(R @ F - np.eye(2), lam, mu)
+        np.testing.assert_allclose(PQF, R @ PF, atol=1e-13)
+
+
+def test_piola_linearisation_and_poisson_stress():
+    """Small strain: P -> lam tr(H) I + mu (H + H^T); Eq. (Plin) for Pbar;
+    lambda = mu: Pbar = -sigma_lin (the footnote to Sec. 4)."""
+    lam, mu = 0.7, 0.4
+    H = np.array([[0.3, -0.2], [0.5, 0.1]]) * 1e-7
+    P, _ = oracle.piola(H, lam, mu)
+    lin = lam * np.trace(H) * np.eye(2) + mu * (H + H.T)
+    np.testing.assert_allclose(P, lin, atol=1e-13)
+    Pb = oracle.poisson_stress(H, mu)
+    np.testing.assert_allclose(Pb, -mu * (H + H.T + np.trace(H) * np.eye(2)), atol=1e-22)
+    Pb1 = oracle.poisson_stress(H, 1.0)
+    sig = 1.0 * np.trace(H) * np.eye(2) + 1.0 * (H + H.T)
+    np.testing.assert_allclose(Pb1, -sig, atol=1e-22)
+
+
+def test_simple_shear_closed_form():
+    """F = [[1, g], [0, 1]]: P = mu [[0, g], [g, 0]] exactly, so P + Pbar = 0."""
+    for lam, mu in ((0.5, 0.3), (2.0, 1.0)):
+        for g in (1e-3, 0.1, 0.7):
+            H = np.array([[0.0, g], [0.0, 0.0]])
+            P, J = oracle.piola(H, lam, mu)
+            np.testing.assert_allclose(P, mu * np.array([[0, g], [g, 0]]), atol=1e-15)
+            assert np.abs(P + oracle.poisson_stress(H, mu)).max() < 1e-15
+
+
+# ------------------------------------------------------------ whole solver
+
+def _total_momentum(o):
+    return o["v"].sum(axis=(0, 1))
+
+
+@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR])
+def test_periodic_momentum_and_mass_conserved(scheme):
+    """Periodic body, b = 0: sum of j and of r are invariants of the scheme
+    (collision conserves them, streaming permutes, the periodic divergence
+    telescopes).  With b != 0 the total momentum grows by rho0 b N dt."""
+    p = W.smooth_random(20, 14, W.all_periodic(), seed=5, lam=0.3, mu=0.3, amp=0.01)
+    s = oracle.solver_from(p, scheme)
+    o0 = s.read()
+    M0, R0 = _total_momentum(o0), o0["r"].sum()
+    s.step(150)
+    o1 = s.read()
+    np.testing.assert_allclose(_total_momentum(o1), M0, atol=1e-13)
+    assert abs(o1["r"].sum() - R0) < 1e-13
+    assert np.abs(o1["u"] - o0["u"]).max() > 1e-4  # the body did move
+    p.body = (1e-4, -2e-4)
+    s = oracle.solver_from(p, scheme)
+    s.step(40)
+    o2 = s.read()
+    expect = M0 + np.array(p.body) * p.nodes * s.t
+    np.testing.assert_allclose(_total_momentum(o2), expect, atol=1e-12)
+
+
+def _shear_amplitude_series(n, amp, omega, scheme, periods=3.0):
+    p = W.shear_wave(n=n, amp=amp, omega=omega)
+    s = oracle.solver_from(p, scheme)
+    k = 2 * math.pi / n
+    basis = np.sin(k * np.arange(n))
+    w_ex = k * math.sqrt(p.mu / p.rho0)
+    nst = int(periods * 2 * math.pi / w_ex / s.dt) + 2
+    ts, a = [], []
+    for _ in range(nst):
+        u = s.read()["u"][:, :, 0].mean(axis=1)
+        a.append(2 * np.mean(u * basis))
+        ts.append(s.t)
+        s.step(1)
+    return np.array(ts), np.array(a), w_ex
+
+
+def _freq_from_zero_crossings(t, a, w_guess=None):
+    """Angular frequency of a(t) by a least-squares fit of
+    alpha cos(w t) + beta sin(w t) (w scanned, then refined)."""
+    from scipy.optimize import minimize_scalar
+
+    def resid(w):
+        M = np.stack([np.cos(w * t), np.sin(w * t)], axis=1)
+        coef, *_ = np.linalg.lstsq(M, a, rcond=None)
+        return float(np.sum((M @ coef - a) ** 2))
+
+    if w_guess is None:
+        z = [i for i in range(len(a) - 1) if a[i] * a[i + 1] < 0]
+        w_guess = math.pi / np.mean(np.diff(t[z])) if len(z) > 1 else 1.0
+    res = minimize_scalar(resid, bounds=(0.8 * w_guess, 1.2 * w_guess), method="bounded",
+                          options={"xatol": 1e-12 * w_guess})
+    return res.x
+
+
+@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR])
+def test_shear_wave_exact_solution_second_order(scheme):
+    """u_x = A sin(ky) cos(wt), w = k sqrt(mu/rho0) solves the nonlinear
+    equations exactly (simple shear: P + Pbar = 0, no source).  The lattice
+    frequency error must fall at second order in dX, for a large amplitude
+    too, and the wave must neither grow nor decay."""
+    errs = []
+    for n in (32, 64, 128):
+        t, a, w_ex = _shear_amplitude_series(n, 0.05 * n, 1.0, scheme, periods=4.0)
+        errs.append(abs(_freq_from_zero_crossings(t, a, w_ex) / w_ex - 1))
+        assert np.abs(a).max() < 1.001 * abs(a[0])
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.7 < o < 2.5 for o in orders), (errs, orders)
+    assert errs[1] < 5e-4
+
+
+def test_shear_wave_config_period():
+    """64 x 64 body of the shear-wave workload: one period lasts 64 sqrt(3)
+    steps within the lattice error (reading dt = dX / (sqrt(3) C_s))."""
+    t, a, w_ex = _shear_amplitude_series(64, 0.01, 1.0, oracle.PREDICTOR, periods=4.0)
+    steps_per_period = 2 * math.pi / _freq_from_zero_crossings(t, a, w_ex) / (t[1] - t[0])
+    assert abs(steps_per_period / (64 * math.sqrt(3)) - 1) < 1e-3
+
+
+def test_pwave_frequency_converges():
+    """Small-strain longitudinal wave with lambda != mu (exercises the source
+    1S): w -> k sqrt((lambda + 2 mu)/rho0) at second order."""
+    errs = []
+    for n in (32, 64, 128):
+        p = W.longitudinal_wave(n=n, amp=1e-6 * n, lam=0.5, mu=0.3)
+        s = oracle.solver_from(p, oracle.PREDICTOR)
+        k = 2 * math.pi / n
+        basis = np.sin(k * np.arange(n))
+        w_ex = k * math.sqrt((p.lam + 2 * p.mu) / p.rho0)
+        nst = int(3 * 2 * math.pi / w_ex / s.dt) + 2
+        ts, a = [], []
+        for _ in range(nst):
+            u = s.read()["u"][:, :, 1].mean(axis=1)
+            a.append(2 * np.mean(u * basis))
+            ts.append(s.t)
+            s.step(1)
+        errs.append(abs(_freq_from_zero_crossings(np.array(ts), np.array(a), w_ex) / w_ex - 1))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.7 < o < 2.5 for o in orders), (errs, orders)
+
+
+@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR])
+def test_neumann_patch_test_static(scheme):
+    """Affine u = H0 X, v = 0, tractions T* = P(I + H0) N on all four edges
+    (corners included): the body must stay exactly at rest."""
+    H0 = np.array([[0.02, 0.01], [-0.015, 0.03]])
+    P, _ = oracle.piola(H0, 1.0, 1.0)
+    T = [tuple(P @ np.array(n)) for n in ([-1, 0], [1, 0], [0, -1], [0, 1])]
+    p = W.affine_patch(12, 10, H0, tractions=T)
+    s = oracle.solver_from(p, scheme)
+    o0 = s.read()
+    s.step(500)
+    o = s.read()
+    assert np.abs(o["u"] - o0["u"]).max() < 1e-11
+    assert np.abs(o["v"]).max() < 1e-12
+    np.testing.assert_allclose(o["P"].reshape(-1, 2, 2), np.broadcast_to(P, (p.nodes, 2, 2)), atol=1e-12)
+
+
+def test_rigid_rotation_stays_put():
+    """u = (R - I) X with traction-free edges: P(R) = 0, the body must not move."""
+    R = _rot(0.1)
+    p = W.affine_patch(12, 10, R - np.eye(2))
+    s = oracle.solver_from(p)
+    o0 = s.read()
+    s.step(400)
+    o = s.read()
+    assert np.abs(o["u"] - o0["u"]).max() < 1e-10
+    assert np.abs(o["P"]).max() < 1e-10
+
+
+@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR])
+def test_dirichlet_uniform_motion(scheme):
+    """Uniform v0 with all edges moving at v* = v0 (bounce-back, Eq. bbcon):
+    u = v0 t exactly, no strain."""
+    v = (0.01, -0.02)
+    p = W.uniform_motion(12, 10, v)
+    s = oracle.solver_from(p, scheme)
+    s.step(300)
+    o = s.read()
+    np.testing.assert_allclose(o["u"], np.broadcast_to(np.array(v) * s.t, o["u"].shape), atol=1e-12)
+    np.testing.assert_allclose(o["v"], np.broadcast_to(v, o["v"].shape), atol=1e-13)
+    assert np.abs(o["P"]).max() < 1e-12
+
+
+def test_neutral_stability_at_lambda_eq_mu():
+    """Reading of Pbar in f^eq (second moment of the populations): at the
+    paper's lambda = mu, seeded noise in a traction-free clamped body neither
+    grows nor blows up."""
+    p = W.uniform_motion(24, 16, (0.0, 0.0), lam=0.3, mu=0.3)
+    p.edges = W.clamped_free_edges()
+    p.u0 = 1e-7 * np.random.default_rng(9).standard_normal(p.u0.shape)
+    p.v0 = np.zeros_like(p.u0)
+    s = oracle.solver_from(p)
+    s.step(100)
+    a1 = np.abs(s.read()["v"]).max()
+    s.step(1500)
+    a2 = np.abs(s.read()["v"]).max()
+    assert np.isfinite(a2) and a2 < 3 * a1
+
+
+def test_static_body_force_balance():
+    """A periodic body at rest with no load stays exactly at rest."""
+    p = W.uniform_motion(8, 8, (0, 0))
+    p.edges = W.all_periodic()
+    s = oracle.solver_from(p)
+    s.step(50)
+    o = s.read()
+    assert np.abs(o["u"]).max() == 0.0 and np.abs(o["P"]).max() == 0.0
+
+
+def test_problem_validation():
+    p = W.uniform_motion(8, 8, (0, 0))
+    bad = [W.Edge(W.PERIODIC), W.Edge(W.NEUMANN), W.Edge(W.NEUMANN), W.Edge(W.NEUMANN)]
+    p.edges = bad
+    with pytest.raises(ValueError):
+        oracle.solver_from(p)
+    p = W.uniform_motion(2, 8, (0, 0))
+    with pytest.raises(ValueError):
+        oracle.solver_from(p)
