@@ -1,0 +1,184 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) Lagrangian large-deformation lattice
+ * Boltzmann solver (Faust, Schlueter, Mueller & Mueller, arXiv 2208.13769).
+ *
+ * The library advances one 2D plane-strain body (a "context") by the update of
+ * Algorithm 1 (Sec. 5): BGK collision with He forcing (Eq. col), streaming
+ * (Eq. stream), bounce-back / anti-bounce-back boundary rules (Eqs. bbcon,
+ * abbcon, Sec. 6), moments (Eq. moment), the trapezoidal displacement update,
+ * H = Grad u (Eq. defgrad), the neo-Hooke first Piola-Kirchhoff stress P(F)
+ * of Sec. 7, the Poisson stress Pbar(H) (Eq. Plin) and the source
+ * 1S = rho0 b + Div(P + Pbar) (Eq. source1).
+ *
+ * Conventions shared by every entry point:
+ *  - Plain C types only.  Every call returns an lbm_status and never aborts,
+ *    prints or throws.  A CUDA error inside a call puts the context in a
+ *    sticky error state: later calls on it return LBM_E_CUDA.
+ *  - The library owns all device memory of a context (allocated in
+ *    lbm_create, freed in lbm_destroy).  Host buffers passed in are only read
+ *    (or written, for outputs) during the call; the caller keeps ownership.
+ *  - Work is issued on the context's CUDA stream (lbm_desc.cuda_stream, or
+ *    the legacy default stream when NULL).  lbm_step is asynchronous;
+ *    lbm_read_fields and lbm_sync synchronise that stream.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *  - Units: any consistent set.  The time step is derived, not passed:
+ *    dt = dX / (sqrt(3) C_s), C_s = sqrt(mu / rho0) (Sec. 7's printed time
+ *    steps follow this relation).
+ *  - Geometry: nx x ny nodes.  Along a bounded axis node k sits at
+ *    (k + 1/2) dX and the walls lie half a spacing outside the edge nodes;
+ *    along a periodic axis node k sits at k dX.
+ *  - Field layout on the host: row-major [ny][nx][ncomp], FP64.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+/* Entry points keep default visibility when the library is built with
+ * hidden visibility for everything else. */
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_E_INVALID = 1,  /* bad argument; nothing was changed */
+    LBM_E_OOM = 2,      /* device or host allocation failed */
+    LBM_E_CUDA = 3,     /* CUDA runtime error; the context is unusable */
+    LBM_E_UNSTABLE = 4, /* a non-finite value or J <= 0 was met (Sec. 7 needs J > 0) */
+    LBM_E_TIMEOUT = 5,  /* a bounded device-side wait gave up */
+    LBM_E_STATE = 6     /* call out of order (e.g. step before material/boundaries) */
+} lbm_status;
+
+/* Storage type of the populations (the arithmetic type follows in brackets):
+ * F64 (FP64), F32 (FP32), F16 and BF16 (FP32 arithmetic, populations stored
+ * as 16-bit values of f_i / (w_i 2^-s) with a per-context power-of-two scale
+ * s; f^eq vanishes at rest, so these are deviations from the rest state). */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3 } lbm_storage;
+
+/* Displacement carry: NATIVE keeps u in the arithmetic type; COMPENSATED keeps
+ * it as an unevaluated sum of two FP32 numbers (about 48 significant bits),
+ * so that Grad u stays accurate when |u| is large.  F16/BF16 always use
+ * COMPENSATED; F64 always uses FP64. */
+typedef enum { LBM_UCARRY_NATIVE = 0, LBM_UCARRY_COMPENSATED = 1 } lbm_ucarry;
+
+/* Time level of the source 1S in the moment computation (Sec. 5):
+ * EXPLICIT  -- Algorithm 1: the time-t source enters collision and moment.
+ * PREDICTOR -- the predictor-corrector the paper's footnote to Sec. 5 offers:
+ *              1S(t+dt) evaluated from the explicitly predicted u*(t+dt)
+ *              corrects j and u and is the next collision's source.  Default. */
+typedef enum { LBM_SCHEME_EXPLICIT = 0, LBM_SCHEME_PREDICTOR = 1 } lbm_scheme;
+
+typedef struct {
+    int32_t nx, ny;      /* nodes along x and y; each >= 3 */
+    double dX;           /* lattice spacing (> 0) */
+    int32_t storage;     /* lbm_storage */
+    int32_t u_carry;     /* lbm_ucarry (ignored for F64, F16, BF16) */
+    int32_t scheme;      /* lbm_scheme */
+    int32_t f16_scale_log2; /* s for F16/BF16 (0 = library default 10) */
+    const double* u0;    /* host, [ny][nx][2] initial displacement, NULL = 0 */
+    const double* v0;    /* host, [ny][nx][2] initial velocity, NULL = 0 */
+    void* cuda_stream;   /* cudaStream_t to issue work on; NULL = default stream */
+    int32_t device;      /* CUDA device ordinal */
+} lbm_desc;
+
+/* Creates a context: validates desc, allocates the device state and copies u0,
+ * v0 to the device.  The populations are initialised lazily, by the first
+ * lbm_step or lbm_read_fields after material and boundaries are set
+ * (Algorithm 1's initialisation: f_i = f_i^eq(r, j, Pbar) with r = -rho0 Div u0,
+ * j = rho0 v0, Pbar = Pbar(Grad u0)).  *out receives the context, or NULL on
+ * error.  Errors: LBM_E_INVALID (null pointers, nx or ny < 3, dX <= 0, unknown
+ * enum, size overflow), LBM_E_OOM, LBM_E_CUDA. */
+LBM_API lbm_status lbm_create(const lbm_desc* desc, lbm_ctx** out);
+
+/* Material of Sec. 7 (2D compressible neo-Hooke, plane strain) and the BGK
+ * relaxation omega = dt / tau (Eq. col; the paper never fixes tau).
+ * body_force: b, per unit mass (NULL = 0).  Requires mu > 0, rho0 > 0,
+ * lambda > -mu, 0 < omega < 2; else LBM_E_INVALID.  Only before the first
+ * step (afterwards LBM_E_STATE). */
+LBM_API lbm_status lbm_set_material(lbm_ctx* ctx, double lambda, double mu, double rho0, double omega,
+                            const double body_force[2]);
+
+/* Edge kinds for lbm_set_boundary. */
+enum { LBM_PERIODIC = 0, LBM_DIRICHLET = 1, LBM_NEUMANN = 2 };
+
+/* Boundary condition of one edge (Sec. 6).  edge: 0 = x-, 1 = x+, 2 = y-,
+ * 3 = y+.  PERIODIC must be set on both edges of an axis.
+ * DIRICHLET: prescribed displacement u*(t) = value + rate t, imposed through
+ *   bounce-back with the wall momentum j* = rho0 rate (Eq. bbcon).
+ * NEUMANN: prescribed first Piola-Kirchhoff traction T*(t): value (T0) before
+ *   times[0] and from times[2] on; between, it rises linearly from T0 to
+ *   rate (T1) over times[1] (times[1] = 0: a step).  Imposed through
+ *   anti-bounce-back with Pbar* (Eq. abbcon, Sec. 6).
+ * times may be NULL (0, 0, +inf).  Only before the first step. */
+LBM_API lbm_status lbm_set_boundary(lbm_ctx* ctx, int32_t edge, int32_t kind, const double value[2],
+                            const double rate[2], const double times[3]);
+
+/* Advances nsteps (>= 0) time steps: one fused stream-collide-constitutive
+ * kernel launch per step on the context's stream (replayed as CUDA graphs for
+ * long runs).  The observable fields (u, v, r) are captured at the last step.
+ * Asynchronous.  Errors: LBM_E_STATE (material or boundaries unset),
+ * LBM_E_INVALID (nsteps < 0), LBM_E_CUDA. */
+LBM_API lbm_status lbm_step(lbm_ctx* ctx, int64_t nsteps);
+
+/* Field bits for lbm_read_fields; the output holds the requested fields in
+ * this bit order, each as [ny][nx][ncomp] FP64. */
+enum {
+    LBM_FIELD_U = 1,      /* displacement u, 2 comps */
+    LBM_FIELD_V = 2,      /* velocity v = j / rho0, 2 comps */
+    LBM_FIELD_P = 4,      /* first Piola-Kirchhoff P(Grad u), 4 comps row-major */
+    LBM_FIELD_PBAR = 8,   /* Poisson stress Pbar(Grad u), 3 comps (11, 12, 22) */
+    LBM_FIELD_R = 16,     /* zeroth moment r = sum_i f_i, 1 comp */
+    LBM_FIELD_SIGMA = 32, /* Cauchy stress J^-1 P F^T, 3 comps (11, 12, 22) */
+    LBM_FIELD_J = 64      /* J = det F, 1 comp */
+};
+
+/* Number of doubles lbm_read_fields writes for mask (0 for an invalid mask). */
+LBM_API int64_t lbm_fields_size(const lbm_ctx* ctx, uint32_t mask);
+
+/* Reads fields at the current time t_n = n dt into host memory out
+ * (out_len doubles, at least lbm_fields_size).  Stresses are evaluated from
+ * u(t_n) with the solver's central differences and ghost rules.  Synchronises
+ * the stream.  *t_out (may be NULL) receives t_n.  Returns LBM_E_UNSTABLE if
+ * any step so far met a non-finite value or J <= 0 (the fields are still
+ * written).  Errors: LBM_E_INVALID (mask, out_len), LBM_E_STATE, LBM_E_CUDA. */
+LBM_API lbm_status lbm_read_fields(lbm_ctx* ctx, uint32_t mask, double* out, int64_t out_len,
+                           double* t_out);
+
+/* Diagnostics at the current time (deterministic fixed-order reduction):
+ * out[0..1] total momentum sum j, out[2] kinetic energy sum |j|^2 / (2 rho0),
+ * out[3] strain energy sum W(F) (Sec. 7's W, with ln J), out[4] min J,
+ * out[5] 1 if a non-finite value was met else 0 -- all per unit cell volume
+ * dX^2 omitted (plain node sums).  Synchronises.  out: 6 host doubles. */
+LBM_API lbm_status lbm_diagnostics(lbm_ctx* ctx, double out[6]);
+
+/* Blocks until the context's queued work is done; reports LBM_E_UNSTABLE like
+ * lbm_read_fields. */
+LBM_API lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* Steps taken so far and the derived time step (NULL pointers allowed). */
+LBM_API lbm_status lbm_get_info(const lbm_ctx* ctx, int64_t* steps, double* dt);
+
+/* Bytes of device memory the context holds, and the algorithmic bytes one
+ * node update moves (populations plus carries, read once and written once). */
+LBM_API lbm_status lbm_memory_info(const lbm_ctx* ctx, int64_t* device_bytes, int64_t* bytes_per_node_update);
+
+/* Frees the context and its device memory (NULL is allowed). */
+LBM_API lbm_status lbm_destroy(lbm_ctx* ctx);
+
+/* Static description of a status code. */
+LBM_API const char* lbm_status_string(lbm_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -86,6 +86,7 @@ def lib():
             L.orc_destroy.argtypes = [C.c_void_p]
             L.orc_read.argtypes = [C.c_void_p] + [dp] * 7
             L.orc_read_populations.argtypes = [C.c_void_p, dp]
+            L.orc_read_grad.argtypes = [C.c_void_p, dp]
             L.orc_time.restype = C.c_double
             L.orc_time.argtypes = [C.c_void_p]
             L.orc_dt.restype = C.c_double
@@ -254,6 +255,12 @@ class Solver:
         }
         lib().orc_read(self._h, _dp(out["u"]), _dp(out["v"]), _dp(out["P"]),
                        _dp(out["Pbar"]), _dp(out["r"]), _dp(out["J"]), _dp(out["sigma"]))
+        return out
+
+    def grad(self) -> np.ndarray:
+        """H = Grad u at the current time, [ny][nx][2][2]."""
+        out = np.zeros((self.p.ny, self.p.nx, 2, 2))
+        lib().orc_read_grad(self._h, _dp(out))
         return out
 
     def populations(self) -> np.ndarray:

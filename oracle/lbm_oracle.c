@@ -685,6 +685,13 @@ void orc_read(const orc_state* s, double* u, double* v, double* P, double* Pb, d
         }
 }
 
+/* Displacement gradient H = Grad u(t) (R15), [ny][nx][4] row-major 2x2. */
+void orc_read_grad(const orc_state* s, double* H) {
+    double t = s->step * s->dt;
+    for (int y = 0; y < s->p.ny; y++)
+        for (int x = 0; x < s->p.nx; x++) grad_u(s, s->u, x, y, t, H + 4 * IDX(s, x, y));
+}
+
 /* Raw populations f_i(X, t) (after streaming), [9][ny][nx]. */
 void orc_read_populations(const orc_state* s, double* out) {
     for (int i = 0; i < 9; i++) memcpy(out + (long)i * s->n, s->f[i], sizeof(double) * s->n);

@@ -1,0 +1,527 @@
+// lbm_api.cu -- the C ABI of include/lbm.h: contexts, device memory, launch
+// sequencing, CUDA-graph replay of step chunks, read-out and diagnostics.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "lbm.h"
+#include "lbm_kernels.h"
+
+using namespace lbm;
+
+namespace {
+
+constexpr int kGraphChunk = 64;  // steps per captured graph (even: keeps the ping-pong parity)
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+size_t elem_size_storage(int fmt) {
+    switch (fmt) {
+        case kFmtF64: return 8;
+        case kFmtF32:
+        case kFmtF32C: return 4;
+        default: return 2;
+    }
+}
+size_t elem_size_compute(int fmt) { return fmt == kFmtF64 ? 8 : 4; }
+size_t elem_size_ucarry(int fmt) { return fmt == kFmtF64 ? 8 : 4; }
+int ucarry_planes(int fmt) { return (fmt == kFmtF64 || fmt == kFmtF32) ? 1 : 2; }
+
+}  // namespace
+
+struct lbm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int fmt = kFmtF32;
+    int scheme = 1;
+    int32_t nx = 0, ny = 0;
+    double dX = 1.0;
+    int32_t f16_scale_log2 = 10;
+    // layout
+    int64_t pitch = 0, plane = 0;
+    int32_t xoff = 0;
+    int tile_x = 0, tile_y = 0, tiles_x = 0, tiles_y = 0;
+    // device memory
+    void* f[2] = {nullptr, nullptr};
+    void* a[2] = {nullptr, nullptr};
+    void* s[2] = {nullptr, nullptr};
+    double* fields = nullptr;
+    double* u0 = nullptr;
+    double* v0 = nullptr;
+    int32_t* flag = nullptr;
+    int64_t* counter = nullptr;
+    double* partials = nullptr;
+    double* diag = nullptr;
+    double* readout = nullptr;
+    size_t readout_cap = 0;
+    int diag_blocks = 1;
+    int64_t device_bytes = 0;
+    // problem
+    bool material_set = false;
+    bool bc_set[4] = {false, false, false, false};
+    EdgeBC bc[4];
+    double lambda = 0, mu = 0, rho0 = 0, omega = 1, body[2] = {0, 0};
+    double dt = 0, c = 0, cs2 = 0;
+    // progress
+    bool initialized = false;
+    int parity = 0;
+    int64_t steps = 0;
+    bool sticky = false;
+    bool variant_warm = false;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+lbm_status fail_cuda(lbm_ctx* ctx, cudaError_t e) {
+    (void)e;
+    if (ctx) ctx->sticky = true;
+    return LBM_E_CUDA;
+}
+
+#define LBM_CUDA(ctx, call)                          \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return fail_cuda((ctx), e_); \
+    } while (0)
+
+StepParams make_params(const lbm_ctx* c, int parity) {
+    StepParams p;
+    memset(&p, 0, sizeof(p));
+    p.nx = c->nx;
+    p.ny = c->ny;
+    p.xoff = c->xoff;
+    p.periodic_x = c->bc[0].kind == kPeriodic;
+    p.periodic_y = c->bc[2].kind == kPeriodic;
+    p.scheme = c->scheme;
+    p.pitch = c->pitch;
+    p.plane = c->plane;
+    p.tiles_x = c->tiles_x;
+    p.tiles_y = c->tiles_y;
+    p.f_src = c->f[parity];
+    p.f_dst = c->f[parity ^ 1];
+    p.a_src = c->a[parity];
+    p.a_dst = c->a[parity ^ 1];
+    p.s_src = c->s[parity];
+    p.s_dst = c->s[parity ^ 1];
+    p.fields = c->fields;
+    p.u0 = c->u0;
+    p.v0 = c->v0;
+    p.flag = c->flag;
+    p.counter = c->counter;
+    p.parity = parity;
+    p.dX = c->dX;
+    p.dt = c->dt;
+    p.c = c->c;
+    p.cs2 = c->cs2;
+    p.omega = c->omega;
+    p.rho0 = c->rho0;
+    p.lambda = c->lambda;
+    p.mu = c->mu;
+    p.body[0] = c->body[0];
+    p.body[1] = c->body[1];
+    for (int i = 0; i < 9; ++i) {
+        const double w = (i == 0) ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+        const double dec = w * ldexp(1.0, -c->f16_scale_log2);
+        p.dec_scale[i] = float(dec);
+        p.enc_scale[i] = float(1.0 / dec);
+    }
+    for (int e = 0; e < 4; ++e) p.bc[e] = c->bc[e];
+    return p;
+}
+
+ReadoutParams make_readout(const lbm_ctx* c) {
+    ReadoutParams r;
+    memset(&r, 0, sizeof(r));
+    r.nx = c->nx;
+    r.ny = c->ny;
+    r.periodic_x = c->bc[0].kind == kPeriodic;
+    r.periodic_y = c->bc[2].kind == kPeriodic;
+    r.dX = c->dX;
+    r.lambda = c->lambda;
+    r.mu = c->mu;
+    r.rho0 = c->rho0;
+    r.t = double(c->steps) * c->dt;
+    r.fields = c->fields;
+    for (int e = 0; e < 4; ++e) r.bc[e] = c->bc[e];
+    return r;
+}
+
+lbm_status ready(const lbm_ctx* c) {
+    if (!c) return LBM_E_INVALID;
+    if (c->sticky) return LBM_E_CUDA;
+    if (!c->material_set) return LBM_E_STATE;
+    for (int e = 0; e < 4; ++e)
+        if (!c->bc_set[e]) return LBM_E_STATE;
+    return LBM_OK;
+}
+
+lbm_status launch(lbm_ctx* c, int mode, bool fields) {
+    StepParams p = make_params(c, c->parity);
+    LBM_CUDA(c, launch_fused_step(c->fmt, p, c->stream, mode, fields));
+    c->parity ^= 1;
+    if (mode == 0) c->steps += 1;
+    return LBM_OK;
+}
+
+lbm_status ensure_initialized(lbm_ctx* c) {
+    if (c->initialized) return LBM_OK;
+    lbm_status st = launch(c, 1, true);
+    if (st != LBM_OK) return st;
+    c->initialized = true;
+    return LBM_OK;
+}
+
+// A graph of kGraphChunk plain steps starting at parity `par`.
+lbm_status get_graph(lbm_ctx* c, int par, cudaGraphExec_t* out) {
+    if (c->graph[par]) {
+        *out = c->graph[par];
+        return LBM_OK;
+    }
+    cudaGraph_t g = nullptr;
+    LBM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < kGraphChunk && err == cudaSuccess; ++k) {
+        StepParams p = make_params(c, par ^ (k & 1));
+        err = launch_fused_step(c->fmt, p, c->stream, 0, false);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (err != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail_cuda(c, err);
+    }
+    if (e2 != cudaSuccess) return fail_cuda(c, e2);
+    cudaGraphExec_t ex = nullptr;
+    err = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (err != cudaSuccess) return fail_cuda(c, err);
+    c->graph[par] = ex;
+    *out = ex;
+    return LBM_OK;
+}
+
+lbm_status check_flag(lbm_ctx* c) {
+    int32_t h = 0;
+    LBM_CUDA(c, cudaMemcpyAsync(&h, c->flag, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return (h & 1) ? LBM_E_UNSTABLE : LBM_OK;
+}
+
+void free_all(lbm_ctx* c) {
+    for (int k = 0; k < 2; ++k) {
+        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+        cudaFree(c->f[k]);
+        cudaFree(c->a[k]);
+        cudaFree(c->s[k]);
+    }
+    cudaFree(c->fields);
+    cudaFree(c->u0);
+    cudaFree(c->v0);
+    cudaFree(c->flag);
+    cudaFree(c->counter);
+    cudaFree(c->partials);
+    cudaFree(c->diag);
+    cudaFree(c->readout);
+}
+
+bool finite_pair(const double* v) { return v == nullptr || (isfinite(v[0]) && isfinite(v[1])); }
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
+    if (!out) return LBM_E_INVALID;
+    *out = nullptr;
+    if (!d) return LBM_E_INVALID;
+    if (d->nx < 3 || d->ny < 3 || !(d->dX > 0) || !isfinite(d->dX)) return LBM_E_INVALID;
+    if (d->storage < LBM_F64 || d->storage > LBM_BF16) return LBM_E_INVALID;
+    if (d->u_carry != LBM_UCARRY_NATIVE && d->u_carry != LBM_UCARRY_COMPENSATED) return LBM_E_INVALID;
+    if (d->scheme != LBM_SCHEME_EXPLICIT && d->scheme != LBM_SCHEME_PREDICTOR) return LBM_E_INVALID;
+    if (d->f16_scale_log2 < -60 || d->f16_scale_log2 > 60) return LBM_E_INVALID;
+    // sizes: 64-bit element counts, 32-bit node coordinates
+    const int64_t nodes = int64_t(d->nx) * d->ny;
+    if (d->nx > (1 << 30) || d->ny > (1 << 30) || nodes > (int64_t(1) << 40)) return LBM_E_INVALID;
+
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_E_OOM;
+    c->device = d->device;
+    DeviceGuard guard(c->device);
+    if (!guard.ok) {
+        delete c;
+        return LBM_E_INVALID;
+    }
+    c->stream = static_cast<cudaStream_t>(d->cuda_stream);
+    c->nx = d->nx;
+    c->ny = d->ny;
+    c->dX = d->dX;
+    c->scheme = d->scheme;
+    c->f16_scale_log2 = d->f16_scale_log2 ? d->f16_scale_log2 : 10;
+    switch (d->storage) {
+        case LBM_F64: c->fmt = kFmtF64; break;
+        case LBM_F32: c->fmt = d->u_carry == LBM_UCARRY_COMPENSATED ? kFmtF32C : kFmtF32; break;
+        case LBM_F16: c->fmt = kFmtF16; break;
+        default: c->fmt = kFmtBF16; break;
+    }
+    for (int e = 0; e < 4; ++e) {
+        memset(&c->bc[e], 0, sizeof(EdgeBC));
+        c->bc[e].times[2] = INFINITY;
+    }
+    tile_shape(c->fmt, &c->tile_x, &c->tile_y);
+    c->tiles_x = int((d->nx + c->tile_x - 1) / c->tile_x);
+    c->tiles_y = int((d->ny + c->tile_y - 1) / c->tile_y);
+
+    // plane layout: x = 0 on a 16-byte boundary, rows padded to 128 bytes
+    const int64_t es = int64_t(elem_size_storage(c->fmt));
+    c->xoff = int32_t(16 / es);
+    const int64_t row_align = 128 / es;
+    c->pitch = ((c->xoff + d->nx + 1) + row_align - 1) / row_align * row_align;
+    c->plane = c->pitch * (d->ny + 2);
+
+    const size_t fbytes = size_t(9) * c->plane * elem_size_storage(c->fmt);
+    const size_t abytes = size_t(2 * ucarry_planes(c->fmt)) * c->plane * elem_size_ucarry(c->fmt);
+    const size_t sbytes = size_t(2) * c->plane * elem_size_compute(c->fmt);
+    const size_t fldbytes = size_t(5) * nodes * sizeof(double);
+    const size_t ubytes = size_t(2) * nodes * sizeof(double);
+    c->diag_blocks = diagnostics_blocks(nodes);
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
+        err = cudaMalloc(&c->f[k], fbytes);
+        if (err == cudaSuccess) err = cudaMalloc(&c->a[k], abytes);
+        if (err == cudaSuccess) err = cudaMalloc(&c->s[k], sbytes);
+    }
+    if (err == cudaSuccess) err = cudaMalloc(&c->fields, fldbytes);
+    if (err == cudaSuccess && d->u0) err = cudaMalloc(&c->u0, ubytes);
+    if (err == cudaSuccess && d->v0) err = cudaMalloc(&c->v0, ubytes);
+    if (err == cudaSuccess) err = cudaMalloc(&c->flag, sizeof(int32_t));
+    if (err == cudaSuccess) err = cudaMalloc(&c->counter, 2 * sizeof(int64_t));
+    if (err == cudaSuccess) err = cudaMalloc(&c->partials, size_t(c->diag_blocks) * 8 * sizeof(double));
+    if (err == cudaSuccess) err = cudaMalloc(&c->diag, 8 * sizeof(double));
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return err == cudaErrorMemoryAllocation ? LBM_E_OOM : LBM_E_CUDA;
+    }
+    c->device_bytes = int64_t(2 * (fbytes + abytes + sbytes) + fldbytes + 2 * (d->u0 ? ubytes : 0));
+    for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
+        err = cudaMemsetAsync(c->f[k], 0, fbytes, c->stream);
+        if (err == cudaSuccess) err = cudaMemsetAsync(c->a[k], 0, abytes, c->stream);
+        if (err == cudaSuccess) err = cudaMemsetAsync(c->s[k], 0, sbytes, c->stream);
+    }
+    if (err == cudaSuccess) err = cudaMemsetAsync(c->fields, 0, fldbytes, c->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(c->counter, 0, 2 * sizeof(int64_t), c->stream);
+    if (err == cudaSuccess && d->u0) err = cudaMemcpyAsync(c->u0, d->u0, ubytes, cudaMemcpyHostToDevice, c->stream);
+    if (err == cudaSuccess && d->v0) err = cudaMemcpyAsync(c->v0, d->v0, ubytes, cudaMemcpyHostToDevice, c->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+    if (err != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return LBM_E_CUDA;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_material(lbm_ctx* c, double lambda, double mu, double rho0, double omega,
+                            const double body_force[2]) {
+    if (!c) return LBM_E_INVALID;
+    if (c->sticky) return LBM_E_CUDA;
+    if (c->initialized) return LBM_E_STATE;
+    if (!(mu > 0) || !(rho0 > 0) || !(lambda > -mu) || !(omega > 0) || !(omega < 2)) return LBM_E_INVALID;
+    if (!isfinite(mu) || !isfinite(rho0) || !isfinite(lambda) || !finite_pair(body_force)) return LBM_E_INVALID;
+    c->lambda = lambda;
+    c->mu = mu;
+    c->rho0 = rho0;
+    c->omega = omega;
+    c->body[0] = body_force ? body_force[0] : 0.0;
+    c->body[1] = body_force ? body_force[1] : 0.0;
+    // dt = dX / (sqrt(3) C_s), C_s = sqrt(mu / rho0); lattice speed c = dX / dt
+    const double Cs = sqrt(mu / rho0);
+    c->dt = c->dX / (sqrt(3.0) * Cs);
+    c->c = c->dX / c->dt;
+    c->cs2 = Cs * Cs;
+    c->material_set = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_boundary(lbm_ctx* c, int32_t edge, int32_t kind, const double value[2],
+                            const double rate[2], const double times[3]) {
+    if (!c) return LBM_E_INVALID;
+    if (c->sticky) return LBM_E_CUDA;
+    if (c->initialized) return LBM_E_STATE;
+    if (edge < 0 || edge > 3 || kind < LBM_PERIODIC || kind > LBM_NEUMANN) return LBM_E_INVALID;
+    if (!finite_pair(value) || !finite_pair(rate)) return LBM_E_INVALID;
+    EdgeBC e;
+    memset(&e, 0, sizeof(e));
+    e.kind = kind;
+    for (int a = 0; a < 2; ++a) {
+        e.value[a] = value ? value[a] : 0.0;
+        e.rate[a] = rate ? rate[a] : 0.0;
+    }
+    e.times[0] = times ? times[0] : 0.0;
+    e.times[1] = times ? times[1] : 0.0;
+    e.times[2] = times ? times[2] : INFINITY;
+    if (times && (isnan(times[0]) || isnan(times[1]) || isnan(times[2]) || times[1] < 0)) return LBM_E_INVALID;
+    // a periodic edge must pair with a periodic opposite edge
+    const int other = edge ^ 1;
+    if (c->bc_set[other] && ((c->bc[other].kind == kPeriodic) != (kind == LBM_PERIODIC))) return LBM_E_INVALID;
+    c->bc[edge] = e;
+    c->bc_set[edge] = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
+    lbm_status st = ready(c);
+    if (st != LBM_OK) return st;
+    if (nsteps < 0) return LBM_E_INVALID;
+    DeviceGuard guard(c->device);
+    if (!guard.ok) return fail_cuda(c, cudaErrorInvalidDevice);
+    st = ensure_initialized(c);
+    if (st != LBM_OK || nsteps == 0) return st;
+    int64_t left = nsteps;
+    // plain launches until the variant is warm (attributes set outside capture)
+    if (!c->variant_warm && left > 1) {
+        st = launch(c, 0, false);
+        if (st != LBM_OK) return st;
+        --left;
+        c->variant_warm = true;
+    }
+    while (left > kGraphChunk) {
+        cudaGraphExec_t g;
+        st = get_graph(c, c->parity, &g);
+        if (st != LBM_OK) return st;
+        LBM_CUDA(c, cudaGraphLaunch(g, c->stream));
+        c->steps += kGraphChunk;  // kGraphChunk is even: parity unchanged
+        left -= kGraphChunk;
+    }
+    while (left > 1) {
+        st = launch(c, 0, false);
+        if (st != LBM_OK) return st;
+        --left;
+    }
+    return launch(c, 0, true);
+}
+
+int64_t lbm_fields_size(const lbm_ctx* c, uint32_t mask) {
+    if (!c || mask == 0 || (mask & ~127u)) return 0;
+    static const int comps[7] = {2, 2, 4, 3, 1, 3, 1};
+    int64_t n = 0;
+    for (int b = 0; b < 7; ++b)
+        if (mask & (1u << b)) n += comps[b];
+    return n * int64_t(c->nx) * c->ny;
+}
+
+lbm_status lbm_read_fields(lbm_ctx* c, uint32_t mask, double* out, int64_t out_len, double* t_out) {
+    lbm_status st = ready(c);
+    if (st != LBM_OK) return st;
+    const int64_t need = lbm_fields_size(c, mask);
+    if (need == 0 || !out || out_len < need) return LBM_E_INVALID;
+    DeviceGuard guard(c->device);
+    if (!guard.ok) return fail_cuda(c, cudaErrorInvalidDevice);
+    st = ensure_initialized(c);
+    if (st != LBM_OK) return st;
+    const size_t bytes = size_t(need) * sizeof(double);
+    if (bytes > c->readout_cap) {
+        cudaFree(c->readout);
+        c->readout = nullptr;
+        c->readout_cap = 0;
+        cudaError_t e = cudaMalloc(&c->readout, bytes);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            return LBM_E_OOM;
+        }
+        LBM_CUDA(c, e);
+        c->readout_cap = bytes;
+    }
+    ReadoutParams rp = make_readout(c);
+    LBM_CUDA(c, launch_readout(rp, mask, c->readout, c->stream));
+    LBM_CUDA(c, cudaMemcpyAsync(out, c->readout, bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (t_out) *t_out = double(c->steps) * c->dt;
+    return check_flag(c);
+}
+
+lbm_status lbm_diagnostics(lbm_ctx* c, double out[6]) {
+    lbm_status st = ready(c);
+    if (st != LBM_OK) return st;
+    if (!out) return LBM_E_INVALID;
+    DeviceGuard guard(c->device);
+    if (!guard.ok) return fail_cuda(c, cudaErrorInvalidDevice);
+    st = ensure_initialized(c);
+    if (st != LBM_OK) return st;
+    ReadoutParams rp = make_readout(c);
+    LBM_CUDA(c, launch_diagnostics(rp, c->partials, c->diag_blocks, c->diag, c->stream));
+    double h[8];
+    LBM_CUDA(c, cudaMemcpyAsync(h, c->diag, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    st = check_flag(c);
+    for (int q = 0; q < 6; ++q) out[q] = h[q];
+    return st;
+}
+
+lbm_status lbm_sync(lbm_ctx* c) {
+    if (!c) return LBM_E_INVALID;
+    if (c->sticky) return LBM_E_CUDA;
+    DeviceGuard guard(c->device);
+    if (!guard.ok) return fail_cuda(c, cudaErrorInvalidDevice);
+    return check_flag(c);
+}
+
+lbm_status lbm_get_info(const lbm_ctx* c, int64_t* steps, double* dt) {
+    if (!c) return LBM_E_INVALID;
+    if (steps) *steps = c->steps;
+    if (dt) *dt = c->dt;
+    return LBM_OK;
+}
+
+lbm_status lbm_memory_info(const lbm_ctx* c, int64_t* device_bytes, int64_t* bytes_per_node_update) {
+    if (!c) return LBM_E_INVALID;
+    if (device_bytes) *device_bytes = c->device_bytes;
+    if (bytes_per_node_update) {
+        const int64_t per = int64_t(9 * elem_size_storage(c->fmt)) +
+                            int64_t(2 * ucarry_planes(c->fmt) * elem_size_ucarry(c->fmt)) +
+                            int64_t(2 * elem_size_compute(c->fmt));
+        *bytes_per_node_update = 2 * per;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_ctx* c) {
+    if (!c) return LBM_OK;
+    {
+        DeviceGuard guard(c->device);
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        else cudaDeviceSynchronize();
+        free_all(c);
+    }
+    delete c;
+    return LBM_OK;
+}
+
+const char* lbm_status_string(lbm_status s) {
+    switch (s) {
+        case LBM_OK: return "ok";
+        case LBM_E_INVALID: return "invalid argument";
+        case LBM_E_OOM: return "out of memory";
+        case LBM_E_CUDA: return "CUDA error (context unusable)";
+        case LBM_E_UNSTABLE: return "unstable: non-finite value or J <= 0 met";
+        case LBM_E_TIMEOUT: return "device-side wait timed out";
+        case LBM_E_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

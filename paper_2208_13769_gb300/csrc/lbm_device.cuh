@@ -1,0 +1,188 @@
+// lbm_device.cuh -- device-side pieces of the fused Lagrangian LBM step.
+//
+// D2Q9 lattice (Sec. 3), equilibrium and source populations (Sec. 5),
+// neo-Hooke P(F) (Sec. 7), Poisson stress Pbar(H) (Eq. Plin), the storage
+// codecs of the populations and the displacement-carry number types.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "lbm_params.h"
+
+namespace lbm {
+
+// ---------------------------------------------------------------- lattice
+// Directions: 0 rest; 1..4 axis links (+x, +y, -x, -y); 5..8 diagonals
+// (+x+y, -x+y, -x-y, +x-y).  Weights 4/9, 1/9, 1/36.
+__host__ __device__ constexpr int ex(int i) {
+    return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int i) {
+    return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+}
+template <class T>
+__host__ __device__ constexpr T wgt(int i) {
+    return i == 0 ? T(4) / T(9) : (i <= 4 ? T(1) / T(9) : T(1) / T(36));
+}
+static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2, "axis opposites");
+static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "diagonal opposites");
+
+// Per-step constants in the arithmetic type T.
+template <class T>
+struct Consts {
+    T c, inv_c, inv_cs2, omega, one_m_omega, force_pref, half_dt, k_u, rho0, inv_rho0, lam, mu,
+        inv_2dx, b0, b1;
+    __device__ void load(const StepParams& p) {
+        c = T(p.c);
+        inv_c = T(1.0 / p.c);
+        inv_cs2 = T(1.0 / p.cs2);
+        omega = T(p.omega);
+        one_m_omega = T(1.0 - p.omega);
+        force_pref = T(p.dt * (1.0 - 0.5 * p.omega));
+        half_dt = T(0.5 * p.dt);
+        k_u = T(p.dt / (2.0 * p.rho0));
+        rho0 = T(p.rho0);
+        inv_rho0 = T(1.0 / p.rho0);
+        lam = T(p.lambda);
+        mu = T(p.mu);
+        inv_2dx = T(1.0 / (2.0 * p.dX));
+        b0 = T(p.body[0]);
+        b1 = T(p.body[1]);
+    }
+};
+
+// Even part of the equilibrium for direction i, divided by w_i:
+//   r + (Pbar - r Cs^2 I):(C_i C_i - Cs^2 I) / (2 Cs^4)
+// expanded with c^2 = 3 Cs^2 into
+//   r (2 - 3/2 |e_i|^2) + (3 e_i.Pbar.e_i - tr Pbar) / (2 Cs^2).
+template <class T>
+__device__ __forceinline__ T feq_even_over_w(int i, T r, T pxx, T pxy, T pyy, T inv_cs2) {
+    const int e2 = ex(i) * ex(i) + ey(i) * ey(i);
+    const T tr = pxx + pyy;
+    T epe = T(ex(i) * ex(i)) * pxx + T(ey(i) * ey(i)) * pyy + T(2 * ex(i) * ey(i)) * pxy;
+    T rterm = (e2 == 0) ? T(2) * r : (e2 == 1 ? T(0.5) * r : -r);
+    return rterm + (T(3) * epe - tr) * (T(0.5) * inv_cs2);
+}
+
+// Odd part of f^eq / w_i: C_i . j / Cs^2 = 3 (e_i . j) / c.
+template <class T>
+__device__ __forceinline__ T feq_odd_over_w(int i, T j0, T j1, T inv_c) {
+    return T(3) * (T(ex(i)) * j0 + T(ey(i)) * j1) * inv_c;
+}
+
+// ---------------------------------------------------------------- material
+// Neo-Hooke (Sec. 7): P = mu F + (lambda/2 (J^2 - 1) - mu) F^-T with
+// J - 1 = H11 + H22 + H11 H22 - H12 H21.  Returns J.
+template <class T>
+__device__ __forceinline__ T piola(T h11, T h12, T h21, T h22, T lam, T mu, T& p11, T& p12, T& p21,
+                                   T& p22) {
+    T jm1 = h11 + h22 + (h11 * h22 - h12 * h21);
+    T J = T(1) + jm1;
+    T invJ = T(1) / J;
+    T coef = (T(0.5) * lam * jm1 * (T(2) + jm1) - mu) * invJ;
+    // F^-T * J = [[F22, -F21], [-F12, F11]]
+    p11 = mu * (T(1) + h11) + coef * (T(1) + h22);
+    p12 = mu * h12 - coef * h21;
+    p21 = mu * h21 - coef * h12;
+    p22 = mu * (T(1) + h22) + coef * (T(1) + h11);
+    return J;
+}
+
+// ---------------------------------------------------------------- storage
+// Population codecs: stored value <-> arithmetic value.
+template <class S, class T>
+struct Codec;
+template <>
+struct Codec<double, double> {
+    __device__ __forceinline__ static double ld(double s, int, const StepParams&) { return s; }
+    __device__ __forceinline__ static double st(double v, int, const StepParams&) { return v; }
+};
+template <>
+struct Codec<float, float> {
+    __device__ __forceinline__ static float ld(float s, int, const StepParams&) { return s; }
+    __device__ __forceinline__ static float st(float v, int, const StepParams&) { return v; }
+};
+// 16-bit storage keeps h_i = f_i / (w_i 2^-s); the scale pair per direction
+// (w_i 2^-s and its inverse) is precomputed on the host.
+template <>
+struct Codec<__half, float> {
+    __device__ __forceinline__ static float ld(__half s, int i, const StepParams& p) {
+        return __half2float(s) * p.dec_scale[i];
+    }
+    __device__ __forceinline__ static __half st(float v, int i, const StepParams& p) {
+        return __float2half_rn(v * p.enc_scale[i]);
+    }
+};
+template <>
+struct Codec<__nv_bfloat16, float> {
+    __device__ __forceinline__ static float ld(__nv_bfloat16 s, int i, const StepParams& p) {
+        return __bfloat162float(s) * p.dec_scale[i];
+    }
+    __device__ __forceinline__ static __nv_bfloat16 st(float v, int i, const StepParams& p) {
+        return __float2bfloat16_rn(v * p.enc_scale[i]);
+    }
+};
+
+// ---------------------------------------------------------------- u-carry
+// Displacement number types.  Each provides: load from / store to the carry
+// planes, add a small increment, difference of two values (in the arithmetic
+// type T), difference against an FP64 value, and conversion to double.
+
+template <class T>
+struct UPlain {  // u kept in T itself (FP64 or FP32)
+    T v;
+    static constexpr int planes = 1;
+    __device__ __forceinline__ static UPlain load(const void* base, int64_t idx, int64_t) {
+        return UPlain{static_cast<const T*>(base)[idx]};
+    }
+    __device__ __forceinline__ void store(void* base, int64_t idx, int64_t) const {
+        static_cast<T*>(base)[idx] = v;
+    }
+    __device__ __forceinline__ static UPlain from_double(double d) { return UPlain{T(d)}; }
+    __device__ __forceinline__ UPlain add(T d) const { return UPlain{v + d}; }
+    __device__ __forceinline__ T minus(const UPlain& o) const { return v - o.v; }
+    __device__ __forceinline__ T minus_d(double d) const { return T(double(v) - d); }
+    __device__ __forceinline__ double to_double() const { return double(v); }
+};
+
+// Unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)/2), "double-float".
+// Addition uses Knuth's two-sum followed by a renormalising fast two-sum.
+struct UComp {
+    float hi, lo;
+    static constexpr int planes = 2;  // hi plane, then lo plane (same pitch)
+    __device__ __forceinline__ static UComp load(const void* base, int64_t idx, int64_t plane) {
+        const float* b = static_cast<const float*>(base);
+        return UComp{b[idx], b[idx + plane]};
+    }
+    __device__ __forceinline__ void store(void* base, int64_t idx, int64_t plane) const {
+        float* b = static_cast<float*>(base);
+        b[idx] = hi;
+        b[idx + plane] = lo;
+    }
+    __device__ __forceinline__ static UComp from_double(double d) {
+        float h = __double2float_rn(d);
+        return UComp{h, __double2float_rn(d - double(h))};
+    }
+    __device__ __forceinline__ UComp add(float d) const {
+        float s = __fadd_rn(hi, d);
+        float bb = __fsub_rn(s, hi);
+        float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(d, bb));
+        float l = __fadd_rn(lo, e);
+        float h2 = __fadd_rn(s, l);
+        return UComp{h2, __fsub_rn(l, __fsub_rn(h2, s))};
+    }
+    __device__ __forceinline__ float minus(const UComp& o) const {
+        return __fadd_rn(__fsub_rn(hi, o.hi), __fsub_rn(lo, o.lo));
+    }
+    __device__ __forceinline__ float minus_d(double d) const {
+        return __double2float_rn((double(hi) - d) + double(lo));
+    }
+    __device__ __forceinline__ double to_double() const { return double(hi) + double(lo); }
+};
+
+}  // namespace lbm

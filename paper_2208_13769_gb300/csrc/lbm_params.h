@@ -1,0 +1,55 @@
+// lbm_params.h -- parameter blocks shared by the host library and the
+// kernels of the fused Lagrangian LBM step (plain C++ structs, passed by
+// value as kernel arguments).
+#pragma once
+
+#include <stdint.h>
+
+namespace lbm {
+
+enum EdgeKind : int32_t { kPeriodic = 0, kDirichlet = 1, kNeumann = 2 };
+
+// One edge (0 = x-, 1 = x+, 2 = y-, 3 = y+) of Sec. 6's boundary value problem.
+struct EdgeBC {
+    int32_t kind;
+    int32_t pad;
+    double value[2];  // Dirichlet: u* at t = 0;  Neumann: T0
+    double rate[2];   // Dirichlet: v*;           Neumann: T1
+    double times[3];  // Neumann: t_on, t_ramp, t_off
+};
+
+struct StepParams {
+    // geometry: populations and carries live in planes of (ny + 2) rows of
+    // `pitch` elements; node (x, y), x in [-1, nx], y in [-1, ny], sits at
+    // (y + 1) * pitch + x + xoff.  Row y = -1 / ny and column x = -1 / nx are
+    // the ghost layer that receives bounced and wrapped populations.
+    int32_t nx, ny;
+    int32_t xoff;
+    int32_t periodic_x, periodic_y;
+    int32_t scheme;  // 0 explicit (Algorithm 1), 1 predictor-corrector
+    int64_t pitch;   // elements per row (storage or carry element type)
+    int64_t plane;   // elements per plane
+    int32_t tiles_x, tiles_y;
+
+    const void* f_src;  // 9 planes of f^col(t_n), storage type
+    void* f_dst;        // 9 planes of f^col(t_n+1)
+    const void* a_src;  // u-carry A: 2 comps x (1 or 2) planes
+    void* a_dst;
+    const void* s_src;  // source carry 1S: 2 planes, arithmetic type
+    void* s_dst;
+    double* fields;      // NULL, or 5 planes [ny][nx] FP64: u_x, u_y, v_x, v_y, r
+    const double* u0;    // init only: [ny][nx][2]
+    const double* v0;    // init only: [ny][nx][2]
+    int32_t* flag;       // bit 0: non-finite value or J <= 0 met
+    int64_t* counter;    // two step counters (ping-pong by parity)
+    int32_t parity;
+    int32_t pad2;
+
+    double dX, dt, c, cs2, omega, rho0, lambda, mu;
+    double body[2];
+    float enc_scale[9];  // 16-bit storage: 1 / (w_i 2^-s)
+    float dec_scale[9];  // w_i 2^-s
+    EdgeBC bc[4];
+};
+
+}  // namespace lbm

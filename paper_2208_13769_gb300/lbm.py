@@ -1,0 +1,246 @@
+"""ctypes binding of the C ABI in include/lbm.h (liblbm_gb300.so).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  There is no CPU fallback -- if the shared library cannot be
+built or loaded, importing the entry points raises.
+
+The module exposes the C functions under their C names (lbm_create, ...),
+plus :class:`Body`, a small RAII wrapper that creates a context from a
+:class:`paper_2208_13769_gb300.workloads.Problem`.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK, LBM_E_INVALID, LBM_E_OOM, LBM_E_CUDA, LBM_E_UNSTABLE, LBM_E_TIMEOUT, LBM_E_STATE = range(7)
+LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = range(4)
+LBM_UCARRY_NATIVE, LBM_UCARRY_COMPENSATED = 0, 1
+LBM_SCHEME_EXPLICIT, LBM_SCHEME_PREDICTOR = 0, 1
+LBM_PERIODIC, LBM_DIRICHLET, LBM_NEUMANN = 0, 1, 2
+LBM_FIELD_U, LBM_FIELD_V, LBM_FIELD_P, LBM_FIELD_PBAR, LBM_FIELD_R, LBM_FIELD_SIGMA, LBM_FIELD_J = (
+    1, 2, 4, 8, 16, 32, 64)
+FIELD_COMPS = {LBM_FIELD_U: 2, LBM_FIELD_V: 2, LBM_FIELD_P: 4, LBM_FIELD_PBAR: 3, LBM_FIELD_R: 1,
+               LBM_FIELD_SIGMA: 3, LBM_FIELD_J: 1}
+FIELD_NAMES = {LBM_FIELD_U: "u", LBM_FIELD_V: "v", LBM_FIELD_P: "P", LBM_FIELD_PBAR: "Pbar",
+               LBM_FIELD_R: "r", LBM_FIELD_SIGMA: "sigma", LBM_FIELD_J: "J"}
+STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}
+
+
+class lbm_desc(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("dX", C.c_double),
+        ("storage", C.c_int32), ("u_carry", C.c_int32), ("scheme", C.c_int32),
+        ("f16_scale_log2", C.c_int32),
+        ("u0", C.c_void_p), ("v0", C.c_void_p), ("cuda_stream", C.c_void_p),
+        ("device", C.c_int32),
+    ]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+_SIGNATURES = {
+    "lbm_create": (C.c_int, [C.POINTER(lbm_desc), C.POINTER(C.c_void_p)]),
+    "lbm_set_material": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double,
+                                   C.POINTER(C.c_double)]),
+    "lbm_set_boundary": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "lbm_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "lbm_fields_size": (C.c_int64, [C.c_void_p, C.c_uint32]),
+    "lbm_read_fields": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_double), C.c_int64,
+                                  C.POINTER(C.c_double)]),
+    "lbm_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "lbm_sync": (C.c_int, [C.c_void_p]),
+    "lbm_get_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "lbm_memory_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "lbm_destroy": (C.c_int, [C.c_void_p]),
+    "lbm_status_string": (C.c_char_p, [C.c_int]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads liblbm_gb300.so, building it first when the sources are newer."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library missing: {path}")
+            L = C.CDLL(path)
+            for name, (res, args) in _SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().lbm_status_string(int(status)).decode()
+
+
+def _check(status: int, what: str, allow=()):
+    if status != LBM_OK and status not in allow:
+        raise LbmError(status, what)
+    return status
+
+
+def _dbl(a) -> Optional[C.Array]:
+    if a is None:
+        return None
+    return (C.c_double * len(a))(*[float(x) for x in a])
+
+
+# ------------------------------------------------------------- C names
+
+def lbm_create(desc: lbm_desc) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().lbm_create(C.byref(desc), C.byref(h)), "lbm_create")
+    return h
+
+
+def lbm_set_material(ctx, lam, mu, rho0, omega, body_force=None):
+    return _check(lib().lbm_set_material(ctx, lam, mu, rho0, omega, _dbl(body_force)), "lbm_set_material")
+
+
+def lbm_set_boundary(ctx, edge, kind, value=None, rate=None, times=None):
+    return _check(lib().lbm_set_boundary(ctx, int(edge), int(kind), _dbl(value), _dbl(rate), _dbl(times)),
+                  "lbm_set_boundary")
+
+
+def lbm_step(ctx, nsteps: int):
+    return _check(lib().lbm_step(ctx, int(nsteps)), "lbm_step")
+
+
+def lbm_fields_size(ctx, mask: int) -> int:
+    return int(lib().lbm_fields_size(ctx, int(mask)))
+
+
+def lbm_read_fields(ctx, mask: int, out: np.ndarray, allow_unstable: bool = False) -> tuple:
+    """Fills the float64 host buffer ``out``; returns (status, t)."""
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    t = C.c_double()
+    st = lib().lbm_read_fields(ctx, int(mask), out.ctypes.data_as(C.POINTER(C.c_double)), out.size,
+                               C.byref(t))
+    _check(st, "lbm_read_fields", allow=(LBM_E_UNSTABLE,) if allow_unstable else ())
+    return st, t.value
+
+
+def lbm_diagnostics(ctx, allow_unstable: bool = False) -> tuple:
+    out = np.zeros(6)
+    st = lib().lbm_diagnostics(ctx, out.ctypes.data_as(C.POINTER(C.c_double)))
+    _check(st, "lbm_diagnostics", allow=(LBM_E_UNSTABLE,) if allow_unstable else ())
+    return st, out
+
+
+def lbm_sync(ctx, allow_unstable: bool = False) -> int:
+    return _check(lib().lbm_sync(ctx), "lbm_sync", allow=(LBM_E_UNSTABLE,) if allow_unstable else ())
+
+
+def lbm_get_info(ctx) -> tuple:
+    s, d = C.c_int64(), C.c_double()
+    _check(lib().lbm_get_info(ctx, C.byref(s), C.byref(d)), "lbm_get_info")
+    return s.value, d.value
+
+
+def lbm_memory_info(ctx) -> tuple:
+    a, b = C.c_int64(), C.c_int64()
+    _check(lib().lbm_memory_info(ctx, C.byref(a), C.byref(b)), "lbm_memory_info")
+    return a.value, b.value
+
+
+def lbm_destroy(ctx):
+    return _check(lib().lbm_destroy(ctx), "lbm_destroy")
+
+
+def lbm_status_string(status: int) -> str:
+    return status_string(status)
+
+
+# ------------------------------------------------------------- convenience
+
+class Body:
+    """One solver context for a workloads.Problem-like object.
+
+    storage: "f64" | "f32" | "f16" | "bf16"; compensated: FP32-pair u-carry
+    for "f32"; scheme: LBM_SCHEME_PREDICTOR (default) or LBM_SCHEME_EXPLICIT;
+    stream: an integer cudaStream_t handle (e.g. torch's stream.cuda_stream)."""
+
+    def __init__(self, prob, storage: str = "f64", compensated: bool = False,
+                 scheme: int = LBM_SCHEME_PREDICTOR, stream: int = 0, device: int = 0,
+                 f16_scale_log2: int = 0):
+        self.prob = prob
+        d = lbm_desc()
+        d.nx, d.ny, d.dX = prob.nx, prob.ny, prob.dX
+        d.storage = STORAGE[storage]
+        d.u_carry = LBM_UCARRY_COMPENSATED if compensated else LBM_UCARRY_NATIVE
+        d.scheme = scheme
+        d.f16_scale_log2 = f16_scale_log2
+        self._u0 = None if prob.u0 is None else np.ascontiguousarray(prob.u0, dtype=np.float64)
+        self._v0 = None if prob.v0 is None else np.ascontiguousarray(prob.v0, dtype=np.float64)
+        d.u0 = None if self._u0 is None else self._u0.ctypes.data
+        d.v0 = None if self._v0 is None else self._v0.ctypes.data
+        d.cuda_stream = stream or None
+        d.device = device
+        self.ctx = lbm_create(d)
+        self._u0 = self._v0 = None  # copied to the device by lbm_create
+        lbm_set_material(self.ctx, prob.lam, prob.mu, prob.rho0, prob.omega, prob.body)
+        for k, e in enumerate(prob.edges):
+            lbm_set_boundary(self.ctx, k, e.kind, e.value, e.rate, e.times)
+
+    def step(self, n: int) -> None:
+        lbm_step(self.ctx, n)
+
+    def read(self, mask: int = 127, allow_unstable: bool = False) -> dict:
+        n = lbm_fields_size(self.ctx, mask)
+        buf = np.empty(n, dtype=np.float64)
+        st, t = lbm_read_fields(self.ctx, mask, buf, allow_unstable=allow_unstable)
+        out, off = {"t": t, "status": st}, 0
+        ny, nx = self.prob.ny, self.prob.nx
+        for bit in (1, 2, 4, 8, 16, 32, 64):
+            if mask & bit:
+                k = FIELD_COMPS[bit]
+                blk = buf[off:off + k * nx * ny].reshape(ny, nx, k)
+                out[FIELD_NAMES[bit]] = blk[:, :, 0] if k == 1 else blk
+                off += k * nx * ny
+        return out
+
+    def diagnostics(self, allow_unstable: bool = False):
+        return lbm_diagnostics(self.ctx, allow_unstable)[1]
+
+    def info(self):
+        return lbm_get_info(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,146 @@
+"""GPU library vs the FP64 CPU oracle, element by element, on seeded inputs.
+
+Tolerances: relative L2 error of u, v and P <= 1e-12 for FP64 storage and
+<= 1e-5 for FP32 storage after the stated step count.  Sizes span several
+fused-kernel tiles (64 x 16 for FP32, 32 x 16 for FP64) with ragged tails,
+periodic axes shorter than a tile, every boundary kind and both schemes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_13769_gb300 import lbm
+from paper_2208_13769_gb300 import workloads as W
+from parity_util import compare, rel_l2, run_both
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+Pp = W.Edge(W.PERIODIC)
+N0 = W.Edge(W.NEUMANN)
+D0 = W.Edge(W.DIRICHLET)
+
+
+def _cases():
+    cases = {
+        "shear_wave_64": (W.shear_wave(64), 1000),
+        "periodic_100x70": (W.smooth_random(100, 70, W.all_periodic(), seed=11, amp=0.02, lam=0.45), 300),
+        "clamped_96x50": (W.smooth_random(96, 50, W.clamped_free_edges(), seed=12, amp=0.01, vamp=0.005,
+                                          lam=0.3, mu=0.3), 400),
+        "periodic_short_20x8": (W.smooth_random(20, 8, W.all_periodic(), seed=13, amp=0.02, lam=0.45), 200),
+        "x_periodic_y_walls_70x37": (W.smooth_random(70, 37, [Pp, Pp, D0, N0], seed=14, amp=0.01,
+                                                     lam=0.3, mu=0.3), 300),
+        "all_dirichlet_moving_33x40": (W.smooth_random(33, 40, [W.Edge(W.DIRICHLET, value=(0.0, 0.0),
+                                                                       rate=(0.003, -0.002))] * 4,
+                                                       seed=15, amp=0.01, lam=0.45), 300),
+        "tiny_3x3_neumann": (W.smooth_random(3, 3, [N0] * 4, seed=16, amp=0.001, lam=0.3, mu=0.3), 50),
+        "tiny_4x5_mixed": (W.smooth_random(4, 5, [D0, N0, N0, D0], seed=17, amp=0.001, lam=0.3, mu=0.3), 50),
+    }
+    t = W.tension_block(40, T1=0.1)
+    cases["tension_ramp_40"] = (t, 208)
+    return cases
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("scheme", [oracle.PREDICTOR, oracle.EXPLICIT])
+def test_fp64_parity(name, scheme):
+    prob, steps = CASES[name]
+    ref, got = run_both(prob, steps, "f64", scheme=scheme)
+    compare(ref, got, TOL["f64"], keys=("u", "v", "P", "Pbar", "r", "J", "sigma"))
+
+
+@pytest.mark.parametrize("name", ["shear_wave_64", "periodic_100x70", "clamped_96x50", "tension_ramp_40",
+                                  "x_periodic_y_walls_70x37", "periodic_short_20x8"])
+@pytest.mark.parametrize("compensated", [False, True])
+def test_fp32_parity(name, compensated):
+    prob, steps = CASES[name]
+    ref, got = run_both(prob, steps, "f32", compensated=compensated)
+    compare(ref, got, TOL["f32"])
+
+
+def test_initial_fields_match_without_stepping():
+    prob = CASES["clamped_96x50"][0]
+    ref, got = run_both(prob, 0, "f64")
+    compare(ref, got, 1e-14, keys=("u", "v", "P", "r", "J"))
+    assert got["t"] == 0.0
+
+
+def test_chunked_stepping_is_bitwise_identical():
+    """Graph replay (long lbm_step) and one-step launches give the same bits."""
+    prob = CASES["periodic_100x70"][0]
+    with lbm.Body(prob, storage="f32") as a, lbm.Body(prob, storage="f32") as b:
+        a.step(203)
+        for _ in range(203):
+            b.step(1)
+        ra, rb = a.read(), b.read()
+        for k in ("u", "v", "P", "r"):
+            assert np.array_equal(ra[k], rb[k]), k
+        assert a.info()[0] == b.info()[0] == 203
+
+
+def test_diagnostics_match_oracle_sums():
+    prob = CASES["clamped_96x50"][0]
+    s = oracle.solver_from(prob)
+    s.step(100)
+    ref = s.read()
+    with lbm.Body(prob, storage="f64") as b:
+        b.step(100)
+        d = b.diagnostics()
+    j = prob.rho0 * ref["v"]
+    np.testing.assert_allclose(d[0:2], j.sum(axis=(0, 1)), rtol=1e-10, atol=1e-13)
+    np.testing.assert_allclose(d[2], (j ** 2).sum() / (2 * prob.rho0), rtol=1e-10)
+    W_sum = sum(oracle.strain_energy(h, prob.lam, prob.mu) for h in s.grad().reshape(-1, 4))
+    np.testing.assert_allclose(d[3], W_sum, rtol=1e-10)
+    assert math.isclose(d[4], ref["J"].min(), rel_tol=1e-12)
+    assert d[5] == 0.0
+
+
+def test_unstable_state_is_reported():
+    """An initial field with J < 0 is flagged: LBM_E_UNSTABLE, not a fault."""
+    prob = W.smooth_random(40, 30, W.all_periodic(), seed=3, amp=0.0)
+    x = np.arange(40)
+    prob.u0[:, :, 0] = -2.0 * np.sin(2 * np.pi * x / 40)[None, :] * 40 / (2 * np.pi) * 1.5
+    with lbm.Body(prob, storage="f32") as b:
+        b.step(5)
+        out = b.read(allow_unstable=True)
+        assert out["status"] == lbm.LBM_E_UNSTABLE
+        with pytest.raises(lbm.LbmError) as ei:
+            b.read()
+        assert ei.value.status == lbm.LBM_E_UNSTABLE
+
+
+def test_call_order_and_argument_errors():
+    prob = CASES["tiny_3x3_neumann"][0]
+    d = lbm.lbm_desc()
+    d.nx, d.ny, d.dX, d.storage, d.scheme = 8, 8, 1.0, lbm.LBM_F32, 1
+    ctx = lbm.lbm_create(d)
+    try:
+        L = lbm.lib()
+        assert L.lbm_step(ctx, 1) == lbm.LBM_E_STATE
+        assert L.lbm_set_material(ctx, 0.3, -1.0, 1.0, 1.0, None) == lbm.LBM_E_INVALID
+        assert L.lbm_set_material(ctx, 0.3, 0.3, 1.0, 2.5, None) == lbm.LBM_E_INVALID
+        lbm.lbm_set_material(ctx, 0.3, 0.3, 1.0, 1.0)
+        lbm.lbm_set_boundary(ctx, 0, lbm.LBM_PERIODIC)
+        assert L.lbm_set_boundary(ctx, 1, lbm.LBM_NEUMANN, None, None, None) == lbm.LBM_E_INVALID
+        assert L.lbm_set_boundary(ctx, 4, lbm.LBM_NEUMANN, None, None, None) == lbm.LBM_E_INVALID
+        for e in (1, 2, 3):
+            lbm.lbm_set_boundary(ctx, e, lbm.LBM_PERIODIC)
+        assert L.lbm_step(ctx, -1) == lbm.LBM_E_INVALID
+        lbm.lbm_step(ctx, 3)
+        assert L.lbm_set_material(ctx, 0.3, 0.3, 1.0, 1.0, None) == lbm.LBM_E_STATE
+        buf = np.zeros(10)
+        assert L.lbm_read_fields(ctx, 1, buf.ctypes.data_as(lbm.C.POINTER(lbm.C.c_double)), 10, None) == \
+            lbm.LBM_E_INVALID
+        assert L.lbm_read_fields(ctx, 0, buf.ctypes.data_as(lbm.C.POINTER(lbm.C.c_double)), 10, None) == \
+            lbm.LBM_E_INVALID
+        assert lbm.lbm_get_info(ctx)[0] == 3
+        dev, per = lbm.lbm_memory_info(ctx)
+        assert per == 104 and dev > 0
+    finally:
+        lbm.lbm_destroy(ctx)
