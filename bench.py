@@ -1,0 +1,359 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the fused Lagrangian-LBM step on GB300.
+
+Workload (one "step" = one time step of the whole body, i.e. one launch of
+the fused stream-collide-constitutive kernel): a 4096 x 2048-node plane-strain
+neo-Hooke body, left edge clamped, other edges traction-free, initial
+transverse velocity v_y = v_max x / L, FP32 populations and arithmetic.
+
+Prints ONE JSON line (rank 0) with MLUPS (million lattice-node updates per
+second), the HBM roofline fraction of the fused kernel, the end-to-end number
+through the C ABI with host buffers, the CPU oracle as a reported baseline,
+and the SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the body
+(independent problems, no collective on the data path; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+FALLBACK_HBM_GBS = 6800.0
+METRIC = "MLUPS and % HBM roofline, plain vs batched/low-precision; p50/p99 solve latency"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--nx", type=int, default=4096)
+    ap.add_argument("--ny", type=int, default=2048)
+    ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16", "bf16"])
+    ap.add_argument("--native-ucarry", dest="compensated", action="store_false",
+                    help="plain FP32 displacement carry (default: compensated FP32 pair)")
+    ap.add_argument("--nu", type=float, default=0.25)
+    ap.add_argument("--vmax", type=float, default=0.01)
+    ap.add_argument("--forms", default="f32n,f16,bf16",
+                    help="extra population formats timed on the same body ('' to skip)")
+    ap.add_argument("--form-steps", type=int, default=500)
+    ap.add_argument("--cpu-steps", type=int, default=0, help="oracle sample steps (0 = auto, ~10-20 s)")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(a):
+    from paper_2208_13769_gb300 import workloads as W
+
+    return W.clamped_body(nx=a.nx, ny=a.ny, mu=0.3, nu=a.nu, vmax=a.vmax)
+
+
+def config_of(a, prob):
+    return {
+        "workload": f"clamped neo-Hooke body {a.nx}x{a.ny} nodes, FP32 populations/arithmetic",
+        "nx": a.nx, "ny": a.ny, "mu": prob.mu, "lambda": prob.lam, "nu": a.nu, "rho0": prob.rho0,
+        "omega": prob.omega, "v_max": a.vmax, "edges": "x- clamped (Dirichlet), x+/y-/y+ traction-free",
+        "storage": a.storage, "u_carry": "compensated" if a.compensated else "native",
+        "scheme": "predictor-corrector",
+        "l2": "no flush: the state (two ping-pong copies, ~1 GB) is 8x the 129 MB L2",
+    }
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2208_13769_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(storage, compensated, nodes):
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary, scaled to `nodes`; None if absent or taken on other sources."""
+    path = os.path.join(ROOT, "profiles", "fused_step_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    key = storage + ("c" if compensated and storage == "f32" else "")
+    e = d.get("formats", {}).get(key)
+    if not e:
+        return None
+    return e["dram_bytes_per_node"] * nodes
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        try:
+            os.unlink(self.file.name)
+        except OSError:
+            pass
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle (CPU)
+
+def oracle_sample(prob, steps):
+    """Times the FP64 CPU oracle as it stands on `steps` steps of prob."""
+    import oracle
+
+    s = oracle.solver_from(prob)
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    s.close()
+    return prob.nodes * steps / dt / 1e6, dt, oracle.threads()
+
+
+def auto_cpu_steps(prob, budget_s=12.0):
+    mlups, dt, _ = oracle_sample(prob, 1)
+    per = prob.nodes / (mlups * 1e6)
+    return max(1, min(200, int(budget_s / max(per, 1e-9))))
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    prob = workload(a)
+    steps = a.cpu_steps or auto_cpu_steps(prob)
+    vals = []
+    for _ in range(max(1, a.warmup and 1)):
+        oracle_sample(prob, 1)
+    t_all = 0.0
+    cores = 1
+    for _ in range(max(1, min(a.steps, 3))):
+        v, dt, cores = oracle_sample(prob, steps)
+        vals.append(v)
+        t_all += dt
+    value = statistics.median(vals)
+    sample = f"{steps} time steps of the full {a.nx}x{a.ny} body per timed repetition, {len(vals)} repetitions"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": a.gpus,
+        "steps": len(vals), "warmup": 1, "ms_per_step": 1e3 * prob.nodes / (value * 1e6),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_of(a, prob),
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- native (GPU)
+
+def time_steps(body, stream, steps):
+    import torch
+
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    body.step(steps)
+    end.record(stream)
+    end.synchronize()
+    torch.cuda.synchronize()
+    return start.elapsed_time(end) / 1e3
+
+
+def run_native(a):
+    import torch
+
+    from paper_2208_13769_gb300 import lbm
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    prob = workload(a)
+    nodes = prob.nodes
+    stream = torch.cuda.Stream()
+    body = lbm.Body(prob, storage=a.storage, compensated=a.compensated, stream=stream.cuda_stream,
+                    device=local)
+    _, bytes_per_node = lbm.lbm_memory_info(body.ctx)
+    body.step(a.warmup)
+    body.read(lbm.LBM_FIELD_U, allow_unstable=True)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    secs = time_steps(body, stream, a.steps)
+    clk = clocks.stop()
+    barrier()
+    secs = max_over_ranks(secs)
+    status = body.read(lbm.LBM_FIELD_U, allow_unstable=True)["status"]
+    body.close()
+
+    ms_per_step = 1e3 * secs / a.steps
+    value = world * nodes * a.steps / secs / 1e6
+    peak, peak_kind = measured_peak()
+    achieved = bytes_per_node * nodes / (secs / a.steps) / 1e9
+    traffic = ncu_traffic(a.storage, a.compensated, nodes)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_node": bytes_per_node,
+            "kernel": "fused_step_kernel"}
+
+    # extra population formats on the same body
+    forms = {}
+    for f in [x for x in a.forms.split(",") if x]:
+        st, comp = {"f32c": ("f32", True), "f32n": ("f32", False)}.get(f, (f, False))
+        b = lbm.Body(prob, storage=st, compensated=comp, stream=stream.cuda_stream, device=local)
+        _, bpn = lbm.lbm_memory_info(b.ctx)
+        b.step(a.warmup)
+        torch.cuda.synchronize()
+        s = time_steps(b, stream, a.form_steps)
+        ok = b.read(lbm.LBM_FIELD_U, allow_unstable=True)["status"] == lbm.LBM_OK
+        b.close()
+        ach = bpn * nodes / (s / a.form_steps) / 1e9
+        forms[f] = {"mlups": nodes * a.form_steps / s / 1e6, "bytes_per_node_update": bpn,
+                    "achieved_gbs": ach, "frac": ach / peak, "steps": a.form_steps, "stable": ok}
+
+    # end to end through the C ABI from host buffers: create (H2D of u0, v0),
+    # K steps, read u (D2H)
+    e2e = None
+    if not a.no_e2e:
+        barrier()
+        t0 = time.perf_counter()
+        b = lbm.Body(prob, storage=a.storage, compensated=a.compensated, stream=stream.cuda_stream,
+                     device=local)
+        b.step(a.steps)
+        out = b.read(lbm.LBM_FIELD_U, allow_unstable=True)
+        t1 = time.perf_counter()
+        b.close()
+        e_secs = max_over_ranks(t1 - t0)
+        h2d = 2 * nodes * 2 * 8
+        d2h = out["u"].nbytes
+        e2e = {"value": world * nodes * a.steps / e_secs / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d / a.steps, "d2h_bytes_per_step": d2h / a.steps,
+               "h2d_bytes_total": h2d, "d2h_bytes_total": d2h, "seconds": e_secs,
+               "includes": "context creation, u0/v0 upload, initialisation, K steps, u read-back"}
+
+    cpu = None
+    if rank == 0 and not a.no_cpu:
+        steps = a.cpu_steps or auto_cpu_steps(prob)
+        v, dt, cores = oracle_sample(prob, steps)
+        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"{steps} time steps of the full {a.nx}x{a.ny} body ({dt:.1f} s, FP64 oracle)"}
+
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "f16": "f16", "bf16": "bf16"}[a.storage],
+        "data": "synthetic", "config": config_of(a, prob), "roofline": roof, "cpu_baseline": cpu,
+        "e2e": e2e, "gpu_launches": a.steps, "clocks": clk, "forms": forms,
+        "status": lbm.status_string(status),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_native(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -17,8 +17,8 @@
  *  - The library owns all device memory of a context (allocated in
  *    lbm_create, freed in lbm_destroy).  Host buffers passed in are only read
  *    (or written, for outputs) during the call; the caller keeps ownership.
- *  - Work is issued on the context's CUDA stream (lbm_desc.cuda_stream, or
- *    the legacy default stream when NULL).  lbm_step is asynchronous;
+ *  - Work is issued on the context's CUDA stream (lbm_desc.cuda_stream, or a
+ *    stream the context owns when that is NULL).  lbm_step is asynchronous;
  *    lbm_read_fields and lbm_sync synchronise that stream.
  *  - A context is not thread-safe; distinct contexts are independent.
  *  - Units: any consistent set.  The time step is derived, not passed:
@@ -86,7 +86,8 @@ typedef struct {
     int32_t f16_scale_log2; /* s for F16/BF16 (0 = library default 10) */
     const double* u0;    /* host, [ny][nx][2] initial displacement, NULL = 0 */
     const double* v0;    /* host, [ny][nx][2] initial velocity, NULL = 0 */
-    void* cuda_stream;   /* cudaStream_t to issue work on; NULL = default stream */
+    void* cuda_stream;   /* cudaStream_t to issue work on; NULL: the context
+                            creates (and destroys) a non-blocking stream of its own */
     int32_t device;      /* CUDA device ordinal */
 } lbm_desc;
 
@@ -173,6 +174,10 @@ LBM_API lbm_status lbm_memory_info(const lbm_ctx* ctx, int64_t* device_bytes, in
 
 /* Frees the context and its device memory (NULL is allowed). */
 LBM_API lbm_status lbm_destroy(lbm_ctx* ctx);
+
+/* Description of the CUDA error that made the context unusable ("none" if
+ * there was none).  Static storage; valid for the context's lifetime. */
+LBM_API const char* lbm_last_cuda_error(const lbm_ctx* ctx);
 
 /* Static description of a status code. */
 LBM_API const char* lbm_status_string(lbm_status status);

@@ -45,6 +45,8 @@ int ucarry_planes(int fmt) { return (fmt == kFmtF64 || fmt == kFmtF32) ? 1 : 2; 
 struct lbm_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    bool owns_stream = false;
+    cudaError_t last_error = cudaSuccess;
     int fmt = kFmtF32;
     int scheme = 1;
     int32_t nx = 0, ny = 0;
@@ -53,7 +55,7 @@ struct lbm_ctx {
     // layout
     int64_t pitch = 0, plane = 0;
     int32_t xoff = 0;
-    int tile_x = 0, tile_y = 0, tiles_x = 0, tiles_y = 0;
+    int tile_x = 0, tile_y = 0, tiles_x = 0, tiles_y = 0, chunk_rows = 0;
     // device memory
     void* f[2] = {nullptr, nullptr};
     void* a[2] = {nullptr, nullptr};
@@ -87,8 +89,10 @@ struct lbm_ctx {
 namespace {
 
 lbm_status fail_cuda(lbm_ctx* ctx, cudaError_t e) {
-    (void)e;
-    if (ctx) ctx->sticky = true;
+    if (ctx) {
+        ctx->sticky = true;
+        ctx->last_error = e;
+    }
     return LBM_E_CUDA;
 }
 
@@ -111,6 +115,7 @@ StepParams make_params(const lbm_ctx* c, int parity) {
     p.plane = c->plane;
     p.tiles_x = c->tiles_x;
     p.tiles_y = c->tiles_y;
+    p.chunk_rows = c->chunk_rows;
     p.f_src = c->f[parity];
     p.f_dst = c->f[parity ^ 1];
     p.a_src = c->a[parity];
@@ -235,6 +240,7 @@ void free_all(lbm_ctx* c) {
     cudaFree(c->partials);
     cudaFree(c->diag);
     cudaFree(c->readout);
+    if (c->owns_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
 bool finite_pair(const double* v) { return v == nullptr || (isfinite(v[0]) && isfinite(v[1])); }
@@ -265,6 +271,15 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
         return LBM_E_INVALID;
     }
     c->stream = static_cast<cudaStream_t>(d->cuda_stream);
+    if (!c->stream) {
+        // graphs cannot be captured on the legacy default stream: own one
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return LBM_E_CUDA;
+        }
+        c->owns_stream = true;
+    }
     c->nx = d->nx;
     c->ny = d->ny;
     c->dX = d->dX;
@@ -280,9 +295,19 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
         memset(&c->bc[e], 0, sizeof(EdgeBC));
         c->bc[e].times[2] = INFINITY;
     }
+    // column strips of tile_x nodes; rows split into chunks so that the grid
+    // holds about four CTAs per SM (152 SMs), with chunks of 32..256 rows
     tile_shape(c->fmt, &c->tile_x, &c->tile_y);
     c->tiles_x = int((d->nx + c->tile_x - 1) / c->tile_x);
-    c->tiles_y = int((d->ny + c->tile_y - 1) / c->tile_y);
+    {
+        const int64_t want_chunks = (4 * 152 + c->tiles_x - 1) / c->tiles_x;
+        int64_t rows = (d->ny + want_chunks - 1) / want_chunks;
+        if (rows < 32) rows = 32;
+        if (rows > 256) rows = 256;
+        if (rows > d->ny) rows = d->ny;
+        c->chunk_rows = int(rows);
+        c->tiles_y = int((d->ny + rows - 1) / rows);
+    }
 
     // plane layout: x = 0 on a 16-byte boundary, rows padded to 128 bytes
     const int64_t es = int64_t(elem_size_storage(c->fmt));
@@ -509,6 +534,11 @@ lbm_status lbm_destroy(lbm_ctx* c) {
     }
     delete c;
     return LBM_OK;
+}
+
+const char* lbm_last_cuda_error(const lbm_ctx* c) {
+    if (!c) return "no context";
+    return c->last_error == cudaSuccess ? "none" : cudaGetErrorString(c->last_error);
 }
 
 const char* lbm_status_string(lbm_status s) {

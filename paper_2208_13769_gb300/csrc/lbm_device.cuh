@@ -76,20 +76,30 @@ __device__ __forceinline__ T feq_odd_over_w(int i, T j0, T j1, T inv_c) {
 }
 
 // ---------------------------------------------------------------- material
-// Neo-Hooke (Sec. 7): P = mu F + (lambda/2 (J^2 - 1) - mu) F^-T with
-// J - 1 = H11 + H22 + H11 H22 - H12 H21.  Returns J.
+// Q = P(F) + Pbar(H): the neo-Hooke first Piola-Kirchhoff stress of Sec. 7,
+// P = mu (F - F^-T) + lambda/2 (J^2 - 1) F^-T, plus the Poisson stress of
+// Eq. (Plin), Pbar = -mu (H + H^T + tr H I) -- the nonlinear remainder that
+// drives 1S.  Both stresses are O(mu |H|) while Q is O((lambda - mu) |H|) +
+// O(mu |H|^2), so Q is expanded in H before it is evaluated: with
+// d = J - 1 = tr H + D, D = H11 H22 - H12 H21,
+//   J Q11 = mu (2 D - d (1 + 2 H11 + H22)) + lambda/2 d (2 + d) (1 + H22)
+//   J Q22 = mu (2 D - d (1 + 2 H22 + H11)) + lambda/2 d (2 + d) (1 + H11)
+//   J Q12 = -H21 d (mu + lambda/2 (2 + d)),  J Q21 = -H12 d (mu + lambda/2 (2 + d)).
+// No term of order mu cancels, so the rounding error of Q is relative to
+// mu |H| rather than to mu.  Returns J.
 template <class T>
-__device__ __forceinline__ T piola(T h11, T h12, T h21, T h22, T lam, T mu, T& p11, T& p12, T& p21,
-                                   T& p22) {
-    T jm1 = h11 + h22 + (h11 * h22 - h12 * h21);
-    T J = T(1) + jm1;
-    T invJ = T(1) / J;
-    T coef = (T(0.5) * lam * jm1 * (T(2) + jm1) - mu) * invJ;
-    // F^-T * J = [[F22, -F21], [-F12, F11]]
-    p11 = mu * (T(1) + h11) + coef * (T(1) + h22);
-    p12 = mu * h12 - coef * h21;
-    p21 = mu * h21 - coef * h12;
-    p22 = mu * (T(1) + h22) + coef * (T(1) + h11);
+__device__ __forceinline__ T stress_remainder(T h11, T h12, T h21, T h22, T lam, T mu, T& q11, T& q12,
+                                              T& q21, T& q22) {
+    const T D = h11 * h22 - h12 * h21;
+    const T d = (h11 + h22) + D;
+    const T J = T(1) + d;
+    const T invJ = T(1) / J;
+    const T vol = T(0.5) * lam * d * (T(2) + d);
+    q11 = (mu * (T(2) * D - d * (T(1) + T(2) * h11 + h22)) + vol * (T(1) + h22)) * invJ;
+    q22 = (mu * (T(2) * D - d * (T(1) + T(2) * h22 + h11)) + vol * (T(1) + h11)) * invJ;
+    const T g = -d * (mu + T(0.5) * lam * (T(2) + d)) * invJ;
+    q12 = g * h21;
+    q21 = g * h12;
     return J;
 }
 

@@ -29,7 +29,9 @@ struct StepParams {
     int32_t scheme;  // 0 explicit (Algorithm 1), 1 predictor-corrector
     int64_t pitch;   // elements per row (storage or carry element type)
     int64_t plane;   // elements per plane
-    int32_t tiles_x, tiles_y;
+    int32_t tiles_x, tiles_y;  // grid: column strips x row chunks
+    int32_t chunk_rows;        // rows per chunk (>= 3)
+    int32_t pad0;
 
     const void* f_src;  // 9 planes of f^col(t_n), storage type
     void* f_dst;        // 9 planes of f^col(t_n+1)

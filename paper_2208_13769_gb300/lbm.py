@@ -68,6 +68,7 @@ _SIGNATURES = {
     "lbm_memory_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "lbm_destroy": (C.c_int, [C.c_void_p]),
     "lbm_status_string": (C.c_char_p, [C.c_int]),
+    "lbm_last_cuda_error": (C.c_char_p, [C.c_void_p]),
 }
 
 
@@ -126,7 +127,10 @@ def lbm_set_boundary(ctx, edge, kind, value=None, rate=None, times=None):
 
 
 def lbm_step(ctx, nsteps: int):
-    return _check(lib().lbm_step(ctx, int(nsteps)), "lbm_step")
+    st = lib().lbm_step(ctx, int(nsteps))
+    if st == LBM_E_CUDA:
+        raise LbmError(st, f"lbm_step ({lbm_last_cuda_error(ctx)})")
+    return _check(st, "lbm_step")
 
 
 def lbm_fields_size(ctx, mask: int) -> int:
@@ -170,6 +174,10 @@ def lbm_destroy(ctx):
     return _check(lib().lbm_destroy(ctx), "lbm_destroy")
 
 
+def lbm_last_cuda_error(ctx) -> str:
+    return lib().lbm_last_cuda_error(ctx).decode()
+
+
 def lbm_status_string(status: int) -> str:
     return status_string(status)
 
@@ -180,16 +188,19 @@ class Body:
     """One solver context for a workloads.Problem-like object.
 
     storage: "f64" | "f32" | "f16" | "bf16"; compensated: FP32-pair u-carry
-    for "f32"; scheme: LBM_SCHEME_PREDICTOR (default) or LBM_SCHEME_EXPLICIT;
+    for "f32" (default True: a plain FP32 u loses Grad u to rounding once
+    |u| >> |H| dX); scheme: LBM_SCHEME_PREDICTOR (default) or LBM_SCHEME_EXPLICIT;
     stream: an integer cudaStream_t handle (e.g. torch's stream.cuda_stream)."""
 
-    def __init__(self, prob, storage: str = "f64", compensated: bool = False,
+    def __init__(self, prob, storage: str = "f64", compensated: Optional[bool] = None,
                  scheme: int = LBM_SCHEME_PREDICTOR, stream: int = 0, device: int = 0,
                  f16_scale_log2: int = 0):
         self.prob = prob
         d = lbm_desc()
         d.nx, d.ny, d.dX = prob.nx, prob.ny, prob.dX
         d.storage = STORAGE[storage]
+        if compensated is None:
+            compensated = True
         d.u_carry = LBM_UCARRY_COMPENSATED if compensated else LBM_UCARRY_NATIVE
         d.scheme = scheme
         d.f16_scale_log2 = f16_scale_log2

@@ -12,7 +12,7 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def run_both(prob, steps, storage="f64", compensated=False, scheme=oracle.PREDICTOR, chunks=None):
+def run_both(prob, steps, storage="f64", compensated=None, scheme=oracle.PREDICTOR, chunks=None):
     """Advance the oracle and the GPU library by `steps` from the same inputs;
     returns (oracle fields, gpu fields)."""
     s = oracle.solver_from(prob, scheme)
