@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 
 #include "lbm.h"
@@ -54,7 +55,7 @@ struct lbm_ctx {
     int32_t f16_scale_log2 = 10;
     // layout
     int64_t pitch = 0, plane = 0;
-    int32_t xoff = 0;
+    int ring_slots = 0;
     int tile_x = 0, tile_y = 0, tiles_x = 0, tiles_y = 0, chunk_rows = 0;
     // device memory
     void* f[2] = {nullptr, nullptr};
@@ -84,6 +85,14 @@ struct lbm_ctx {
     bool sticky = false;
     bool variant_warm = false;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // launch plan (built at initialisation, once the boundaries are known)
+    bool planned = false;
+    bool has_interior = false;
+    int irect[4] = {0, 0, 0, 0};
+    int i_tiles_x = 0, i_tiles_y = 0, i_chunk = 0, i_ring = 0;
+    int nband = 0;
+    int brect[4][4];
+    int b_tiles_x = 0, b_tiles_y = 0, b_chunk = 0;
 };
 
 namespace {
@@ -107,7 +116,7 @@ StepParams make_params(const lbm_ctx* c, int parity) {
     memset(&p, 0, sizeof(p));
     p.nx = c->nx;
     p.ny = c->ny;
-    p.xoff = c->xoff;
+    p.ring_slots = c->ring_slots;
     p.periodic_x = c->bc[0].kind == kPeriodic;
     p.periodic_y = c->bc[2].kind == kPeriodic;
     p.scheme = c->scheme;
@@ -174,9 +183,89 @@ lbm_status ready(const lbm_ctx* c) {
     return LBM_OK;
 }
 
+// Interior rectangle (nodes >= 2 from bounded edges, >= 3 from periodic
+// seams) for the lean kernel, the bands around it for the general kernel.
+void build_plan(lbm_ctx* c) {
+    const bool perx = c->bc[0].kind == kPeriodic, pery = c->bc[2].kind == kPeriodic;
+    const int bx = perx ? 3 : 2, by = pery ? 3 : 2;
+    const int nx = c->nx, ny = c->ny;
+    const int W = c->tile_x;
+    c->has_interior = nx - 2 * bx >= 8 && ny - 2 * by >= 8;
+    c->nband = 0;
+    if (c->has_interior) {
+        int r[4] = {bx, nx - bx, by, ny - by};
+        for (int k = 0; k < 4; ++k) c->irect[k] = r[k];
+        const int w = r[1] - r[0], h = r[3] - r[2];
+        c->i_ring = 7;  // lookahead of 4 rows
+        const size_t smem = interior_smem(c->fmt, c->i_ring);
+        const int per_sm = std::max(1, int((228 * 1024) / (smem + 1024)));
+        // exactly one wave of equal CTAs: strips x chunks <= 152 x per_sm
+        c->i_tiles_x = (w + W - 1) / W;
+        const int64_t slots = int64_t(152) * std::min(per_sm, 4);
+        const int64_t chunks = std::max<int64_t>(1, slots / c->i_tiles_x);
+        int64_t rows = (h + chunks - 1) / chunks;
+        rows = std::max<int64_t>(rows, 16);
+        rows = std::min<int64_t>(rows, h);
+        c->i_chunk = int(rows);
+        c->i_tiles_y = int((h + rows - 1) / rows);
+        int bands[4][4] = {{0, nx, 0, by}, {0, nx, ny - by, ny}, {0, bx, by, ny - by}, {nx - bx, nx, by, ny - by}};
+        for (int b = 0; b < 4; ++b)
+            for (int k = 0; k < 4; ++k) c->brect[b][k] = bands[b][k];
+        c->nband = 4;
+        c->b_chunk = 8;
+    } else {
+        int all[4] = {0, nx, 0, ny};
+        for (int k = 0; k < 4; ++k) c->brect[0][k] = all[k];
+        c->nband = 1;
+        c->b_chunk = c->chunk_rows;
+    }
+    c->b_tiles_x = 1;
+    c->b_tiles_y = 1;
+    for (int b = 0; b < c->nband; ++b) {
+        const int w = c->brect[b][1] - c->brect[b][0], h = c->brect[b][3] - c->brect[b][2];
+        c->b_tiles_x = std::max(c->b_tiles_x, (w + W - 1) / W);
+        c->b_tiles_y = std::max(c->b_tiles_y, (h + c->b_chunk - 1) / c->b_chunk);
+    }
+    c->planned = true;
+}
+
+// Launches of one time step (mode 0) or the initialisation (mode 1).
+cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int parity) {
+    StepParams p = make_params(c, parity);
+    if (mode == 1) {
+        p.nrect = 1;
+        p.rect[0][0] = 0;
+        p.rect[0][1] = c->nx;
+        p.rect[0][2] = 0;
+        p.rect[0][3] = c->ny;
+        p.write_counter = 1;
+        return launch_fused_step(c->fmt, p, c->stream, 1, fields);
+    }
+    if (c->has_interior) {
+        StepParams pi = p;
+        pi.nrect = 1;
+        for (int k = 0; k < 4; ++k) pi.rect[0][k] = c->irect[k];
+        pi.tiles_x = c->i_tiles_x;
+        pi.tiles_y = c->i_tiles_y;
+        pi.chunk_rows = c->i_chunk;
+        pi.ring_slots = c->i_ring;
+        pi.write_counter = 0;
+        cudaError_t e = launch_interior(c->fmt, pi, c->stream, fields);
+        if (e != cudaSuccess) return e;
+    }
+    p.nrect = c->nband;
+    for (int b = 0; b < c->nband; ++b)
+        for (int k = 0; k < 4; ++k) p.rect[b][k] = c->brect[b][k];
+    p.tiles_x = c->b_tiles_x;
+    p.tiles_y = c->b_tiles_y;
+    p.chunk_rows = c->b_chunk;
+    p.write_counter = 1;
+    return launch_fused_step(c->fmt, p, c->stream, 0, fields);
+}
+
 lbm_status launch(lbm_ctx* c, int mode, bool fields) {
-    StepParams p = make_params(c, c->parity);
-    LBM_CUDA(c, launch_fused_step(c->fmt, p, c->stream, mode, fields));
+    if (!c->planned) build_plan(c);
+    LBM_CUDA(c, launch_step_kernels(c, mode, fields, c->parity));
     c->parity ^= 1;
     if (mode == 0) c->steps += 1;
     return LBM_OK;
@@ -199,10 +288,7 @@ lbm_status get_graph(lbm_ctx* c, int par, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
     LBM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t err = cudaSuccess;
-    for (int k = 0; k < kGraphChunk && err == cudaSuccess; ++k) {
-        StepParams p = make_params(c, par ^ (k & 1));
-        err = launch_fused_step(c->fmt, p, c->stream, 0, false);
-    }
+    for (int k = 0; k < kGraphChunk && err == cudaSuccess; ++k) err = launch_step_kernels(c, 0, false, par ^ (k & 1));
     cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
     if (err != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -218,10 +304,14 @@ lbm_status get_graph(lbm_ctx* c, int par, cudaGraphExec_t* out) {
     return LBM_OK;
 }
 
+// Device flag bits: 1 non-finite value or J <= 0; 4 a bounded wait gave up;
+// 8 a bulk copy was refused for misalignment (an internal error).
 lbm_status check_flag(lbm_ctx* c) {
     int32_t h = 0;
     LBM_CUDA(c, cudaMemcpyAsync(&h, c->flag, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (h & 8) return fail_cuda(c, cudaErrorMisalignedAddress);
+    if (h & 4) return LBM_E_TIMEOUT;
     return (h & 1) ? LBM_E_UNSTABLE : LBM_OK;
 }
 
@@ -296,25 +386,31 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
         c->bc[e].times[2] = INFINITY;
     }
     // column strips of tile_x nodes; rows split into chunks so that the grid
-    // holds about four CTAs per SM (152 SMs), with chunks of 32..256 rows
+    // holds about one wave of co-resident CTAs on the 152 SMs (chunks of at
+    // least 16 rows)
     tile_shape(c->fmt, &c->tile_x, &c->tile_y);
-    c->tiles_x = int((d->nx + c->tile_x - 1) / c->tile_x);
+    c->ring_slots = 4;  // row-pair slots of the bulk-copy ring: one pair of lookahead
     {
-        const int64_t want_chunks = (4 * 152 + c->tiles_x - 1) / c->tiles_x;
-        int64_t rows = (d->ny + want_chunks - 1) / want_chunks;
-        if (rows < 32) rows = 32;
-        if (rows > 256) rows = 256;
+        const size_t smem = step_smem_bytes(c->fmt, c->ring_slots);
+        const int per_sm = smem > 0 ? int((228 * 1024) / (smem + 1024)) : 1;
+        c->tiles_x = int((d->nx + c->tile_x - 1) / c->tile_x);
+        const int64_t want = int64_t(152) * (per_sm > 0 ? per_sm : 1);
+        const int64_t chunks = (want + c->tiles_x - 1) / c->tiles_x;
+        int64_t rows = (d->ny + chunks - 1) / chunks;
+        if (rows < 16) rows = 16;
         if (rows > d->ny) rows = d->ny;
         c->chunk_rows = int(rows);
         c->tiles_y = int((d->ny + rows - 1) / rows);
     }
 
-    // plane layout: x = 0 on a 16-byte boundary, rows padded to 128 bytes
-    const int64_t es = int64_t(elem_size_storage(c->fmt));
-    c->xoff = int32_t(16 / es);
-    const int64_t row_align = 128 / es;
-    c->pitch = ((c->xoff + d->nx + 1) + row_align - 1) / row_align * row_align;
-    c->plane = c->pitch * (d->ny + 2);
+    // plane layout: kPadCols columns / kPadRows rows of padding on each side,
+    // pitch a multiple of 64 elements covering the widest bulk-copied segment
+    // a strip may start as far right as nx - 2 (the right edge band); its
+    // segment then reaches nx - 2 - 15 + (tile + 4) + kSegExtra
+    const int64_t seg_end = int64_t(d->nx) + c->tile_x + 4 + kSegExtra;
+    int64_t need = kPadCols + std::max<int64_t>(seg_end, int64_t(c->tile_x) + 4 + kSegExtra + 8) + 16;
+    c->pitch = (need + 63) / 64 * 64;
+    c->plane = c->pitch * (int64_t(d->ny) + 2 * kPadRows);
 
     const size_t fbytes = size_t(9) * c->plane * elem_size_storage(c->fmt);
     const size_t abytes = size_t(2 * ucarry_planes(c->fmt)) * c->plane * elem_size_ucarry(c->fmt);

@@ -87,13 +87,17 @@ __device__ __forceinline__ T feq_odd_over_w(int i, T j0, T j1, T inv_c) {
 //   J Q12 = -H21 d (mu + lambda/2 (2 + d)),  J Q21 = -H12 d (mu + lambda/2 (2 + d)).
 // No term of order mu cancels, so the rounding error of Q is relative to
 // mu |H| rather than to mu.  Returns J.
+// Correctly rounded reciprocal (no division slow path).
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
 template <class T>
 __device__ __forceinline__ T stress_remainder(T h11, T h12, T h21, T h22, T lam, T mu, T& q11, T& q12,
                                               T& q21, T& q22) {
     const T D = h11 * h22 - h12 * h21;
     const T d = (h11 + h22) + D;
     const T J = T(1) + d;
-    const T invJ = T(1) / J;
+    const T invJ = rcp_rn(J);
     const T vol = T(0.5) * lam * d * (T(2) + d);
     q11 = (mu * (T(2) * D - d * (T(1) + T(2) * h11 + h22)) + vol * (T(1) + h22)) * invJ;
     q22 = (mu * (T(2) * D - d * (T(1) + T(2) * h22 + h11)) + vol * (T(1) + h11)) * invJ;
@@ -139,53 +143,54 @@ struct Codec<__nv_bfloat16, float> {
 };
 
 // ---------------------------------------------------------------- u-carry
-// Displacement number types.  Each provides: load from / store to the carry
-// planes, add a small increment, difference of two values (in the arithmetic
-// type T), difference against an FP64 value, and conversion to double.
+// Displacement number types.  Each provides: the element type and number of
+// planes per component in memory, construction from the planes of a row
+// segment, adding an increment (in the arithmetic type), renormalisation
+// before storing, differences (in the arithmetic type), the difference to an
+// FP64 value, and conversion to double.
 
 template <class T>
 struct UPlain {  // u kept in T itself (FP64 or FP32)
-    T v;
+    using Elem = T;
     static constexpr int planes = 1;
-    __device__ __forceinline__ static UPlain load(const void* base, int64_t idx, int64_t) {
-        return UPlain{static_cast<const T*>(base)[idx]};
-    }
-    __device__ __forceinline__ void store(void* base, int64_t idx, int64_t) const {
-        static_cast<T*>(base)[idx] = v;
-    }
+    T v;
+    __device__ __forceinline__ static UPlain from_planes(const T* base, int e, int) { return UPlain{base[e]}; }
+    __device__ __forceinline__ static UPlain ld_global(const T* base, int64_t o, int64_t) { return UPlain{base[o]}; }
     __device__ __forceinline__ static UPlain from_double(double d) { return UPlain{T(d)}; }
     __device__ __forceinline__ UPlain add(T d) const { return UPlain{v + d}; }
+    __device__ __forceinline__ UPlain renorm() const { return *this; }
+    __device__ __forceinline__ T part(int) const { return v; }
     __device__ __forceinline__ T minus(const UPlain& o) const { return v - o.v; }
     __device__ __forceinline__ T minus_d(double d) const { return T(double(v) - d); }
     __device__ __forceinline__ double to_double() const { return double(v); }
 };
 
-// Unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)/2), "double-float".
-// Addition uses Knuth's two-sum followed by a renormalising fast two-sum.
+// Unevaluated sum hi + lo of two floats ("double-float", about 48
+// significant bits).  Increments go into lo (lo stays small, so its rounding
+// is far below ulp(hi)); renorm() folds lo back with Knuth's two-sum before
+// the value is stored.  Stored as two planes per component: hi, then lo.
 struct UComp {
+    using Elem = float;
+    static constexpr int planes = 2;
     float hi, lo;
-    static constexpr int planes = 2;  // hi plane, then lo plane (same pitch)
-    __device__ __forceinline__ static UComp load(const void* base, int64_t idx, int64_t plane) {
-        const float* b = static_cast<const float*>(base);
-        return UComp{b[idx], b[idx + plane]};
+    __device__ __forceinline__ static UComp from_planes(const float* base, int e, int seg) {
+        return UComp{base[e], base[seg + e]};
     }
-    __device__ __forceinline__ void store(void* base, int64_t idx, int64_t plane) const {
-        float* b = static_cast<float*>(base);
-        b[idx] = hi;
-        b[idx + plane] = lo;
+    __device__ __forceinline__ static UComp ld_global(const float* base, int64_t o, int64_t plane) {
+        return UComp{base[o], base[o + plane]};
     }
     __device__ __forceinline__ static UComp from_double(double d) {
-        float h = __double2float_rn(d);
+        const float h = __double2float_rn(d);
         return UComp{h, __double2float_rn(d - double(h))};
     }
-    __device__ __forceinline__ UComp add(float d) const {
-        float s = __fadd_rn(hi, d);
-        float bb = __fsub_rn(s, hi);
-        float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(d, bb));
-        float l = __fadd_rn(lo, e);
-        float h2 = __fadd_rn(s, l);
-        return UComp{h2, __fsub_rn(l, __fsub_rn(h2, s))};
+    __device__ __forceinline__ UComp add(float d) const { return UComp{hi, __fadd_rn(lo, d)}; }
+    __device__ __forceinline__ UComp renorm() const {
+        const float s = __fadd_rn(hi, lo);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(lo, bb));
+        return UComp{s, e};
     }
+    __device__ __forceinline__ float part(int c) const { return c == 0 ? hi : lo; }
     __device__ __forceinline__ float minus(const UComp& o) const {
         return __fadd_rn(__fsub_rn(hi, o.hi), __fsub_rn(lo, o.lo));
     }

@@ -1,0 +1,334 @@
+// lbm_interior.cu -- the fused step for the interior of the body.
+//
+// Every node at least 2 nodes from a bounded edge (3 from a periodic seam)
+// needs none of the boundary machinery: no ghost rule in Grad u or Div Q, no
+// bounced population, no periodic image.  This kernel advances exactly those
+// nodes; the general kernel of lbm_step.cu advances the thin bands along the
+// edges in the same step (both read the same source buffers and write
+// disjoint nodes).
+//
+// Each CTA owns a strip of W = NT - 4 columns and a chunk of rows, one thread
+// per column, and walks the rows as a three-stage pipeline with a lag of one
+// row per stage:
+//   stage A, row a     : pull-stream, first moment, predicted u*   (W + 4 cols)
+//   stage B, row a - 1 : H = Grad u*, Q = P(F) + Pbar(H)           (W + 2 cols)
+//   stage C, row a - 2 : 1S = rho0 b + Div Q, corrected j and u, equilibrium,
+//                        BGK collision with He forcing, store       (W cols)
+// The 9 population segments of each row arrive in a ring of shared-memory
+// slots by bulk asynchronous copies (cp.async.bulk, one mbarrier per slot)
+// issued D rows ahead of stage A; the two carries are prefetched one row
+// ahead into registers.  u* and Q live in 3-row rolling buffers.  The same
+// lattice-unit arithmetic as the general kernel (see lbm_step.cu).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm_device.cuh"
+#include "lbm_kernels.h"
+#include "lbm_pipeline.cuh"
+
+namespace lbm {
+
+namespace {
+
+template <class UT, class TC, int NT>
+__host__ __device__ constexpr size_t interior_smem_fixed() {
+    return (256 + sizeof(UT) * 6 * NT + sizeof(TC) * 12 * NT + 127) / 128 * 128;
+}
+
+template <class TS, int NT>
+__host__ __device__ constexpr size_t interior_row_bytes() {
+    return size_t(9) * (NT + kSegExtra) * sizeof(TS);
+}
+
+}  // namespace
+
+template <class TS, class TC, class UT, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) interior_step_kernel(const __grid_constant__ StepParams p) {
+    using CT = typename UT::Elem;
+    constexpr int W = NT - 4;
+    constexpr int SEG = NT + kSegExtra;
+    constexpr int UP = UT::planes;
+    constexpr int ROW_BYTES = int(interior_row_bytes<TS, NT>());
+    static_assert(ROW_BYTES % 16 == 0, "row size");
+    constexpr int ALIGN_COLS = 16 / int(sizeof(TS));
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int R = p.ring_slots;  // row slots: lookahead + 3
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    UT* su = reinterpret_cast<UT*>(smem + 256);                          // [3][2][NT]
+    TC* sq = reinterpret_cast<TC*>(smem + 256 + sizeof(UT) * 6 * NT);   // [3][4][NT]
+    unsigned char* ring = smem + interior_smem_fixed<UT, TC, NT>();
+    __shared__ int s_abort;
+
+    LatConsts<TC> k;
+    k.load(p);
+    const int64_t pitch = p.pitch, plane = p.plane;
+    const int t = threadIdx.x;
+    const int rx0 = p.rect[0][0], rx1 = p.rect[0][1], ry0 = p.rect[0][2], ry1 = p.rect[0][3];
+    if (int(blockIdx.x) * W >= rx1 - rx0 || int(blockIdx.y) * p.chunk_rows >= ry1 - ry0) return;
+    int x0 = rx0 + int(blockIdx.x) * W;
+    if (x0 > rx1 - W) x0 = rx1 - W > rx0 ? rx1 - W : rx0;
+    int y_begin = ry0 + int(blockIdx.y) * p.chunk_rows;
+    if (y_begin > ry1 - p.chunk_rows) y_begin = ry1 - p.chunk_rows > ry0 ? ry1 - p.chunk_rows : ry0;
+    const int y_end = min(ry1, y_begin + p.chunk_rows);
+    const int x_end = min(rx1, x0 + W);
+    int seg0 = x0 - 8;  // 16-byte aligned first column of the row segments
+    seg0 = (seg0 >= 0 ? seg0 : seg0 - (ALIGN_COLS - 1)) / ALIGN_COLS * ALIGN_COLS;
+
+    const TS* __restrict__ fsrc = static_cast<const TS*>(p.f_src);
+    TS* __restrict__ fdst = static_cast<TS*>(p.f_dst);
+    const CT* __restrict__ a_src = static_cast<const CT*>(p.a_src);
+    CT* __restrict__ a_dst = static_cast<CT*>(p.a_dst);
+    const TC* __restrict__ s_src = static_cast<const TC*>(p.s_src);
+    TC* __restrict__ s_dst = static_cast<TC*>(p.s_dst);
+
+    const int gx = x0 - 2 + t;  // this thread's column (inside the body)
+    const bool colA = gx < x_end + 2;
+    const bool colB = t >= 1 && gx < x_end + 1;
+    const bool colC = t >= 2 && gx < x_end;
+    const int tm = t > 0 ? t - 1 : t, tp = t < NT - 1 ? t + 1 : t;
+    const int e_own = gx - seg0;
+    const int64_t col_off = int64_t(gx) + kPadCols;
+
+    const int a0 = y_begin - 2;
+    const int niter = (y_end - y_begin) + 4;
+    const TS* src_seg = fsrc + int64_t(kPadRows) * pitch + seg0 + kPadCols;  // row 0 of plane 0
+
+    // bulk copies of row a into ring slot s (thread 0); the 16-byte alignment
+    // of every address is checked before anything is issued
+    auto issue_row = [&](int a, int s) -> bool {
+        unsigned char* base = ring + size_t(s) * ROW_BYTES;
+        const uintptr_t acc = reinterpret_cast<uintptr_t>(base) | reinterpret_cast<uintptr_t>(src_seg) |
+                              uintptr_t(pitch * int64_t(sizeof(TS))) | uintptr_t(plane * int64_t(sizeof(TS)));
+        if (acc & 15) return false;
+        mbar_expect_tx(&bars[s], uint32_t(ROW_BYTES));
+        TS* dst = reinterpret_cast<TS*>(base);
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            bulk_load(dst + i * SEG, src_seg + i * plane + int64_t(a - ey(i)) * pitch, SEG * sizeof(TS), &bars[s]);
+        return true;
+    };
+
+    if (t == 0) {
+        s_abort = 0;
+        for (int s = 0; s < R; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int D = R - 3;
+    uint32_t phase = 0, issued = 0;
+    if (t == 0)
+        for (int j = 0; j < D && j < niter; ++j) {
+            if (issue_row(a0 + j, j)) issued |= 1u << j;
+            else s_abort = 2;
+        }
+
+    // carries prefetched one row ahead
+    UT an0, an1;
+    TC sn_old0 = TC(0), sn_old1 = TC(0);
+    int64_t off_a = int64_t(a0 + kPadRows) * pitch + col_off;  // row a of stage A, this column
+    if (colA) {
+        an0 = UT::ld_global(a_src, off_a, plane);
+        an1 = UT::ld_global(a_src + UP * plane, off_a, plane);
+    }
+
+    bool bad = false;
+    int sA = 0, ra = 0;
+    for (int q = 0; q < niter; ++q) {
+        const int sB = sA == 0 ? 2 : sA - 1;  // slot of row a - 1
+        const int sC = sA == 2 ? 0 : sA + 1;  // slot of row a - 2 (and Q of row a - 3 in sq[sA])
+        const int rc = ra >= 2 ? ra - 2 : ra - 2 + R;
+        const TC so0 = sn_old0, so1 = sn_old1;  // source carry of stage C's row
+
+        // ---------------- stage A: row a
+        if (!s_abort && !mbar_wait(&bars[ra], (phase >> ra) & 1u)) s_abort = 1;
+        phase ^= 1u << ra;
+        issued &= ~(1u << ra);
+        if (colA) {
+            const TS* pf = reinterpret_cast<const TS*>(ring + size_t(ra) * ROW_BYTES) + e_own;
+            TC g[9];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) g[i] = Codec<TS, TC>::ld(pf[i * SEG - ex(i)], i, p);
+            const TC m0 = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+            const TC m1 = (g[2] - g[4]) + (g[5] - g[8]) + (g[6] - g[7]);
+            su[(sA * 2) * NT + t] = an0.add(k.ku * m0);
+            su[(sA * 2 + 1) * NT + t] = an1.add(k.ku * m1);
+            if (q + 1 < niter) {
+                off_a += pitch;
+                an0 = UT::ld_global(a_src, off_a, plane);
+                an1 = UT::ld_global(a_src + UP * plane, off_a, plane);
+            }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        if (t == 0 && q + D < niter) {
+            const int rn = ra + D < R ? ra + D : ra + D - R;  // slot of row a - 3, done
+            fence_proxy_async();
+            if (issue_row(a0 + q + D, rn)) issued |= 1u << rn;
+            else s_abort = 2;
+        }
+        // source carry of the next iteration's stage C row (a - 1)
+        if (colC && q >= 3 && q + 1 < niter) {
+            const int64_t o = int64_t(a0 + q - 1 + kPadRows) * pitch + col_off;
+            sn_old0 = s_src[o];
+            sn_old1 = s_src[o + plane];
+        }
+
+        // ---------------- stage B: row a - 1
+        if (colB && q >= 2) {
+            const UT* r0 = su + (sB * 2) * NT;
+            const UT* rm = su + (sC * 2) * NT;
+            const UT* rp = su + (sA * 2) * NT;
+            const TC h11 = r0[tp].minus(r0[tm]) * k.inv_2dx;
+            const TC h21 = r0[NT + tp].minus(r0[NT + tm]) * k.inv_2dx;
+            const TC h12 = rp[t].minus(rm[t]) * k.inv_2dx;
+            const TC h22 = rp[NT + t].minus(rm[NT + t]) * k.inv_2dx;
+            TC q11, q12, q21, q22;
+            const TC J = stress_remainder<TC>(h11, h12, h21, h22, k.lam, k.mu, q11, q12, q21, q22);
+            bad |= !(J > TC(0));  // also catches a non-finite displacement gradient
+            TC* qr = sq + (sB * 4) * NT;
+            qr[t] = q11;
+            qr[NT + t] = q12;
+            qr[2 * NT + t] = q21;
+            qr[3 * NT + t] = q22;
+        }
+        __syncthreads();
+
+        // ---------------- stage C: row a - 2
+        if (colC && q >= 4) {
+            const int gy = a0 + q - 2;
+            const TC* qc = sq + (sC * 4) * NT;  // Q of row a - 2
+            const TC* qm = sq + (sA * 4) * NT;  // Q of row a - 3
+            const TC* qp = sq + (sB * 4) * NT;  // Q of row a - 1
+            // s = (dt / c) 1S, 1S = rho0 b + Div(P + Pbar)   (Eq. source1)
+            const TC sn0 = k.sb0 + k.sq_scale * ((qc[tp] - qc[tm]) + (qp[NT + t] - qm[NT + t]));
+            const TC sn1 = k.sb1 + k.sq_scale * ((qc[2 * NT + tp] - qc[2 * NT + tm]) + (qp[3 * NT + t] - qm[3 * NT + t]));
+
+            const TS* pf = reinterpret_cast<const TS*>(ring + size_t(rc) * ROW_BYTES) + e_own;
+            TC f[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = Codec<TS, TC>::ld(pf[i * SEG - ex(i)], i, p);
+            const TC r = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+            const TC m0 = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+            const TC m1 = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
+            const TC dg = (f[5] + f[6]) + (f[7] + f[8]);
+            const TC pxx = (f[1] + f[3]) + dg;
+            const TC pyy = (f[2] + f[4]) + dg;
+            const TC pxy = (f[5] - f[6]) + (f[7] - f[8]);
+            TC j0, j1, du0 = TC(0), du1 = TC(0);
+            if (p.scheme == 1) {
+                j0 = m0 + TC(0.5) * sn0;
+                j1 = m1 + TC(0.5) * sn1;
+                du0 = k.ku * (TC(0.5) * (sn0 - so0));
+                du1 = k.ku * (TC(0.5) * (sn1 - so1));
+            } else {
+                j0 = m0 + TC(0.5) * so0;
+                j1 = m1 + TC(0.5) * so1;
+            }
+
+            // equilibrium, He forcing and BGK collision by opposite pairs
+            const TC tr15 = TC(1.5) * (pxx + pyy);
+            const TC E0 = TC(2) * r - tr15;
+            const TC Ex = TC(0.5) * r + TC(4.5) * pxx - tr15;
+            const TC Ey = TC(0.5) * r + TC(4.5) * pyy - tr15;
+            const TC Ed = -r + TC(4.5) * (pxx + pyy) - tr15;
+            const TC Ep = Ed + TC(9) * pxy, Em = Ed - TC(9) * pxy;
+            const TC w0 = wgt<TC>(0), w1 = wgt<TC>(1), w5 = wgt<TC>(5);
+            const TC b0 = TC(3) * (k.omega * j0 + k.force_pref * sn0);
+            const TC b1 = TC(3) * (k.omega * j1 + k.force_pref * sn1);
+            const TC ax = w1 * (k.omega * Ex), ay = w1 * (k.omega * Ey);
+            const TC ap = w5 * (k.omega * Ep), am = w5 * (k.omega * Em);
+            const TC bx = w1 * b0, by = w1 * b1;
+            const TC bp = w5 * (b0 + b1), bm = w5 * (b1 - b0);
+            TC fc[9];
+            fc[0] = k.one_m_omega * f[0] + w0 * (k.omega * E0);
+            fc[1] = k.one_m_omega * f[1] + (ax + bx);
+            fc[3] = k.one_m_omega * f[3] + (ax - bx);
+            fc[2] = k.one_m_omega * f[2] + (ay + by);
+            fc[4] = k.one_m_omega * f[4] + (ay - by);
+            fc[5] = k.one_m_omega * f[5] + (ap + bp);
+            fc[7] = k.one_m_omega * f[7] + (ap - bp);
+            fc[6] = k.one_m_omega * f[6] + (am + bm);
+            fc[8] = k.one_m_omega * f[8] + (am - bm);
+            const int64_t o = int64_t(gy + kPadRows) * pitch + col_off;
+            TS* dst = fdst + o;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) dst[i * plane] = Codec<TS, TC>::st(fc[i], i, p);
+
+            // carries: A' = u + ku (jh + s/2), u = u* + du;  s' = s
+            const UT ux = su[(sC * 2) * NT + t], uy = su[(sC * 2 + 1) * NT + t];
+            const UT A0 = ux.add(du0 + k.ku * (j0 + TC(0.5) * sn0)).renorm();
+            const UT A1 = uy.add(du1 + k.ku * (j1 + TC(0.5) * sn1)).renorm();
+#pragma unroll
+            for (int c = 0; c < UP; ++c) {
+                a_dst[c * plane + o] = A0.part(c);
+                a_dst[(UP + c) * plane + o] = A1.part(c);
+            }
+            s_dst[o] = sn0;
+            s_dst[plane + o] = sn1;
+            if (p.fields != nullptr) {
+                const int64_t fo = int64_t(gy) * p.nx + gx;
+                const int64_t np = int64_t(p.nx) * p.ny;
+                p.fields[fo] = ux.add(du0).to_double();
+                p.fields[np + fo] = uy.add(du1).to_double();
+                p.fields[2 * np + fo] = double(j0 * k.c_over_rho0);
+                p.fields[3 * np + fo] = double(j1 * k.c_over_rho0);
+                p.fields[4 * np + fo] = double(r);
+                if (!(fabs(double(j0)) + fabs(double(j1)) < 1e300)) bad = true;
+            }
+        }
+        sA = sA == 2 ? 0 : sA + 1;
+        ra = ra + 1 == R ? 0 : ra + 1;
+    }
+    if (bad) atomicOr(p.flag, 1);
+    if (s_abort && t == 0) {
+        atomicOr(p.flag, s_abort == 2 ? 8 : 4);
+        for (int s = 0; s < R; ++s)
+            if (issued & (1u << s)) (void)mbar_wait(&bars[s], (phase >> s) & 1u);
+    }
+}
+
+template <class TS, class TC, class UT, int NT>
+size_t interior_smem_bytes(int ring_slots) {
+    return interior_smem_fixed<UT, TC, NT>() + interior_row_bytes<TS, NT>() * size_t(ring_slots);
+}
+
+template <class TS, class TC, class UT, int NT, int MINB>
+cudaError_t launch_interior_t(const StepParams& p, cudaStream_t s) {
+    auto kern = interior_step_kernel<TS, TC, UT, NT, MINB>;
+    const size_t sm = interior_smem_bytes<TS, TC, UT, NT>(p.ring_slots);
+    static size_t configured = 0;
+    if (sm > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        if (e != cudaSuccess) return e;
+        configured = sm;
+    }
+    dim3 grid(p.tiles_x, p.tiles_y, 1);
+    kern<<<grid, NT, sm, s>>>(p);
+    return cudaGetLastError();
+}
+
+size_t interior_smem(int fmt, int ring_slots) {
+    switch (fmt) {
+        case kFmtF64: return interior_smem_bytes<double, double, UPlain<double>, 128>(ring_slots);
+        case kFmtF32: return interior_smem_bytes<float, float, UPlain<float>, 128>(ring_slots);
+        case kFmtF32C: return interior_smem_bytes<float, float, UComp, 128>(ring_slots);
+        case kFmtF16: return interior_smem_bytes<__half, float, UComp, 128>(ring_slots);
+        default: return interior_smem_bytes<__nv_bfloat16, float, UComp, 128>(ring_slots);
+    }
+}
+
+cudaError_t launch_interior(int fmt, const StepParams& p0, cudaStream_t s, bool fields) {
+    StepParams p = p0;
+    if (!fields) p.fields = nullptr;
+    switch (fmt) {
+        case kFmtF64: return launch_interior_t<double, double, UPlain<double>, 128, 2>(p, s);
+        case kFmtF32: return launch_interior_t<float, float, UPlain<float>, 128, 4>(p, s);
+        case kFmtF32C: return launch_interior_t<float, float, UComp, 128, 4>(p, s);
+        case kFmtF16: return launch_interior_t<__half, float, UComp, 128, 4>(p, s);
+        case kFmtBF16: return launch_interior_t<__nv_bfloat16, float, UComp, 128, 4>(p, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lbm

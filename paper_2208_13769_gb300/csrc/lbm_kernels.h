@@ -19,6 +19,14 @@ enum Format : int {
 // Tile shape (nodes) the fused kernel uses for a format.
 void tile_shape(int fmt, int* tx, int* ty);
 
+// Dynamic shared memory of the fused step for a ring of `ring_slots` rows.
+size_t step_smem_bytes(int fmt, int ring_slots);
+
+// The interior kernel (lbm_interior.cu): nodes of p.rect[0] only, which must
+// lie at least 2 nodes from bounded edges and 3 from periodic seams.
+size_t interior_smem(int fmt, int ring_slots);
+cudaError_t launch_interior(int fmt, const StepParams& p, cudaStream_t s, bool fields);
+
 // One fused step (mode 0) or the initialisation (mode 1); fields: also write
 // u, v, r to p.fields.
 cudaError_t launch_fused_step(int fmt, const StepParams& p, cudaStream_t s, int mode, bool fields);

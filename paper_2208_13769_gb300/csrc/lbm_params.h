@@ -9,6 +9,17 @@ namespace lbm {
 
 enum EdgeKind : int32_t { kPeriodic = 0, kDirichlet = 1, kNeumann = 2 };
 
+// Layout of the state planes: node (x, y), x in [-3, nx + 3), y in [-3, ny + 3),
+// sits at (y + kPadRows) * pitch + x + kPadCols.  Along a periodic axis the 3
+// outer rows/columns hold images of the nodes across the seam; along a
+// bounded axis the first ghost row/column holds the populations the boundary
+// rules send back.  pitch is a multiple of 64 elements and kPadCols a
+// multiple of 8, so every row segment the step kernel copies in bulk starts on
+// a 16-byte boundary.
+constexpr int kPadRows = 3;
+constexpr int kPadCols = 8;
+constexpr int kSegExtra = 16;  // row segment = block size + 16 elements
+
 // One edge (0 = x-, 1 = x+, 2 = y-, 3 = y+) of Sec. 6's boundary value problem.
 struct EdgeBC {
     int32_t kind;
@@ -19,18 +30,18 @@ struct EdgeBC {
 };
 
 struct StepParams {
-    // geometry: populations and carries live in planes of (ny + 2) rows of
-    // `pitch` elements; node (x, y), x in [-1, nx], y in [-1, ny], sits at
-    // (y + 1) * pitch + x + xoff.  Row y = -1 / ny and column x = -1 / nx are
-    // the ghost layer that receives bounced and wrapped populations.
+    // geometry (see kPadRows / kPadCols)
     int32_t nx, ny;
-    int32_t xoff;
+    int32_t ring_slots;  // row-pair slots of the bulk-copy ring (lookahead + 3)
     int32_t periodic_x, periodic_y;
     int32_t scheme;  // 0 explicit (Algorithm 1), 1 predictor-corrector
     int64_t pitch;   // elements per row (storage or carry element type)
     int64_t plane;   // elements per plane
     int32_t tiles_x, tiles_y;  // grid: column strips x row chunks
     int32_t chunk_rows;        // rows per chunk (>= 3)
+    int32_t nrect;             // rectangles of output nodes (blockIdx.z picks one)
+    int32_t rect[4][4];        // x_lo, x_hi, y_lo, y_hi of each rectangle
+    int32_t write_counter;     // this launch advances the step counter
     int32_t pad0;
 
     const void* f_src;  // 9 planes of f^col(t_n), storage type

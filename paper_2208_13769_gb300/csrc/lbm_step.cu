@@ -5,17 +5,27 @@
 // One launch advances the whole body from t_n to t_n+1.  1S at a node needs
 // P + Pbar on its 4 neighbours, which need u on a 2-node halo, which needs the
 // streamed populations there.  Each CTA owns a strip of W = NT - 4 columns and
-// a chunk of rows, and walks the rows as a three-stage pipeline (one thread
-// per column):
+// a chunk of rows and walks the rows as a three-stage pipeline, one thread per
+// column:
 //   stage A, row a     : pull-stream, first moment, predicted u*   (W + 4 cols)
 //   stage B, row a - 2 : H = Grad u*, Q = P(F) + Pbar(H)           (W + 2 cols)
 //   stage C, row a - 4 : 1S = rho0 b + Div Q, corrected j and u, equilibrium,
 //                        BGK collision with He forcing, store       (W cols)
-// u* and Q live in 5-row rolling buffers in shared memory (a ghost rule at a
-// bounded edge reaches two rows inward, so each stage lags the previous one
-// by two rows).  Only 4 columns of stage A, 2 of stage B and a few warm-up
-// rows per chunk are recomputed; every state value crosses HBM once per step
-// in each direction (stage C re-reads its row's populations from L1).
+// (a ghost rule at a bounded edge reaches two rows inward, hence the lag of
+// two rows per stage).  The input rows -- 9 population segments (each from
+// the row its link comes from), the u-carry and the source carry -- are
+// brought into a ring of shared-memory row slots by bulk asynchronous copies
+// (cp.async.bulk, completion on an mbarrier per slot) issued D rows ahead of
+// stage A, so global-memory latency overlaps the compute of the rows in
+// between.  u* and Q live in 5-row rolling buffers.  Only 4 columns of stage
+// A, 2 of stage B and a few warm-up rows per chunk are recomputed; every
+// state value crosses HBM once per step in each direction.
+//
+// Periodic axes: the state arrays carry 3 image rows/columns beyond each
+// periodic edge (kept current by the writes of stage C), so every row segment
+// a strip needs is contiguous.  Bounded axes: the first ghost row/column
+// receives the populations the boundary rules of Sec. 6 send back, so the
+// pull never branches.
 //
 // Lattice units inside the kernel: m = sum_i e_i f_i, Pf = sum_i e_i e_i f_i,
 // s = (dt / c) 1S, jh = j / c, so that the equilibrium (Sec. 5) reads
@@ -23,276 +33,338 @@
 // and no rounded physical constant enters the lattice dynamics.
 //
 // State per node (two ping-pong copies):
-//   f^col_i (9 planes, storage type; a ghost row/column around the body
-//            receives the populations the boundary rules of Sec. 6 send back
-//            and the wrapped ones of periodic axes, so the pull never branches);
-//   A = u_n + dX/(2 rho0) (jh_n + s_n / 2)   (u-carry, 2 comps);
-//   s_n                                      (source carry, 2 comps);
+//   f^col_i                                    (9 planes, storage type)
+//   A = u_n + dX/(2 rho0) (jh_n + s_n / 2)     (u-carry, 2 comps)
+//   s_n                                        (source carry, 2 comps)
 // so that u*_n+1 = A + dX/(2 rho0) m  and  jh_n+1 = m + s_(n+1 or n) / 2.
 #include <cuda_runtime.h>
-
-#include <type_traits>
+#include <stdint.h>
 
 #include "lbm_device.cuh"
 #include "lbm_kernels.h"
+#include "lbm_pipeline.cuh"
 
 namespace lbm {
 
-namespace {
 
-constexpr int kDepth = 5;  // rows held by the rolling buffers
-
-// Strip / chunk origin, clamped so that every strip (chunk) is full when the
-// axis is at least one strip long; the last one then overlaps its neighbour
-// and the overlapping nodes are computed identically by both CTAs.
-__device__ __forceinline__ int clamped_origin(int b, int T, int n) {
-    const int o = b * T;
-    const int last = n - T;
-    return last <= 0 ? 0 : (o > last ? last : o);
-}
-
-__device__ __forceinline__ int wrap_coord(int g, int n) {
-    int w = g % n;
-    return w < 0 ? w + n : w;
-}
-
-// T*(t) of a Neumann edge: T0 outside [t_on, t_off), ramping to T1 over t_ramp.
-__device__ __forceinline__ void traction(const EdgeBC& e, double t, double& tx, double& ty) {
-    double s;
-    if (t < e.times[0] || t >= e.times[2])
-        s = 0.0;
-    else if (e.times[1] > 0.0)
-        s = fmin(1.0, (t - e.times[0]) / e.times[1]);
-    else
-        s = 1.0;
-    tx = e.value[0] + (e.rate[0] - e.value[0]) * s;
-    ty = e.value[1] + (e.rate[1] - e.value[1]) * s;
-}
-
-// u(+1) - u(-1) along one axis around u0 with the ghost rules of bounded
-// edges (Dirichlet: u_g = 2 u*(t) - u0; Neumann: quadratic extrapolation).
-// um, up: neighbours below/above; u1, u2: first and second inward neighbours
-// (used only when a ghost is needed).
-template <class TC, class UT>
-__device__ __forceinline__ TC du_axis(const UT& um, const UT& u0, const UT& up, const UT& u1, const UT& u2,
-                                      bool ghost_lo, bool ghost_hi, const EdgeBC& e, int comp, double t) {
-    if (!ghost_lo && !ghost_hi) return up.minus(um);
-    if (e.kind == kDirichlet) {
-        const double us = e.value[comp] + e.rate[comp] * t;
-        const TC v = u0.minus_d(us) + u1.minus_d(us);
-        return ghost_hi ? -v : v;
-    }
-    const TC v = TC(3) * u1.minus(u0) - u2.minus(u1);
-    return ghost_hi ? -v : v;
-}
-
-// Q(+1) - Q(-1) with the quadratic ghost of bounded edges.
-template <class TC>
-__device__ __forceinline__ TC dq_axis(TC qm, TC q0, TC qp, TC q1, TC q2, bool ghost_lo, bool ghost_hi) {
-    if (!ghost_lo && !ghost_hi) return qp - qm;
-    const TC v = TC(4) * q1 - TC(3) * q0 - q2;
-    return ghost_hi ? -v : v;
-}
-
-template <class TC>
-struct LatConsts {
-    TC omega, force_pref, ku, inv_2dx, sq_scale, sb0, sb1, lam, mu, inv_c2, c_over_rho0, rho0_over_c, rho0;
-    __device__ __forceinline__ void load(const StepParams& p) {
-        omega = TC(p.omega);
-        force_pref = TC(1.0 - 0.5 * p.omega);
-        ku = TC(p.dX / (2.0 * p.rho0));
-        inv_2dx = TC(1.0 / (2.0 * p.dX));
-        sq_scale = TC(p.dt * p.dt / (2.0 * p.dX * p.dX));
-        sb0 = TC(p.dt * p.dt / p.dX * p.rho0 * p.body[0]);
-        sb1 = TC(p.dt * p.dt / p.dX * p.rho0 * p.body[1]);
-        lam = TC(p.lambda);
-        mu = TC(p.mu);
-        inv_c2 = TC(1.0 / (p.c * p.c));
-        c_over_rho0 = TC(p.c / p.rho0);
-        rho0_over_c = TC(p.rho0 / p.c);
-        rho0 = TC(p.rho0);
-    }
-};
-
-// Lattice-unit equilibrium over w_i: even part (r, Pf) and odd part (jh).
-template <class T>
-__device__ __forceinline__ T eq_even(int i, T r, T pxx, T pxy, T pyy) {
-    const int e2 = ex(i) * ex(i) + ey(i) * ey(i);
-    const T epe = T(ex(i) * ex(i)) * pxx + T(ey(i) * ey(i)) * pyy + T(2 * ex(i) * ey(i)) * pxy;
-    const T rterm = (e2 == 0) ? T(2) * r : (e2 == 1 ? T(0.5) * r : -r);
-    return rterm + T(1.5) * (T(3) * epe - (pxx + pyy));
-}
-template <class T>
-__device__ __forceinline__ T eq_odd(int i, T a0, T a1) {
-    return T(3) * (T(ex(i)) * a0 + T(ey(i)) * a1);
-}
-
-template <int S>
-struct Slot {
-    static constexpr int v = ((S % kDepth) + kDepth) % kDepth;
-};
-
-}  // namespace
+// Shared-memory layout: [R pair slots] x [2 rows] x [9 population segments of
+// NT + kSegExtra elements] for the bulk-copy ring; u* and Q in 3 pair slots
+// (6 rows) each.
 
 template <class TS, class TC, class UT, int NT, int MODE>
 __global__ void __launch_bounds__(NT) strip_step_kernel(const __grid_constant__ StepParams p) {
-    constexpr int W = NT - 4;  // output columns per strip
-    __shared__ UT su[kDepth][2][NT];
-    __shared__ TC sq[kDepth][4][NT];
-    // initialisation only: r0 and Pbar(Grad u0) / c^2 from stage B to stage C
-    __shared__ TC sinit[MODE == 1 ? kDepth : 1][4][MODE == 1 ? NT : 1];
+    using CT = typename UT::Elem;        // carry element type
+    constexpr int W = NT - 4;            // output columns per strip
+    constexpr int SEG = NT + kSegExtra;  // elements per row segment
+    constexpr int UP = UT::planes;
+    constexpr int ROW_BYTES = 9 * SEG * int(sizeof(TS));
+    constexpr int PAIR_BYTES = 2 * ROW_BYTES;
+    static_assert(ROW_BYTES % 16 == 0, "row segment size");
+    constexpr int ALIGN_COLS = 16 / int(sizeof(TS));
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int R = p.ring_slots;  // pair slots: lookahead + 3
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);                                 // [R]
+    UT* su = reinterpret_cast<UT*>(smem + 256);                                          // [3][2 rows][2 comps][NT]
+    TC* sq = reinterpret_cast<TC*>(smem + 256 + sizeof(UT) * 12 * NT);                   // [3][2 rows][4][NT]
+    TC* sinit = sq + 24 * NT;                                                            // MODE 1: [3][2][4][NT]
+    unsigned char* ring = smem + step_smem_fixed<UT, TC, NT>(MODE);
+    __shared__ int s_abort;
+    __shared__ EdgeNow<TC, UT> s_edge[4];
 
     LatConsts<TC> k;
     k.load(p);
-    const int nx = p.nx, ny = p.ny;
+    Geo g;
+    g.nx = p.nx;
+    g.ny = p.ny;
+    g.pitch = p.pitch;
+    g.plane = p.plane;
+    g.perx = p.periodic_x != 0;
+    g.pery = p.periodic_y != 0;
+    const int nx = g.nx, ny = g.ny;
+    const int64_t pitch = g.pitch, plane = g.plane;
     const int t = threadIdx.x;
-    const int x0 = clamped_origin(blockIdx.x, W, nx);
-    const int y_begin = clamped_origin(blockIdx.y, p.chunk_rows, ny);
-    const int y_end = min(ny, y_begin + p.chunk_rows);
-    const int64_t pitch = p.pitch, plane = p.plane;
-    const bool perx = p.periodic_x != 0, pery = p.periodic_y != 0;
+    // output rectangle of this CTA's launch slice, strip and chunk inside it
+    // (origins clamped so the last strip / chunk is full when it fits)
+    const int rx0 = p.rect[blockIdx.z][0], rx1 = p.rect[blockIdx.z][1];
+    const int ry0 = p.rect[blockIdx.z][2], ry1 = p.rect[blockIdx.z][3];
+    if (int(blockIdx.x) * W >= rx1 - rx0 || int(blockIdx.y) * p.chunk_rows >= ry1 - ry0) return;
+    int x0 = rx0 + int(blockIdx.x) * W;
+    if (x0 > rx1 - W) x0 = rx1 - W > rx0 ? rx1 - W : rx0;
+    int y_begin = ry0 + int(blockIdx.y) * p.chunk_rows;
+    if (y_begin > ry1 - p.chunk_rows) y_begin = ry1 - p.chunk_rows > ry0 ? ry1 - p.chunk_rows : ry0;
+    const int y_end = min(ry1, y_begin + p.chunk_rows);
+    int seg0 = x0 - 8;  // first column of the row segments: 16-byte aligned
+    seg0 = (seg0 >= 0 ? seg0 : seg0 - (ALIGN_COLS - 1)) / ALIGN_COLS * ALIGN_COLS;
     const TS* __restrict__ fsrc = static_cast<const TS*>(p.f_src);
     TS* __restrict__ fdst = static_cast<TS*>(p.f_dst);
+    const CT* __restrict__ a_src = static_cast<const CT*>(p.a_src);
+    CT* __restrict__ a_dst = static_cast<CT*>(p.a_dst);
     const TC* __restrict__ s_src = static_cast<const TC*>(p.s_src);
     TC* __restrict__ s_dst = static_cast<TC*>(p.s_dst);
 
-    // time of the collision this launch performs
-    int64_t n_now = 0;
+    int64_t n_now = 0;  // the collision of this launch is at t_now = n_now dt
     if (MODE == 0) n_now = p.counter[p.parity] + 1;
-    if (blockIdx.x == 0 && blockIdx.y == 0 && t == 0) p.counter[p.parity ^ 1] = n_now;
+    if (p.write_counter && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t == 0)
+        p.counter[p.parity ^ 1] = n_now;
     const double t_now = double(n_now) * p.dt;
 
-    // this thread's column (stage A at every t, stage B at t in [1, NT-2],
-    // stage C at t in [2, NT-3])
-    const int gx_raw = x0 - 2 + t;
-    int gx = gx_raw;
-    bool col_ok = true;
-    if (gx < 0 || gx >= nx) {
-        if (perx) gx = wrap_coord(gx, nx);
-        else col_ok = false;
-    }
-    const bool colB = col_ok && t >= 1 && t <= NT - 2;
-    const bool colC = t >= 2 && t <= NT - 3 && gx_raw < nx;
-    const bool gxl = !perx && gx == 0, gxh = !perx && gx == nx - 1;
-    // inward neighbours in the strip for the x ghost rules
+    // ---- this thread's column
+    const int gxr = x0 - 2 + t;  // raw column (an image beyond a periodic edge)
+    const bool colA = g.perx ? (gxr >= -2 && gxr < nx + 2) : (gxr >= 0 && gxr < nx);
+    const int gx = g.perx ? wrap_coord(gxr, nx) : gxr;
+    const bool colB = colA && t >= 1 && t <= NT - 2;
+    const bool colC = t >= 2 && t <= NT - 3 && gxr >= rx0 && gxr < rx1;
+    const bool gxl = !g.perx && gx == 0, gxh = !g.perx && gx == nx - 1;
+    const bool edge_x = gxl || gxh;
     const int tin1 = gxl ? min(t + 1, NT - 1) : max(t - 1, 0);
     const int tin2 = gxl ? min(t + 2, NT - 1) : max(t - 2, 0);
     const int tm = t > 0 ? t - 1 : t, tp = t < NT - 1 ? t + 1 : t;
-    const EdgeBC& ebx = gxl ? p.bc[0] : p.bc[1];
-    const int64_t xo = int64_t(gx) + p.xoff;
+    const int e_own = gxr - seg0;              // element of this column in a segment
+    const int64_t col_off = int64_t(gxr) + kPadCols;  // raw column in the planes
+    // periodic image of an output column (one at most for axes of >= 6 nodes)
+    const bool short_x = g.perx && nx < 6, short_y = g.pery && ny < 6;
+    const int img_x = (!g.perx || short_x) ? 0 : (gx < 3 ? nx : (gx >= nx - 3 ? -nx : 0));
+
+    const int a0 = y_begin - 2;            // first row of stage A
+    const int a_last = y_end + 1;          // last row of stage A
+    const int npairs = (a_last - a0 + 2) / 2;
+    auto row_loaded = [&](int a) { return a >= a0 && a <= a_last && (g.pery || (a >= 0 && a < ny)); };
+    auto row_bytes = [&](int pair) {
+        return uint32_t(ROW_BYTES) * (uint32_t(row_loaded(a0 + 2 * pair)) + uint32_t(row_loaded(a0 + 2 * pair + 1)));
+    };
+    // issue the bulk copies of a row pair into ring slot s (thread 0 only);
+    // every address is checked for 16-byte alignment before anything is issued
+    auto issue_pair = [&](int pair, int s) -> bool {
+        unsigned char* base = ring + size_t(s) * PAIR_BYTES;
+        const uint32_t bytes = row_bytes(pair);
+        if (bytes == 0) return true;
+        uintptr_t acc = reinterpret_cast<uintptr_t>(base);
+        const TS* src0 = fsrc + g.at(seg0, 0);
+        acc |= reinterpret_cast<uintptr_t>(src0) | uintptr_t(pitch * int64_t(sizeof(TS))) |
+               uintptr_t(plane * int64_t(sizeof(TS)));
+        if (acc & 15) return false;
+        mbar_expect_tx(&bars[s], bytes);
+        for (int h = 0; h < 2; ++h) {
+            const int a = a0 + 2 * pair + h;
+            if (!row_loaded(a)) continue;
+            TS* dst = reinterpret_cast<TS*>(base + h * ROW_BYTES);
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                bulk_load(dst + i * SEG, src0 + i * plane + int64_t(a - ey(i)) * pitch, SEG * sizeof(TS), &bars[s]);
+        }
+        return true;
+    };
+
+    if (t == 0) {
+        s_abort = 0;
+        if (MODE == 0) {
+            for (int s = 0; s < R; ++s) mbar_init(&bars[s], 1);
+            fence_mbar_init();
+        }
+    }
+    if (t < 4) edge_now<TC, UT>(s_edge[t], p.bc[t], t_now, p.rho0 / p.c);
+    __syncthreads();
+    const EdgeNow<TC, UT>& ebx = s_edge[gxl ? 0 : 1];
+    const int D = R - 3;  // pairs of lookahead
+    uint32_t phase = 0, issued = 0;
+    if (MODE == 0 && t == 0) {
+        for (int pr = 0; pr < D && pr < npairs && !s_abort; ++pr) {
+            if (issue_pair(pr, pr)) issued |= (row_bytes(pr) ? 1u : 0u) << pr;
+            else s_abort = 2;
+        }
+    }
+    // carries of the first pair of stage A, prefetched into registers
+    UT anext[2][2];
+    TC snext[2][2] = {{TC(0), TC(0)}, {TC(0), TC(0)}};
+    auto load_a = [&](int pair) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int a = a0 + 2 * pair + h;
+            if (MODE == 0 && colA && row_loaded(a)) {
+                const int64_t o = int64_t(a + kPadRows) * pitch + col_off;
+                anext[h][0] = UT::ld_global(a_src, o, plane);
+                anext[h][1] = UT::ld_global(a_src + UP * plane, o, plane);
+            }
+        }
+    };
+    auto load_s = [&](int pair) {  // source carry of stage C's rows of `pair`
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int kr = a0 + 2 * pair + h;
+            if (MODE == 0 && colC && kr >= y_begin && kr < y_end) {
+                const int64_t o = int64_t(kr + kPadRows) * pitch + col_off;
+                snext[h][0] = s_src[o];
+                snext[h][1] = s_src[o + plane];
+            }
+        }
+    };
+    load_a(0);
 
     bool bad = false;
-    const int niter = (y_end - y_begin) + 6;
-
-    auto body = [&](int q, auto slot_tag) {
-        constexpr int S = decltype(slot_tag)::value;
-        const int a = y_begin - 2 + q;
-
-        // ---------------- stage A: row a in [y_begin - 2, y_end + 1]
-        if (a <= y_end + 1) {
-            constexpr int sa = Slot<S>::v;
-            int gy = a;
-            bool ok = col_ok;
-            if (gy < 0 || gy >= ny) {
-                if (pery) gy = wrap_coord(gy, ny);
-                else ok = false;
-            }
-            if (ok) {
-                if (MODE == 0) {
-                    const int64_t id = int64_t(gy + 1) * pitch + xo;
-                    TC g[9];
+    int sa = 0;  // su / sq pair slot of stage A's rows
+    int ra = 0;  // ring pair slot of stage A's rows
+    const int niter = npairs + 2;
+    for (int q = 0; q < niter; ++q) {
+        const int sb = sa == 0 ? 2 : sa - 1;  // pair slot of stage B's rows (a-2, a-1)
+        const int sc = sa == 2 ? 0 : sa + 1;  // pair slot of stage C's rows (a-4, a-3)
+        const int rc = ra >= 2 ? ra - 2 : ra - 2 + R;  // ring slot of stage C's rows
+        const int a = a0 + 2 * q;
+        // stage C's source carries (rows of pair q - 2, prefetched last iteration)
+        TC scur[2][2];
 #pragma unroll
-                    for (int i = 1; i < 9; ++i)
-                        g[i] = Codec<TS, TC>::ld(fsrc[i * plane + id - int64_t(ey(i)) * pitch - ex(i)], i, p);
-                    const TC m0 = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
-                    const TC m1 = (g[2] - g[4]) + (g[5] - g[8]) + (g[6] - g[7]);
-                    const UT a0 = UT::load(p.a_src, id, plane);
-                    const UT a1 = UT::load(p.a_src, id + UT::planes * plane, plane);
-                    su[sa][0][t] = a0.add(k.ku * m0);
-                    su[sa][1][t] = a1.add(k.ku * m1);
-                } else {
-                    const int64_t h = (int64_t(gy) * nx + gx) * 2;
-                    su[sa][0][t] = UT::from_double(p.u0 ? p.u0[h] : 0.0);
-                    su[sa][1][t] = UT::from_double(p.u0 ? p.u0[h + 1] : 0.0);
+        for (int h = 0; h < 2; ++h) {
+            scur[h][0] = snext[h][0];
+            scur[h][1] = snext[h][1];
+        }
+
+        // ---------------- stage A: rows a, a+1
+        if (q < npairs) {
+            if (MODE == 0 && row_bytes(q)) {
+                if (!s_abort && !mbar_wait(&bars[ra], (phase >> ra) & 1u)) s_abort = 1;
+                phase ^= 1u << ra;
+                issued &= ~(1u << ra);
+            }
+            UT acur[2][2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                acur[h][0] = anext[h][0];
+                acur[h][1] = anext[h][1];
+            }
+            if (q + 1 < npairs) load_a(q + 1);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int ar = a + h;
+                UT* urow = su + ((sa * 2 + h) * 2) * NT;
+                if (MODE == 0) {
+                    if (colA && row_loaded(ar)) {
+                        const TS* pf = reinterpret_cast<const TS*>(ring + size_t(ra) * PAIR_BYTES + h * ROW_BYTES) + e_own;
+                        TC fA[9];
+#pragma unroll
+                        for (int i = 1; i < 9; ++i) fA[i] = Codec<TS, TC>::ld(pf[i * SEG - ex(i)], i, p);
+                        const TC m0 = (fA[1] - fA[3]) + (fA[5] - fA[6]) + (fA[8] - fA[7]);
+                        const TC m1 = (fA[2] - fA[4]) + (fA[5] - fA[8]) + (fA[6] - fA[7]);
+                        urow[t] = acur[h][0].add(k.ku * m0);
+                        urow[NT + t] = acur[h][1].add(k.ku * m1);
+                    }
+                } else if (colA && ar <= a_last) {
+                    int gy = ar;
+                    bool ok = true;
+                    if (gy < 0 || gy >= ny) {
+                        if (g.pery) gy = wrap_coord(gy, ny);
+                        else ok = false;
+                    }
+                    if (ok) {
+                        const int64_t hh = (int64_t(gy) * nx + gx) * 2;
+                        urow[t] = UT::from_double(p.u0 ? p.u0[hh] : 0.0);
+                        urow[NT + t] = UT::from_double(p.u0 ? p.u0[hh + 1] : 0.0);
+                    }
                 }
             }
         }
         __syncthreads();
+        if (s_abort) break;  // uniform: written before the barrier
+        // refill: the ring slot of pair q + D last served stage C of pair q - 3
+        if (MODE == 0 && t == 0 && q + D < npairs) {
+            const int rn = ra + D < R ? ra + D : ra + D - R;
+            fence_proxy_async();
+            if (issue_pair(q + D, rn)) issued |= (row_bytes(q + D) ? 1u : 0u) << rn;
+            else s_abort = 2;
+        }
+        load_s(q - 1);  // stage C's rows of the next iteration (pair q - 1)
 
-        // ---------------- stage B: row m = a - 2 in [y_begin - 1, y_end]
-        {
-            constexpr int s0 = Slot<S - 2>::v, sp = Slot<S - 1>::v, sp2 = Slot<S>::v;
-            constexpr int sm = Slot<S - 3>::v, sm2 = Slot<S - 4>::v;
-            const int m = a - 2;
-            int gy = m;
-            bool ok = colB && m >= y_begin - 1 && m <= y_end;
-            if (gy < 0 || gy >= ny) {
-                if (pery) gy = wrap_coord(gy, ny);
-                else ok = false;
-            }
-            if (ok) {
-                const bool gyl = !pery && gy == 0, gyh = !pery && gy == ny - 1;
-                const EdgeBC& eby = gyl ? p.bc[2] : p.bc[3];
-                const int r1 = gyl ? sp : sm, r2 = gyl ? sp2 : sm2;
-                TC h[2][2];
+        // ---------------- stage B: rows a-2, a-1 (window rows w0..w5 = a-4..a+1)
+        if (colB) {
+            const UT* wrow[6] = {su + ((sc * 2 + 0) * 2) * NT, su + ((sc * 2 + 1) * 2) * NT,
+                                 su + ((sb * 2 + 0) * 2) * NT, su + ((sb * 2 + 1) * 2) * NT,
+                                 su + ((sa * 2 + 0) * 2) * NT, su + ((sa * 2 + 1) * 2) * NT};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = a - 2 + h;
+                int gy = m;
+                bool ok = m >= y_begin - 1 && m <= y_end;
+                if (gy < 0 || gy >= ny) {
+                    if (g.pery) gy = wrap_coord(gy, ny);
+                    else ok = false;
+                }
+                if (!ok) continue;
+                const bool gyl = !g.pery && gy == 0, gyh = !g.pery && gy == ny - 1;
+                const EdgeNow<TC, UT>& eby = s_edge[gyl ? 2 : 3];
+                const int w = 2 + h;  // window index of row m
+                TC hh[2][2];
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    const UT u0 = su[s0][c][t];
-                    h[c][0] = du_axis<TC, UT>(su[s0][c][tm], u0, su[s0][c][tp], su[s0][c][tin1], su[s0][c][tin2],
-                                              gxl, gxh, ebx, c, t_now) * k.inv_2dx;
-                    h[c][1] = du_axis<TC, UT>(su[sm][c][t], u0, su[sp][c][t], su[r1][c][t], su[r2][c][t], gyl, gyh,
-                                              eby, c, t_now) * k.inv_2dx;
+                    const UT* r0 = wrow[w] + c * NT;
+                    const UT u0 = r0[t];
+                    hh[c][0] = du_axis<TC, UT>(r0[tm], u0, r0[tp], r0[tin1], r0[tin2], gxl, gxh, ebx, c) *
+                               k.inv_2dx;
+                    const UT* rm = wrow[w - 1] + c * NT;
+                    const UT* rp = wrow[w + 1] + c * NT;
+                    const UT* r1 = (gyl ? wrow[w + 1] : wrow[w - 1]) + c * NT;
+                    const UT* r2 = (gyl ? wrow[w + 2] : wrow[w - 2]) + c * NT;
+                    hh[c][1] = du_axis<TC, UT>(rm[t], u0, rp[t], r1[t], r2[t], gyl, gyh, eby, c) * k.inv_2dx;
                 }
                 TC q11, q12, q21, q22;
-                const TC J = stress_remainder<TC>(h[0][0], h[0][1], h[1][0], h[1][1], k.lam, k.mu, q11, q12, q21, q22);
+                const TC J = stress_remainder<TC>(hh[0][0], hh[0][1], hh[1][0], hh[1][1], k.lam, k.mu, q11, q12,
+                                                  q21, q22);
                 bad |= !(J > TC(0)) || !(fabs(q11) + fabs(q12) + fabs(q21) + fabs(q22) < TC(1e30));
-                sq[s0][0][t] = q11;
-                sq[s0][1][t] = q12;
-                sq[s0][2][t] = q21;
-                sq[s0][3][t] = q22;
+                TC* qrow = sq + ((sb * 2 + h) * 4) * NT;
+                qrow[t] = q11;
+                qrow[NT + t] = q12;
+                qrow[2 * NT + t] = q21;
+                qrow[3 * NT + t] = q22;
                 if (MODE == 1) {
-                    const TC tr = h[0][0] + h[1][1];
-                    sinit[s0 * (MODE == 1)][0][t * (MODE == 1)] = -k.rho0 * tr;
-                    sinit[s0 * (MODE == 1)][1][t * (MODE == 1)] = -k.mu * (TC(2) * h[0][0] + tr) * k.inv_c2;
-                    sinit[s0 * (MODE == 1)][2][t * (MODE == 1)] = -k.mu * (h[0][1] + h[1][0]) * k.inv_c2;
-                    sinit[s0 * (MODE == 1)][3][t * (MODE == 1)] = -k.mu * (TC(2) * h[1][1] + tr) * k.inv_c2;
+                    const TC tr = hh[0][0] + hh[1][1];
+                    TC* irow = sinit + ((sb * 2 + h) * 4) * NT;
+                    irow[t] = -k.rho0 * tr;
+                    irow[NT + t] = -k.mu * (TC(2) * hh[0][0] + tr) * k.inv_c2;
+                    irow[2 * NT + t] = -k.mu * (hh[0][1] + hh[1][0]) * k.inv_c2;
+                    irow[3 * NT + t] = -k.mu * (TC(2) * hh[1][1] + tr) * k.inv_c2;
                 }
             }
         }
         __syncthreads();
 
-        // ---------------- stage C: row kr = a - 4 in [y_begin, y_end)
-        {
-            constexpr int qs0 = Slot<S - 4>::v, qsp = Slot<S - 3>::v, qsp2 = Slot<S - 2>::v;
-            constexpr int qsm = Slot<S - 5>::v, qsm2 = Slot<S - 6>::v;
-            const int kr = a - 4;
-            if (colC && kr >= y_begin && kr < y_end) {
-                const int gy = kr;
-                const bool gyl = !pery && gy == 0, gyh = !pery && gy == ny - 1;
-                const int64_t id = int64_t(gy + 1) * pitch + xo;
-                TC f[9];
+        // ---------------- stage C: rows a-4, a-3 (Q window rows a-6..a-1)
+        if (colC) {
+            const TC* qw[6] = {sq + ((sa * 2 + 0) * 4) * NT, sq + ((sa * 2 + 1) * 4) * NT,
+                               sq + ((sc * 2 + 0) * 4) * NT, sq + ((sc * 2 + 1) * 4) * NT,
+                               sq + ((sb * 2 + 0) * 4) * NT, sq + ((sb * 2 + 1) * 4) * NT};
 #pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    f[i] = Codec<TS, TC>::ld(fsrc[i * plane + id - int64_t(ey(i)) * pitch - ex(i)], i, p);
+            for (int h = 0; h < 2; ++h) {
+                const int kr = a - 4 + h;
+                if (kr < y_begin || kr >= y_end) continue;
+                const int gy = kr;
+                const bool gyl = !g.pery && gy == 0, gyh = !g.pery && gy == ny - 1;
+                const int w = 2 + h;  // window index of row kr
 
                 // s = (dt / c) 1S, 1S = rho0 b + Div(P + Pbar)   (Eq. source1)
-                const int r1 = gyl ? qsp : qsm, r2 = gyl ? qsp2 : qsm2;
                 TC dQ[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
+                    const TC* r0 = qw[w] + c * NT;
                     if ((c & 1) == 0)  // Q_a1: derivative along x
-                        dQ[c] = dq_axis<TC>(sq[qs0][c][tm], sq[qs0][c][t], sq[qs0][c][tp], sq[qs0][c][tin1],
-                                            sq[qs0][c][tin2], gxl, gxh);
-                    else  // Q_a2: derivative along y
-                        dQ[c] = dq_axis<TC>(sq[qsm][c][t], sq[qs0][c][t], sq[qsp][c][t], sq[r1][c][t],
-                                            sq[r2][c][t], gyl, gyh);
+                        dQ[c] = dq_axis<TC>(r0[tm], r0[t], r0[tp], r0[tin1], r0[tin2], gxl, gxh);
+                    else {  // Q_a2: derivative along y
+                        const TC* r1 = (gyl ? qw[w + 1] : qw[w - 1]) + c * NT;
+                        const TC* r2 = (gyl ? qw[w + 2] : qw[w - 2]) + c * NT;
+                        dQ[c] = dq_axis<TC>(qw[w - 1][c * NT + t], r0[t], qw[w + 1][c * NT + t], r1[t], r2[t], gyl,
+                                            gyh);
+                    }
                 }
                 const TC sn0 = k.sb0 + k.sq_scale * (dQ[0] + dQ[1]);
                 const TC sn1 = k.sb1 + k.sq_scale * (dQ[2] + dQ[3]);
 
+                const UT* urow = su + ((sc * 2 + h) * 2) * NT;
+                UT ux = urow[t], uy = urow[NT + t];
                 TC r, j0, j1, pxx, pxy, pyy;
-                UT ux = su[Slot<S - 4>::v][0][t], uy = su[Slot<S - 4>::v][1][t];
+                TC du0 = TC(0), du1 = TC(0);  // predictor correction of u*
+                TC f[9];
                 if (MODE == 0) {
+                    const TS* pf =
+                        reinterpret_cast<const TS*>(ring + size_t(rc) * PAIR_BYTES + h * ROW_BYTES) + e_own;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) f[i] = Codec<TS, TC>::ld(pf[i * SEG - ex(i)], i, p);
                     r = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
                     const TC m0 = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
                     const TC m1 = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
@@ -300,99 +372,134 @@ __global__ void __launch_bounds__(NT) strip_step_kernel(const __grid_constant__ 
                     pxx = (f[1] + f[3]) + dg;
                     pyy = (f[2] + f[4]) + dg;
                     pxy = (f[5] - f[6]) + (f[7] - f[8]);
-                    const TC so0 = s_src[id], so1 = s_src[id + plane];
+                    const TC so0 = scur[h][0], so1 = scur[h][1];
                     if (p.scheme == 1) {
                         j0 = m0 + TC(0.5) * sn0;
                         j1 = m1 + TC(0.5) * sn1;
-                        ux = ux.add(k.ku * (TC(0.5) * (sn0 - so0)));
-                        uy = uy.add(k.ku * (TC(0.5) * (sn1 - so1)));
+                        du0 = k.ku * (TC(0.5) * (sn0 - so0));
+                        du1 = k.ku * (TC(0.5) * (sn1 - so1));
                     } else {
                         j0 = m0 + TC(0.5) * so0;
                         j1 = m1 + TC(0.5) * so1;
                     }
                 } else {
                     // initialisation of Algorithm 1: r = -rho0 Div u0,
-                    // j = rho0 v0, Pbar = Pbar(Grad u0) (from stage B)
-                    constexpr int si = Slot<S - 4>::v;
-                    r = sinit[si * (MODE == 1)][0][t * (MODE == 1)];
-                    pxx = sinit[si * (MODE == 1)][1][t * (MODE == 1)];
-                    pxy = sinit[si * (MODE == 1)][2][t * (MODE == 1)];
-                    pyy = sinit[si * (MODE == 1)][3][t * (MODE == 1)];
+                    // j = rho0 v0, Pbar = Pbar(Grad u0) (from stage B), f = f^eq
+                    const TC* irow = sinit + ((sc * 2 + h) * 4) * NT;
+                    r = irow[t];
+                    pxx = irow[NT + t];
+                    pxy = irow[2 * NT + t];
+                    pyy = irow[3 * NT + t];
                     const int64_t hh = (int64_t(gy) * nx + gx) * 2;
                     j0 = k.rho0_over_c * TC(p.v0 ? p.v0[hh] : 0.0);
                     j1 = k.rho0_over_c * TC(p.v0 ? p.v0[hh + 1] : 0.0);
                 }
 
-                // equilibrium (Sec. 5), source populations (Eq. source), BGK
-                // collision with He forcing (Eq. col)
-                TC fc[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const TC w = wgt<TC>(i);
-                    const TC feq = w * (eq_even<TC>(i, r, pxx, pxy, pyy) + eq_odd<TC>(i, j0, j1));
-                    const TC fi = (MODE == 0) ? f[i] : feq;
-                    fc[i] = fi - k.omega * (fi - feq) + k.force_pref * w * eq_odd<TC>(i, sn0, sn1);
-                    fdst[i * plane + id] = Codec<TS, TC>::st(fc[i], i, p);
+                // equilibrium (Sec. 5), He forcing (Eq. source), BGK collision
+                // (Eq. col), by opposite pairs: f^col_i = (1 - omega) f_i
+                //   + w_i (omega E_i + 3 e_i.(omega jh + (1 - omega/2) s)),
+                // E_i the even part of f^eq_i / w_i (equal for i and opposite)
+                const TC tr15 = TC(1.5) * (pxx + pyy);
+                const TC E0 = TC(2) * r - tr15;
+                const TC Ex = TC(0.5) * r + TC(4.5) * pxx - tr15;
+                const TC Ey = TC(0.5) * r + TC(4.5) * pyy - tr15;
+                const TC Ed = -r + TC(4.5) * (pxx + pyy) - tr15;
+                const TC Ep = Ed + TC(9) * pxy, Em = Ed - TC(9) * pxy;
+                const TC w0 = wgt<TC>(0), w1 = wgt<TC>(1), w5 = wgt<TC>(5);
+                if (MODE == 1) {
+                    const TC o0 = TC(3) * j0, o1 = TC(3) * j1;
+                    f[0] = w0 * E0;
+                    f[1] = w1 * (Ex + o0);
+                    f[3] = w1 * (Ex - o0);
+                    f[2] = w1 * (Ey + o1);
+                    f[4] = w1 * (Ey - o1);
+                    f[5] = w5 * (Ep + o0 + o1);
+                    f[7] = w5 * (Ep - o0 - o1);
+                    f[6] = w5 * (Em - o0 + o1);
+                    f[8] = w5 * (Em + o0 - o1);
                 }
+                const TC b0 = TC(3) * (k.omega * j0 + k.force_pref * sn0);
+                const TC b1 = TC(3) * (k.omega * j1 + k.force_pref * sn1);
+                const TC ax = w1 * (k.omega * Ex), ay = w1 * (k.omega * Ey);
+                const TC ap = w5 * (k.omega * Ep), am = w5 * (k.omega * Em);
+                const TC bx = w1 * b0, by = w1 * b1;
+                const TC bp = w5 * (b0 + b1), bm = w5 * (b1 - b0);
+                TC fc[9];
+                fc[0] = k.one_m_omega * f[0] + w0 * (k.omega * E0);
+                fc[1] = k.one_m_omega * f[1] + (ax + bx);
+                fc[3] = k.one_m_omega * f[3] + (ax - bx);
+                fc[2] = k.one_m_omega * f[2] + (ay + by);
+                fc[4] = k.one_m_omega * f[4] + (ay - by);
+                fc[5] = k.one_m_omega * f[5] + (ap + bp);
+                fc[7] = k.one_m_omega * f[7] + (ap - bp);
+                fc[6] = k.one_m_omega * f[6] + (am + bm);
+                fc[8] = k.one_m_omega * f[8] + (am - bm);
 
-                // links that leave the body: boundary rules of Sec. 6, or the
-                // periodic wrap, into the ghost layer of the destination
-                if (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1) {
-                    const TC q11 = sq[qs0][0][t], q12 = sq[qs0][1][t], q21 = sq[qs0][2][t], q22 = sq[qs0][3][t];
+                // stores with the periodic images of seam nodes
+                const int64_t o = int64_t(gy + kPadRows) * pitch + col_off;
+                const int64_t img_y =
+                    (!g.pery || short_y) ? 0 : (gy < 3 ? int64_t(ny) * pitch : (gy >= ny - 3 ? -int64_t(ny) * pitch : 0));
+                const bool slow = short_x || short_y;
+                auto put = [&](auto* base, auto v) {
+                    if (slow) {
+                        store_img(base, g, gx, gy, v);
+                        return;
+                    }
+                    base[o] = v;
+                    if (img_x) base[o + img_x] = v;
+                    if (img_y) base[o + img_y] = v;
+                    if (img_x && img_y) base[o + img_y + img_x] = v;
+                };
+#pragma unroll
+                for (int i = 0; i < 9; ++i) put(fdst + i * plane, Codec<TS, TC>::st(fc[i], i, p));
+
+                // links that leave the body through a bounded edge: boundary
+                // rules of Sec. 6 into the first ghost row/column
+                if (edge_x || gyl || gyh) {
+                    const TC* qrow = qw[w];
+                    const TC q11 = qrow[t], q12 = qrow[NT + t], q21 = qrow[2 * NT + t], q22 = qrow[3 * NT + t];
 #pragma unroll
                     for (int i = 1; i < 9; ++i) {
                         const int dx = gx + ex(i), dy = gy + ey(i);
-                        const bool cx = dx < 0 || dx >= nx, cy = dy < 0 || dy >= ny;
-                        if (!cx && !cy) continue;
-                        const bool bx = cx && !perx, by = cy && !pery;
-                        if (!bx && !by) {
-                            // periodic: the puller at wrap(D) reads wrap(D) - e_i
-                            const int wx = cx ? wrap_coord(dx, nx) : dx;
-                            const int wy = cy ? wrap_coord(dy, ny) : dy;
-                            fdst[i * plane + int64_t(wy - ey(i) + 1) * pitch + (wx - ex(i)) + p.xoff] =
-                                Codec<TS, TC>::st(fc[i], i, p);
-                            continue;
-                        }
+                        const bool bx2 = !g.perx && (dx < 0 || dx >= nx);
+                        const bool by2 = !g.pery && (dy < 0 || dy >= ny);
+                        if (!bx2 && !by2) continue;
                         const int oi = opp(i);
-                        const EdgeBC* ea = bx ? &p.bc[dx < 0 ? 0 : 1] : nullptr;
-                        const EdgeBC* eb = by ? &p.bc[dy < 0 ? 2 : 3] : nullptr;
-                        int nd = 0;
-                        double js0 = 0.0, js1 = 0.0;
-                        if (ea && ea->kind == kDirichlet) {
-                            js0 += ea->rate[0];
-                            js1 += ea->rate[1];
-                            ++nd;
-                        }
-                        if (eb && eb->kind == kDirichlet) {
-                            js0 += eb->rate[0];
-                            js1 += eb->rate[1];
-                            ++nd;
-                        }
+                        const EdgeNow<TC, UT>* ea = bx2 ? &s_edge[dx < 0 ? 0 : 1] : nullptr;
+                        const EdgeNow<TC, UT>* eb = by2 ? &s_edge[dy < 0 ? 2 : 3] : nullptr;
+                        const bool da = ea && ea->kind == kDirichlet, db = eb && eb->kind == kDirichlet;
                         TC val;
-                        if (nd > 0) {
-                            // Eq. (bbcon): jh* = rho0 v* / c
-                            const TC a0 = TC(js0 / nd) * k.rho0_over_c, a1 = TC(js1 / nd) * k.rho0_over_c;
-                            val = fc[i] - TC(2) * wgt<TC>(i) * eq_odd<TC>(i, a0, a1);
+                        if (da || db) {
+                            // Eq. (bbcon) with jh* = rho0 v* / c (averaged over
+                            // the Dirichlet edges of a corner link)
+                            TC a0c, a1c;
+                            if (da && db) {
+                                a0c = TC(0.5) * (ea->jh[0] + eb->jh[0]);
+                                a1c = TC(0.5) * (ea->jh[1] + eb->jh[1]);
+                            } else {
+                                const EdgeNow<TC, UT>* e = da ? ea : eb;
+                                a0c = e->jh[0];
+                                a1c = e->jh[1];
+                            }
+                            val = fc[i] - TC(2) * wgt<TC>(i) * eq_odd<TC>(i, a0c, a1c);
                         } else {
-                            // Eq. (abbcon) with Pbar* of Sec. 6 in the wall-normal frame
-                            const int sx = bx ? (dx < 0 ? -1 : 1) : 0, sy = by ? (dy < 0 ? -1 : 1) : 0;
-                            const double inv_len = (sx != 0 && sy != 0) ? 0.70710678118654752440 : 1.0;
-                            double T0 = 0.0, T1 = 0.0;
+                            // Eq. (abbcon) with Pbar* of Sec. 6 in the wall-normal
+                            // frame; a corner link: N = (N1 + N2)/sqrt(2),
+                            // T* = (T1 + T2)/sqrt(2)
+                            const int sx = bx2 ? (dx < 0 ? -1 : 1) : 0, sy = by2 ? (dy < 0 ? -1 : 1) : 0;
+                            const TC inv_len = (sx != 0 && sy != 0) ? TC(0.70710678118654752440) : TC(1);
+                            TC T0 = TC(0), T1 = TC(0);
                             if (ea) {
-                                double ta, tb;
-                                traction(*ea, t_now, ta, tb);
-                                T0 += ta;
-                                T1 += tb;
+                                T0 += ea->T[0];
+                                T1 += ea->T[1];
                             }
                             if (eb) {
-                                double ta, tb;
-                                traction(*eb, t_now, ta, tb);
-                                T0 += ta;
-                                T1 += tb;
+                                T0 += eb->T[0];
+                                T1 += eb->T[1];
                             }
-                            const TC N0 = TC(sx * inv_len), N1 = TC(sy * inv_len);
-                            const TC g0 = -TC(T0 * inv_len) + q11 * N0 + q12 * N1;
-                            const TC g1 = -TC(T1 * inv_len) + q21 * N0 + q22 * N1;
+                            const TC N0 = TC(sx) * inv_len, N1 = TC(sy) * inv_len;
+                            const TC g0 = -T0 * inv_len + q11 * N0 + q12 * N1;
+                            const TC g1 = -T1 * inv_len + q21 * N0 + q22 * N1;
                             const TC t0 = -N1, t1 = N0;
                             const TC pnn = (N0 * g0 + N1 * g1) * k.inv_c2;
                             const TC pnt = (t0 * g0 + t1 * g1) * k.inv_c2;
@@ -402,47 +509,65 @@ __global__ void __launch_bounds__(NT) strip_step_kernel(const __grid_constant__ 
                             const TC sxy = pnn * N0 * N1 + pnt * (N0 * t1 + t0 * N1) + ptt * t0 * t1;
                             val = -fc[i] + TC(2) * wgt<TC>(i) * eq_even<TC>(i, r, sxx, sxy, syy);
                         }
-                        fdst[oi * plane + int64_t(dy + 1) * pitch + dx + p.xoff] = Codec<TS, TC>::st(val, oi, p);
+                        store_img(fdst + oi * plane, g, dx, dy, Codec<TS, TC>::st(val, oi, p));
                     }
                 }
 
-                // carries for the next step
-                const UT A0 = ux.add(k.ku * (j0 + TC(0.5) * sn0));
-                const UT A1 = uy.add(k.ku * (j1 + TC(0.5) * sn1));
-                A0.store(p.a_dst, id, plane);
-                A1.store(p.a_dst, id + UT::planes * plane, plane);
-                s_dst[id] = sn0;
-                s_dst[id + plane] = sn1;
+                // carries for the next step: A' = u + ku (jh + s/2), u = u* + du
+                const UT A0 = ux.add(du0 + k.ku * (j0 + TC(0.5) * sn0)).renorm();
+                const UT A1 = uy.add(du1 + k.ku * (j1 + TC(0.5) * sn1)).renorm();
+#pragma unroll
+                for (int c = 0; c < UP; ++c) {
+                    put(a_dst + c * plane, A0.part(c));
+                    put(a_dst + (UP + c) * plane, A1.part(c));
+                }
+                put(s_dst, sn0);
+                put(s_dst + plane, sn1);
                 if (p.fields != nullptr) {
-                    const int64_t o = int64_t(gy) * nx + gx;
+                    const int64_t fo = int64_t(gy) * nx + gx;
                     const int64_t np = int64_t(nx) * ny;
-                    p.fields[o] = ux.to_double();
-                    p.fields[np + o] = uy.to_double();
-                    p.fields[2 * np + o] = double(j0 * k.c_over_rho0);
-                    p.fields[3 * np + o] = double(j1 * k.c_over_rho0);
-                    p.fields[4 * np + o] = double(r);
+                    p.fields[fo] = ux.add(du0).to_double();
+                    p.fields[np + fo] = uy.add(du1).to_double();
+                    p.fields[2 * np + fo] = double(j0 * k.c_over_rho0);
+                    p.fields[3 * np + fo] = double(j1 * k.c_over_rho0);
+                    p.fields[4 * np + fo] = double(r);
                     if (!(fabs(double(j0)) + fabs(double(j1)) < 1e300)) bad = true;
                 }
             }
         }
-    };
-
-    for (int q = 0; q < niter; q += kDepth) {
-        body(q, std::integral_constant<int, 0>{});
-        if (q + 1 < niter) body(q + 1, std::integral_constant<int, 1>{});
-        if (q + 2 < niter) body(q + 2, std::integral_constant<int, 2>{});
-        if (q + 3 < niter) body(q + 3, std::integral_constant<int, 3>{});
-        if (q + 4 < niter) body(q + 4, std::integral_constant<int, 4>{});
+        sa = sa == 2 ? 0 : sa + 1;
+        ra = ra + 1 == R ? 0 : ra + 1;
     }
     if (bad) atomicOr(p.flag, 1);
+    if (MODE == 0 && s_abort && t == 0) {
+        // a wait gave up or an address was misaligned: report, then let the
+        // copies already in flight land before the CTA exits
+        atomicOr(p.flag, s_abort == 2 ? 8 : 4);
+        for (int s = 0; s < R; ++s)
+            if (issued & (1u << s)) (void)mbar_wait(&bars[s], (phase >> s) & 1u);
+    }
 }
 
 // ---------------------------------------------------------------- launchers
 
+template <class TS, class TC, class UT, int NT>
+size_t smem_bytes(int ring_slots, int mode) {
+    const size_t pair = size_t(2) * 9 * (NT + kSegExtra) * sizeof(TS);
+    return step_smem_fixed<UT, TC, NT>(mode) + (mode == 1 ? 0 : pair * ring_slots);
+}
+
 template <class TS, class TC, class UT, int NT, int MODE>
 cudaError_t launch_one(const StepParams& p, cudaStream_t s) {
-    dim3 grid(p.tiles_x, p.tiles_y);
-    strip_step_kernel<TS, TC, UT, NT, MODE><<<grid, NT, 0, s>>>(p);
+    auto kern = strip_step_kernel<TS, TC, UT, NT, MODE>;
+    const size_t sm = smem_bytes<TS, TC, UT, NT>(p.ring_slots, MODE);
+    static size_t configured = 0;  // largest dynamic shared memory set so far
+    if (sm > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        if (e != cudaSuccess) return e;
+        configured = sm;
+    }
+    dim3 grid(p.tiles_x, p.tiles_y, p.nrect > 0 ? p.nrect : 1);
+    kern<<<grid, NT, sm, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -456,6 +581,7 @@ struct Variant {
         if (!fields) p.fields = nullptr;
         return mode == 1 ? launch_one<TS, TC, UT, NT, 1>(p, s) : launch_one<TS, TC, UT, NT, 0>(p, s);
     }
+    static size_t smem(int ring) { return smem_bytes<TS, TC, UT, NT>(ring, 0); }
 };
 
 using V64 = Variant<double, double, UPlain<double>, 128>;
@@ -473,6 +599,16 @@ void tile_shape(int fmt, int* tx, int* ty) {
         default: *tx = Vb16::width; break;
     }
     *ty = 128;
+}
+
+size_t step_smem_bytes(int fmt, int ring_slots) {
+    switch (fmt) {
+        case kFmtF64: return V64::smem(ring_slots);
+        case kFmtF32: return V32::smem(ring_slots);
+        case kFmtF32C: return V32c::smem(ring_slots);
+        case kFmtF16: return V16::smem(ring_slots);
+        default: return Vb16::smem(ring_slots);
+    }
 }
 
 cudaError_t launch_fused_step(int fmt, const StepParams& p, cudaStream_t s, int mode, bool fields) {

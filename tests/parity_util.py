@@ -25,8 +25,22 @@ def run_both(prob, steps, storage="f64", compensated=None, scheme=oracle.PREDICT
     return ref, got
 
 
-def compare(ref, got, tol, keys=("u", "v", "P")):
-    errs = {k: rel_l2(got[k], ref[k]) for k in keys}
+def moment_scale(ref, prob):
+    """Natural scale of the zeroth moment r = sum_i f_i: the populations are
+    of order |r| + rho0 |v| / c + |Pbar| / c^2 (c = dX / dt = sqrt(3 mu / rho0)),
+    and the rounding of r is relative to them, not to |r| alone."""
+    c = np.sqrt(3.0 * prob.mu / prob.rho0)
+    return (np.linalg.norm(ref["r"]) + prob.rho0 * np.linalg.norm(ref["v"]) / c
+            + np.linalg.norm(ref["Pbar"]) / c ** 2)
+
+
+def compare(ref, got, tol, keys=("u", "v", "P"), prob=None):
+    errs = {}
+    for k in keys:
+        if k == "r" and prob is not None:
+            errs[k] = np.linalg.norm(np.asarray(got[k]) - ref[k]) / moment_scale(ref, prob)
+        else:
+            errs[k] = rel_l2(got[k], ref[k])
     bad = {k: e for k, e in errs.items() if not (e <= tol)}
     assert not bad, (bad, errs)
     return errs

