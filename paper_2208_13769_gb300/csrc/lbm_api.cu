@@ -56,7 +56,7 @@ struct lbm_ctx {
     // layout
     int64_t pitch = 0, plane = 0;
     int ring_slots = 0;
-    int tile_x = 0, tile_y = 0, tiles_x = 0, tiles_y = 0, chunk_rows = 0;
+    int tile_x = 0, tiles_x = 0, tiles_y = 0, chunk_rows = 0, band_w = 0, interior_w = 0;
     // device memory
     void* f[2] = {nullptr, nullptr};
     void* a[2] = {nullptr, nullptr};
@@ -92,7 +92,9 @@ struct lbm_ctx {
     int i_tiles_x = 0, i_tiles_y = 0, i_chunk = 0, i_ring = 0;
     int nband = 0;
     int brect[4][4];
-    int b_tiles_x = 0, b_tiles_y = 0, b_chunk = 0;
+    int b_chunk = 0;
+    int b_base[5] = {0, 0, 0, 0, 0};
+    int b_strips[4] = {1, 1, 1, 1};
 };
 
 namespace {
@@ -189,13 +191,13 @@ void build_plan(lbm_ctx* c) {
     const bool perx = c->bc[0].kind == kPeriodic, pery = c->bc[2].kind == kPeriodic;
     const int bx = perx ? 3 : 2, by = pery ? 3 : 2;
     const int nx = c->nx, ny = c->ny;
-    const int W = c->tile_x;
     c->has_interior = nx - 2 * bx >= 8 && ny - 2 * by >= 8;
     c->nband = 0;
     if (c->has_interior) {
-        int r[4] = {bx, nx - bx, by, ny - by};
+        const int r[4] = {bx, nx - bx, by, ny - by};
         for (int k = 0; k < 4; ++k) c->irect[k] = r[k];
         const int w = r[1] - r[0], h = r[3] - r[2];
+        const int W = c->interior_w;
         c->i_ring = 7;  // lookahead of 4 rows
         const size_t smem = interior_smem(c->fmt, c->i_ring);
         const int per_sm = std::max(1, int((228 * 1024) / (smem + 1024)));
@@ -208,23 +210,22 @@ void build_plan(lbm_ctx* c) {
         rows = std::min<int64_t>(rows, h);
         c->i_chunk = int(rows);
         c->i_tiles_y = int((h + rows - 1) / rows);
-        int bands[4][4] = {{0, nx, 0, by}, {0, nx, ny - by, ny}, {0, bx, by, ny - by}, {nx - bx, nx, by, ny - by}};
+        const int bands[4][4] = {{0, nx, 0, by}, {0, nx, ny - by, ny}, {0, bx, by, ny - by}, {nx - bx, nx, by, ny - by}};
         for (int b = 0; b < 4; ++b)
             for (int k = 0; k < 4; ++k) c->brect[b][k] = bands[b][k];
         c->nband = 4;
-        c->b_chunk = 8;
     } else {
-        int all[4] = {0, nx, 0, ny};
+        const int all[4] = {0, nx, 0, ny};
         for (int k = 0; k < 4; ++k) c->brect[0][k] = all[k];
         c->nband = 1;
-        c->b_chunk = c->chunk_rows;
     }
-    c->b_tiles_x = 1;
-    c->b_tiles_y = 1;
+    c->b_chunk = 8;
+    c->b_base[0] = 0;
     for (int b = 0; b < c->nband; ++b) {
         const int w = c->brect[b][1] - c->brect[b][0], h = c->brect[b][3] - c->brect[b][2];
-        c->b_tiles_x = std::max(c->b_tiles_x, (w + W - 1) / W);
-        c->b_tiles_y = std::max(c->b_tiles_y, (h + c->b_chunk - 1) / c->b_chunk);
+        c->b_strips[b] = (w + c->band_w - 1) / c->band_w;
+        const int chunks = (h + c->b_chunk - 1) / c->b_chunk;
+        c->b_base[b + 1] = c->b_base[b] + c->b_strips[b] * chunks;
     }
     c->planned = true;
 }
@@ -238,6 +239,10 @@ cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int parity) {
         p.rect[0][1] = c->nx;
         p.rect[0][2] = 0;
         p.rect[0][3] = c->ny;
+        p.rect_strips[0] = c->tiles_x;
+        p.tile_base[0] = 0;
+        p.tile_base[1] = c->tiles_x * c->tiles_y;
+        p.chunk_rows = c->chunk_rows;
         p.write_counter = 1;
         return launch_fused_step(c->fmt, p, c->stream, 1, fields);
     }
@@ -254,10 +259,11 @@ cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int parity) {
         if (e != cudaSuccess) return e;
     }
     p.nrect = c->nband;
-    for (int b = 0; b < c->nband; ++b)
+    for (int b = 0; b < c->nband; ++b) {
         for (int k = 0; k < 4; ++k) p.rect[b][k] = c->brect[b][k];
-    p.tiles_x = c->b_tiles_x;
-    p.tiles_y = c->b_tiles_y;
+        p.rect_strips[b] = c->b_strips[b];
+    }
+    for (int b = 0; b <= c->nband; ++b) p.tile_base[b] = c->b_base[b];
     p.chunk_rows = c->b_chunk;
     p.write_counter = 1;
     return launch_fused_step(c->fmt, p, c->stream, 0, fields);
@@ -385,30 +391,29 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
         memset(&c->bc[e], 0, sizeof(EdgeBC));
         c->bc[e].times[2] = INFINITY;
     }
-    // column strips of tile_x nodes; rows split into chunks so that the grid
-    // holds about one wave of co-resident CTAs on the 152 SMs (chunks of at
-    // least 16 rows)
-    tile_shape(c->fmt, &c->tile_x, &c->tile_y);
-    c->ring_slots = 4;  // row-pair slots of the bulk-copy ring: one pair of lookahead
+    // strip widths of the three launch shapes; rows of the initialisation
+    // split into chunks of at least 16 so the grid holds about two CTAs per SM
+    int init_w = 0, band_w = 0, interior_w = 0;
+    strip_widths(&init_w, &band_w, &interior_w);
+    c->tile_x = init_w;
+    c->band_w = band_w;
+    c->interior_w = interior_w;
+    c->ring_slots = 4;  // row-pair slots of the general kernel's ring
     {
-        const size_t smem = step_smem_bytes(c->fmt, c->ring_slots);
-        const int per_sm = smem > 0 ? int((228 * 1024) / (smem + 1024)) : 1;
-        c->tiles_x = int((d->nx + c->tile_x - 1) / c->tile_x);
-        const int64_t want = int64_t(152) * (per_sm > 0 ? per_sm : 1);
-        const int64_t chunks = (want + c->tiles_x - 1) / c->tiles_x;
+        const int strips = (d->nx + init_w - 1) / init_w;
+        const int64_t chunks = std::max<int64_t>(1, (2 * 152) / strips);
         int64_t rows = (d->ny + chunks - 1) / chunks;
-        if (rows < 16) rows = 16;
-        if (rows > d->ny) rows = d->ny;
+        rows = std::min<int64_t>(std::max<int64_t>(rows, 16), d->ny);
         c->chunk_rows = int(rows);
+        c->tiles_x = strips;
         c->tiles_y = int((d->ny + rows - 1) / rows);
     }
 
     // plane layout: kPadCols columns / kPadRows rows of padding on each side,
-    // pitch a multiple of 64 elements covering the widest bulk-copied segment
-    // a strip may start as far right as nx - 2 (the right edge band); its
-    // segment then reaches nx - 2 - 15 + (tile + 4) + kSegExtra
-    const int64_t seg_end = int64_t(d->nx) + c->tile_x + 4 + kSegExtra;
-    int64_t need = kPadCols + std::max<int64_t>(seg_end, int64_t(c->tile_x) + 4 + kSegExtra + 8) + 16;
+    // pitch a multiple of 64 elements covering the widest bulk-copied row
+    // segment (a strip may start as far right as nx - 2, the right edge band)
+    const int64_t seg_end = int64_t(d->nx) + init_w + 4 + kSegExtra;
+    int64_t need = kPadCols + std::max<int64_t>(seg_end, int64_t(init_w) + 4 + kSegExtra + 8) + 16;
     c->pitch = (need + 63) / 64 * 64;
     c->plane = c->pitch * (int64_t(d->ny) + 2 * kPadRows);
 

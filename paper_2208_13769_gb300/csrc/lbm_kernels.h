@@ -16,11 +16,10 @@ enum Format : int {
     kFmtBF16 = 4   // BF16 / FP32 / compensated FP32 pair
 };
 
-// Tile shape (nodes) the fused kernel uses for a format.
-void tile_shape(int fmt, int* tx, int* ty);
+// Output columns per strip: general kernel at initialisation, general
+// kernel on the edge bands, interior kernel.
+void strip_widths(int* init_w, int* band_w, int* interior_w);
 
-// Dynamic shared memory of the fused step for a ring of `ring_slots` rows.
-size_t step_smem_bytes(int fmt, int ring_slots);
 
 // The interior kernel (lbm_interior.cu): nodes of p.rect[0] only, which must
 // lie at least 2 nodes from bounded edges and 3 from periodic seams.

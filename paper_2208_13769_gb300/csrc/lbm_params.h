@@ -39,8 +39,10 @@ struct StepParams {
     int64_t plane;   // elements per plane
     int32_t tiles_x, tiles_y;  // grid: column strips x row chunks
     int32_t chunk_rows;        // rows per chunk (>= 3)
-    int32_t nrect;             // rectangles of output nodes (blockIdx.z picks one)
+    int32_t nrect;             // rectangles of output nodes
     int32_t rect[4][4];        // x_lo, x_hi, y_lo, y_hi of each rectangle
+    int32_t tile_base[5];      // general kernel: first CTA of each rectangle in a 1-D grid
+    int32_t rect_strips[4];    // general kernel: column strips of each rectangle
     int32_t write_counter;     // this launch advances the step counter
     int32_t pad0;
 

@@ -86,12 +86,16 @@ __global__ void __launch_bounds__(NT) strip_step_kernel(const __grid_constant__ 
     const int t = threadIdx.x;
     // output rectangle of this CTA's launch slice, strip and chunk inside it
     // (origins clamped so the last strip / chunk is full when it fits)
-    const int rx0 = p.rect[blockIdx.z][0], rx1 = p.rect[blockIdx.z][1];
-    const int ry0 = p.rect[blockIdx.z][2], ry1 = p.rect[blockIdx.z][3];
-    if (int(blockIdx.x) * W >= rx1 - rx0 || int(blockIdx.y) * p.chunk_rows >= ry1 - ry0) return;
-    int x0 = rx0 + int(blockIdx.x) * W;
+    // 1-D grid over the (rectangle, strip, chunk) tiles
+    int rb = 0;
+    while (rb + 1 < p.nrect && int(blockIdx.x) >= p.tile_base[rb + 1]) ++rb;
+    const int local = int(blockIdx.x) - p.tile_base[rb];
+    const int bxs = local % p.rect_strips[rb], bys = local / p.rect_strips[rb];
+    const int rx0 = p.rect[rb][0], rx1 = p.rect[rb][1];
+    const int ry0 = p.rect[rb][2], ry1 = p.rect[rb][3];
+    int x0 = rx0 + bxs * W;
     if (x0 > rx1 - W) x0 = rx1 - W > rx0 ? rx1 - W : rx0;
-    int y_begin = ry0 + int(blockIdx.y) * p.chunk_rows;
+    int y_begin = ry0 + bys * p.chunk_rows;
     if (y_begin > ry1 - p.chunk_rows) y_begin = ry1 - p.chunk_rows > ry0 ? ry1 - p.chunk_rows : ry0;
     const int y_end = min(ry1, y_begin + p.chunk_rows);
     int seg0 = x0 - 8;  // first column of the row segments: 16-byte aligned
@@ -105,7 +109,7 @@ __global__ void __launch_bounds__(NT) strip_step_kernel(const __grid_constant__ 
 
     int64_t n_now = 0;  // the collision of this launch is at t_now = n_now dt
     if (MODE == 0) n_now = p.counter[p.parity] + 1;
-    if (p.write_counter && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t == 0)
+    if (p.write_counter && blockIdx.x == 0 && t == 0)
         p.counter[p.parity ^ 1] = n_now;
     const double t_now = double(n_now) * p.dt;
 
@@ -566,49 +570,39 @@ cudaError_t launch_one(const StepParams& p, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         configured = sm;
     }
-    dim3 grid(p.tiles_x, p.tiles_y, p.nrect > 0 ? p.nrect : 1);
-    kern<<<grid, NT, sm, s>>>(p);
+    kern<<<dim3(p.tile_base[p.nrect > 0 ? p.nrect : 1]), NT, sm, s>>>(p);
     return cudaGetLastError();
 }
 
 // `fields` selects at run time whether the launch also writes u, v, r (the
 // same instantiation runs either way, so results are bit-identical).
-template <class TS, class TC, class UT, int NT>
+// `fields` selects at run time whether the launch also writes u, v, r (the
+// same instantiation runs either way, so results are bit-identical).
+// Initialisation: 128-thread CTAs over the whole body; edge bands: one-warp
+// CTAs (a band is 2 or 3 nodes thick, so a strip of 28 output columns wastes
+// little and many CTAs hide the row-pipeline latency).
+template <class TS, class TC, class UT>
 struct Variant {
-    static constexpr int width = NT - 4;
+    static constexpr int kInitNT = 128, kBandNT = 32;
     static cudaError_t run(const StepParams& p0, cudaStream_t s, int mode, bool fields) {
         StepParams p = p0;
         if (!fields) p.fields = nullptr;
-        return mode == 1 ? launch_one<TS, TC, UT, NT, 1>(p, s) : launch_one<TS, TC, UT, NT, 0>(p, s);
+        return mode == 1 ? launch_one<TS, TC, UT, kInitNT, 1>(p, s) : launch_one<TS, TC, UT, kBandNT, 0>(p, s);
     }
-    static size_t smem(int ring) { return smem_bytes<TS, TC, UT, NT>(ring, 0); }
 };
 
-using V64 = Variant<double, double, UPlain<double>, 128>;
-using V32 = Variant<float, float, UPlain<float>, 128>;
-using V32c = Variant<float, float, UComp, 128>;
-using V16 = Variant<__half, float, UComp, 128>;
-using Vb16 = Variant<__nv_bfloat16, float, UComp, 128>;
+using V64 = Variant<double, double, UPlain<double>>;
+using V32 = Variant<float, float, UPlain<float>>;
+using V32c = Variant<float, float, UComp>;
+using V16 = Variant<__half, float, UComp>;
+using Vb16 = Variant<__nv_bfloat16, float, UComp>;
 
-void tile_shape(int fmt, int* tx, int* ty) {
-    switch (fmt) {
-        case kFmtF64: *tx = V64::width; break;
-        case kFmtF32: *tx = V32::width; break;
-        case kFmtF32C: *tx = V32c::width; break;
-        case kFmtF16: *tx = V16::width; break;
-        default: *tx = Vb16::width; break;
-    }
-    *ty = 128;
-}
-
-size_t step_smem_bytes(int fmt, int ring_slots) {
-    switch (fmt) {
-        case kFmtF64: return V64::smem(ring_slots);
-        case kFmtF32: return V32::smem(ring_slots);
-        case kFmtF32C: return V32c::smem(ring_slots);
-        case kFmtF16: return V16::smem(ring_slots);
-        default: return Vb16::smem(ring_slots);
-    }
+// Strip widths (output columns) of the general kernel: initialisation, bands;
+// and of the interior kernel.
+void strip_widths(int* init_w, int* band_w, int* interior_w) {
+    *init_w = 128 - 4;
+    *band_w = 32 - 4;
+    *interior_w = 128 - 4;
 }
 
 cudaError_t launch_fused_step(int fmt, const StepParams& p, cudaStream_t s, int mode, bool fields) {
