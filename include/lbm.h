@@ -175,6 +175,47 @@ LBM_API lbm_status lbm_memory_info(const lbm_ctx* ctx, int64_t* device_bytes, in
 /* Frees the context and its device memory (NULL is allowed). */
 LBM_API lbm_status lbm_destroy(lbm_ctx* ctx);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free diagnostics (no counterpart in the paper).
+ *
+ * For callers that cannot call cudaMalloc -- code running while a CUDA graph
+ * is being captured, code confined to a fixed memory pool, or a process whose
+ * device allocator belongs to another runtime that forbids side allocations.
+ * lbm_diagnostics_noalloc computes the same six numbers as lbm_diagnostics
+ * from caller-owned device fields and allocates nothing: its scratch (partial
+ * sums of at most 1024 CTAs, 64 KiB) is a static array inside the library,
+ * held on every GPU that loads the library until the process exits.
+ *
+ * fields_dev: device, 5 planes of nx*ny FP64 in row-major [ny][nx] order --
+ *   u_x, u_y, v_x, v_y, r (r is not used).
+ * geo: body size, spacing, material, and per edge (x-, x+, y-, y+) the kind
+ *   and, for Dirichlet edges, the prescribed displacement at the fields' time
+ *   (used by the ghost rule of Grad u).
+ * out_dev: device, 8 doubles: sum j_x, sum j_y, kinetic energy, strain
+ *   energy, min J, non-finite flag, then two zeros.  Written asynchronously on
+ *   cuda_stream (NULL: the legacy default stream); read it after the stream
+ *   has finished.
+ * Limits: nx, ny >= 3 and nx * ny <= LBM_NOALLOC_MAX_NODES; larger bodies,
+ *   null pointers, unknown edge kinds or an unpaired periodic edge return
+ *   LBM_E_INVALID without launching anything.
+ * The first call on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and may return wrong sums.  Each call
+ * overwrites every partial it reads, so no clearing between calls is needed.
+ * Errors: LBM_E_INVALID, LBM_E_CUDA. */
+typedef struct {
+    int32_t nx, ny;
+    double dX, lambda, mu, rho0;
+    int32_t edge_kind[4];
+    double edge_u[4][2];
+} lbm_field_geometry;
+
+#define LBM_NOALLOC_MAX_NODES 2147483647LL
+
+LBM_API lbm_status lbm_diagnostics_noalloc(const lbm_field_geometry* geo, const double* fields_dev,
+                                           double* out_dev, void* cuda_stream);
+
 /* Description of the CUDA error that made the context unusable ("none" if
  * there was none).  Static storage; valid for the context's lifetime. */
 LBM_API const char* lbm_last_cuda_error(const lbm_ctx* ctx);

@@ -43,6 +43,14 @@ class lbm_desc(C.Structure):
     ]
 
 
+class lbm_field_geometry(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("dX", C.c_double), ("lam", C.c_double),
+        ("mu", C.c_double), ("rho0", C.c_double), ("edge_kind", C.c_int32 * 4),
+        ("edge_u", (C.c_double * 2) * 4),
+    ]
+
+
 class LbmError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
@@ -69,6 +77,7 @@ _SIGNATURES = {
     "lbm_destroy": (C.c_int, [C.c_void_p]),
     "lbm_status_string": (C.c_char_p, [C.c_int]),
     "lbm_last_cuda_error": (C.c_char_p, [C.c_void_p]),
+    "lbm_diagnostics_noalloc": (C.c_int, [C.POINTER(lbm_field_geometry), C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -172,6 +181,13 @@ def lbm_memory_info(ctx) -> tuple:
 
 def lbm_destroy(ctx):
     return _check(lib().lbm_destroy(ctx), "lbm_destroy")
+
+
+def lbm_diagnostics_noalloc(geo: lbm_field_geometry, fields_dev: int, out_dev: int, stream: int = 0) -> int:
+    """Diagnostics of caller-owned device fields (device pointers as ints);
+    allocates nothing.  Returns the status."""
+    return int(lib().lbm_diagnostics_noalloc(C.byref(geo), C.c_void_p(fields_dev), C.c_void_p(out_dev),
+                                             C.c_void_p(stream or None)))
 
 
 def lbm_last_cuda_error(ctx) -> str:
