@@ -130,6 +130,21 @@ LBM_API lbm_status lbm_set_boundary(lbm_ctx* ctx, int32_t edge, int32_t kind, co
  * LBM_E_INVALID (nsteps < 0), LBM_E_CUDA. */
 LBM_API lbm_status lbm_step(lbm_ctx* ctx, int64_t nsteps);
 
+/* Measurement aid (no counterpart in the paper).  Advances `nsteps` time
+ * steps exactly as lbm_step does (same kernels, same arithmetic, same
+ * results), but launch by launch without graphs, with a CUDA event on the
+ * context's stream before and after each of a step's two launches (the
+ * interior kernel and the edge-band kernel).  out[0] is the mean duration of
+ * the interior launch, out[1] of the edge-band launch, out[2] of their sum,
+ * in milliseconds, averaged over all steps but the last (which also writes
+ * the read-out fields; with nsteps == 1 it is the only one); out[3] is the
+ * number of nodes the interior launch advances (nodes at least 2 from a
+ * bounded edge and 3 from a periodic seam).  out[0] and out[3] are 0 for a
+ * body too small to have an interior.  Synchronises the stream.
+ * Errors: LBM_E_INVALID (nsteps outside 1..4096, out NULL), LBM_E_STATE,
+ * LBM_E_OOM, LBM_E_CUDA, and LBM_E_UNSTABLE / LBM_E_TIMEOUT as lbm_sync. */
+LBM_API lbm_status lbm_profile_steps(lbm_ctx* ctx, int64_t nsteps, double out[4]);
+
 /* Field bits for lbm_read_fields; the output holds the requested fields in
  * this bit order, each as [ny][nx][ncomp] FP64. */
 enum {

@@ -230,6 +230,34 @@ void build_plan(lbm_ctx* c) {
     c->planned = true;
 }
 
+// The interior launch of one time step (nothing if the body has no interior).
+cudaError_t launch_interior_part(lbm_ctx* c, const StepParams& p, bool fields) {
+    if (!c->has_interior) return cudaSuccess;
+    StepParams pi = p;
+    pi.nrect = 1;
+    for (int k = 0; k < 4; ++k) pi.rect[0][k] = c->irect[k];
+    pi.tiles_x = c->i_tiles_x;
+    pi.tiles_y = c->i_tiles_y;
+    pi.chunk_rows = c->i_chunk;
+    pi.ring_slots = c->i_ring;
+    pi.write_counter = 0;
+    return launch_interior(c->fmt, pi, c->stream, fields);
+}
+
+// The edge-band launch of one time step (the whole body without an interior).
+cudaError_t launch_band_part(lbm_ctx* c, const StepParams& p0, bool fields) {
+    StepParams p = p0;
+    p.nrect = c->nband;
+    for (int b = 0; b < c->nband; ++b) {
+        for (int k = 0; k < 4; ++k) p.rect[b][k] = c->brect[b][k];
+        p.rect_strips[b] = c->b_strips[b];
+    }
+    for (int b = 0; b <= c->nband; ++b) p.tile_base[b] = c->b_base[b];
+    p.chunk_rows = c->b_chunk;
+    p.write_counter = 1;
+    return launch_fused_step(c->fmt, p, c->stream, 0, fields);
+}
+
 // Launches of one time step (mode 0) or the initialisation (mode 1).
 cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int parity) {
     StepParams p = make_params(c, parity);
@@ -246,27 +274,9 @@ cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int parity) {
         p.write_counter = 1;
         return launch_fused_step(c->fmt, p, c->stream, 1, fields);
     }
-    if (c->has_interior) {
-        StepParams pi = p;
-        pi.nrect = 1;
-        for (int k = 0; k < 4; ++k) pi.rect[0][k] = c->irect[k];
-        pi.tiles_x = c->i_tiles_x;
-        pi.tiles_y = c->i_tiles_y;
-        pi.chunk_rows = c->i_chunk;
-        pi.ring_slots = c->i_ring;
-        pi.write_counter = 0;
-        cudaError_t e = launch_interior(c->fmt, pi, c->stream, fields);
-        if (e != cudaSuccess) return e;
-    }
-    p.nrect = c->nband;
-    for (int b = 0; b < c->nband; ++b) {
-        for (int k = 0; k < 4; ++k) p.rect[b][k] = c->brect[b][k];
-        p.rect_strips[b] = c->b_strips[b];
-    }
-    for (int b = 0; b <= c->nband; ++b) p.tile_base[b] = c->b_base[b];
-    p.chunk_rows = c->b_chunk;
-    p.write_counter = 1;
-    return launch_fused_step(c->fmt, p, c->stream, 0, fields);
+    cudaError_t e = launch_interior_part(c, p, fields);
+    if (e != cudaSuccess) return e;
+    return launch_band_part(c, p, fields);
 }
 
 lbm_status launch(lbm_ctx* c, int mode, bool fields) {
@@ -541,6 +551,56 @@ lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
         --left;
     }
     return launch(c, 0, true);
+}
+
+lbm_status lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double out[4]) {
+    lbm_status st = ready(c);
+    if (st != LBM_OK) return st;
+    if (nsteps < 1 || nsteps > 4096 || !out) return LBM_E_INVALID;
+    DeviceGuard guard(c->device);
+    if (!guard.ok) return fail_cuda(c, cudaErrorInvalidDevice);
+    st = ensure_initialized(c);
+    if (st != LBM_OK) return st;
+    if (!c->planned) build_plan(c);
+    // events e[2k] before step k's interior launch, e[2k+1] between its two
+    // launches, e[2k+2] after its band launch
+    const int64_t nev = 2 * nsteps + 1;
+    cudaEvent_t* ev = new (std::nothrow) cudaEvent_t[size_t(nev)];
+    if (!ev) return LBM_E_OOM;
+    int64_t made = 0;
+    cudaError_t err = cudaSuccess;
+    for (; made < nev && err == cudaSuccess; ++made) err = cudaEventCreate(&ev[made]);
+    if (err != cudaSuccess) --made;
+    if (err == cudaSuccess) err = cudaEventRecord(ev[0], c->stream);
+    for (int64_t k = 0; k < nsteps && err == cudaSuccess; ++k) {
+        const bool fields = k + 1 == nsteps;  // the last step refreshes the read-out fields
+        const StepParams p = make_params(c, c->parity);
+        err = launch_interior_part(c, p, fields);
+        if (err == cudaSuccess) err = cudaEventRecord(ev[2 * k + 1], c->stream);
+        if (err == cudaSuccess) err = launch_band_part(c, p, fields);
+        if (err == cudaSuccess) err = cudaEventRecord(ev[2 * k + 2], c->stream);
+        if (err == cudaSuccess) {
+            c->parity ^= 1;
+            c->steps += 1;
+        }
+    }
+    if (err == cudaSuccess) err = cudaEventSynchronize(ev[nev - 1]);
+    double sum[3] = {0, 0, 0};
+    const int64_t counted = nsteps > 1 ? nsteps - 1 : 1;  // the last step also writes the fields
+    for (int64_t k = 0; k < counted && err == cudaSuccess; ++k) {
+        float a = 0, b = 0;
+        err = cudaEventElapsedTime(&a, ev[2 * k], ev[2 * k + 1]);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&b, ev[2 * k + 1], ev[2 * k + 2]);
+        sum[0] += a;
+        sum[1] += b;
+        sum[2] += double(a) + double(b);
+    }
+    for (int64_t q = 0; q < made; ++q) cudaEventDestroy(ev[q]);
+    delete[] ev;
+    if (err != cudaSuccess) return fail_cuda(c, err);
+    for (int q = 0; q < 3; ++q) out[q] = sum[q] / double(counted);
+    out[3] = c->has_interior ? double(c->irect[1] - c->irect[0]) * double(c->irect[3] - c->irect[2]) : 0.0;
+    return check_flag(c);
 }
 
 int64_t lbm_fields_size(const lbm_ctx* c, uint32_t mask) {

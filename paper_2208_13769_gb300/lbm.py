@@ -67,6 +67,7 @@ _SIGNATURES = {
     "lbm_set_boundary": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "lbm_profile_steps": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
     "lbm_fields_size": (C.c_int64, [C.c_void_p, C.c_uint32]),
     "lbm_read_fields": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_double), C.c_int64,
                                   C.POINTER(C.c_double)]),
@@ -140,6 +141,15 @@ def lbm_step(ctx, nsteps: int):
     if st == LBM_E_CUDA:
         raise LbmError(st, f"lbm_step ({lbm_last_cuda_error(ctx)})")
     return _check(st, "lbm_step")
+
+
+def lbm_profile_steps(ctx, nsteps: int, allow_unstable: bool = False) -> tuple:
+    """Advances nsteps steps launch by launch; returns (status, [interior ms,
+    band ms, step ms, interior nodes]), the times averaged over the steps."""
+    out = np.zeros(4)
+    st = lib().lbm_profile_steps(ctx, int(nsteps), out.ctypes.data_as(C.POINTER(C.c_double)))
+    _check(st, "lbm_profile_steps", allow=(LBM_E_UNSTABLE,) if allow_unstable else ())
+    return st, out
 
 
 def lbm_fields_size(ctx, mask: int) -> int:
