@@ -16,6 +16,7 @@ using namespace lbm;
 namespace {
 
 constexpr int kGraphChunk = 64;  // steps per captured graph (even: keeps the ping-pong parity)
+constexpr int kInteriorW = 124;  // output columns per strip of the interior kernel (128 threads)
 
 struct DeviceGuard {
     int prev = -1;
@@ -55,8 +56,6 @@ struct lbm_ctx {
     int32_t f16_scale_log2 = 10;
     // layout
     int64_t pitch = 0, plane = 0;
-    int ring_slots = 0;
-    int tile_x = 0, tiles_x = 0, tiles_y = 0, chunk_rows = 0, band_w = 0, interior_w = 0;
     // device memory
     void* f[2] = {nullptr, nullptr};
     void* a[2] = {nullptr, nullptr};
@@ -92,9 +91,9 @@ struct lbm_ctx {
     int i_tiles_x = 0, i_tiles_y = 0, i_chunk = 0, i_ring = 0;
     int nband = 0;
     int brect[4][4];
-    int b_chunk = 0;
-    int b_base[5] = {0, 0, 0, 0, 0};
-    int b_strips[4] = {1, 1, 1, 1};
+    StepParams* dparams = nullptr;  // device: make_params(parity 0), make_params(parity 1)
+    EdgeTile* dtiles = nullptr;     // device: tiles of the edge bands
+    int n_etiles = 0;
 };
 
 namespace {
@@ -118,15 +117,11 @@ StepParams make_params(const lbm_ctx* c, int parity) {
     memset(&p, 0, sizeof(p));
     p.nx = c->nx;
     p.ny = c->ny;
-    p.ring_slots = c->ring_slots;
     p.periodic_x = c->bc[0].kind == kPeriodic;
     p.periodic_y = c->bc[2].kind == kPeriodic;
     p.scheme = c->scheme;
     p.pitch = c->pitch;
     p.plane = c->plane;
-    p.tiles_x = c->tiles_x;
-    p.tiles_y = c->tiles_y;
-    p.chunk_rows = c->chunk_rows;
     p.f_src = c->f[parity];
     p.f_dst = c->f[parity ^ 1];
     p.a_src = c->a[parity];
@@ -186,8 +181,10 @@ lbm_status ready(const lbm_ctx* c) {
 }
 
 // Interior rectangle (nodes >= 2 from bounded edges, >= 3 from periodic
-// seams) for the lean kernel, the bands around it for the general kernel.
-void build_plan(lbm_ctx* c) {
+// seams) for the lean kernel, the bands around it as tiles of the edge
+// kernel; the parameter table of both parities and the tile list go to the
+// device.
+cudaError_t build_plan(lbm_ctx* c) {
     const bool perx = c->bc[0].kind == kPeriodic, pery = c->bc[2].kind == kPeriodic;
     const int bx = perx ? 3 : 2, by = pery ? 3 : 2;
     const int nx = c->nx, ny = c->ny;
@@ -197,7 +194,7 @@ void build_plan(lbm_ctx* c) {
         const int r[4] = {bx, nx - bx, by, ny - by};
         for (int k = 0; k < 4; ++k) c->irect[k] = r[k];
         const int w = r[1] - r[0], h = r[3] - r[2];
-        const int W = c->interior_w;
+        const int W = kInteriorW;
         c->i_ring = 7;  // lookahead of 4 rows
         const size_t smem = interior_smem(c->fmt, c->i_ring);
         const int per_sm = std::max(1, int((228 * 1024) / (smem + 1024)));
@@ -219,68 +216,71 @@ void build_plan(lbm_ctx* c) {
         for (int k = 0; k < 4; ++k) c->brect[0][k] = all[k];
         c->nband = 1;
     }
-    c->b_chunk = 8;
-    c->b_base[0] = 0;
-    for (int b = 0; b < c->nband; ++b) {
-        const int w = c->brect[b][1] - c->brect[b][0], h = c->brect[b][3] - c->brect[b][2];
-        c->b_strips[b] = (w + c->band_w - 1) / c->band_w;
-        const int chunks = (h + c->b_chunk - 1) / c->b_chunk;
-        c->b_base[b + 1] = c->b_base[b] + c->b_strips[b] * chunks;
-    }
+    int n = 0;
+    for (int b = 0; b < c->nband; ++b) n += edge_tiles_of_rect(c->brect[b], 0, nullptr, 0, false);
+    EdgeTile* h = new (std::nothrow) EdgeTile[size_t(n)];
+    if (!h) return cudaErrorMemoryAllocation;
+    int m = 0;
+    for (int b = 0; b < c->nband; ++b) m += edge_tiles_of_rect(c->brect[b], 0, h + m, n - m, m == 0);
+    StepParams hp[2] = {make_params(c, 0), make_params(c, 1)};
+    cudaError_t e = cudaMalloc(&c->dtiles, sizeof(EdgeTile) * size_t(n));
+    if (e == cudaSuccess) e = cudaMalloc(&c->dparams, sizeof(hp));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->dtiles, h, sizeof(EdgeTile) * size_t(n), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->dparams, hp, sizeof(hp), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // h is freed below
+    delete[] h;
+    if (e != cudaSuccess) return e;
+    c->n_etiles = n;
     c->planned = true;
+    return cudaSuccess;
 }
 
 // The interior launch of one time step (nothing if the body has no interior).
 cudaError_t launch_interior_part(lbm_ctx* c, const StepParams& p, bool fields) {
     if (!c->has_interior) return cudaSuccess;
     StepParams pi = p;
-    pi.nrect = 1;
-    for (int k = 0; k < 4; ++k) pi.rect[0][k] = c->irect[k];
+    for (int k = 0; k < 4; ++k) pi.rect[k] = c->irect[k];
     pi.tiles_x = c->i_tiles_x;
     pi.tiles_y = c->i_tiles_y;
     pi.chunk_rows = c->i_chunk;
     pi.ring_slots = c->i_ring;
-    pi.write_counter = 0;
     return launch_interior(c->fmt, pi, c->stream, fields);
 }
 
 // The edge-band launch of one time step (the whole body without an interior).
-cudaError_t launch_band_part(lbm_ctx* c, const StepParams& p0, bool fields) {
-    StepParams p = p0;
-    p.nrect = c->nband;
-    for (int b = 0; b < c->nband; ++b) {
-        for (int k = 0; k < 4; ++k) p.rect[b][k] = c->brect[b][k];
-        p.rect_strips[b] = c->b_strips[b];
-    }
-    for (int b = 0; b <= c->nband; ++b) p.tile_base[b] = c->b_base[b];
-    p.chunk_rows = c->b_chunk;
-    p.write_counter = 1;
-    return launch_fused_step(c->fmt, p, c->stream, 0, fields);
+cudaError_t launch_band_part(lbm_ctx* c, int parity, bool fields) {
+    EdgeLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.params = c->dparams + parity;
+    L.tiles = c->dtiles;
+    L.fields = fields ? 1 : 0;
+    return launch_edge(c->fmt, L, c->n_etiles, c->stream, 0);
 }
 
 // Launches of one time step (mode 0) or the initialisation (mode 1).
 cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int parity) {
-    StepParams p = make_params(c, parity);
     if (mode == 1) {
-        p.nrect = 1;
-        p.rect[0][0] = 0;
-        p.rect[0][1] = c->nx;
-        p.rect[0][2] = 0;
-        p.rect[0][3] = c->ny;
-        p.rect_strips[0] = c->tiles_x;
-        p.tile_base[0] = 0;
-        p.tile_base[1] = c->tiles_x * c->tiles_y;
-        p.chunk_rows = c->chunk_rows;
-        p.write_counter = 1;
-        return launch_fused_step(c->fmt, p, c->stream, 1, fields);
+        EdgeLaunch L;
+        memset(&L, 0, sizeof(L));
+        L.params = c->dparams + parity;
+        L.tiles = nullptr;
+        L.fields = fields ? 1 : 0;
+        L.rect[0] = 0;
+        L.rect[1] = c->nx;
+        L.rect[2] = 0;
+        L.rect[3] = c->ny;
+        L.rtiles_x = (c->nx + 27) / 28;
+        const int64_t ntiles = int64_t(L.rtiles_x) * ((c->ny + 3) / 4);
+        if (ntiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
+        return launch_edge(c->fmt, L, int(ntiles), c->stream, 1);
     }
-    cudaError_t e = launch_interior_part(c, p, fields);
+    cudaError_t e = launch_interior_part(c, make_params(c, parity), fields);
     if (e != cudaSuccess) return e;
-    return launch_band_part(c, p, fields);
+    return launch_band_part(c, parity, fields);
 }
 
 lbm_status launch(lbm_ctx* c, int mode, bool fields) {
-    if (!c->planned) build_plan(c);
+    if (!c->planned) LBM_CUDA(c, build_plan(c));
     LBM_CUDA(c, launch_step_kernels(c, mode, fields, c->parity));
     c->parity ^= 1;
     if (mode == 0) c->steps += 1;
@@ -346,6 +346,8 @@ void free_all(lbm_ctx* c) {
     cudaFree(c->partials);
     cudaFree(c->diag);
     cudaFree(c->readout);
+    cudaFree(c->dparams);
+    cudaFree(c->dtiles);
     if (c->owns_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -401,29 +403,13 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
         memset(&c->bc[e], 0, sizeof(EdgeBC));
         c->bc[e].times[2] = INFINITY;
     }
-    // strip widths of the three launch shapes; rows of the initialisation
-    // split into chunks of at least 16 so the grid holds about two CTAs per SM
-    int init_w = 0, band_w = 0, interior_w = 0;
-    strip_widths(&init_w, &band_w, &interior_w);
-    c->tile_x = init_w;
-    c->band_w = band_w;
-    c->interior_w = interior_w;
-    c->ring_slots = 4;  // row-pair slots of the general kernel's ring
-    {
-        const int strips = (d->nx + init_w - 1) / init_w;
-        const int64_t chunks = std::max<int64_t>(1, (2 * 152) / strips);
-        int64_t rows = (d->ny + chunks - 1) / chunks;
-        rows = std::min<int64_t>(std::max<int64_t>(rows, 16), d->ny);
-        c->chunk_rows = int(rows);
-        c->tiles_x = strips;
-        c->tiles_y = int((d->ny + rows - 1) / rows);
-    }
-
     // plane layout: kPadCols columns / kPadRows rows of padding on each side,
     // pitch a multiple of 64 elements covering the widest bulk-copied row
-    // segment (a strip may start as far right as nx - 2, the right edge band)
-    const int64_t seg_end = int64_t(d->nx) + init_w + 4 + kSegExtra;
-    int64_t need = kPadCols + std::max<int64_t>(seg_end, int64_t(init_w) + 4 + kSegExtra + 8) + 16;
+    // segment of the interior kernel (a strip may start as far right as
+    // nx - 2 - kInteriorW; its segment spans kInteriorW + 4 + kSegExtra
+    // elements from 8 columns left of the strip)
+    const int64_t seg_end = int64_t(d->nx) + kInteriorW + 4 + kSegExtra;
+    int64_t need = kPadCols + std::max<int64_t>(seg_end, int64_t(kInteriorW) + 4 + kSegExtra + 8) + 16;
     c->pitch = (need + 63) / 64 * 64;
     c->plane = c->pitch * (int64_t(d->ny) + 2 * kPadRows);
 
@@ -561,7 +547,7 @@ lbm_status lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double out[4]) {
     if (!guard.ok) return fail_cuda(c, cudaErrorInvalidDevice);
     st = ensure_initialized(c);
     if (st != LBM_OK) return st;
-    if (!c->planned) build_plan(c);
+    if (!c->planned) LBM_CUDA(c, build_plan(c));
     // events e[2k] before step k's interior launch, e[2k+1] between its two
     // launches, e[2k+2] after its band launch
     const int64_t nev = 2 * nsteps + 1;
@@ -577,7 +563,7 @@ lbm_status lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double out[4]) {
         const StepParams p = make_params(c, c->parity);
         err = launch_interior_part(c, p, fields);
         if (err == cudaSuccess) err = cudaEventRecord(ev[2 * k + 1], c->stream);
-        if (err == cudaSuccess) err = launch_band_part(c, p, fields);
+        if (err == cudaSuccess) err = launch_band_part(c, c->parity, fields);
         if (err == cudaSuccess) err = cudaEventRecord(ev[2 * k + 2], c->stream);
         if (err == cudaSuccess) {
             c->parity ^= 1;

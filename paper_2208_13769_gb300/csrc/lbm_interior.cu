@@ -1,9 +1,14 @@
 // lbm_interior.cu -- the fused step for the interior of the body.
 //
+// One launch advances the body from t_n to t_n+1 (Algorithm 1 of arXiv
+// 2208.13769, with the paper's footnote predictor for u).  1S at a node needs
+// P + Pbar on its 4 neighbours, which need u on a 2-node halo, which needs the
+// streamed populations there.
+//
 // Every node at least 2 nodes from a bounded edge (3 from a periodic seam)
 // needs none of the boundary machinery: no ghost rule in Grad u or Div Q, no
 // bounced population, no periodic image.  This kernel advances exactly those
-// nodes; the general kernel of lbm_step.cu advances the thin bands along the
+// nodes; the edge kernel of lbm_edge.cu advances the thin bands along the
 // edges in the same step (both read the same source buffers and write
 // disjoint nodes).
 //
@@ -17,8 +22,18 @@
 // The 9 population segments of each row arrive in a ring of shared-memory
 // slots by bulk asynchronous copies (cp.async.bulk, one mbarrier per slot)
 // issued D rows ahead of stage A; the two carries are prefetched one row
-// ahead into registers.  u* and Q live in 3-row rolling buffers.  The same
-// lattice-unit arithmetic as the general kernel (see lbm_step.cu).
+// ahead into registers.  u* and Q live in 3-row rolling buffers.
+//
+// Lattice units inside the kernels: m = sum_i e_i f_i, Pf = sum_i e_i e_i f_i,
+// s = (dt / c) 1S, jh = j / c, so that the equilibrium (Sec. 5) reads
+//   f_i^eq = w_i [ r (2 - 3/2 |e_i|^2) + 3 e_i.jh + 3/2 (3 e_i.Pf.e_i - tr Pf) ]
+// and no rounded physical constant enters the lattice dynamics.
+//
+// State per node (two ping-pong copies):
+//   f^col_i                                    (9 planes, storage type)
+//   A = u_n + dX/(2 rho0) (jh_n + s_n / 2)     (u-carry, 2 comps)
+//   s_n                                        (source carry, 2 comps)
+// so that u*_n+1 = A + dX/(2 rho0) m  and  jh_n+1 = m + s_(n+1 or n) / 2.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -64,7 +79,7 @@ __global__ void __launch_bounds__(NT, MINB) interior_step_kernel(const __grid_co
     k.load(p);
     const int64_t pitch = p.pitch, plane = p.plane;
     const int t = threadIdx.x;
-    const int rx0 = p.rect[0][0], rx1 = p.rect[0][1], ry0 = p.rect[0][2], ry1 = p.rect[0][3];
+    const int rx0 = p.rect[0], rx1 = p.rect[1], ry0 = p.rect[2], ry1 = p.rect[3];
     if (int(blockIdx.x) * W >= rx1 - rx0 || int(blockIdx.y) * p.chunk_rows >= ry1 - ry0) return;
     int x0 = rx0 + int(blockIdx.x) * W;
     if (x0 > rx1 - W) x0 = rx1 - W > rx0 ? rx1 - W : rx0;

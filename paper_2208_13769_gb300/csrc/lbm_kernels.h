@@ -16,19 +16,38 @@ enum Format : int {
     kFmtBF16 = 4   // BF16 / FP32 / compensated FP32 pair
 };
 
-// Output columns per strip: general kernel at initialisation, general
-// kernel on the edge bands, interior kernel.
-void strip_widths(int* init_w, int* band_w, int* interior_w);
-
 
 // The interior kernel (lbm_interior.cu): nodes of p.rect[0] only, which must
 // lie at least 2 nodes from bounded edges and 3 from periodic seams.
 size_t interior_smem(int fmt, int ring_slots);
 cudaError_t launch_interior(int fmt, const StepParams& p, cudaStream_t s, bool fields);
 
-// One fused step (mode 0) or the initialisation (mode 1); fields: also write
-// u, v, r to p.fields.
-cudaError_t launch_fused_step(int fmt, const StepParams& p, cudaStream_t s, int mode, bool fields);
+// The edge kernel (lbm_edge.cu): small 2-D tiles with every boundary rule.
+// A tile's threads cover its output nodes and a 2-node halo: tw x
+// (kEdgeThreads / tw) nodes, (tw - 4) x (kEdgeThreads / tw - 4) of them output.
+constexpr int kEdgeThreads = 256;
+
+struct EdgeTile {
+    int32_t inst;    // entry of the parameter table
+    int32_t x0, y0;  // first output node
+    int32_t x1, y1;  // one past the last output node
+    int16_t tw;      // threads along x: 32 (wide tile) or 8 (narrow tile)
+    int16_t lead;    // this tile advances the instance's step counter
+};
+
+struct EdgeLaunch {
+    const StepParams* params;  // device table, indexed by EdgeTile::inst
+    const EdgeTile* tiles;     // device tile list; NULL: wide tiles over rect
+    int32_t fields;            // also write u, v, r to params.fields
+    int32_t rtiles_x;          // implicit grid: tiles per row of rect
+    int32_t rect[4];           // implicit grid: x_lo, x_hi, y_lo, y_hi
+};
+
+// One step (mode 0) or the initialisation (mode 1) over ntiles tiles.
+cudaError_t launch_edge(int fmt, const EdgeLaunch& L, int ntiles, cudaStream_t s, int mode);
+
+// Tiles of one band rectangle (count only when out is NULL).
+int edge_tiles_of_rect(const int rect[4], int inst, EdgeTile* out, int cap, bool lead_first);
 
 // Read-out parameters: stresses from the FP64 displacement field.
 struct ReadoutParams {

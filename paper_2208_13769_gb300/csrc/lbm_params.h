@@ -1,6 +1,6 @@
 // lbm_params.h -- parameter blocks shared by the host library and the
 // kernels of the fused Lagrangian LBM step (plain C++ structs, passed by
-// value as kernel arguments).
+// value as kernel arguments or kept in device tables).
 #pragma once
 
 #include <stdint.h>
@@ -32,19 +32,15 @@ struct EdgeBC {
 struct StepParams {
     // geometry (see kPadRows / kPadCols)
     int32_t nx, ny;
-    int32_t ring_slots;  // row-pair slots of the bulk-copy ring (lookahead + 3)
     int32_t periodic_x, periodic_y;
-    int32_t scheme;  // 0 explicit (Algorithm 1), 1 predictor-corrector
     int64_t pitch;   // elements per row (storage or carry element type)
     int64_t plane;   // elements per plane
-    int32_t tiles_x, tiles_y;  // grid: column strips x row chunks
-    int32_t chunk_rows;        // rows per chunk (>= 3)
-    int32_t nrect;             // rectangles of output nodes
-    int32_t rect[4][4];        // x_lo, x_hi, y_lo, y_hi of each rectangle
-    int32_t tile_base[5];      // general kernel: first CTA of each rectangle in a 1-D grid
-    int32_t rect_strips[4];    // general kernel: column strips of each rectangle
-    int32_t write_counter;     // this launch advances the step counter
-    int32_t pad0;
+    int32_t scheme;  // 0 explicit (Algorithm 1), 1 predictor-corrector
+    // interior kernel: output rectangle, its grid and its row ring
+    int32_t rect[4];     // x_lo, x_hi, y_lo, y_hi
+    int32_t tiles_x, tiles_y;  // column strips x row chunks
+    int32_t chunk_rows;        // rows per chunk
+    int32_t ring_slots;        // row slots of the bulk-copy ring (lookahead + 3)
 
     const void* f_src;  // 9 planes of f^col(t_n), storage type
     void* f_dst;        // 9 planes of f^col(t_n+1)

@@ -12,7 +12,6 @@ namespace lbm {
 
 namespace {
 
-constexpr int kDepth = 5;               // rows held by the u* and Q rolling buffers
 constexpr uint32_t kSpinLimit = 1u << 22;  // bounded mbarrier polling
 
 __device__ __forceinline__ int wrap_coord(int g, int n) {
@@ -183,14 +182,6 @@ __device__ __forceinline__ void store_img(T* base, const Geo& g, int x, int y, T
         if (ix) base[g.at(x + ix, y - g.ny)] = v;
         if (g.perx && x < 3 && x >= g.nx - 3) base[g.at(x - g.nx, y - g.ny)] = v;
     }
-}
-
-// Bytes of shared memory before the bulk-copy ring: 256 for the mbarriers,
-// u* (3 pair slots x 2 rows x 2 comps x NT), Q (3 x 2 x 4 x NT) and, for the
-// initialisation, the same again for r0 and Pbar(Grad u0).
-template <class UT, class TC, int NT>
-__host__ __device__ constexpr size_t step_smem_fixed(int mode) {
-    return (256 + sizeof(UT) * 12 * NT + sizeof(TC) * 24 * NT * (mode == 1 ? 2 : 1) + 127) / 128 * 128;
 }
 
 }  // namespace

@@ -39,6 +39,10 @@ def _cases():
                                                        seed=15, amp=0.01, lam=0.45), 300),
         "tiny_3x3_neumann": (W.smooth_random(3, 3, [N0] * 4, seed=16, amp=0.02, lam=0.3, mu=0.3), 50),
         "tiny_4x5_mixed": (W.smooth_random(4, 5, [D0, N0, N0, D0], seed=17, amp=0.02, lam=0.3, mu=0.3), 50),
+        # ragged edge tiles: one-row / one-column remainders of the tile grid
+        "small_8x5_neumann": (W.smooth_random(8, 5, [N0] * 4, seed=18, amp=0.02, lam=0.3, mu=0.3), 50),
+        "tall_4x9_mixed": (W.smooth_random(4, 9, [N0, D0, D0, N0], seed=19, amp=0.02, lam=0.3, mu=0.3), 50),
+        "ragged_33x13_mixed": (W.smooth_random(33, 13, [D0, N0, N0, D0], seed=20, amp=0.02, lam=0.3, mu=0.3), 80),
     }
     t = W.tension_block(40, T1=0.1)
     cases["tension_ramp_40"] = (t, 208)
