@@ -48,6 +48,10 @@ struct lbm_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool owns_stream = false;
+    // the edge-band launch of a step runs on a side stream, concurrently with
+    // the interior launch on the main stream (fork / join by events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaError_t last_error = cudaSuccess;
     int fmt = kFmtF32;
     int scheme = 1;
@@ -248,13 +252,13 @@ cudaError_t launch_interior_part(lbm_ctx* c, const StepParams& p, bool fields) {
 }
 
 // The edge-band launch of one time step (the whole body without an interior).
-cudaError_t launch_band_part(lbm_ctx* c, int parity, bool fields) {
+cudaError_t launch_band_part(lbm_ctx* c, int parity, bool fields, cudaStream_t st) {
     EdgeLaunch L;
     memset(&L, 0, sizeof(L));
     L.params = c->dparams + parity;
     L.tiles = c->dtiles;
     L.fields = fields ? 1 : 0;
-    return launch_edge(c->fmt, L, c->n_etiles, c->stream, 0);
+    return launch_edge(c->fmt, L, c->n_etiles, st, 0);
 }
 
 // Launches of one time step (mode 0) or the initialisation (mode 1).
@@ -274,9 +278,16 @@ cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int parity) {
         if (ntiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
         return launch_edge(c->fmt, L, int(ntiles), c->stream, 1);
     }
-    cudaError_t e = launch_interior_part(c, make_params(c, parity), fields);
-    if (e != cudaSuccess) return e;
-    return launch_band_part(c, parity, fields);
+    if (!c->has_interior) return launch_band_part(c, parity, fields, c->stream);
+    // interior first on the main stream, then the edge tiles on the side
+    // stream: the small edge CTAs fill the room the interior CTAs leave
+    cudaError_t e = cudaEventRecord(c->ev_fork, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    if (e == cudaSuccess) e = launch_interior_part(c, make_params(c, parity), fields);
+    if (e == cudaSuccess) e = launch_band_part(c, parity, fields, c->side);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    return e;
 }
 
 lbm_status launch(lbm_ctx* c, int mode, bool fields) {
@@ -348,6 +359,9 @@ void free_all(lbm_ctx* c) {
     cudaFree(c->readout);
     cudaFree(c->dparams);
     cudaFree(c->dtiles);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->owns_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -387,6 +401,14 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
             return LBM_E_CUDA;
         }
         c->owns_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return LBM_E_CUDA;
     }
     c->nx = d->nx;
     c->ny = d->ny;
@@ -563,7 +585,7 @@ lbm_status lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double out[4]) {
         const StepParams p = make_params(c, c->parity);
         err = launch_interior_part(c, p, fields);
         if (err == cudaSuccess) err = cudaEventRecord(ev[2 * k + 1], c->stream);
-        if (err == cudaSuccess) err = launch_band_part(c, c->parity, fields);
+        if (err == cudaSuccess) err = launch_band_part(c, c->parity, fields, c->stream);
         if (err == cudaSuccess) err = cudaEventRecord(ev[2 * k + 2], c->stream);
         if (err == cudaSuccess) {
             c->parity ^= 1;
