@@ -191,6 +191,50 @@ LBM_API lbm_status lbm_memory_info(const lbm_ctx* ctx, int64_t* device_bytes, in
 LBM_API lbm_status lbm_destroy(lbm_ctx* ctx);
 
 /* ------------------------------------------------------------------------
+ * Batches: many bodies advanced by shared launches.
+ *
+ * The method's step (Algorithm 1 with the boundary rules of Sec. 6) applied
+ * to several independent bodies at once: each time step is one launch over
+ * the interior tiles of every member and one over their edge tiles, so small
+ * or uneven bodies share the GPU instead of each paying its own launches;
+ * chunks of 64 steps replay as one CUDA graph.  Every member goes through
+ * the same kernels and arithmetic as when stepped alone: results are
+ * bit-identical to lbm_step on each member.
+ */
+typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
+
+/* Groups n existing contexts.  Members must be distinct, on one device, of
+ * one storage format and u-carry (scheme, material, boundaries, sizes and
+ * step counts may differ), with material and boundaries set; they are
+ * initialised here if they were not, and must outlive the batch.
+ * cuda_stream: the batch's stream (NULL: the batch owns a non-blocking one);
+ * each lbm_batch_step orders itself after work already enqueued on the
+ * members' streams and their later work after itself.  Allocates the batch's
+ * parameter table and work lists (a few hundred bytes per member and per
+ * tile).  Synchronises.  Errors: LBM_E_INVALID (n < 1, NULL or repeated
+ * member, mixed devices or formats), LBM_E_STATE (a member not ready),
+ * LBM_E_OOM, LBM_E_CUDA. */
+LBM_API lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_stream, lbm_batch** out);
+
+/* Advances every member by nsteps time steps (its step count and time too);
+ * the last step also refreshes each member's read-out fields, so
+ * lbm_read_fields / lbm_diagnostics on a member then see the new state.
+ * Asynchronous.  Errors: LBM_E_INVALID (nsteps < 0), LBM_E_STATE (a member
+ * was stepped on its own since the batch was made), LBM_E_CUDA. */
+LBM_API lbm_status lbm_batch_step(lbm_batch* batch, int64_t nsteps);
+
+/* Synchronises and writes each member's status (as lbm_sync) to status[i]
+ * (n entries; may be NULL); returns the first non-OK status, else LBM_OK. */
+LBM_API lbm_status lbm_batch_sync(lbm_batch* batch, int32_t* status);
+
+/* Batch time steps taken, and the CTAs of its interior and edge launches. */
+LBM_API lbm_status lbm_batch_get_info(const lbm_batch* batch, int64_t* steps, int32_t* interior_ctas,
+                                      int32_t* edge_ctas);
+
+/* Frees the batch (not its members; NULL is allowed).  Synchronises. */
+LBM_API lbm_status lbm_batch_destroy(lbm_batch* batch);
+
+/* ------------------------------------------------------------------------
  * Allocation-free diagnostics (no counterpart in the paper).
  *
  * For callers that cannot call cudaMalloc -- code running while a CUDA graph

@@ -9,6 +9,7 @@
 #include <new>
 
 #include "lbm.h"
+#include "lbm_context.h"
 #include "lbm_kernels.h"
 
 using namespace lbm;
@@ -17,18 +18,6 @@ namespace {
 
 constexpr int kGraphChunk = 64;  // steps per captured graph (even: keeps the ping-pong parity)
 constexpr int kInteriorW = 124;  // output columns per strip of the interior kernel (128 threads)
-
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
 size_t elem_size_storage(int fmt) {
     switch (fmt) {
@@ -44,65 +33,7 @@ int ucarry_planes(int fmt) { return (fmt == kFmtF64 || fmt == kFmtF32) ? 1 : 2; 
 
 }  // namespace
 
-struct lbm_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool owns_stream = false;
-    // the edge-band launch of a step runs on a side stream, concurrently with
-    // the interior launch on the main stream (fork / join by events)
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    cudaError_t last_error = cudaSuccess;
-    int fmt = kFmtF32;
-    int scheme = 1;
-    int32_t nx = 0, ny = 0;
-    double dX = 1.0;
-    int32_t f16_scale_log2 = 10;
-    // layout
-    int64_t pitch = 0, plane = 0;
-    // device memory
-    void* f[2] = {nullptr, nullptr};
-    void* a[2] = {nullptr, nullptr};
-    void* s[2] = {nullptr, nullptr};
-    double* fields = nullptr;
-    double* u0 = nullptr;
-    double* v0 = nullptr;
-    int32_t* flag = nullptr;
-    int64_t* counter = nullptr;
-    double* partials = nullptr;
-    double* diag = nullptr;
-    double* readout = nullptr;
-    size_t readout_cap = 0;
-    int diag_blocks = 1;
-    int64_t device_bytes = 0;
-    // problem
-    bool material_set = false;
-    bool bc_set[4] = {false, false, false, false};
-    EdgeBC bc[4];
-    double lambda = 0, mu = 0, rho0 = 0, omega = 1, body[2] = {0, 0};
-    double dt = 0, c = 0, cs2 = 0;
-    // progress
-    bool initialized = false;
-    int parity = 0;
-    int64_t steps = 0;
-    bool sticky = false;
-    bool variant_warm = false;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    // launch plan (built at initialisation, once the boundaries are known)
-    bool planned = false;
-    bool has_interior = false;
-    int irect[4] = {0, 0, 0, 0};
-    int i_tiles_x = 0, i_tiles_y = 0, i_chunk = 0, i_ring = 0;
-    int nband = 0;
-    int brect[4][4];
-    StepParams* dparams = nullptr;  // device: make_params(parity 0), make_params(parity 1)
-    EdgeTile* dtiles = nullptr;     // device: tiles of the edge bands
-    int n_etiles = 0;
-};
-
-namespace {
-
-lbm_status fail_cuda(lbm_ctx* ctx, cudaError_t e) {
+lbm_status lbm::ctx_fail_cuda(lbm_ctx* ctx, cudaError_t e) {
     if (ctx) {
         ctx->sticky = true;
         ctx->last_error = e;
@@ -113,10 +44,10 @@ lbm_status fail_cuda(lbm_ctx* ctx, cudaError_t e) {
 #define LBM_CUDA(ctx, call)                          \
     do {                                             \
         cudaError_t e_ = (call);                     \
-        if (e_ != cudaSuccess) return fail_cuda((ctx), e_); \
+        if (e_ != cudaSuccess) return ctx_fail_cuda((ctx), e_); \
     } while (0)
 
-StepParams make_params(const lbm_ctx* c, int parity) {
+StepParams lbm::make_params(const lbm_ctx* c, int parity) {
     StepParams p;
     memset(&p, 0, sizeof(p));
     p.nx = c->nx;
@@ -158,7 +89,7 @@ StepParams make_params(const lbm_ctx* c, int parity) {
     return p;
 }
 
-ReadoutParams make_readout(const lbm_ctx* c) {
+static ReadoutParams make_readout(const lbm_ctx* c) {
     ReadoutParams r;
     memset(&r, 0, sizeof(r));
     r.nx = c->nx;
@@ -175,7 +106,7 @@ ReadoutParams make_readout(const lbm_ctx* c) {
     return r;
 }
 
-lbm_status ready(const lbm_ctx* c) {
+lbm_status lbm::ctx_ready(const lbm_ctx* c) {
     if (!c) return LBM_E_INVALID;
     if (c->sticky) return LBM_E_CUDA;
     if (!c->material_set) return LBM_E_STATE;
@@ -188,7 +119,7 @@ lbm_status ready(const lbm_ctx* c) {
 // seams) for the lean kernel, the bands around it as tiles of the edge
 // kernel; the parameter table of both parities and the tile list go to the
 // device.
-cudaError_t build_plan(lbm_ctx* c) {
+static cudaError_t build_plan(lbm_ctx* c) {
     const bool perx = c->bc[0].kind == kPeriodic, pery = c->bc[2].kind == kPeriodic;
     const int bx = perx ? 3 : 2, by = pery ? 3 : 2;
     const int nx = c->nx, ny = c->ny;
@@ -240,7 +171,7 @@ cudaError_t build_plan(lbm_ctx* c) {
 }
 
 // The interior launch of one time step (nothing if the body has no interior).
-cudaError_t launch_interior_part(lbm_ctx* c, const StepParams& p, bool fields) {
+static cudaError_t launch_interior_part(lbm_ctx* c, const StepParams& p, bool fields) {
     if (!c->has_interior) return cudaSuccess;
     StepParams pi = p;
     for (int k = 0; k < 4; ++k) pi.rect[k] = c->irect[k];
@@ -252,7 +183,7 @@ cudaError_t launch_interior_part(lbm_ctx* c, const StepParams& p, bool fields) {
 }
 
 // The edge-band launch of one time step (the whole body without an interior).
-cudaError_t launch_band_part(lbm_ctx* c, int parity, bool fields, cudaStream_t st) {
+static cudaError_t launch_band_part(lbm_ctx* c, int parity, bool fields, cudaStream_t st) {
     EdgeLaunch L;
     memset(&L, 0, sizeof(L));
     L.params = c->dparams + parity;
@@ -262,7 +193,7 @@ cudaError_t launch_band_part(lbm_ctx* c, int parity, bool fields, cudaStream_t s
 }
 
 // Launches of one time step (mode 0) or the initialisation (mode 1).
-cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int parity) {
+static cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int parity) {
     if (mode == 1) {
         EdgeLaunch L;
         memset(&L, 0, sizeof(L));
@@ -290,7 +221,7 @@ cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int parity) {
     return e;
 }
 
-lbm_status launch(lbm_ctx* c, int mode, bool fields) {
+static lbm_status launch(lbm_ctx* c, int mode, bool fields) {
     if (!c->planned) LBM_CUDA(c, build_plan(c));
     LBM_CUDA(c, launch_step_kernels(c, mode, fields, c->parity));
     c->parity ^= 1;
@@ -298,7 +229,7 @@ lbm_status launch(lbm_ctx* c, int mode, bool fields) {
     return LBM_OK;
 }
 
-lbm_status ensure_initialized(lbm_ctx* c) {
+lbm_status lbm::ctx_ensure_initialized(lbm_ctx* c) {
     if (c->initialized) return LBM_OK;
     lbm_status st = launch(c, 1, true);
     if (st != LBM_OK) return st;
@@ -307,7 +238,7 @@ lbm_status ensure_initialized(lbm_ctx* c) {
 }
 
 // A graph of kGraphChunk plain steps starting at parity `par`.
-lbm_status get_graph(lbm_ctx* c, int par, cudaGraphExec_t* out) {
+static lbm_status get_graph(lbm_ctx* c, int par, cudaGraphExec_t* out) {
     if (c->graph[par]) {
         *out = c->graph[par];
         return LBM_OK;
@@ -319,13 +250,13 @@ lbm_status get_graph(lbm_ctx* c, int par, cudaGraphExec_t* out) {
     cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
     if (err != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
-        return fail_cuda(c, err);
+        return ctx_fail_cuda(c, err);
     }
-    if (e2 != cudaSuccess) return fail_cuda(c, e2);
+    if (e2 != cudaSuccess) return ctx_fail_cuda(c, e2);
     cudaGraphExec_t ex = nullptr;
     err = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
-    if (err != cudaSuccess) return fail_cuda(c, err);
+    if (err != cudaSuccess) return ctx_fail_cuda(c, err);
     c->graph[par] = ex;
     *out = ex;
     return LBM_OK;
@@ -333,16 +264,16 @@ lbm_status get_graph(lbm_ctx* c, int par, cudaGraphExec_t* out) {
 
 // Device flag bits: 1 non-finite value or J <= 0; 4 a bounded wait gave up;
 // 8 a bulk copy was refused for misalignment (an internal error).
-lbm_status check_flag(lbm_ctx* c) {
+lbm_status lbm::ctx_check_flag(lbm_ctx* c) {
     int32_t h = 0;
     LBM_CUDA(c, cudaMemcpyAsync(&h, c->flag, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (h & 8) return fail_cuda(c, cudaErrorMisalignedAddress);
+    if (h & 8) return ctx_fail_cuda(c, cudaErrorMisalignedAddress);
     if (h & 4) return LBM_E_TIMEOUT;
     return (h & 1) ? LBM_E_UNSTABLE : LBM_OK;
 }
 
-void free_all(lbm_ctx* c) {
+static void free_all(lbm_ctx* c) {
     for (int k = 0; k < 2; ++k) {
         if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
         cudaFree(c->f[k]);
@@ -365,9 +296,9 @@ void free_all(lbm_ctx* c) {
     if (c->owns_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
-bool finite_pair(const double* v) { return v == nullptr || (isfinite(v[0]) && isfinite(v[1])); }
+static bool finite_pair(const double* v) { return v == nullptr || (isfinite(v[0]) && isfinite(v[1])); }
 
-}  // namespace
+
 
 extern "C" {
 
@@ -530,12 +461,12 @@ lbm_status lbm_set_boundary(lbm_ctx* c, int32_t edge, int32_t kind, const double
 }
 
 lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
-    lbm_status st = ready(c);
+    lbm_status st = ctx_ready(c);
     if (st != LBM_OK) return st;
     if (nsteps < 0) return LBM_E_INVALID;
     DeviceGuard guard(c->device);
-    if (!guard.ok) return fail_cuda(c, cudaErrorInvalidDevice);
-    st = ensure_initialized(c);
+    if (!guard.ok) return ctx_fail_cuda(c, cudaErrorInvalidDevice);
+    st = ctx_ensure_initialized(c);
     if (st != LBM_OK || nsteps == 0) return st;
     int64_t left = nsteps;
     // plain launches until the variant is warm (attributes set outside capture)
@@ -562,12 +493,12 @@ lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
 }
 
 lbm_status lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double out[4]) {
-    lbm_status st = ready(c);
+    lbm_status st = ctx_ready(c);
     if (st != LBM_OK) return st;
     if (nsteps < 1 || nsteps > 4096 || !out) return LBM_E_INVALID;
     DeviceGuard guard(c->device);
-    if (!guard.ok) return fail_cuda(c, cudaErrorInvalidDevice);
-    st = ensure_initialized(c);
+    if (!guard.ok) return ctx_fail_cuda(c, cudaErrorInvalidDevice);
+    st = ctx_ensure_initialized(c);
     if (st != LBM_OK) return st;
     if (!c->planned) LBM_CUDA(c, build_plan(c));
     // events e[2k] before step k's interior launch, e[2k+1] between its two
@@ -605,10 +536,10 @@ lbm_status lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double out[4]) {
     }
     for (int64_t q = 0; q < made; ++q) cudaEventDestroy(ev[q]);
     delete[] ev;
-    if (err != cudaSuccess) return fail_cuda(c, err);
+    if (err != cudaSuccess) return ctx_fail_cuda(c, err);
     for (int q = 0; q < 3; ++q) out[q] = sum[q] / double(counted);
     out[3] = c->has_interior ? double(c->irect[1] - c->irect[0]) * double(c->irect[3] - c->irect[2]) : 0.0;
-    return check_flag(c);
+    return ctx_check_flag(c);
 }
 
 int64_t lbm_fields_size(const lbm_ctx* c, uint32_t mask) {
@@ -621,13 +552,13 @@ int64_t lbm_fields_size(const lbm_ctx* c, uint32_t mask) {
 }
 
 lbm_status lbm_read_fields(lbm_ctx* c, uint32_t mask, double* out, int64_t out_len, double* t_out) {
-    lbm_status st = ready(c);
+    lbm_status st = ctx_ready(c);
     if (st != LBM_OK) return st;
     const int64_t need = lbm_fields_size(c, mask);
     if (need == 0 || !out || out_len < need) return LBM_E_INVALID;
     DeviceGuard guard(c->device);
-    if (!guard.ok) return fail_cuda(c, cudaErrorInvalidDevice);
-    st = ensure_initialized(c);
+    if (!guard.ok) return ctx_fail_cuda(c, cudaErrorInvalidDevice);
+    st = ctx_ensure_initialized(c);
     if (st != LBM_OK) return st;
     const size_t bytes = size_t(need) * sizeof(double);
     if (bytes > c->readout_cap) {
@@ -646,22 +577,22 @@ lbm_status lbm_read_fields(lbm_ctx* c, uint32_t mask, double* out, int64_t out_l
     LBM_CUDA(c, launch_readout(rp, mask, c->readout, c->stream));
     LBM_CUDA(c, cudaMemcpyAsync(out, c->readout, bytes, cudaMemcpyDeviceToHost, c->stream));
     if (t_out) *t_out = double(c->steps) * c->dt;
-    return check_flag(c);
+    return ctx_check_flag(c);
 }
 
 lbm_status lbm_diagnostics(lbm_ctx* c, double out[6]) {
-    lbm_status st = ready(c);
+    lbm_status st = ctx_ready(c);
     if (st != LBM_OK) return st;
     if (!out) return LBM_E_INVALID;
     DeviceGuard guard(c->device);
-    if (!guard.ok) return fail_cuda(c, cudaErrorInvalidDevice);
-    st = ensure_initialized(c);
+    if (!guard.ok) return ctx_fail_cuda(c, cudaErrorInvalidDevice);
+    st = ctx_ensure_initialized(c);
     if (st != LBM_OK) return st;
     ReadoutParams rp = make_readout(c);
     LBM_CUDA(c, launch_diagnostics(rp, c->partials, c->diag_blocks, c->diag, c->stream));
     double h[8];
     LBM_CUDA(c, cudaMemcpyAsync(h, c->diag, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-    st = check_flag(c);
+    st = ctx_check_flag(c);
     for (int q = 0; q < 6; ++q) out[q] = h[q];
     return st;
 }
@@ -670,8 +601,8 @@ lbm_status lbm_sync(lbm_ctx* c) {
     if (!c) return LBM_E_INVALID;
     if (c->sticky) return LBM_E_CUDA;
     DeviceGuard guard(c->device);
-    if (!guard.ok) return fail_cuda(c, cudaErrorInvalidDevice);
-    return check_flag(c);
+    if (!guard.ok) return ctx_fail_cuda(c, cudaErrorInvalidDevice);
+    return ctx_check_flag(c);
 }
 
 lbm_status lbm_get_info(const lbm_ctx* c, int64_t* steps, double* dt) {

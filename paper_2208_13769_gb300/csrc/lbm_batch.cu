@@ -1,0 +1,349 @@
+// lbm_batch.cu -- many bodies advanced by shared launches (the C ABI's
+// lbm_batch_* entry points).
+//
+// Each time step of a batch is one launch of the interior kernel over the
+// work list of every member's interior tiles and one launch of the edge
+// kernel over every member's edge tiles (concurrent, on two streams), each
+// CTA reading its body's parameters from a device table.  So small and
+// uneven bodies share the GPU instead of each paying a launch per step, and
+// chunks of 64 steps replay as one CUDA graph.  Every node of every member
+// goes through the same kernels and arithmetic as when the member is
+// stepped alone, so the results are bit-identical.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_context.h"
+#include "lbm_kernels.h"
+
+using namespace lbm;
+
+namespace {
+
+constexpr int kBatchGraphChunk = 64;  // steps per captured graph (even)
+constexpr int kBatchStripW = 124;     // output columns per interior strip
+constexpr int kBatchRing = 7;         // interior row ring (lookahead 4)
+
+}  // namespace
+
+struct lbm_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool owns_stream = false;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_sync = nullptr;
+    std::vector<lbm_ctx*> m;
+    std::vector<int> base_parity;  // member parity when the batch step count is even
+    int fmt = 0;
+    StepParams* dtab = nullptr;  // [2][n]: entry q * n + i = member i at parity base_parity[i] ^ q
+    InteriorWork* dwork = nullptr;
+    int n_work = 0;
+    EdgeTile* dedge = nullptr;
+    int n_edge = 0;
+    int chunk_rows = 0;
+    int64_t steps = 0;
+    bool warm = false;
+    bool sticky = false;
+    cudaError_t last_error = cudaSuccess;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+lbm_status batch_fail(lbm_batch* b, cudaError_t e) {
+    b->sticky = true;
+    b->last_error = e;
+    return LBM_E_CUDA;
+}
+
+#define BATCH_CUDA(b, call)                              \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return batch_fail((b), e_); \
+    } while (0)
+
+void batch_free(lbm_batch* b) {
+    for (int k = 0; k < 2; ++k)
+        if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+    cudaFree(b->dtab);
+    cudaFree(b->dwork);
+    cudaFree(b->dedge);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->ev_sync) cudaEventDestroy(b->ev_sync);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->owns_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+// One batch time step from table parity q.
+cudaError_t batch_launch(lbm_batch* b, int q, bool fields) {
+    const int n = int(b->m.size());
+    InteriorLaunch il;
+    memset(&il, 0, sizeof(il));
+    il.params = b->dtab + size_t(q) * n;
+    il.work = b->dwork;
+    il.fields = fields ? 1 : 0;
+    EdgeLaunch el;
+    memset(&el, 0, sizeof(el));
+    el.params = b->dtab + size_t(q) * n;
+    el.tiles = b->dedge;
+    el.fields = fields ? 1 : 0;
+    if (b->n_work == 0) return launch_edge(b->fmt, el, b->n_edge, b->stream, 0);
+    cudaError_t e = cudaEventRecord(b->ev_fork, b->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+    if (e == cudaSuccess) e = launch_interior_batch(b->fmt, il, b->n_work, kBatchRing, b->stream);
+    if (e == cudaSuccess) e = launch_edge(b->fmt, el, b->n_edge, b->side, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+    return e;
+}
+
+void advance_members(lbm_batch* b, int64_t k) {
+    for (lbm_ctx* c : b->m) {
+        c->steps += k;
+        if (k & 1) c->parity ^= 1;
+    }
+    b->steps += k;
+}
+
+lbm_status batch_graph(lbm_batch* b, int q, cudaGraphExec_t* out) {
+    if (b->graph[q]) {
+        *out = b->graph[q];
+        return LBM_OK;
+    }
+    cudaGraph_t g = nullptr;
+    BATCH_CUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < kBatchGraphChunk && err == cudaSuccess; ++k) err = batch_launch(b, q ^ (k & 1), false);
+    const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (err != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return batch_fail(b, err);
+    }
+    if (e2 != cudaSuccess) return batch_fail(b, e2);
+    cudaGraphExec_t ex = nullptr;
+    err = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (err != cudaSuccess) return batch_fail(b, err);
+    b->graph[q] = ex;
+    *out = ex;
+    return LBM_OK;
+}
+
+// Orders `waiter` after the work enqueued so far on `s`.
+cudaError_t stream_after(cudaStream_t waiter, cudaStream_t s, cudaEvent_t ev) {
+    if (waiter == s) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(ev, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(waiter, ev, 0);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_stream, lbm_batch** out) {
+    if (!out) return LBM_E_INVALID;
+    *out = nullptr;
+    if (!members || n < 1) return LBM_E_INVALID;
+    for (int i = 0; i < n; ++i) {
+        if (!members[i]) return LBM_E_INVALID;
+        for (int j = 0; j < i; ++j)
+            if (members[j] == members[i]) return LBM_E_INVALID;
+        if (members[i]->device != members[0]->device || members[i]->fmt != members[0]->fmt) return LBM_E_INVALID;
+        const lbm_status st = ctx_ready(members[i]);
+        if (st != LBM_OK) return st;
+    }
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return LBM_E_OOM;
+    b->device = members[0]->device;
+    b->fmt = members[0]->fmt;
+    DeviceGuard guard(b->device);
+    if (!guard.ok) {
+        delete b;
+        return LBM_E_INVALID;
+    }
+    try {
+        b->m.assign(members, members + n);
+        b->base_parity.resize(size_t(n));
+    } catch (...) {
+        delete b;
+        return LBM_E_OOM;
+    }
+    // every member planned and initialised, its work finished
+    for (int i = 0; i < n; ++i) {
+        lbm_status st = ctx_ensure_initialized(members[i]);
+        if (st == LBM_OK) st = ctx_check_flag(members[i]);
+        if (st != LBM_OK && st != LBM_E_UNSTABLE) {
+            delete b;
+            return st;
+        }
+        b->base_parity[size_t(i)] = members[i]->parity;
+    }
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaSuccess;
+    if (!b->stream) {
+        e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        b->owns_stream = e == cudaSuccess;
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_sync, cudaEventDisableTiming);
+
+    // interior tiles: rows per chunk so that the batch holds about four waves
+    // of 4 CTAs per SM (at least 32 rows, at most 256)
+    int64_t interior_nodes = 0;
+    for (lbm_ctx* c : b->m)
+        if (c->has_interior)
+            interior_nodes += int64_t(c->irect[1] - c->irect[0]) * (c->irect[3] - c->irect[2]);
+    b->chunk_rows = int(std::min<int64_t>(256, std::max<int64_t>(32, interior_nodes / (int64_t(kBatchStripW) * 152 * 4 * 4))));
+    std::vector<StepParams> tab;
+    std::vector<InteriorWork> work;
+    std::vector<EdgeTile> tiles;
+    try {
+        tab.resize(size_t(2) * n);
+        for (int q = 0; q < 2; ++q)
+            for (int i = 0; i < n; ++i) {
+                lbm_ctx* c = b->m[size_t(i)];
+                StepParams p = make_params(c, b->base_parity[size_t(i)] ^ q);
+                for (int k = 0; k < 4; ++k) p.rect[k] = c->irect[k];
+                p.chunk_rows = b->chunk_rows;
+                p.ring_slots = kBatchRing;
+                tab[size_t(q) * n + i] = p;
+            }
+        for (int i = 0; i < n; ++i) {
+            lbm_ctx* c = b->m[size_t(i)];
+            if (c->has_interior) {
+                const int w = c->irect[1] - c->irect[0], h = c->irect[3] - c->irect[2];
+                const int sx = (w + kBatchStripW - 1) / kBatchStripW, sy = (h + b->chunk_rows - 1) / b->chunk_rows;
+                for (int by = 0; by < sy; ++by)
+                    for (int bx = 0; bx < sx; ++bx) work.push_back(InteriorWork{i, bx, by, 0});
+            }
+            bool first = true;
+            for (int r = 0; r < c->nband; ++r) {
+                const int cnt = edge_tiles_of_rect(c->brect[r], i, nullptr, 0, false);
+                const size_t at = tiles.size();
+                tiles.resize(at + size_t(cnt));
+                edge_tiles_of_rect(c->brect[r], i, tiles.data() + at, cnt, first);
+                first = first && cnt == 0;
+            }
+        }
+    } catch (...) {
+        batch_free(b);
+        delete b;
+        return LBM_E_OOM;
+    }
+    if (work.size() > 0x7fffffff || tiles.size() > 0x7fffffff) e = cudaErrorInvalidValue;
+    b->n_work = int(work.size());
+    b->n_edge = int(tiles.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->dtab, sizeof(StepParams) * tab.size());
+    if (e == cudaSuccess && b->n_work) e = cudaMalloc(&b->dwork, sizeof(InteriorWork) * work.size());
+    if (e == cudaSuccess && b->n_edge) e = cudaMalloc(&b->dedge, sizeof(EdgeTile) * tiles.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->dtab, tab.data(), sizeof(StepParams) * tab.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && b->n_work)
+        e = cudaMemcpyAsync(b->dwork, work.data(), sizeof(InteriorWork) * work.size(), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess && b->n_edge)
+        e = cudaMemcpyAsync(b->dedge, tiles.data(), sizeof(EdgeTile) * tiles.size(), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host tables die with this scope
+    // sets the interior batch kernel's shared-memory limit outside any capture
+    if (e == cudaSuccess) {
+        InteriorLaunch il;
+        memset(&il, 0, sizeof(il));
+        e = launch_interior_batch(b->fmt, il, 0, kBatchRing, b->stream);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        batch_free(b);
+        delete b;
+        return e == cudaErrorMemoryAllocation ? LBM_E_OOM : LBM_E_CUDA;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
+    if (!b) return LBM_E_INVALID;
+    if (b->sticky) return LBM_E_CUDA;
+    if (nsteps < 0) return LBM_E_INVALID;
+    const int n = int(b->m.size());
+    for (int i = 0; i < n; ++i) {
+        lbm_ctx* c = b->m[size_t(i)];
+        if (c->sticky) return LBM_E_CUDA;
+        // a member stepped on its own since the batch was made is out of phase
+        if (c->parity != (b->base_parity[size_t(i)] ^ int(b->steps & 1))) return LBM_E_STATE;
+    }
+    if (nsteps == 0) return LBM_OK;
+    DeviceGuard guard(b->device);
+    if (!guard.ok) return batch_fail(b, cudaErrorInvalidDevice);
+    // the batch stream waits for work the members enqueued on their streams
+    for (lbm_ctx* c : b->m) BATCH_CUDA(b, stream_after(b->stream, c->stream, c->ev_join));
+    int64_t left = nsteps;
+    if (!b->warm && left > 1) {
+        BATCH_CUDA(b, batch_launch(b, int(b->steps & 1), false));
+        advance_members(b, 1);
+        --left;
+        b->warm = true;
+    }
+    while (left > kBatchGraphChunk) {
+        cudaGraphExec_t g;
+        const lbm_status st = batch_graph(b, int(b->steps & 1), &g);
+        if (st != LBM_OK) return st;
+        BATCH_CUDA(b, cudaGraphLaunch(g, b->stream));
+        advance_members(b, kBatchGraphChunk);
+        left -= kBatchGraphChunk;
+    }
+    while (left > 0) {
+        BATCH_CUDA(b, batch_launch(b, int(b->steps & 1), left == 1));
+        advance_members(b, 1);
+        --left;
+    }
+    // members' own streams wait for the batch before their next calls
+    BATCH_CUDA(b, cudaEventRecord(b->ev_sync, b->stream));
+    for (lbm_ctx* c : b->m)
+        if (c->stream != b->stream) BATCH_CUDA(b, cudaStreamWaitEvent(c->stream, b->ev_sync, 0));
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_sync(lbm_batch* b, int32_t* status) {
+    if (!b) return LBM_E_INVALID;
+    if (b->sticky) return LBM_E_CUDA;
+    DeviceGuard guard(b->device);
+    if (!guard.ok) return batch_fail(b, cudaErrorInvalidDevice);
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+    lbm_status worst = LBM_OK;
+    for (size_t i = 0; i < b->m.size(); ++i) {
+        const lbm_status st = ctx_check_flag(b->m[i]);
+        if (status) status[i] = st;
+        if (worst == LBM_OK) worst = st;
+    }
+    return worst;
+}
+
+lbm_status lbm_batch_get_info(const lbm_batch* b, int64_t* steps, int32_t* interior_ctas, int32_t* edge_ctas) {
+    if (!b) return LBM_E_INVALID;
+    if (steps) *steps = b->steps;
+    if (interior_ctas) *interior_ctas = b->n_work;
+    if (edge_ctas) *edge_ctas = b->n_edge;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return LBM_OK;
+    {
+        DeviceGuard guard(b->device);
+        if (b->stream) cudaStreamSynchronize(b->stream);
+        batch_free(b);
+    }
+    delete b;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+// lbm_context.h -- the solver context behind the C ABI's lbm_ctx handle, and
+// the context helpers that the single-body and the batched entry points share
+// (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm.h"
+#include "lbm_kernels.h"
+
+namespace lbm {
+
+// Makes `dev` current for the scope, restoring the previous device after.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace lbm
+
+struct lbm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool owns_stream = false;
+    // the edge-band launch of a step runs on a side stream, concurrently with
+    // the interior launch on the main stream (fork / join by events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaError_t last_error = cudaSuccess;
+    int fmt = lbm::kFmtF32;
+    int scheme = 1;
+    int32_t nx = 0, ny = 0;
+    double dX = 1.0;
+    int32_t f16_scale_log2 = 10;
+    // layout
+    int64_t pitch = 0, plane = 0;
+    // device memory
+    void* f[2] = {nullptr, nullptr};
+    void* a[2] = {nullptr, nullptr};
+    void* s[2] = {nullptr, nullptr};
+    double* fields = nullptr;
+    double* u0 = nullptr;
+    double* v0 = nullptr;
+    int32_t* flag = nullptr;
+    int64_t* counter = nullptr;
+    double* partials = nullptr;
+    double* diag = nullptr;
+    double* readout = nullptr;
+    size_t readout_cap = 0;
+    int diag_blocks = 1;
+    int64_t device_bytes = 0;
+    // problem
+    bool material_set = false;
+    bool bc_set[4] = {false, false, false, false};
+    lbm::EdgeBC bc[4];
+    double lambda = 0, mu = 0, rho0 = 0, omega = 1, body[2] = {0, 0};
+    double dt = 0, c = 0, cs2 = 0;
+    // progress
+    bool initialized = false;
+    int parity = 0;
+    int64_t steps = 0;
+    bool sticky = false;
+    bool variant_warm = false;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // launch plan (built at initialisation, once the boundaries are known)
+    bool planned = false;
+    bool has_interior = false;
+    int irect[4] = {0, 0, 0, 0};
+    int i_tiles_x = 0, i_tiles_y = 0, i_chunk = 0, i_ring = 0;
+    int nband = 0;
+    int brect[4][4];
+    lbm::StepParams* dparams = nullptr;  // device: make_params(parity 0), make_params(parity 1)
+    lbm::EdgeTile* dtiles = nullptr;     // device: tiles of the edge bands
+    int n_etiles = 0;
+};
+
+namespace lbm {
+
+// Marks the context unusable after a CUDA error; returns LBM_E_CUDA.
+lbm_status ctx_fail_cuda(lbm_ctx* c, cudaError_t e);
+// Parameters of one step from parity `parity` (source buffers of that parity).
+StepParams make_params(const lbm_ctx* c, int parity);
+// LBM_OK once material and all four boundaries are set and no CUDA error
+// occurred; LBM_E_STATE / LBM_E_CUDA / LBM_E_INVALID otherwise.
+lbm_status ctx_ready(const lbm_ctx* c);
+// Plans the launches and runs the initialisation of Algorithm 1 once.
+lbm_status ctx_ensure_initialized(lbm_ctx* c);
+// Synchronises the context's stream and maps its device flag to a status.
+lbm_status ctx_check_flag(lbm_ctx* c);
+
+}  // namespace lbm

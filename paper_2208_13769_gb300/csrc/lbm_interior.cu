@@ -57,8 +57,9 @@ __host__ __device__ constexpr size_t interior_row_bytes() {
 
 }  // namespace
 
-template <class TS, class TC, class UT, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) interior_step_kernel(const __grid_constant__ StepParams p) {
+// One tile (column strip bx, row chunk by of p.rect) of one body.
+template <class TS, class TC, class UT, int NT>
+__device__ __forceinline__ void interior_tile(const StepParams& p, int bx, int by, double* fields) {
     using CT = typename UT::Elem;
     constexpr int W = NT - 4;
     constexpr int SEG = NT + kSegExtra;
@@ -80,10 +81,10 @@ __global__ void __launch_bounds__(NT, MINB) interior_step_kernel(const __grid_co
     const int64_t pitch = p.pitch, plane = p.plane;
     const int t = threadIdx.x;
     const int rx0 = p.rect[0], rx1 = p.rect[1], ry0 = p.rect[2], ry1 = p.rect[3];
-    if (int(blockIdx.x) * W >= rx1 - rx0 || int(blockIdx.y) * p.chunk_rows >= ry1 - ry0) return;
-    int x0 = rx0 + int(blockIdx.x) * W;
+    if (bx * W >= rx1 - rx0 || by * p.chunk_rows >= ry1 - ry0) return;
+    int x0 = rx0 + bx * W;
     if (x0 > rx1 - W) x0 = rx1 - W > rx0 ? rx1 - W : rx0;
-    int y_begin = ry0 + int(blockIdx.y) * p.chunk_rows;
+    int y_begin = ry0 + by * p.chunk_rows;
     if (y_begin > ry1 - p.chunk_rows) y_begin = ry1 - p.chunk_rows > ry0 ? ry1 - p.chunk_rows : ry0;
     const int y_end = min(ry1, y_begin + p.chunk_rows);
     const int x_end = min(rx1, x0 + W);
@@ -281,14 +282,14 @@ __global__ void __launch_bounds__(NT, MINB) interior_step_kernel(const __grid_co
             }
             s_dst[o] = sn0;
             s_dst[plane + o] = sn1;
-            if (p.fields != nullptr) {
+            if (fields != nullptr) {
                 const int64_t fo = int64_t(gy) * p.nx + gx;
                 const int64_t np = int64_t(p.nx) * p.ny;
-                p.fields[fo] = ux.add(du0).to_double();
-                p.fields[np + fo] = uy.add(du1).to_double();
-                p.fields[2 * np + fo] = double(j0 * k.c_over_rho0);
-                p.fields[3 * np + fo] = double(j1 * k.c_over_rho0);
-                p.fields[4 * np + fo] = double(r);
+                fields[fo] = ux.add(du0).to_double();
+                fields[np + fo] = uy.add(du1).to_double();
+                fields[2 * np + fo] = double(j0 * k.c_over_rho0);
+                fields[3 * np + fo] = double(j1 * k.c_over_rho0);
+                fields[4 * np + fo] = double(r);
                 if (!(fabs(double(j0)) + fabs(double(j1)) < 1e300)) bad = true;
             }
         }
@@ -301,6 +302,26 @@ __global__ void __launch_bounds__(NT, MINB) interior_step_kernel(const __grid_co
         for (int s = 0; s < R; ++s)
             if (issued & (1u << s)) (void)mbar_wait(&bars[s], (phase >> s) & 1u);
     }
+}
+
+template <class TS, class TC, class UT, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) interior_step_kernel(const __grid_constant__ StepParams p) {
+    interior_tile<TS, TC, UT, NT>(p, int(blockIdx.x), int(blockIdx.y), p.fields);
+}
+
+// A batch of bodies: one CTA per work item (body, strip, chunk); the body's
+// parameters come from the device table into shared memory.
+template <class TS, class TC, class UT, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) interior_batch_kernel(const __grid_constant__ InteriorLaunch L) {
+    __shared__ __align__(16) StepParams sp;
+    const InteriorWork w = L.work[blockIdx.x];
+    {
+        const int4* src = reinterpret_cast<const int4*>(L.params + w.inst);
+        int4* dst = reinterpret_cast<int4*>(&sp);
+        for (int q = int(threadIdx.x); q < int(sizeof(StepParams) / 16); q += NT) dst[q] = src[q];
+    }
+    __syncthreads();
+    interior_tile<TS, TC, UT, NT>(sp, w.bx, w.by, L.fields ? sp.fields : nullptr);
 }
 
 template <class TS, class TC, class UT, int NT>
@@ -321,6 +342,33 @@ cudaError_t launch_interior_t(const StepParams& p, cudaStream_t s) {
     dim3 grid(p.tiles_x, p.tiles_y, 1);
     kern<<<grid, NT, sm, s>>>(p);
     return cudaGetLastError();
+}
+
+template <class TS, class TC, class UT, int NT, int MINB>
+cudaError_t launch_interior_batch_t(const InteriorLaunch& L, int nwork, int ring_slots, cudaStream_t s) {
+    auto kern = interior_batch_kernel<TS, TC, UT, NT, MINB>;
+    const size_t sm = interior_smem_bytes<TS, TC, UT, NT>(ring_slots);
+    static size_t configured = 0;
+    if (sm > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        if (e != cudaSuccess) return e;
+        configured = sm;
+    }
+    if (nwork <= 0) return cudaSuccess;
+    kern<<<nwork, NT, sm, s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interior_batch(int fmt, const InteriorLaunch& L, int nwork, int ring_slots, cudaStream_t s) {
+    switch (fmt) {
+        case kFmtF64: return launch_interior_batch_t<double, double, UPlain<double>, 128, 2>(L, nwork, ring_slots, s);
+        case kFmtF32: return launch_interior_batch_t<float, float, UPlain<float>, 128, 4>(L, nwork, ring_slots, s);
+        case kFmtF32C: return launch_interior_batch_t<float, float, UComp, 128, 4>(L, nwork, ring_slots, s);
+        case kFmtF16: return launch_interior_batch_t<__half, float, UComp, 128, 4>(L, nwork, ring_slots, s);
+        case kFmtBF16:
+            return launch_interior_batch_t<__nv_bfloat16, float, UComp, 128, 4>(L, nwork, ring_slots, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 size_t interior_smem(int fmt, int ring_slots) {

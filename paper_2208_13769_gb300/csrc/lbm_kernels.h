@@ -22,6 +22,21 @@ enum Format : int {
 size_t interior_smem(int fmt, int ring_slots);
 cudaError_t launch_interior(int fmt, const StepParams& p, cudaStream_t s, bool fields);
 
+// Interior tiles of a batch of bodies: work item = (entry of the parameter
+// table, column strip, row chunk) of that body's rect / chunk_rows.
+struct InteriorWork {
+    int32_t inst, bx, by, pad;
+};
+struct InteriorLaunch {
+    const StepParams* params;  // device table, indexed by InteriorWork::inst
+    const InteriorWork* work;  // device work list, one CTA each
+    int32_t fields;            // also write u, v, r to params.fields
+    int32_t pad;
+};
+// The setting of the dynamic shared-memory limit happens on the first call
+// (also with nwork == 0), which must precede any stream capture.
+cudaError_t launch_interior_batch(int fmt, const InteriorLaunch& L, int nwork, int ring_slots, cudaStream_t s);
+
 // The edge kernel (lbm_edge.cu): small 2-D tiles with every boundary rule.
 // A tile's threads cover its output nodes and a 2-node halo: tw x
 // (kEdgeThreads / tw) nodes, (tw - 4) x (kEdgeThreads / tw - 4) of them output.

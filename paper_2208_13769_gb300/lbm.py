@@ -79,6 +79,12 @@ _SIGNATURES = {
     "lbm_status_string": (C.c_char_p, [C.c_int]),
     "lbm_last_cuda_error": (C.c_char_p, [C.c_void_p]),
     "lbm_diagnostics_noalloc": (C.c_int, [C.POINTER(lbm_field_geometry), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lbm_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "lbm_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "lbm_batch_sync": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "lbm_batch_get_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_int32)]),
+    "lbm_batch_destroy": (C.c_int, [C.c_void_p]),
 }
 
 
@@ -200,6 +206,36 @@ def lbm_diagnostics_noalloc(geo: lbm_field_geometry, fields_dev: int, out_dev: i
                                              C.c_void_p(stream or None)))
 
 
+def lbm_batch_create(ctxs, stream: int = 0) -> C.c_void_p:
+    arr = (C.c_void_p * len(ctxs))(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    h = C.c_void_p()
+    _check(lib().lbm_batch_create(arr, len(ctxs), C.c_void_p(stream or None), C.byref(h)), "lbm_batch_create")
+    return h
+
+
+def lbm_batch_step(batch, nsteps: int):
+    return _check(lib().lbm_batch_step(batch, int(nsteps)), "lbm_batch_step")
+
+
+def lbm_batch_sync(batch, n: int) -> tuple:
+    """Returns (first non-OK status or OK, per-member statuses)."""
+    st = (C.c_int32 * n)()
+    worst = lib().lbm_batch_sync(batch, st)
+    if worst == LBM_E_CUDA:
+        raise LbmError(worst, "lbm_batch_sync")
+    return worst, [int(x) for x in st]
+
+
+def lbm_batch_get_info(batch) -> tuple:
+    s, a, b = C.c_int64(), C.c_int32(), C.c_int32()
+    _check(lib().lbm_batch_get_info(batch, C.byref(s), C.byref(a), C.byref(b)), "lbm_batch_get_info")
+    return s.value, a.value, b.value
+
+
+def lbm_batch_destroy(batch):
+    return _check(lib().lbm_batch_destroy(batch), "lbm_batch_destroy")
+
+
 def lbm_last_cuda_error(ctx) -> str:
     return lib().lbm_last_cuda_error(ctx).decode()
 
@@ -269,6 +305,42 @@ class Body:
         if getattr(self, "ctx", None) is not None:
             lbm_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several Body objects (one storage format) advanced by shared launches;
+    each member's results are bit-identical to stepping it alone."""
+
+    def __init__(self, bodies, stream: int = 0):
+        self.bodies = list(bodies)
+        self.handle = lbm_batch_create([b.ctx for b in self.bodies], stream)
+
+    def step(self, n: int) -> None:
+        lbm_batch_step(self.handle, n)
+
+    def sync(self) -> list:
+        return lbm_batch_sync(self.handle, len(self.bodies))[1]
+
+    def info(self) -> dict:
+        s, a, b = lbm_batch_get_info(self.handle)
+        return {"steps": s, "interior_ctas": a, "edge_ctas": b}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            lbm_batch_destroy(self.handle)
+            self.handle = None
 
     def __enter__(self):
         return self
