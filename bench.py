@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--forms", default="f32n,f16,bf16",
                     help="extra population formats timed on the same body ('' to skip)")
     ap.add_argument("--form-steps", type=int, default=500)
+    ap.add_argument("--batch", type=int, default=256,
+                    help="bodies of the batched workload (seeded, sides 64..1024; 0 to skip)")
+    ap.add_argument("--batch-steps", type=int, default=256)
     ap.add_argument("--cpu-steps", type=int, default=0, help="oracle sample steps (0 = auto, ~10-20 s)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -224,6 +227,8 @@ def run_reference(a):
 # ---------------------------------------------------------------- native (GPU)
 
 def time_steps(body, stream, steps):
+    """Seconds of body.step(steps) (anything with a step(n) method), by CUDA
+    events on the stream the library launches on."""
     import torch
 
     start = torch.cuda.Event(enable_timing=True)
@@ -317,6 +322,45 @@ def run_native(a):
         forms[f] = {"mlups": nodes * a.form_steps / s / 1e6, "bytes_per_node_update": bpn,
                     "achieved_gbs": ach, "frac": ach / peak, "steps": a.form_steps, "stable": ok}
 
+    # batched workload: many uneven bodies advanced by shared launches, and
+    # the same bodies stepped one after another
+    batched = None
+    if a.batch > 0:
+        from paper_2208_13769_gb300 import workloads as W
+
+        spec = W.body_batch(a.batch)
+        bnodes = sum(p.nx * p.ny for p in spec.problems)
+        bodies = [lbm.Body(p, storage=a.storage, compensated=a.compensated, stream=stream.cuda_stream,
+                           device=local) for p in spec.problems]
+        bt = lbm.Batch(bodies, stream=stream.cuda_stream)
+        bt.step(a.warmup)
+        bsec = time_steps(bt, stream, a.batch_steps)
+        info = bt.info()
+        statuses = bt.sync()
+        bt.close()
+
+        class _OneByOne:
+            @staticmethod
+            def step(n):
+                for b in bodies:
+                    b.step(n)
+
+        osteps = max(2, a.batch_steps // 2)
+        osec = time_steps(_OneByOne, stream, osteps)
+        for b in bodies:
+            b.close()
+        bach = bytes_per_node * bnodes / (bsec / a.batch_steps) / 1e9
+        batched = {
+            "workload": f"{a.batch} bodies, sides U{{64..1024}}, mu log-U[0.05, 0.4], nu U[0.2, 0.45], "
+                        "half periodic / half clamped, seed 20220825",
+            "nodes": bnodes, "steps": a.batch_steps, "mlups": bnodes * a.batch_steps / bsec / 1e6,
+            "ms_per_step": 1e3 * bsec / a.batch_steps, "achieved_gbs": bach, "frac": bach / peak,
+            "one_by_one_mlups": bnodes * osteps / osec / 1e6, "one_by_one_steps": osteps,
+            "interior_ctas": info["interior_ctas"], "edge_ctas": info["edge_ctas"],
+            "unstable_members": int(sum(1 for x in statuses if x != lbm.LBM_OK)),
+            "note": "members outside the method's stable range (nu > 0.25 with traction-free edges, "
+                    "nu > 0.40 periodic) report LBM_E_UNSTABLE; their cost is the same"}
+
     # end to end through the C ABI from host buffers: create (H2D of u0, v0),
     # K steps, read u (D2H)
     e2e = None
@@ -353,7 +397,7 @@ def run_native(a):
         "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "f16": "f16", "bf16": "bf16"}[a.storage],
         "data": "synthetic", "config": config_of(a, prob), "roofline": roof, "cpu_baseline": cpu,
-        "e2e": e2e, "gpu_launches": 2 * a.steps, "clocks": clk, "forms": forms,
+        "e2e": e2e, "gpu_launches": 2 * a.steps, "clocks": clk, "forms": forms, "batched": batched,
         "status": lbm.status_string(status),
     }
     print(json.dumps(line), flush=True)

@@ -5,9 +5,9 @@
 // machinery of Sec. 6: ghost values in Grad u and Div Q, bounced populations
 // and periodic images.  These bands hold few nodes, so what bounds their cost
 // is latency, not bandwidth.  Each CTA of 256 threads owns an output tile of
-// (tw - 4) x (th - 4) nodes (tw x th = 256; wide tiles 28 x 4 along the
-// bands of the y edges, narrow tiles 4 x 28 along those of the x edges) and
-// one thread per node of the tile and its 2-node halo:
+// (tw - 4) x (th - 4) nodes (tw x th <= 256: tiles exactly as thick as a
+// band, 28 x 4 over larger areas) and one thread per node of the tile and its
+// 2-node halo:
 //   stage A (every thread)      : pull-stream, first moment, predicted u*
 //   stage B (1-node inner ring) : H = Grad u* with the ghost rules,
 //                                 Q = P(F) + Pbar(H)
@@ -110,7 +110,7 @@ __device__ __noinline__ void boundary_links(TS* fdst, Geo g, const StepParams& p
 }
 
 template <class TS, class TC, class UT, int MODE>
-__global__ void __launch_bounds__(kEdgeThreads, 2) edge_tile_kernel(const __grid_constant__ EdgeLaunch L) {
+__global__ void __launch_bounds__(kEdgeThreads, 3) edge_tile_kernel(const __grid_constant__ EdgeLaunch L) {
     using CT = typename UT::Elem;
     constexpr int UP = UT::planes;
     constexpr int N = kEdgeThreads;
@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(kEdgeThreads, 2) edge_tile_kernel(const __grid
         tile.y0 = max(L.rect[2], min(L.rect[2] + by * oh, L.rect[3] - oh));
         tile.y1 = min(L.rect[3], tile.y0 + oh);
         tile.tw = 32;
+        tile.th = uint8_t(N / 32);
         tile.lead = b == 0;
     }
     {
@@ -170,13 +171,13 @@ __global__ void __launch_bounds__(kEdgeThreads, 2) edge_tile_kernel(const __grid
 
     // ---- this thread's node: raw coordinates (an image beyond a periodic
     // seam) and node coordinates
-    const int tw = tile.tw, th = N / tw;
-    const int tx = t % tw, ty = t / tw;
+    const int tw = tile.tw, th = tile.th;
+    const int tx = t % tw, ty = t / tw;  // ty >= th: an idle thread
     const int nxo = tile.x1 - tile.x0, nyo = tile.y1 - tile.y0;  // output extent
     const int gxr = tile.x0 - 2 + tx, gyr = tile.y0 - 2 + ty;
     const bool okx = g.perx ? (gxr >= -2 && gxr < nx + 2) : (gxr >= 0 && gxr < nx);
     const bool oky = g.pery ? (gyr >= -2 && gyr < ny + 2) : (gyr >= 0 && gyr < ny);
-    const bool inA = okx && oky;
+    const bool inA = okx && oky && ty < th;
     const bool inB = inA && tx >= 1 && tx <= nxo + 2 && ty >= 1 && ty <= nyo + 2;
     const bool inC = tx >= 2 && tx < nxo + 2 && ty >= 2 && ty < nyo + 2;
     const int gx = g.perx ? wrap_coord(gxr, nx) : gxr;
@@ -419,28 +420,35 @@ cudaError_t launch_edge(int fmt, const EdgeLaunch& L, int ntiles, cudaStream_t s
     return cudaErrorInvalidValue;
 }
 
-// Tiles of one band rectangle: wide tiles (28 x 4 output nodes) along a
-// band no taller than 4 rows or across a body-sized rectangle, narrow tiles
-// (4 x 28) along a band no wider than 4 columns.  Every tile has the full
-// extent min(rectangle, tile) along both axes, so each output node on a
-// bounded edge (bodies and bands are at least 2 nodes thick) finds the Q of
-// its two inward neighbours, which stage B computes for the output nodes and
-// their 1-node ring, inside the tile.  Returns the number written
-// (at most cap; call with out == nullptr to count).
+// Tiles of one rectangle.  A band at most 3 nodes thick gets tiles exactly
+// as thick (th = thickness + 4 rows of threads, tw = 256 / th columns), so
+// few threads compute halo only; a larger rectangle gets wide tiles of 28 x 4
+// output nodes.  Every tile has the full extent min(rectangle, tile) along
+// both axes (the last one of a row or column is shifted back, recomputing
+// its neighbour's nodes bit for bit), so each output node on a bounded edge
+// (bodies and bands are at least 2 nodes thick) finds the Q of its two
+// inward neighbours, which stage B computes for the output nodes and their
+// 1-node ring, inside the tile.  Returns the number of tiles (written to out,
+// at most cap, when out is not NULL).
 int edge_tiles_of_rect(const int rect[4], int inst, EdgeTile* out, int cap, bool lead_first) {
     const int w = rect[1] - rect[0], h = rect[3] - rect[2];
     if (w <= 0 || h <= 0) return 0;
-    const bool narrow = w <= 4 && h > 4;
-    const int tw = narrow ? 8 : 32;
-    const int ow = tw - 4, oh = kEdgeThreads / tw - 4;
+    int tw, th;
+    if (h <= 3) {
+        th = h + 4;
+        tw = kEdgeThreads / th;
+    } else if (w <= 3) {
+        tw = w + 4;
+        th = kEdgeThreads / tw;
+    } else {
+        tw = 32;
+        th = kEdgeThreads / 32;
+    }
+    const int ow = tw - 4, oh = th - 4;
     int n = 0;
     for (int y = rect[2]; y < rect[3]; y += oh)
         for (int x = rect[0]; x < rect[1]; x += ow) {
             if (out && n < cap) {
-                // the last tile of a row or column is shifted back to full
-                // extent (it recomputes, bit for bit, nodes of its
-                // neighbour): an output node on a bounded edge then always
-                // has its two inward neighbours inside the tile
                 const int xs = x + ow <= rect[1] ? x : (rect[1] - ow > rect[0] ? rect[1] - ow : rect[0]);
                 const int ys = y + oh <= rect[3] ? y : (rect[3] - oh > rect[2] ? rect[3] - oh : rect[2]);
                 EdgeTile& e = out[n];
@@ -449,7 +457,8 @@ int edge_tiles_of_rect(const int rect[4], int inst, EdgeTile* out, int cap, bool
                 e.x1 = xs + ow < rect[1] ? xs + ow : rect[1];
                 e.y0 = ys;
                 e.y1 = ys + oh < rect[3] ? ys + oh : rect[3];
-                e.tw = int16_t(tw);
+                e.tw = uint8_t(tw);
+                e.th = uint8_t(th);
                 e.lead = int16_t(lead_first && n == 0);
             }
             ++n;

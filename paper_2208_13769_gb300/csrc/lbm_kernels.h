@@ -38,15 +38,15 @@ struct InteriorLaunch {
 cudaError_t launch_interior_batch(int fmt, const InteriorLaunch& L, int nwork, int ring_slots, cudaStream_t s);
 
 // The edge kernel (lbm_edge.cu): small 2-D tiles with every boundary rule.
-// A tile's threads cover its output nodes and a 2-node halo: tw x
-// (kEdgeThreads / tw) nodes, (tw - 4) x (kEdgeThreads / tw - 4) of them output.
+// A tile's threads cover its output nodes and a 2-node halo: tw x th nodes
+// (tw x th <= kEdgeThreads), (tw - 4) x (th - 4) of them output.
 constexpr int kEdgeThreads = 256;
 
 struct EdgeTile {
     int32_t inst;    // entry of the parameter table
     int32_t x0, y0;  // first output node
     int32_t x1, y1;  // one past the last output node
-    int16_t tw;      // threads along x: 32 (wide tile) or 8 (narrow tile)
+    uint8_t tw, th;  // threads along x and y
     int16_t lead;    // this tile advances the instance's step counter
 };
 
