@@ -17,7 +17,7 @@ using namespace lbm;
 namespace {
 
 constexpr int kGraphChunk = 64;  // steps per captured graph (even: keeps the ping-pong parity)
-constexpr int kInteriorW = 124;  // output columns per strip of the interior kernel (128 threads)
+constexpr int kSegMax = 144;  // widest row segment the interior kernel copies in bulk (elements)
 
 size_t elem_size_storage(int fmt) {
     switch (fmt) {
@@ -128,13 +128,12 @@ static cudaError_t build_plan(lbm_ctx* c) {
     if (c->has_interior) {
         const int r[4] = {bx, nx - bx, by, ny - by};
         for (int k = 0; k < 4; ++k) c->irect[k] = r[k];
-        const int w = r[1] - r[0], h = r[3] - r[2];
-        const int W = kInteriorW;
+        const int h = r[3] - r[2];
         c->i_ring = 7;  // lookahead of 4 rows
         const size_t smem = interior_smem(c->fmt, c->i_ring);
         const int per_sm = std::max(1, int((228 * 1024) / (smem + 1024)));
         // exactly one wave of equal CTAs: strips x chunks <= 152 x per_sm
-        c->i_tiles_x = (w + W - 1) / W;
+        interior_strips(c->fmt, r[0], r[1], false, &c->i_strip_x0, &c->i_strip_w, &c->i_tiles_x);
         const int64_t slots = int64_t(152) * std::min(per_sm, 4);
         const int64_t chunks = std::max<int64_t>(1, slots / c->i_tiles_x);
         int64_t rows = (h + chunks - 1) / chunks;
@@ -179,6 +178,8 @@ static cudaError_t launch_interior_part(lbm_ctx* c, const StepParams& p, bool fi
     pi.tiles_y = c->i_tiles_y;
     pi.chunk_rows = c->i_chunk;
     pi.ring_slots = c->i_ring;
+    pi.strip_x0 = c->i_strip_x0;
+    pi.strip_w = c->i_strip_w;
     return launch_interior(c->fmt, pi, c->stream, fields);
 }
 
@@ -358,11 +359,10 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
     }
     // plane layout: kPadCols columns / kPadRows rows of padding on each side,
     // pitch a multiple of 64 elements covering the widest bulk-copied row
-    // segment of the interior kernel (a strip may start as far right as
-    // nx - 2 - kInteriorW; its segment spans kInteriorW + 4 + kSegExtra
-    // elements from 8 columns left of the strip)
-    const int64_t seg_end = int64_t(d->nx) + kInteriorW + 4 + kSegExtra;
-    int64_t need = kPadCols + std::max<int64_t>(seg_end, int64_t(kInteriorW) + 4 + kSegExtra + 8) + 16;
+    // segment of the interior kernel (a strip starting as far right as
+    // column nx - 1 reads a segment of up to kSegMax elements from 8 columns
+    // left of it)
+    const int64_t need = kPadCols + int64_t(d->nx) + kSegMax + 16;
     c->pitch = (need + 63) / 64 * 64;
     c->plane = c->pitch * (int64_t(d->ny) + 2 * kPadRows);
 

@@ -25,7 +25,7 @@ using namespace lbm;
 namespace {
 
 constexpr int kBatchGraphChunk = 64;  // steps per captured graph (even)
-constexpr int kBatchStripW = 124;     // output columns per interior strip
+constexpr int kBatchStripW = 120;     // output columns per interior strip (sizing only)
 constexpr int kBatchRing = 7;         // interior row ring (lookahead 4)
 
 }  // namespace
@@ -195,17 +195,28 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_sync, cudaEventDisableTiming);
 
-    // interior tiles: rows per chunk so that the batch holds about four waves
-    // of 4 CTAs per SM (at least 32 rows, at most 256)
+    // interior tiles: rows per chunk so that the batch holds about eight
+    // waves of 4 CTAs per SM (at least 32 rows, at most 256)
     int64_t interior_nodes = 0;
     for (lbm_ctx* c : b->m)
         if (c->has_interior)
             interior_nodes += int64_t(c->irect[1] - c->irect[0]) * (c->irect[3] - c->irect[2]);
-    b->chunk_rows = int(std::min<int64_t>(256, std::max<int64_t>(32, interior_nodes / (int64_t(kBatchStripW) * 152 * 4 * 4))));
+    b->chunk_rows =
+        int(std::min<int64_t>(256, std::max<int64_t>(32, interior_nodes / (int64_t(kBatchStripW) * 152 * 4 * 8))));
     std::vector<StepParams> tab;
     std::vector<InteriorWork> work;
     std::vector<EdgeTile> tiles;
+    std::vector<int> sx0, sw, ns;  // strip grid of each member's interior
     try {
+        sx0.assign(size_t(n), 0);
+        sw.assign(size_t(n), 0);
+        ns.assign(size_t(n), 0);
+        for (int i = 0; i < n; ++i) {
+            const lbm_ctx* c = b->m[size_t(i)];
+            if (c->has_interior)
+                interior_strips(b->fmt, c->irect[0], c->irect[1], true, &sx0[size_t(i)], &sw[size_t(i)],
+                                &ns[size_t(i)]);
+        }
         tab.resize(size_t(2) * n);
         for (int q = 0; q < 2; ++q)
             for (int i = 0; i < n; ++i) {
@@ -214,13 +225,15 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
                 for (int k = 0; k < 4; ++k) p.rect[k] = c->irect[k];
                 p.chunk_rows = b->chunk_rows;
                 p.ring_slots = kBatchRing;
+                p.strip_x0 = sx0[size_t(i)];
+                p.strip_w = sw[size_t(i)];
                 tab[size_t(q) * n + i] = p;
             }
         for (int i = 0; i < n; ++i) {
             lbm_ctx* c = b->m[size_t(i)];
             if (c->has_interior) {
-                const int w = c->irect[1] - c->irect[0], h = c->irect[3] - c->irect[2];
-                const int sx = (w + kBatchStripW - 1) / kBatchStripW, sy = (h + b->chunk_rows - 1) / b->chunk_rows;
+                const int h = c->irect[3] - c->irect[2];
+                const int sx = ns[size_t(i)], sy = (h + b->chunk_rows - 1) / b->chunk_rows;
                 for (int by = 0; by < sy; ++by)
                     for (int bx = 0; bx < sx; ++bx) work.push_back(InteriorWork{i, bx, by, 0});
             }
@@ -233,6 +246,14 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
                 first = first && cnt == 0;
             }
         }
+        // longest tiles first: the short tiles of small bodies fill the tail
+        // of the last wave
+        auto rows_of = [&](const InteriorWork& w) {
+            const lbm_ctx* c = b->m[size_t(w.inst)];
+            return std::min(b->chunk_rows, c->irect[3] - c->irect[2]);
+        };
+        std::stable_sort(work.begin(), work.end(),
+                         [&](const InteriorWork& x, const InteriorWork& y) { return rows_of(x) > rows_of(y); });
     } catch (...) {
         batch_free(b);
         delete b;

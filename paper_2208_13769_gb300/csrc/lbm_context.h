@@ -74,7 +74,7 @@ struct lbm_ctx {
     bool planned = false;
     bool has_interior = false;
     int irect[4] = {0, 0, 0, 0};
-    int i_tiles_x = 0, i_tiles_y = 0, i_chunk = 0, i_ring = 0;
+    int i_tiles_x = 0, i_tiles_y = 0, i_chunk = 0, i_ring = 0, i_strip_x0 = 0, i_strip_w = 0;
     int nband = 0;
     int brect[4][4];
     lbm::StepParams* dparams = nullptr;  // device: make_params(parity 0), make_params(parity 1)

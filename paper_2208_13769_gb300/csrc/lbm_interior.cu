@@ -12,9 +12,10 @@
 // edges in the same step (both read the same source buffers and write
 // disjoint nodes).
 //
-// Each CTA owns a strip of W = NT - 4 columns and a chunk of rows, one thread
-// per column, and walks the rows as a three-stage pipeline with a lag of one
-// row per stage:
+// Each CTA owns a strip of W <= 124 columns (strips never overlap; the first
+// and last strip of a body may be narrower) and a chunk of rows, one thread
+// per column plus a 2-column halo on each side, and walks the rows as a
+// three-stage pipeline with a lag of one row per stage:
 //   stage A, row a     : pull-stream, first moment, predicted u*   (W + 4 cols)
 //   stage B, row a - 1 : H = Grad u*, Q = P(F) + Pbar(H)           (W + 2 cols)
 //   stage C, row a - 2 : 1S = rho0 b + Div Q, corrected j and u, equilibrium,
@@ -50,9 +51,18 @@ __host__ __device__ constexpr size_t interior_smem_fixed() {
     return (256 + sizeof(UT) * 6 * NT + sizeof(TC) * 12 * NT + 127) / 128 * 128;
 }
 
+// Elements of one bulk-copied row segment: a strip of W <= NT - 4 output
+// columns reads columns x0 - 3 .. x0 + W + 2 from a 16-byte aligned start
+// (up to 16 / sizeof(TS) - 1 columns before x0 - 3), in a whole number of
+// 16-byte units.
+template <class TS, int NT>
+__host__ __device__ constexpr int seg_elems() {
+    return sizeof(TS) == 2 ? NT + 16 : NT + 8;
+}
+
 template <class TS, int NT>
 __host__ __device__ constexpr size_t interior_row_bytes() {
-    return size_t(9) * (NT + kSegExtra) * sizeof(TS);
+    return size_t(9) * seg_elems<TS, NT>() * sizeof(TS);
 }
 
 }  // namespace
@@ -61,8 +71,8 @@ __host__ __device__ constexpr size_t interior_row_bytes() {
 template <class TS, class TC, class UT, int NT>
 __device__ __forceinline__ void interior_tile(const StepParams& p, int bx, int by, double* fields) {
     using CT = typename UT::Elem;
-    constexpr int W = NT - 4;
-    constexpr int SEG = NT + kSegExtra;
+    const int W = p.strip_w;
+    constexpr int SEG = seg_elems<TS, NT>();
     constexpr int UP = UT::planes;
     constexpr int ROW_BYTES = int(interior_row_bytes<TS, NT>());
     static_assert(ROW_BYTES % 16 == 0, "row size");
@@ -81,15 +91,17 @@ __device__ __forceinline__ void interior_tile(const StepParams& p, int bx, int b
     const int64_t pitch = p.pitch, plane = p.plane;
     const int t = threadIdx.x;
     const int rx0 = p.rect[0], rx1 = p.rect[1], ry0 = p.rect[2], ry1 = p.rect[3];
-    if (bx * W >= rx1 - rx0 || by * p.chunk_rows >= ry1 - ry0) return;
-    int x0 = rx0 + bx * W;
-    if (x0 > rx1 - W) x0 = rx1 - W > rx0 ? rx1 - W : rx0;
+    // strip bx of the strip grid, clipped to the rectangle
+    const int x0 = p.strip_x0 + bx * W;
+    const int x_lo = max(rx0, x0), x_hi = min(rx1, x0 + W);
+    if (x_lo >= x_hi || by * p.chunk_rows >= ry1 - ry0) return;
     int y_begin = ry0 + by * p.chunk_rows;
     if (y_begin > ry1 - p.chunk_rows) y_begin = ry1 - p.chunk_rows > ry0 ? ry1 - p.chunk_rows : ry0;
     const int y_end = min(ry1, y_begin + p.chunk_rows);
-    const int x_end = min(rx1, x0 + W);
-    int seg0 = x0 - 8;  // 16-byte aligned first column of the row segments
+    // first column of the row segments: 16-byte aligned, inside the plane
+    int seg0 = x0 - 3;
     seg0 = (seg0 >= 0 ? seg0 : seg0 - (ALIGN_COLS - 1)) / ALIGN_COLS * ALIGN_COLS;
+    if (seg0 < -kPadCols) seg0 = -kPadCols;
 
     const TS* __restrict__ fsrc = static_cast<const TS*>(p.f_src);
     TS* __restrict__ fdst = static_cast<TS*>(p.f_dst);
@@ -98,10 +110,10 @@ __device__ __forceinline__ void interior_tile(const StepParams& p, int bx, int b
     const TC* __restrict__ s_src = static_cast<const TC*>(p.s_src);
     TC* __restrict__ s_dst = static_cast<TC*>(p.s_dst);
 
-    const int gx = x0 - 2 + t;  // this thread's column (inside the body)
-    const bool colA = gx < x_end + 2;
-    const bool colB = t >= 1 && gx < x_end + 1;
-    const bool colC = t >= 2 && gx < x_end;
+    const int gx = x0 - 2 + t;  // this thread's column
+    const bool colA = gx >= x_lo - 2 && gx < x_hi + 2;
+    const bool colB = gx >= x_lo - 1 && gx < x_hi + 1;
+    const bool colC = gx >= x_lo && gx < x_hi;
     const int tm = t > 0 ? t - 1 : t, tp = t < NT - 1 ? t + 1 : t;
     const int e_own = gx - seg0;
     const int64_t col_off = int64_t(gx) + kPadCols;
@@ -369,6 +381,24 @@ cudaError_t launch_interior_batch(int fmt, const InteriorLaunch& L, int nwork, i
             return launch_interior_batch_t<__nv_bfloat16, float, UComp, 128, 4>(L, nwork, ring_slots, s);
     }
     return cudaErrorInvalidValue;
+}
+
+void interior_strips(int fmt, int rx0, int rx1, bool aligned, int* strip_x0, int* strip_w, int* nstrips) {
+    int W = 124, xg = rx0;  // 128 threads: the strip and its 2-column halo on each side
+    if (aligned) {
+        // strips on the grid of 32-byte sectors (8 columns of a 4- or 8-byte
+        // plane, 16 of a 2-byte plane; column x sits at x + kPadCols of a plane
+        // row and rows start 256-byte aligned), so that no two CTAs store into
+        // one sector even when they run far apart in time
+        const bool half = fmt == kFmtF16 || fmt == kFmtBF16;
+        W = half ? 112 : 120;
+        const int g0 = half ? -8 : 0;  // g0 + kPadCols is a multiple of the sector's columns
+        auto fdiv = [](int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
+        xg = g0 + fdiv(rx0 - g0, W) * W;
+    }
+    *strip_x0 = xg;
+    *strip_w = W;
+    *nstrips = (rx1 - xg + W - 1) / W;  // the first and last strips may be partial
 }
 
 size_t interior_smem(int fmt, int ring_slots) {

@@ -20,6 +20,11 @@ enum Format : int {
 // The interior kernel (lbm_interior.cu): nodes of p.rect[0] only, which must
 // lie at least 2 nodes from bounded edges and 3 from periodic seams.
 size_t interior_smem(int fmt, int ring_slots);
+// The strip grid of the interior kernel over columns [rx0, rx1): origin of
+// strip 0, output columns per strip, number of strips.  aligned: strips on
+// 32-byte sector boundaries (for CTAs of one body that may run in different
+// waves), else 124-column strips from rx0 (one wave).
+void interior_strips(int fmt, int rx0, int rx1, bool aligned, int* strip_x0, int* strip_w, int* nstrips);
 cudaError_t launch_interior(int fmt, const StepParams& p, cudaStream_t s, bool fields);
 
 // Interior tiles of a batch of bodies: work item = (entry of the parameter

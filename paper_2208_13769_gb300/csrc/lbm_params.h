@@ -18,7 +18,6 @@ enum EdgeKind : int32_t { kPeriodic = 0, kDirichlet = 1, kNeumann = 2 };
 // a 16-byte boundary.
 constexpr int kPadRows = 3;
 constexpr int kPadCols = 8;
-constexpr int kSegExtra = 16;  // row segment = block size + 16 elements
 
 // One edge (0 = x-, 1 = x+, 2 = y-, 3 = y+) of Sec. 6's boundary value problem.
 struct EdgeBC {
@@ -41,6 +40,9 @@ struct StepParams {
     int32_t tiles_x, tiles_y;  // column strips x row chunks
     int32_t chunk_rows;        // rows per chunk
     int32_t ring_slots;        // row slots of the bulk-copy ring (lookahead + 3)
+    int32_t strip_x0;          // first column of strip 0
+    int32_t strip_w;           // output columns per strip
+    int32_t pad1[2];
 
     const void* f_src;  // 9 planes of f^col(t_n), storage type
     void* f_dst;        // 9 planes of f^col(t_n+1)
