@@ -129,12 +129,11 @@ static cudaError_t build_plan(lbm_ctx* c) {
         const int r[4] = {bx, nx - bx, by, ny - by};
         for (int k = 0; k < 4; ++k) c->irect[k] = r[k];
         const int h = r[3] - r[2];
-        c->i_ring = 7;  // lookahead of 4 rows
-        const size_t smem = interior_smem(c->fmt, c->i_ring);
-        const int per_sm = std::max(1, int((228 * 1024) / (smem + 1024)));
-        // exactly one wave of equal CTAs: strips x chunks <= 152 x per_sm
+        c->i_ring = kInteriorRing;
+        const int per_sm = std::max(1, interior_occupancy(c->fmt, c->i_ring));
+        // exactly one wave of equal CTAs: strips x chunks <= SMs x per_sm
         interior_strips(c->fmt, r[0], r[1], false, &c->i_strip_x0, &c->i_strip_w, &c->i_tiles_x);
-        const int64_t slots = int64_t(152) * std::min(per_sm, 4);
+        const int64_t slots = int64_t(c->num_sms) * per_sm;
         const int64_t chunks = std::max<int64_t>(1, slots / c->i_tiles_x);
         int64_t rows = (h + chunks - 1) / chunks;
         rows = std::max<int64_t>(rows, 16);
@@ -341,6 +340,11 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
         free_all(c);
         delete c;
         return LBM_E_CUDA;
+    }
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+        c->num_sms < 1) {
+        cudaGetLastError();
+        c->num_sms = 1;
     }
     c->nx = d->nx;
     c->ny = d->ny;

@@ -26,7 +26,6 @@ namespace {
 
 constexpr int kBatchGraphChunk = 64;  // steps per captured graph (even)
 constexpr int kBatchStripW = 120;     // output columns per interior strip (sizing only)
-constexpr int kBatchRing = 7;         // interior row ring (lookahead 4)
 
 }  // namespace
 
@@ -95,7 +94,7 @@ cudaError_t batch_launch(lbm_batch* b, int q, bool fields) {
     if (b->n_work == 0) return launch_edge(b->fmt, el, b->n_edge, b->stream, 0);
     cudaError_t e = cudaEventRecord(b->ev_fork, b->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
-    if (e == cudaSuccess) e = launch_interior_batch(b->fmt, il, b->n_work, kBatchRing, b->stream);
+    if (e == cudaSuccess) e = launch_interior_batch(b->fmt, il, b->n_work, kInteriorRing, b->stream);
     if (e == cudaSuccess) e = launch_edge(b->fmt, el, b->n_edge, b->side, 0);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
@@ -196,13 +195,14 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_sync, cudaEventDisableTiming);
 
     // interior tiles: rows per chunk so that the batch holds about eight
-    // waves of 4 CTAs per SM (at least 32 rows, at most 256)
+    // waves of resident CTAs (at least 32 rows, at most 256)
     int64_t interior_nodes = 0;
     for (lbm_ctx* c : b->m)
         if (c->has_interior)
             interior_nodes += int64_t(c->irect[1] - c->irect[0]) * (c->irect[3] - c->irect[2]);
+    const int64_t wave = int64_t(b->m[0]->num_sms) * std::max(1, interior_occupancy(b->fmt, kInteriorRing));
     b->chunk_rows =
-        int(std::min<int64_t>(256, std::max<int64_t>(32, interior_nodes / (int64_t(kBatchStripW) * 152 * 4 * 8))));
+        int(std::min<int64_t>(256, std::max<int64_t>(32, interior_nodes / (int64_t(kBatchStripW) * wave * 8))));
     std::vector<StepParams> tab;
     std::vector<InteriorWork> work;
     std::vector<EdgeTile> tiles;
@@ -224,7 +224,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
                 StepParams p = make_params(c, b->base_parity[size_t(i)] ^ q);
                 for (int k = 0; k < 4; ++k) p.rect[k] = c->irect[k];
                 p.chunk_rows = b->chunk_rows;
-                p.ring_slots = kBatchRing;
+                p.ring_slots = kInteriorRing;
                 p.strip_x0 = sx0[size_t(i)];
                 p.strip_w = sw[size_t(i)];
                 tab[size_t(q) * n + i] = p;
@@ -278,7 +278,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
     if (e == cudaSuccess) {
         InteriorLaunch il;
         memset(&il, 0, sizeof(il));
-        e = launch_interior_batch(b->fmt, il, 0, kBatchRing, b->stream);
+        e = launch_interior_batch(b->fmt, il, 0, kInteriorRing, b->stream);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();

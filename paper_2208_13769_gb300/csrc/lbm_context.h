@@ -28,6 +28,7 @@ struct DeviceGuard {
 
 struct lbm_ctx {
     int device = 0;
+    int num_sms = 1;
     cudaStream_t stream = nullptr;
     bool owns_stream = false;
     // the edge-band launch of a step runs on a side stream, concurrently with

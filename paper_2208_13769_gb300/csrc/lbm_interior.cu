@@ -401,6 +401,26 @@ void interior_strips(int fmt, int rx0, int rx1, bool aligned, int* strip_x0, int
     *nstrips = (rx1 - xg + W - 1) / W;  // the first and last strips may be partial
 }
 
+template <class TS, class TC, class UT, int NT, int MINB>
+int interior_occupancy_t(int ring_slots) {
+    auto kern = interior_step_kernel<TS, TC, UT, NT, MINB>;
+    const size_t sm = interior_smem_bytes<TS, TC, UT, NT>(ring_slots);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, sm) != cudaSuccess) return 0;
+    return n;
+}
+
+int interior_occupancy(int fmt, int ring_slots) {
+    switch (fmt) {
+        case kFmtF64: return interior_occupancy_t<double, double, UPlain<double>, 128, 2>(ring_slots);
+        case kFmtF32: return interior_occupancy_t<float, float, UPlain<float>, 128, 4>(ring_slots);
+        case kFmtF32C: return interior_occupancy_t<float, float, UComp, 128, 4>(ring_slots);
+        case kFmtF16: return interior_occupancy_t<__half, float, UComp, 128, 4>(ring_slots);
+        default: return interior_occupancy_t<__nv_bfloat16, float, UComp, 128, 4>(ring_slots);
+    }
+}
+
 size_t interior_smem(int fmt, int ring_slots) {
     switch (fmt) {
         case kFmtF64: return interior_smem_bytes<double, double, UPlain<double>, 128>(ring_slots);

@@ -20,6 +20,12 @@ enum Format : int {
 // The interior kernel (lbm_interior.cu): nodes of p.rect[0] only, which must
 // lie at least 2 nodes from bounded edges and 3 from periodic seams.
 size_t interior_smem(int fmt, int ring_slots);
+// CTAs of the interior kernel resident per SM with this ring (0 on error);
+// also sets the kernel's dynamic shared-memory limit, so call it before any
+// stream capture.
+int interior_occupancy(int fmt, int ring_slots);
+// Rows of the interior kernel's bulk-copy ring (lookahead = ring - 3 rows).
+constexpr int kInteriorRing = 5;
 // The strip grid of the interior kernel over columns [rx0, rx1): origin of
 // strip 0, output columns per strip, number of strips.  aligned: strips on
 // 32-byte sector boundaries (for CTAs of one body that may run in different
