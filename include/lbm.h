@@ -183,7 +183,8 @@ LBM_API lbm_status lbm_sync(lbm_ctx* ctx);
 /* Steps taken so far and the derived time step (NULL pointers allowed). */
 LBM_API lbm_status lbm_get_info(const lbm_ctx* ctx, int64_t* steps, double* dt);
 
-/* Bytes of device memory the context holds, and the algorithmic bytes one
+/* Bytes of device memory the context holds (the copies of u0 and v0 are
+ * released once the initialisation has run), and the algorithmic bytes one
  * node update moves (populations plus carries, read once and written once). */
 LBM_API lbm_status lbm_memory_info(const lbm_ctx* ctx, int64_t* device_bytes, int64_t* bytes_per_node_update);
 

@@ -234,6 +234,16 @@ lbm_status lbm::ctx_ensure_initialized(lbm_ctx* c) {
     lbm_status st = launch(c, 1, true);
     if (st != LBM_OK) return st;
     c->initialized = true;
+    // the initial fields are read only by the initialisation: give them back
+    if (c->u0 || c->v0) {
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+        const int64_t ubytes = int64_t(2) * c->nx * c->ny * int64_t(sizeof(double));
+        if (c->u0) c->device_bytes -= ubytes;
+        if (c->v0) c->device_bytes -= ubytes;
+        cudaFree(c->u0);
+        cudaFree(c->v0);
+        c->u0 = c->v0 = nullptr;
+    }
     return LBM_OK;
 }
 
@@ -395,7 +405,7 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
         delete c;
         return err == cudaErrorMemoryAllocation ? LBM_E_OOM : LBM_E_CUDA;
     }
-    c->device_bytes = int64_t(2 * (fbytes + abytes + sbytes) + fldbytes + 2 * (d->u0 ? ubytes : 0));
+    c->device_bytes = int64_t(2 * (fbytes + abytes + sbytes) + fldbytes + (d->u0 ? ubytes : 0) + (d->v0 ? ubytes : 0));
     for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
         err = cudaMemsetAsync(c->f[k], 0, fbytes, c->stream);
         if (err == cudaSuccess) err = cudaMemsetAsync(c->a[k], 0, abytes, c->stream);

@@ -1,0 +1,144 @@
+"""Scheduling logic of the continuous-batching server, on the host with a
+simulated backend (no GPU): exact step counts, FCFS admission, the memory
+budget, rejection of requests that can never fit, latency accounting."""
+import dataclasses
+
+import numpy as np
+
+from paper_2208_13769_gb300 import serve
+from paper_2208_13769_gb300 import workloads as W
+
+
+@dataclasses.dataclass
+class _P:
+    nx: int
+    ny: int
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, s):
+        self.t += max(0.0, s)
+
+
+class FakeBackend:
+    """A GPU stand-in: a step of a batch takes (sum of member nodes) / rate
+    seconds of the fake clock; it records every step each body receives."""
+
+    def __init__(self, clock, rate=1e9, per_node=100):
+        self.clock, self.rate, self.per_node = clock, rate, per_node
+        self.steps_of = {}
+        self.admit_order = []
+        self.live = 0
+        self.peak_live = 0
+        self.next_id = 0
+
+    def estimate(self, prob):
+        return prob.nx * prob.ny * self.per_node
+
+    def create(self, prob):
+        h = {"id": self.next_id, "nodes": prob.nx * prob.ny}
+        self.next_id += 1
+        self.steps_of[h["id"]] = 0
+        self.admit_order.append(h["id"])
+        self.live += 1
+        self.peak_live = max(self.peak_live, self.live)
+        return h
+
+    def memory(self, h):
+        return h["nodes"] * self.per_node
+
+    def batch(self, bodies):
+        return list(bodies)
+
+    def step(self, batch, n):
+        for h in batch:
+            self.steps_of[h["id"]] += n
+        self.clock.t += n * sum(h["nodes"] for h in batch) / self.rate
+
+    def sync(self, batch):
+        return [0] * len(batch)
+
+    def result(self, h):
+        return np.zeros((1, 1, 2))
+
+    def close(self, h):
+        self.live -= 1
+
+    def close_batch(self, batch):
+        pass
+
+
+def _trace(n=40, seed=3):
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    for _ in range(n):
+        t += float(rng.exponential(0.01))
+        p = _P(int(rng.integers(50, 400)), int(rng.integers(50, 400)))
+        out.append(W.Request(arrival=t, problem=p, steps=int(rng.integers(30, 3000))))
+    return out
+
+
+def test_every_request_gets_exactly_its_steps_in_fcfs_order():
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    reqs = _trace()
+    st = serve.Server(be, hbm_budget=1e12, clock=clock, sleep=clock.sleep).run(reqs)
+    assert st["completed"] == len(reqs) and st["rejected"] == 0
+    order = sorted(range(len(reqs)), key=lambda i: reqs[i].arrival)
+    # bodies are created in arrival order and each receives its own step count
+    assert [be.steps_of[k] for k in be.admit_order] == [reqs[i].steps for i in order]
+    recs = {r.index: r for r in st["records"]}
+    for i, q in enumerate(reqs):
+        r = recs[i]
+        assert r.admitted >= q.arrival - 1e-12 and r.completed > r.admitted
+        # no faster than the request alone on the simulated device
+        assert r.latency >= q.steps * q.problem.nx * q.problem.ny / be.rate - 1e-9
+    assert st["p50_s"] <= st["p99_s"]
+
+
+def test_budget_bounds_memory_and_head_of_line_blocks():
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    reqs = _trace(30, seed=5)
+    biggest = max(q.problem.nx * q.problem.ny for q in reqs) * be.per_node
+    budget = 1.5 * biggest
+    st = serve.Server(be, hbm_budget=budget, clock=clock, sleep=clock.sleep).run(reqs)
+    assert st["completed"] == len(reqs)
+    assert st["peak_hbm_bytes"] <= budget
+    assert be.peak_live < len(reqs)  # the budget forced queueing
+    order = sorted(range(len(reqs)), key=lambda i: reqs[i].arrival)
+    assert [be.steps_of[k] for k in be.admit_order] == [reqs[i].steps for i in order]
+
+
+def test_request_larger_than_the_budget_is_rejected():
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    reqs = _trace(10, seed=7)
+    reqs[4] = dataclasses.replace(reqs[4], problem=_P(5000, 5000))
+    st = serve.Server(be, hbm_budget=5000 * 4000 * be.per_node, clock=clock, sleep=clock.sleep).run(reqs)
+    assert st["rejected"] == 1 and st["completed"] == 9
+
+
+def test_idle_server_waits_for_arrivals():
+    clock = FakeClock()
+    be = FakeBackend(clock, rate=1e12)
+    reqs = [W.Request(arrival=10.0 * k, problem=_P(64, 64), steps=100) for k in range(3)]
+    st = serve.Server(be, clock=clock, sleep=clock.sleep).run(reqs)
+    assert st["completed"] == 3
+    for r in st["records"]:
+        assert r.admitted >= r.arrival and r.latency < 1.0
+    assert st["makespan_s"] >= 20.0
+
+
+def test_trace_at_rate_keeps_requests_and_sets_poisson_arrivals():
+    reqs = _trace(200)
+    out = serve.trace_at_rate(reqs, rate=50.0)
+    assert [q.steps for q in out] == [q.steps for q in reqs]
+    gaps = np.diff([0.0] + [q.arrival for q in out])
+    assert (gaps > 0).all() and abs(gaps.mean() - 1 / 50.0) < 0.3 / 50.0
