@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--batch", type=int, default=256,
                     help="bodies of the batched workload (seeded, sides 64..1024; 0 to skip)")
     ap.add_argument("--batch-steps", type=int, default=256)
+    ap.add_argument("--serve", type=int, default=120,
+                    help="requests of the serving trace replayed at 200/s (0 to skip)")
+    ap.add_argument("--serve-window", type=float, default=12.0,
+                    help="arrival window (s) of the sub-capacity serving run")
     ap.add_argument("--cpu-steps", type=int, default=0, help="oracle sample steps (0 = auto, ~10-20 s)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -361,6 +365,30 @@ def run_native(a):
             "note": "members outside the method's stable range (nu > 0.25 with traction-free edges, "
                     "nu > 0.40 periodic) report LBM_E_UNSTABLE; their cost is the same"}
 
+    # serving: Poisson arrivals of uneven requests, continuous batching, FCFS
+    # admission under a 150 GB budget; first at the trace's 200 requests/s
+    # (far above capacity), then at 0.7 x the capacity that run measured
+    serving = None
+    if a.serve > 0:
+        from paper_2208_13769_gb300 import serve
+        from paper_2208_13769_gb300 import workloads as W
+
+        def strip(st):
+            return {k: v for k, v in st.items() if k != "records"}
+
+        be = serve.GpuBackend(storage="f16", stream=stream.cuda_stream, device=local)
+        trace = W.serving_trace(max_requests=a.serve + 4000)
+        over = strip(serve.Server(be, hbm_budget=150e9).run(trace[:a.serve]))
+        mean_work = float(np.mean([q.problem.nx * q.problem.ny * q.steps for q in trace[:a.serve]]))
+        capacity = over["served_mlups"] * 1e6 / mean_work  # requests per second
+        rate = 0.7 * capacity
+        nsub = max(4, int(rate * a.serve_window))
+        sub_trace = serve.trace_at_rate(trace[a.serve:a.serve + nsub], rate)
+        sub = strip(serve.Server(be, hbm_budget=150e9).run(sub_trace))
+        serving = {"storage": "f16", "trace": "Poisson 200/s, sides U{128..2048}, steps log-U[500, 20000], seed 7",
+                   "overload": dict(over, rate_per_s=200.0), "capacity_requests_per_s": capacity,
+                   "sub_capacity": dict(sub, rate_per_s=rate)}
+
     # end to end through the C ABI from host buffers: create (H2D of u0, v0),
     # K steps, read u (D2H)
     e2e = None
@@ -397,7 +425,7 @@ def run_native(a):
         "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "f16": "f16", "bf16": "bf16"}[a.storage],
         "data": "synthetic", "config": config_of(a, prob), "roofline": roof, "cpu_baseline": cpu,
-        "e2e": e2e, "gpu_launches": 2 * a.steps, "clocks": clk, "forms": forms, "batched": batched,
+        "e2e": e2e, "gpu_launches": 2 * a.steps, "clocks": clk, "forms": forms, "batched": batched, "serving": serving,
         "status": lbm.status_string(status),
     }
     print(json.dumps(line), flush=True)

@@ -118,7 +118,8 @@ def problem_from(wp, scheme: int = PREDICTOR) -> OracleProblem:
 
 
 def solver_from(wp, scheme: int = PREDICTOR) -> "Solver":
-    return Solver(problem_from(wp, scheme), wp.u0, wp.v0)
+    u0, v0 = wp.initial() if hasattr(wp, "initial") else (wp.u0, wp.v0)
+    return Solver(problem_from(wp, scheme), u0, v0)
 
 
 def _f64(x, shape=None) -> np.ndarray:

@@ -266,8 +266,9 @@ class Body:
         d.u_carry = LBM_UCARRY_COMPENSATED if compensated else LBM_UCARRY_NATIVE
         d.scheme = scheme
         d.f16_scale_log2 = f16_scale_log2
-        self._u0 = None if prob.u0 is None else np.ascontiguousarray(prob.u0, dtype=np.float64)
-        self._v0 = None if prob.v0 is None else np.ascontiguousarray(prob.v0, dtype=np.float64)
+        u0, v0 = prob.initial() if hasattr(prob, "initial") else (prob.u0, prob.v0)
+        self._u0 = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64)
+        self._v0 = None if v0 is None else np.ascontiguousarray(v0, dtype=np.float64)
         d.u0 = None if self._u0 is None else self._u0.ctypes.data
         d.v0 = None if self._v0 is None else self._v0.ctypes.data
         d.cuda_stream = stream or None

@@ -23,7 +23,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import List, Optional
+from typing import Callable, List, Optional, Tuple
 
 import numpy as np
 
@@ -56,6 +56,14 @@ class Problem:
     u0: Optional[np.ndarray] = None   # [ny][nx][2] float64
     v0: Optional[np.ndarray] = None   # [ny][nx][2] float64
     name: str = ""
+    # built on demand instead of u0 / v0 (long request traces): () -> (u0, v0)
+    make_initial: Optional[Callable[[], Tuple[np.ndarray, np.ndarray]]] = None
+
+    def initial(self) -> Tuple[Optional[np.ndarray], Optional[np.ndarray]]:
+        """(u0, v0), built now if the problem holds a recipe instead."""
+        if self.make_initial is not None:
+            return self.make_initial()
+        return self.u0, self.v0
 
     @property
     def nodes(self) -> int:
@@ -202,10 +210,11 @@ class BatchSpec:
 
 
 def random_body(rng: np.random.Generator, side_lo: int, side_hi: int, dX: float = 1.0,
-                omega: float = 1.0) -> Problem:
+                omega: float = 1.0, lazy: bool = False) -> Problem:
     """One body: sides U{lo..hi}, mu log-U[0.05, 0.4], nu U[0.2, 0.45],
     periodic or clamped (50/50), low-mode initial displacement of amplitude
-    up to 0.1 L, zero velocity."""
+    up to 0.1 L, zero velocity.  lazy: keep the recipe of u0 / v0
+    (Problem.initial builds them) instead of the arrays."""
     nx = int(rng.integers(side_lo, side_hi + 1))
     ny = int(rng.integers(side_lo, side_hi + 1))
     mu = float(math.exp(rng.uniform(math.log(0.05), math.log(0.4))))
@@ -216,23 +225,31 @@ def random_body(rng: np.random.Generator, side_lo: int, side_hi: int, dX: float 
     phase = float(rng.uniform(0.0, 2 * np.pi))
     axis = int(rng.integers(0, 2))
     edges = all_periodic() if periodic else clamped_free_edges()
-    x = node_coords(nx, dX, periodic)
-    y = node_coords(ny, dX, periodic)
-    X, Y = np.meshgrid(x, y)
     Lx, Ly = nx * dX, ny * dX
-    if periodic:
-        L = Ly if axis == 0 else Lx
-        m = np.sin(2 * np.pi * Y / Ly + phase) if axis == 0 else np.sin(2 * np.pi * X / Lx + phase)
-    else:
-        L = Lx
-        m = np.sin(np.pi * X / (2 * Lx))
+
+    def grid():
+        return np.meshgrid(node_coords(nx, dX, periodic), node_coords(ny, dX, periodic))
+    L = (Ly if axis == 0 else Lx) if periodic else Lx
     A = A_frac * L
-    u0 = np.zeros((ny, nx, 2))
-    u0[:, :, 0] = A * math.cos(theta) * m
-    u0[:, :, 1] = A * math.sin(theta) * m
+
+    def build():
+        X, Y = grid()
+        if periodic:
+            mm = np.sin(2 * np.pi * Y / Ly + phase) if axis == 0 else np.sin(2 * np.pi * X / Lx + phase)
+        else:
+            mm = np.sin(np.pi * X / (2 * Lx))
+        u = np.zeros((ny, nx, 2))
+        u[:, :, 0] = A * math.cos(theta) * mm
+        u[:, :, 1] = A * math.sin(theta) * mm
+        return u, np.zeros_like(u)
+
+    name = f"body_{nx}x{ny}_{'per' if periodic else 'clamp'}"
+    if lazy:
+        return Problem(nx=nx, ny=ny, lam=lame_from_nu(mu, nu), mu=mu, omega=omega, dX=dX, edges=edges,
+                       make_initial=build, name=name)
+    u0, v0 = build()
     return Problem(nx=nx, ny=ny, lam=lame_from_nu(mu, nu), mu=mu, omega=omega, dX=dX,
-                   edges=edges, u0=u0, v0=np.zeros_like(u0),
-                   name=f"body_{nx}x{ny}_{'per' if periodic else 'clamp'}")
+                   edges=edges, u0=u0, v0=v0, name=name)
 
 
 def body_batch(count: int = 256, seed: int = 20220825, side_lo: int = 64, side_hi: int = 1024,
@@ -254,7 +271,7 @@ def serving_trace(rate: float = 200.0, duration: float = 60.0, seed: int = 7,
                   steps_hi: int = 20000, max_requests: Optional[int] = None,
                   lazy_fields: bool = True) -> List[Request]:
     """Poisson arrivals; each request a body as in body_batch with a
-    log-uniform step count."""
+    log-uniform step count (lazy_fields: initial fields built on demand)."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out: List[Request] = []
@@ -262,7 +279,7 @@ def serving_trace(rate: float = 200.0, duration: float = 60.0, seed: int = 7,
         t += float(rng.exponential(1.0 / rate))
         if t >= duration:
             break
-        prob = random_body(rng, side_lo, side_hi)
+        prob = random_body(rng, side_lo, side_hi, lazy=lazy_fields)
         steps = int(round(math.exp(rng.uniform(math.log(steps_lo), math.log(steps_hi)))))
         out.append(Request(arrival=t, problem=prob, steps=steps))
         if max_requests is not None and len(out) >= max_requests:
