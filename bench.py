@@ -228,6 +228,66 @@ def run_reference(a):
     return 0
 
 
+# ---------------------------------------------------------------- ranks
+
+class Ranks:
+    """One process per GPU under torchrun (RANK / WORLD_SIZE / LOCAL_RANK /
+    MASTER_* from the environment): barrier and max over ranks.  Each rank
+    advances its own replica of the workload (independent bodies), so no
+    collective touches the solver's data; these reductions serve the timing
+    only.  backend "nccl" on GPUs, "gloo" on host cores (tests)."""
+
+    def __init__(self, backend: str = "nccl"):
+        import torch
+
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.backend = backend
+        self.dist = None
+        self.device = "cpu"
+        if backend == "nccl":
+            torch.cuda.set_device(self.local)
+            self.device = "cuda"
+        if self.world > 1:
+            import torch.distributed as dist
+
+            if backend == "nccl":
+                dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            else:
+                dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        import torch
+
+        if self.dist is not None:
+            self.dist.barrier()
+        if self.device == "cuda":
+            torch.cuda.synchronize()
+
+    def max(self, x: float) -> float:
+        import torch
+
+        if self.dist is None:
+            return float(x)
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def weak_scaling_value(world: int, units_per_rank: float, steps: int, max_secs: float) -> float:
+    """Whole-job throughput in millions of units per second: every rank
+    advanced units_per_rank units `steps` times; the job took the slowest
+    rank's time."""
+    return world * units_per_rank * steps / max_secs / 1e6
+
+
 # ---------------------------------------------------------------- native (GPU)
 
 def time_steps(body, stream, steps):
@@ -251,29 +311,18 @@ def run_native(a):
 
     from paper_2208_13769_gb300 import lbm
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
     if not torch.cuda.is_available():
         raise RuntimeError("bench.py needs a CUDA GPU")
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ranks = Ranks("nccl")
+    rank, world, local = ranks.rank, ranks.world, ranks.local
+    if world > 1:  # the extra sections run on single-GPU invocations only
+        a.forms, a.batch, a.serve = "", 0, 0
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
+        ranks.barrier()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return ranks.max(x)
 
     prob = workload(a)
     nodes = prob.nodes
@@ -297,7 +346,7 @@ def run_native(a):
     body.close()
 
     ms_per_step = 1e3 * secs / a.steps
-    value = world * nodes * a.steps / secs / 1e6
+    value = weak_scaling_value(world, nodes, a.steps, secs)
     peak, peak_kind = measured_peak()
     interior_ms, band_ms, serial_ms, interior_nodes = (float(x) for x in prof)
     achieved = bytes_per_node * interior_nodes / (interior_ms * 1e-3) / 1e9
@@ -311,8 +360,15 @@ def run_native(a):
                      "note": "whole time step (interior + edge-band launch) at the same bytes per node"},
             "edge_band_kernel": {"launch_ms": band_ms, "nodes": nodes - interior_nodes}}
 
-    # extra population formats on the same body
+    # extra population formats on the same body, each with its displacement
+    # error against the FP64 path (validated against the oracle) after
+    # --form-steps steps
     forms = {}
+    ref_u = None
+    if a.forms:
+        with lbm.Body(prob, storage="f64", stream=stream.cuda_stream, device=local) as b64:
+            b64.step(a.warmup + a.form_steps)
+            ref_u = b64.read(lbm.LBM_FIELD_U, allow_unstable=True)["u"]
     for f in [x for x in a.forms.split(",") if x]:
         st, comp = {"f32c": ("f32", True), "f32n": ("f32", False)}.get(f, (f, False))
         b = lbm.Body(prob, storage=st, compensated=comp, stream=stream.cuda_stream, device=local)
@@ -320,11 +376,14 @@ def run_native(a):
         b.step(a.warmup)
         torch.cuda.synchronize()
         s = time_steps(b, stream, a.form_steps)
-        ok = b.read(lbm.LBM_FIELD_U, allow_unstable=True)["status"] == lbm.LBM_OK
+        out = b.read(lbm.LBM_FIELD_U, allow_unstable=True)
+        ok = out["status"] == lbm.LBM_OK
+        uerr = float(np.linalg.norm(out["u"] - ref_u) / np.linalg.norm(ref_u))
         b.close()
         ach = bpn * nodes / (s / a.form_steps) / 1e9
         forms[f] = {"mlups": nodes * a.form_steps / s / 1e6, "bytes_per_node_update": bpn,
-                    "achieved_gbs": ach, "frac": ach / peak, "steps": a.form_steps, "stable": ok}
+                    "achieved_gbs": ach, "frac": ach / peak, "steps": a.form_steps, "stable": ok,
+                    "u_rel_err_vs_f64": uerr}
 
     # batched workload: many uneven bodies advanced by shared launches, and
     # the same bodies stepped one after another
@@ -416,8 +475,7 @@ def run_native(a):
         cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": f"{steps} time steps of the full {a.nx}x{a.ny} body ({dt:.1f} s, FP64 oracle)"}
 
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
     if rank != 0:
         return 0
     line = {
