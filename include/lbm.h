@@ -235,6 +235,18 @@ LBM_API lbm_status lbm_batch_get_info(const lbm_batch* batch, int64_t* steps, in
 /* Frees the batch (not its members; NULL is allowed).  Synchronises. */
 LBM_API lbm_status lbm_batch_destroy(lbm_batch* batch);
 
+/* Self-test of the device-side time-out path (no counterpart in the paper).
+ * Every wait of the solver's kernels on an mbarrier (the completion of a bulk
+ * copy) polls at most a fixed number of times, then records LBM_E_TIMEOUT
+ * and lets the kernel return instead of hanging.  This launches one CTA whose
+ * barrier can never complete (two arrivals expected, one made) and waits on
+ * it with the same bounded wait, `polls` polls at most (1 .. 2^22); on
+ * return *timed_out is 1 when the wait gave up, 0 if it completed (which
+ * would be a defect).  Nothing faults or hangs; the CUDA context stays usable.
+ * Allocates 4 device bytes; synchronises cuda_stream (NULL: legacy stream).
+ * Errors: LBM_E_INVALID, LBM_E_OOM, LBM_E_CUDA. */
+LBM_API lbm_status lbm_selftest_bounded_wait(uint32_t polls, void* cuda_stream, int32_t* timed_out);
+
 /* ------------------------------------------------------------------------
  * Allocation-free diagnostics (no counterpart in the paper).
  *

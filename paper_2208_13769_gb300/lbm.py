@@ -85,6 +85,7 @@ _SIGNATURES = {
     "lbm_batch_get_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_int32)]),
     "lbm_batch_destroy": (C.c_int, [C.c_void_p]),
+    "lbm_selftest_bounded_wait": (C.c_int, [C.c_uint32, C.c_void_p, C.POINTER(C.c_int32)]),
 }
 
 
@@ -234,6 +235,15 @@ def lbm_batch_get_info(batch) -> tuple:
 
 def lbm_batch_destroy(batch):
     return _check(lib().lbm_batch_destroy(batch), "lbm_batch_destroy")
+
+
+def lbm_selftest_bounded_wait(polls: int, stream: int = 0) -> int:
+    """1 if the device-side bounded wait on a never-completing barrier gave
+    up after `polls` polls (the expected outcome)."""
+    out = C.c_int32(-1)
+    _check(lib().lbm_selftest_bounded_wait(int(polls), C.c_void_p(stream or None), C.byref(out)),
+           "lbm_selftest_bounded_wait")
+    return int(out.value)
 
 
 def lbm_last_cuda_error(ctx) -> str:

@@ -198,3 +198,14 @@ def test_call_order_and_argument_errors():
         assert per == 104 and dev > 0
     finally:
         lbm.lbm_destroy(ctx)
+
+
+def test_bounded_wait_gives_up_and_the_context_survives():
+    """The time-out path of the kernels' bounded mbarrier waits, run for real
+    on a barrier that never completes: the wait returns, nothing faults, and
+    a solver step right after still matches the oracle."""
+    assert lbm.lbm_selftest_bounded_wait(1 << 12) == 1
+    assert lbm.lbm_selftest_bounded_wait(1 << 16) == 1
+    prob, steps = CASES["clamped_96x50"]
+    ref, got = run_both(prob, 20, "f64")
+    compare(ref, got, TOL["f64"])
