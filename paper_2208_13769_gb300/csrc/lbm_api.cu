@@ -86,6 +86,23 @@ StepParams lbm::make_params(const lbm_ctx* c, int parity) {
         p.enc_scale[i] = float(1.0 / dec);
     }
     for (int e = 0; e < 4; ++e) p.bc[e] = c->bc[e];
+    // lattice constants in FP64, and rounded to FP32
+    double* L = p.lat_d;
+    L[kLatOmega] = p.omega;
+    L[kLatOneMOmega] = 1.0 - p.omega;
+    L[kLatForcePref] = 1.0 - 0.5 * p.omega;
+    L[kLatKu] = p.dX / (2.0 * p.rho0);
+    L[kLatInv2dX] = 1.0 / (2.0 * p.dX);
+    L[kLatSqScale] = p.dt * p.dt / (2.0 * p.dX * p.dX);
+    L[kLatSb0] = p.dt * p.dt / p.dX * p.rho0 * p.body[0];
+    L[kLatSb1] = p.dt * p.dt / p.dX * p.rho0 * p.body[1];
+    L[kLatLambda] = p.lambda;
+    L[kLatMu] = p.mu;
+    L[kLatInvC2] = 1.0 / (p.c * p.c);
+    L[kLatCOverRho0] = p.c / p.rho0;
+    L[kLatRho0OverC] = p.rho0 / p.c;
+    L[kLatRho0] = p.rho0;
+    for (int k = 0; k < kLatCount; ++k) p.lat_f[k] = float(L[k]);
     return p;
 }
 

@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kEdgeThreads, 3) edge_tile_kernel(const __grid
     if (MODE == 0) n_now = p.counter[p.parity] + 1;
     if (tile.lead && t == 0) p.counter[p.parity ^ 1] = n_now;
     const double t_now = double(n_now) * p.dt;
-    if (t < 4) edge_now<TC, UT>(s_edge[t], p.bc[t], t_now, p.rho0 / p.c);
+    if (t < 4) edge_now<TC, UT>(s_edge[t], p.bc[t], t_now, p.lat_d[kLatRho0OverC]);
 
     LatConsts<TC> k;
     k.load(p);

@@ -63,6 +63,29 @@ struct StepParams {
     float enc_scale[9];  // 16-bit storage: 1 / (w_i 2^-s)
     float dec_scale[9];  // w_i 2^-s
     EdgeBC bc[4];
+    // lattice constants, computed once on the host in FP64 (kLat* indices);
+    // lat_f holds the same values rounded to FP32
+    double lat_d[16];
+    float lat_f[16];
+};
+
+// Indices into StepParams::lat_d / lat_f.
+enum LatIndex : int {
+    kLatOmega = 0,      // omega = dt / tau
+    kLatOneMOmega,      // 1 - omega
+    kLatForcePref,      // 1 - omega / 2
+    kLatKu,             // dX / (2 rho0)
+    kLatInv2dX,         // 1 / (2 dX)
+    kLatSqScale,        // dt^2 / (2 dX^2)
+    kLatSb0,            // (dt^2 / dX) rho0 b_x
+    kLatSb1,            // (dt^2 / dX) rho0 b_y
+    kLatLambda,         // lambda
+    kLatMu,             // mu
+    kLatInvC2,          // 1 / c^2
+    kLatCOverRho0,      // c / rho0
+    kLatRho0OverC,      // rho0 / c
+    kLatRho0,           // rho0
+    kLatCount
 };
 
 }  // namespace lbm

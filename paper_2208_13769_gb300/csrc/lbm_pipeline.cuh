@@ -120,25 +120,39 @@ __device__ __forceinline__ TC dq_axis(TC qm, TC q0, TC qp, TC q1, TC q2, bool gh
     return ghost_hi ? -v : v;
 }
 
+// Lattice constants of a launch in the arithmetic type, read from the
+// host-computed table (no FP64 arithmetic on the device: its FP64 units are
+// slow on this part).
+template <class TC>
+__device__ __forceinline__ TC lat_const(const StepParams& p, int k);
+template <>
+__device__ __forceinline__ float lat_const<float>(const StepParams& p, int k) {
+    return p.lat_f[k];
+}
+template <>
+__device__ __forceinline__ double lat_const<double>(const StepParams& p, int k) {
+    return p.lat_d[k];
+}
+
 template <class TC>
 struct LatConsts {
     TC omega, one_m_omega, force_pref, ku, inv_2dx, sq_scale, sb0, sb1, lam, mu, inv_c2, c_over_rho0,
         rho0_over_c, rho0;
     __device__ __forceinline__ void load(const StepParams& p) {
-        omega = TC(p.omega);
-        one_m_omega = TC(1.0 - p.omega);
-        force_pref = TC(1.0 - 0.5 * p.omega);
-        ku = TC(p.dX / (2.0 * p.rho0));
-        inv_2dx = TC(1.0 / (2.0 * p.dX));
-        sq_scale = TC(p.dt * p.dt / (2.0 * p.dX * p.dX));
-        sb0 = TC(p.dt * p.dt / p.dX * p.rho0 * p.body[0]);
-        sb1 = TC(p.dt * p.dt / p.dX * p.rho0 * p.body[1]);
-        lam = TC(p.lambda);
-        mu = TC(p.mu);
-        inv_c2 = TC(1.0 / (p.c * p.c));
-        c_over_rho0 = TC(p.c / p.rho0);
-        rho0_over_c = TC(p.rho0 / p.c);
-        rho0 = TC(p.rho0);
+        omega = lat_const<TC>(p, kLatOmega);
+        one_m_omega = lat_const<TC>(p, kLatOneMOmega);
+        force_pref = lat_const<TC>(p, kLatForcePref);
+        ku = lat_const<TC>(p, kLatKu);
+        inv_2dx = lat_const<TC>(p, kLatInv2dX);
+        sq_scale = lat_const<TC>(p, kLatSqScale);
+        sb0 = lat_const<TC>(p, kLatSb0);
+        sb1 = lat_const<TC>(p, kLatSb1);
+        lam = lat_const<TC>(p, kLatLambda);
+        mu = lat_const<TC>(p, kLatMu);
+        inv_c2 = lat_const<TC>(p, kLatInvC2);
+        c_over_rho0 = lat_const<TC>(p, kLatCOverRho0);
+        rho0_over_c = lat_const<TC>(p, kLatRho0OverC);
+        rho0 = lat_const<TC>(p, kLatRho0);
     }
 };
 
