@@ -97,7 +97,9 @@ typedef struct {
  * (Algorithm 1's initialisation: f_i = f_i^eq(r, j, Pbar) with r = -rho0 Div u0,
  * j = rho0 v0, Pbar = Pbar(Grad u0)).  *out receives the context, or NULL on
  * error.  Errors: LBM_E_INVALID (null pointers, nx or ny < 3, dX <= 0, unknown
- * enum, size overflow), LBM_E_OOM, LBM_E_CUDA. */
+ * enum, size overflow: a padded plane of (nx + 168..231) x (ny + 6) nodes must
+ * hold fewer than 2^31 elements, e.g. bodies up to about 46 000 x 46 000),
+ * LBM_E_OOM, LBM_E_CUDA. */
 LBM_API lbm_status lbm_create(const lbm_desc* desc, lbm_ctx** out);
 
 /* Material of Sec. 7 (2D compressible neo-Hooke, plane strain) and the BGK

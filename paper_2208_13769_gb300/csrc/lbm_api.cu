@@ -396,6 +396,11 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
     const int64_t need = kPadCols + int64_t(d->nx) + kSegMax + 16;
     c->pitch = (need + 63) / 64 * 64;
     c->plane = c->pitch * (int64_t(d->ny) + 2 * kPadRows);
+    if (c->plane > 0x7fffffffLL) {  // the interior kernel indexes a plane with 32-bit offsets
+        free_all(c);
+        delete c;
+        return LBM_E_INVALID;
+    }
 
     const size_t fbytes = size_t(9) * c->plane * elem_size_storage(c->fmt);
     const size_t abytes = size_t(2 * ucarry_planes(c->fmt)) * c->plane * elem_size_ucarry(c->fmt);

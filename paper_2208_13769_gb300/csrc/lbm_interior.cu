@@ -151,13 +151,28 @@ __device__ __forceinline__ void interior_tile(const StepParams& p, int bx, int b
             else s_abort = 2;
         }
 
+    // 32-bit element offsets inside a plane (a plane holds fewer than 2^31
+    // elements, checked at context creation) and per-plane base pointers,
+    // which are the same for every thread of the CTA
+    const int32_t pitch32 = int32_t(pitch);
+    int32_t off_a = (a0 + kPadRows) * pitch32 + int32_t(col_off);  // row a of stage A, this column
+    TS* fd[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fd[i] = fdst + int64_t(i) * plane;
+    const CT* as0 = a_src;
+    const CT* as1 = a_src + UP * plane;
+    CT* ad[2 * UP];
+#pragma unroll
+    for (int c = 0; c < 2 * UP; ++c) ad[c] = a_dst + int64_t(c) * plane;
+    const TC* ss1 = s_src + plane;
+    TC* sd1 = s_dst + plane;
+
     // carries prefetched one row ahead
     UT an0, an1;
     TC sn_old0 = TC(0), sn_old1 = TC(0);
-    int64_t off_a = int64_t(a0 + kPadRows) * pitch + col_off;  // row a of stage A, this column
     if (colA) {
-        an0 = UT::ld_global(a_src, off_a, plane);
-        an1 = UT::ld_global(a_src + UP * plane, off_a, plane);
+        an0 = UT::ld_global(as0, off_a, plane);
+        an1 = UT::ld_global(as1, off_a, plane);
     }
 
     bool bad = false;
@@ -182,9 +197,8 @@ __device__ __forceinline__ void interior_tile(const StepParams& p, int bx, int b
             su[(sA * 2) * NT + t] = an0.add(k.ku * m0);
             su[(sA * 2 + 1) * NT + t] = an1.add(k.ku * m1);
             if (q + 1 < niter) {
-                off_a += pitch;
-                an0 = UT::ld_global(a_src, off_a, plane);
-                an1 = UT::ld_global(a_src + UP * plane, off_a, plane);
+                an0 = UT::ld_global(as0, off_a + pitch32, plane);
+                an1 = UT::ld_global(as1, off_a + pitch32, plane);
             }
         }
         __syncthreads();
@@ -197,9 +211,9 @@ __device__ __forceinline__ void interior_tile(const StepParams& p, int bx, int b
         }
         // source carry of the next iteration's stage C row (a - 1)
         if (colC && q >= 3 && q + 1 < niter) {
-            const int64_t o = int64_t(a0 + q - 1 + kPadRows) * pitch + col_off;
+            const int32_t o = off_a - pitch32;  // row a - 1
             sn_old0 = s_src[o];
-            sn_old1 = s_src[o + plane];
+            sn_old1 = ss1[o];
         }
 
         // ---------------- stage B: row a - 1
@@ -278,10 +292,9 @@ __device__ __forceinline__ void interior_tile(const StepParams& p, int bx, int b
             fc[7] = k.one_m_omega * f[7] + (ap - bp);
             fc[6] = k.one_m_omega * f[6] + (am + bm);
             fc[8] = k.one_m_omega * f[8] + (am - bm);
-            const int64_t o = int64_t(gy + kPadRows) * pitch + col_off;
-            TS* dst = fdst + o;
+            const int32_t o = off_a - 2 * pitch32;  // row a - 2 = gy
 #pragma unroll
-            for (int i = 0; i < 9; ++i) dst[i * plane] = Codec<TS, TC>::st(fc[i], i, p);
+            for (int i = 0; i < 9; ++i) fd[i][o] = Codec<TS, TC>::st(fc[i], i, p);
 
             // carries: A' = u + ku (jh + s/2), u = u* + du;  s' = s
             const UT ux = su[(sC * 2) * NT + t], uy = su[(sC * 2 + 1) * NT + t];
@@ -289,11 +302,11 @@ __device__ __forceinline__ void interior_tile(const StepParams& p, int bx, int b
             const UT A1 = uy.add(du1 + k.ku * (j1 + TC(0.5) * sn1)).renorm();
 #pragma unroll
             for (int c = 0; c < UP; ++c) {
-                a_dst[c * plane + o] = A0.part(c);
-                a_dst[(UP + c) * plane + o] = A1.part(c);
+                ad[c][o] = A0.part(c);
+                ad[UP + c][o] = A1.part(c);
             }
             s_dst[o] = sn0;
-            s_dst[plane + o] = sn1;
+            sd1[o] = sn1;
             if (fields != nullptr) {
                 const int64_t fo = int64_t(gy) * p.nx + gx;
                 const int64_t np = int64_t(p.nx) * p.ny;
@@ -307,6 +320,7 @@ __device__ __forceinline__ void interior_tile(const StepParams& p, int bx, int b
         }
         sA = sA == 2 ? 0 : sA + 1;
         ra = ra + 1 == R ? 0 : ra + 1;
+        off_a += pitch32;
     }
     if (bad) atomicOr(p.flag, 1);
     if (s_abort && t == 0) {
