@@ -147,6 +147,36 @@ LBM_API lbm_status lbm_step(lbm_ctx* ctx, int64_t nsteps);
  * LBM_E_OOM, LBM_E_CUDA, and LBM_E_UNSTABLE / LBM_E_TIMEOUT as lbm_sync. */
 LBM_API lbm_status lbm_profile_steps(lbm_ctx* ctx, int64_t nsteps, double out[4]);
 
+/* Decomposition of the interior launch (no counterpart in the paper; it
+ * changes how the work is split, never the result: every setting gives
+ * bit-identical fields). */
+typedef struct {
+    int32_t ring_slots; /* rows of the bulk-copy ring, 4..8 (lookahead = ring - 3); 0: default (5) */
+    int32_t chunk_rows; /* rows per CTA, >= 8; 0: one wave of CTAs over the SMs (default) */
+    int32_t aligned;    /* 1: strips on 32-byte sector boundaries (120 columns; 112 for
+                           16-bit storage); 0: 124-column strips; -1: default (0) */
+} lbm_tuning;
+
+/* Sets the decomposition; only before the first lbm_step / lbm_read_fields /
+ * lbm_diagnostics (LBM_E_STATE after).  Errors: LBM_E_INVALID (out of range). */
+LBM_API lbm_status lbm_set_tuning(lbm_ctx* ctx, const lbm_tuning* tuning);
+
+/* The decomposition in use once the context has run (rows per CTA and ring
+ * depth as planned), else the one requested. */
+LBM_API lbm_status lbm_get_tuning(const lbm_ctx* ctx, lbm_tuning* tuning);
+
+/* Autotuner: times `steps` graph-replayed steps of scratch contexts with
+ * desc's size, storage, carry, scheme, stream and device, zero initial
+ * fields, lambda = mu = 0.3, and the given edge kinds (periodic edges in
+ * pairs), for each candidate decomposition (ring 4, 5, 6 x rows per CTA one
+ * wave, 32, 96, 256 x both strip grids), and returns the fastest in *best
+ * (its time per step in *best_ms, may be NULL).  The time of a step does not
+ * depend on the field values, so the choice holds for any body of that shape.
+ * Allocates and frees one scratch context at a time.  Synchronises.
+ * Errors: LBM_E_INVALID, and those of lbm_create / lbm_step. */
+LBM_API lbm_status lbm_autotune(const lbm_desc* desc, const int32_t edge_kind[4], int64_t steps,
+                                lbm_tuning* best, double* best_ms);
+
 /* Field bits for lbm_read_fields; the output holds the requested fields in
  * this bit order, each as [ny][nx][ncomp] FP64. */
 enum {

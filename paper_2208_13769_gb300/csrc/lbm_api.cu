@@ -146,14 +146,18 @@ static cudaError_t build_plan(lbm_ctx* c) {
         const int r[4] = {bx, nx - bx, by, ny - by};
         for (int k = 0; k < 4; ++k) c->irect[k] = r[k];
         const int h = r[3] - r[2];
-        c->i_ring = kInteriorRing;
+        c->i_ring = c->tune_ring ? c->tune_ring : kInteriorRing;
         const int per_sm = std::max(1, interior_occupancy(c->fmt, c->i_ring));
-        // exactly one wave of equal CTAs: strips x chunks <= SMs x per_sm
-        interior_strips(c->fmt, r[0], r[1], false, &c->i_strip_x0, &c->i_strip_w, &c->i_tiles_x);
-        const int64_t slots = int64_t(c->num_sms) * per_sm;
-        const int64_t chunks = std::max<int64_t>(1, slots / c->i_tiles_x);
-        int64_t rows = (h + chunks - 1) / chunks;
-        rows = std::max<int64_t>(rows, 16);
+        interior_strips(c->fmt, r[0], r[1], c->tune_aligned == 1, &c->i_strip_x0, &c->i_strip_w, &c->i_tiles_x);
+        int64_t rows;
+        if (c->tune_chunk > 0) {
+            rows = c->tune_chunk;
+        } else {
+            // exactly one wave of equal CTAs: strips x chunks <= SMs x per_sm
+            const int64_t slots = int64_t(c->num_sms) * per_sm;
+            const int64_t chunks = std::max<int64_t>(1, slots / c->i_tiles_x);
+            rows = std::max<int64_t>((h + chunks - 1) / chunks, 16);
+        }
         rows = std::min<int64_t>(rows, h);
         c->i_chunk = int(rows);
         c->i_tiles_y = int((h + rows - 1) / rows);
@@ -576,6 +580,99 @@ lbm_status lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double out[4]) {
     for (int q = 0; q < 3; ++q) out[q] = sum[q] / double(counted);
     out[3] = c->has_interior ? double(c->irect[1] - c->irect[0]) * double(c->irect[3] - c->irect[2]) : 0.0;
     return ctx_check_flag(c);
+}
+
+lbm_status lbm_set_tuning(lbm_ctx* c, const lbm_tuning* t) {
+    if (!c || !t) return LBM_E_INVALID;
+    if (c->sticky) return LBM_E_CUDA;
+    if (c->planned) return LBM_E_STATE;
+    if ((t->ring_slots != 0 && (t->ring_slots < 4 || t->ring_slots > 8)) ||
+        (t->chunk_rows != 0 && (t->chunk_rows < 8 || t->chunk_rows > (1 << 20))) || t->aligned < -1 ||
+        t->aligned > 1)
+        return LBM_E_INVALID;
+    c->tune_ring = t->ring_slots;
+    c->tune_chunk = t->chunk_rows;
+    c->tune_aligned = t->aligned;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_tuning(const lbm_ctx* c, lbm_tuning* t) {
+    if (!c || !t) return LBM_E_INVALID;
+    if (c->planned && c->has_interior) {
+        t->ring_slots = c->i_ring;
+        t->chunk_rows = c->i_chunk;
+        t->aligned = c->tune_aligned == 1 ? 1 : 0;
+    } else {
+        t->ring_slots = c->tune_ring;
+        t->chunk_rows = c->tune_chunk;
+        t->aligned = c->tune_aligned;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_autotune(const lbm_desc* d, const int32_t edge_kind[4], int64_t steps, lbm_tuning* best,
+                        double* best_ms) {
+    if (!d || !edge_kind || !best || steps < 1 || steps > 100000) return LBM_E_INVALID;
+    for (int e = 0; e < 4; ++e)
+        if (edge_kind[e] < LBM_PERIODIC || edge_kind[e] > LBM_NEUMANN) return LBM_E_INVALID;
+    if ((edge_kind[0] == LBM_PERIODIC) != (edge_kind[1] == LBM_PERIODIC) ||
+        (edge_kind[2] == LBM_PERIODIC) != (edge_kind[3] == LBM_PERIODIC))
+        return LBM_E_INVALID;
+    lbm_desc sd = *d;  // the same body shape and format, zero initial fields
+    sd.u0 = nullptr;
+    sd.v0 = nullptr;
+    // candidates: ring depth x rows per CTA (0: one wave) x strip grid
+    const int rings[3] = {4, 5, 6};
+    const int chunks[4] = {0, 32, 96, 256};
+    double best_t = INFINITY;
+    lbm_tuning bt = {0, 0, -1};
+    lbm_status last = LBM_OK;
+    for (int a = 0; a < 2; ++a)
+        for (int ri = 0; ri < 3; ++ri)
+            for (int ci = 0; ci < 4; ++ci) {
+                const int ch = chunks[ci];
+                if (ch > 0 && ch >= d->ny) continue;  // the same as one chunk of all rows
+                lbm_ctx* c = nullptr;
+                lbm_status st = lbm_create(&sd, &c);
+                if (st != LBM_OK) return st;
+                const lbm_tuning t = {rings[ri], ch, a};
+                st = lbm_set_tuning(c, &t);
+                if (st == LBM_OK) st = lbm_set_material(c, 0.3, 0.3, 1.0, 1.0, nullptr);
+                for (int e = 0; e < 4 && st == LBM_OK; ++e)
+                    st = lbm_set_boundary(c, e, edge_kind[e], nullptr, nullptr, nullptr);
+                // warm: initialisation, a plain step, the graphs of both parities
+                if (st == LBM_OK) st = lbm_step(c, 2 * kGraphChunk + 2);
+                double ms = INFINITY;
+                if (st == LBM_OK) {
+                    DeviceGuard guard(c->device);
+                    cudaEvent_t e0 = nullptr, e1 = nullptr;
+                    cudaError_t err = cudaEventCreate(&e0);
+                    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+                    if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+                    if (err == cudaSuccess) st = lbm_step(c, steps);
+                    if (err == cudaSuccess && st == LBM_OK) err = cudaEventRecord(e1, c->stream);
+                    if (err == cudaSuccess && st == LBM_OK) err = cudaEventSynchronize(e1);
+                    float f = 0;
+                    if (err == cudaSuccess && st == LBM_OK && cudaEventElapsedTime(&f, e0, e1) == cudaSuccess)
+                        ms = double(f) / double(steps);
+                    if (e0) cudaEventDestroy(e0);
+                    if (e1) cudaEventDestroy(e1);
+                    if (err != cudaSuccess) st = LBM_E_CUDA;
+                }
+                lbm_destroy(c);
+                if (st != LBM_OK) {
+                    last = st;
+                    continue;
+                }
+                if (ms < best_t) {
+                    best_t = ms;
+                    bt = t;
+                }
+            }
+    if (!(best_t < INFINITY)) return last != LBM_OK ? last : LBM_E_CUDA;
+    *best = bt;
+    if (best_ms) *best_ms = best_t;
+    return LBM_OK;
 }
 
 int64_t lbm_fields_size(const lbm_ctx* c, uint32_t mask) {

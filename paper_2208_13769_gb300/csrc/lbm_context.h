@@ -76,6 +76,9 @@ struct lbm_ctx {
     bool has_interior = false;
     int irect[4] = {0, 0, 0, 0};
     int i_tiles_x = 0, i_tiles_y = 0, i_chunk = 0, i_ring = 0, i_strip_x0 = 0, i_strip_w = 0;
+    // requested decomposition of the interior launch (lbm_set_tuning); 0 / -1:
+    // the library's defaults
+    int tune_ring = 0, tune_chunk = 0, tune_aligned = -1;
     int nband = 0;
     int brect[4][4];
     lbm::StepParams* dparams = nullptr;  // device: make_params(parity 0), make_params(parity 1)

@@ -43,6 +43,13 @@ class lbm_desc(C.Structure):
     ]
 
 
+class lbm_tuning(C.Structure):
+    _fields_ = [("ring_slots", C.c_int32), ("chunk_rows", C.c_int32), ("aligned", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"ring_slots": self.ring_slots, "chunk_rows": self.chunk_rows, "aligned": self.aligned}
+
+
 class lbm_field_geometry(C.Structure):
     _fields_ = [
         ("nx", C.c_int32), ("ny", C.c_int32), ("dX", C.c_double), ("lam", C.c_double),
@@ -86,6 +93,10 @@ _SIGNATURES = {
                                      C.POINTER(C.c_int32)]),
     "lbm_batch_destroy": (C.c_int, [C.c_void_p]),
     "lbm_selftest_bounded_wait": (C.c_int, [C.c_uint32, C.c_void_p, C.POINTER(C.c_int32)]),
+    "lbm_set_tuning": (C.c_int, [C.c_void_p, C.POINTER(lbm_tuning)]),
+    "lbm_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(lbm_tuning)]),
+    "lbm_autotune": (C.c_int, [C.POINTER(lbm_desc), C.POINTER(C.c_int32), C.c_int64, C.POINTER(lbm_tuning),
+                               C.POINTER(C.c_double)]),
 }
 
 
@@ -246,6 +257,62 @@ def lbm_selftest_bounded_wait(polls: int, stream: int = 0) -> int:
     return int(out.value)
 
 
+def lbm_set_tuning(ctx, tuning: "lbm_tuning"):
+    return _check(lib().lbm_set_tuning(ctx, C.byref(tuning)), "lbm_set_tuning")
+
+
+def lbm_get_tuning(ctx) -> "lbm_tuning":
+    t = lbm_tuning()
+    _check(lib().lbm_get_tuning(ctx, C.byref(t)), "lbm_get_tuning")
+    return t
+
+
+def lbm_autotune(desc: lbm_desc, edge_kinds, steps: int = 129) -> tuple:
+    """(best lbm_tuning, its ms per step) for bodies shaped like desc."""
+    kinds = (C.c_int32 * 4)(*[int(k) for k in edge_kinds])
+    t, ms = lbm_tuning(), C.c_double()
+    _check(lib().lbm_autotune(C.byref(desc), kinds, int(steps), C.byref(t), C.byref(ms)), "lbm_autotune")
+    return t, ms.value
+
+
+def tuning_from_dict(d: dict) -> lbm_tuning:
+    return lbm_tuning(int(d["ring_slots"]), int(d["chunk_rows"]), int(d["aligned"]))
+
+
+def autotune_cached(prob, storage: str = "f32", compensated: Optional[bool] = None,
+                    scheme: int = LBM_SCHEME_PREDICTOR, cache_path: Optional[str] = None, steps: int = 129,
+                    stream: int = 0, device: int = 0) -> lbm_tuning:
+    """The autotuner's choice for bodies of prob's size and edge kinds, from a
+    JSON cache (keyed by storage, carry, scheme, size and edge kinds) when it
+    holds one, else measured now and stored."""
+    import json
+
+    comp = True if compensated is None else compensated
+    kinds = [e.kind for e in prob.edges]
+    key = f"{storage}:{int(comp)}:{scheme}:{prob.nx}x{prob.ny}:{''.join(str(k) for k in kinds)}"
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as fh:
+            cache = json.load(fh)
+    if key in cache:
+        return tuning_from_dict(cache[key])
+    d = lbm_desc()
+    d.nx, d.ny, d.dX = prob.nx, prob.ny, prob.dX
+    d.storage = STORAGE[storage]
+    d.u_carry = LBM_UCARRY_COMPENSATED if comp else LBM_UCARRY_NATIVE
+    d.scheme = scheme
+    d.cuda_stream = stream or None
+    d.device = device
+    t, ms = lbm_autotune(d, kinds, steps)
+    if cache_path:
+        cache[key] = dict(t.as_dict(), ms_per_step=ms)
+        tmp = cache_path + ".tmp"
+        with open(tmp, "w") as fh:
+            json.dump(cache, fh, indent=1, sort_keys=True)
+        os.replace(tmp, cache_path)
+    return t
+
+
 def lbm_last_cuda_error(ctx) -> str:
     return lib().lbm_last_cuda_error(ctx).decode()
 
@@ -266,7 +333,7 @@ class Body:
 
     def __init__(self, prob, storage: str = "f64", compensated: Optional[bool] = None,
                  scheme: int = LBM_SCHEME_PREDICTOR, stream: int = 0, device: int = 0,
-                 f16_scale_log2: int = 0):
+                 f16_scale_log2: int = 0, tuning: Optional["lbm_tuning"] = None):
         self.prob = prob
         d = lbm_desc()
         d.nx, d.ny, d.dX = prob.nx, prob.ny, prob.dX
@@ -285,6 +352,8 @@ class Body:
         d.device = device
         self.ctx = lbm_create(d)
         self._u0 = self._v0 = None  # copied to the device by lbm_create
+        if tuning is not None:
+            lbm_set_tuning(self.ctx, tuning)
         lbm_set_material(self.ctx, prob.lam, prob.mu, prob.rho0, prob.omega, prob.body)
         for k, e in enumerate(prob.edges):
             lbm_set_boundary(self.ctx, k, e.kind, e.value, e.rate, e.times)

@@ -209,3 +209,33 @@ def test_bounded_wait_gives_up_and_the_context_survives():
     prob, steps = CASES["clamped_96x50"]
     ref, got = run_both(prob, 20, "f64")
     compare(ref, got, TOL["f64"])
+
+
+def test_tuning_changes_the_split_not_the_result():
+    """Every decomposition of the interior launch (ring depth, rows per CTA,
+    strip grid) gives bit-identical fields; the autotuner returns one of the
+    candidates and the tuning in use is reported."""
+    prob, _ = CASES["clamped_96x50"]
+    big = W.smooth_random(400, 300, W.clamped_free_edges(), seed=23, amp=0.01, vamp=0.004, lam=0.3, mu=0.3)
+    for pr in (prob, big):
+        with lbm.Body(pr, storage="f32") as b:
+            b.step(140)
+            ref = b.read(lbm.LBM_FIELD_U | lbm.LBM_FIELD_V | lbm.LBM_FIELD_R)
+        for ring, chunk, aligned in ((4, 0, 0), (6, 32, 1), (8, 9, 0), (5, 256, 1)):
+            t = lbm.lbm_tuning(ring, chunk, aligned)
+            with lbm.Body(pr, storage="f32", tuning=t) as b:
+                b.step(140)
+                got = b.read(lbm.LBM_FIELD_U | lbm.LBM_FIELD_V | lbm.LBM_FIELD_R)
+                used = lbm.lbm_get_tuning(b.ctx)
+            assert used.ring_slots == ring and used.aligned == aligned
+            for k in ("u", "v", "r"):
+                assert np.array_equal(got[k], ref[k]), (pr.name, ring, chunk, aligned, k)
+    d = lbm.lbm_desc()
+    d.nx, d.ny, d.dX, d.storage, d.u_carry, d.scheme = 400, 300, 1.0, lbm.LBM_F32, 1, 1
+    best, ms = lbm.lbm_autotune(d, [e.kind for e in big.edges], 65)
+    assert best.ring_slots in (4, 5, 6) and best.chunk_rows in (0, 32, 96, 256) and best.aligned in (0, 1)
+    assert 0 < ms < 1.0
+    with lbm.Body(big, storage="f32") as b:
+        with pytest.raises(lbm.LbmError):
+            b.step(1)
+            lbm.lbm_set_tuning(b.ctx, best)  # too late: the context has planned its launches
