@@ -8,6 +8,7 @@ linear-elastic P-wave speed, and patch tests in which the exact solution is
 static or uniform.  The D2Q9 lattice used to take moments below is the
 textbook one, typed here independently of the oracle.
 """
+import dataclasses
 import json
 import math
 import os
@@ -345,3 +346,43 @@ def test_problem_validation():
     p = W.uniform_motion(2, 8, (0, 0))
     with pytest.raises(ValueError):
         oracle.solver_from(p)
+
+
+# ---------------------------------------------------------------- brute force
+# A second restatement of the method (tests/brute_force.py: Python floats,
+# link by link) on bodies so small that every node meets a boundary rule, a
+# ghost value or a corner link.
+
+def _tiny_cases():
+    from paper_2208_13769_gb300 import workloads as W
+
+    N0, D0, Pp = W.Edge(W.NEUMANN), W.Edge(W.DIRICHLET), W.Edge(W.PERIODIC)
+    ramp = W.Edge(W.NEUMANN, value=(0.0, 0.0), rate=(0.02, -0.01), times=(0.0, 3.0, 1e9))
+    moving = W.Edge(W.DIRICHLET, value=(0.001, -0.002), rate=(0.003, 0.001))
+    return {
+        "3x3_neumann": W.smooth_random(3, 3, [N0] * 4, seed=31, amp=0.02, lam=0.3, mu=0.3),
+        "4x4_dirichlet_moving": W.smooth_random(4, 4, [moving] * 4, seed=32, amp=0.01, lam=0.45),
+        "5x4_mixed_ramp": W.smooth_random(5, 4, [D0, ramp, N0, moving], seed=33, amp=0.01, lam=0.3, mu=0.3),
+        "4x3_xperiodic_walls": W.smooth_random(4, 3, [Pp, Pp, D0, ramp], seed=34, amp=0.01, lam=0.3, mu=0.3),
+        "3x5_periodic": W.smooth_random(3, 5, [Pp] * 4, seed=35, amp=0.02, lam=0.45),
+        "6x5_body_force": dataclasses.replace(
+            W.smooth_random(6, 5, [N0, D0, N0, N0], seed=36, amp=0.01, lam=0.3, mu=0.3), body=(0.01, -0.02)),
+    }
+
+
+@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR])
+@pytest.mark.parametrize("name", sorted(_tiny_cases()))
+def test_oracle_matches_a_brute_force_restatement(name, scheme):
+    from brute_force import BruteForce
+
+    prob = _tiny_cases()[name]
+    bf = BruteForce(prob, scheme)
+    s = oracle.solver_from(prob, scheme)
+    for steps in (1, 2, 3):
+        bf.step()
+        s.step(1)
+        got, ref = bf.fields(), s.read()
+        for k in ("u", "v", "r"):
+            scale = max(np.abs(ref[k]).max(), 1e-30)
+            assert np.abs(got[k] - ref[k]).max() <= 1e-12 * scale, (name, scheme, steps, k)
+    s.close()
