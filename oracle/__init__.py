@@ -70,40 +70,46 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def load(path: str):
+    """A compiled oracle library at `path`, with its functions' signatures
+    (lib() loads the package's own build; the tests also load copies with
+    planted mistakes, to check that the pins catch them)."""
+    L = C.CDLL(path)
+    dp = C.POINTER(C.c_double)
+    L.orc_create.restype = C.c_void_p
+    L.orc_create.argtypes = [C.POINTER(OracleProblem), dp, dp]
+    L.orc_check.restype = C.c_int
+    L.orc_check.argtypes = [C.POINTER(OracleProblem)]
+    L.orc_step.restype = C.c_int
+    L.orc_step.argtypes = [C.c_void_p, C.c_long]
+    L.orc_destroy.argtypes = [C.c_void_p]
+    L.orc_read.argtypes = [C.c_void_p] + [dp] * 7
+    L.orc_read_populations.argtypes = [C.c_void_p, dp]
+    L.orc_read_grad.argtypes = [C.c_void_p, dp]
+    L.orc_time.restype = C.c_double
+    L.orc_time.argtypes = [C.c_void_p]
+    L.orc_dt.restype = C.c_double
+    L.orc_dt.argtypes = [C.c_void_p]
+    L.orc_step_count.restype = C.c_long
+    L.orc_step_count.argtypes = [C.c_void_p]
+    L.orc_time_step.argtypes = [C.c_double] * 3 + [dp] * 3
+    L.orc_feq.argtypes = [C.c_double, C.c_double, C.c_double, dp, dp, dp]
+    L.orc_psi.argtypes = [C.c_double, C.c_double, dp, dp]
+    L.orc_lattice.argtypes = [C.c_double, dp, dp, C.POINTER(C.c_int32)]
+    L.orc_piola.restype = C.c_double
+    L.orc_piola.argtypes = [dp, C.c_double, C.c_double, dp]
+    L.orc_strain_energy.restype = C.c_double
+    L.orc_strain_energy.argtypes = [dp, C.c_double, C.c_double]
+    L.orc_poisson_stress.argtypes = [dp, C.c_double, dp]
+    L.orc_threads.restype = C.c_int
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = build()
-            L = C.CDLL(path)
-            dp = C.POINTER(C.c_double)
-            L.orc_create.restype = C.c_void_p
-            L.orc_create.argtypes = [C.POINTER(OracleProblem), dp, dp]
-            L.orc_check.restype = C.c_int
-            L.orc_check.argtypes = [C.POINTER(OracleProblem)]
-            L.orc_step.restype = C.c_int
-            L.orc_step.argtypes = [C.c_void_p, C.c_long]
-            L.orc_destroy.argtypes = [C.c_void_p]
-            L.orc_read.argtypes = [C.c_void_p] + [dp] * 7
-            L.orc_read_populations.argtypes = [C.c_void_p, dp]
-            L.orc_read_grad.argtypes = [C.c_void_p, dp]
-            L.orc_time.restype = C.c_double
-            L.orc_time.argtypes = [C.c_void_p]
-            L.orc_dt.restype = C.c_double
-            L.orc_dt.argtypes = [C.c_void_p]
-            L.orc_step_count.restype = C.c_long
-            L.orc_step_count.argtypes = [C.c_void_p]
-            L.orc_time_step.argtypes = [C.c_double] * 3 + [dp] * 3
-            L.orc_feq.argtypes = [C.c_double, C.c_double, C.c_double, dp, dp, dp]
-            L.orc_psi.argtypes = [C.c_double, C.c_double, dp, dp]
-            L.orc_lattice.argtypes = [C.c_double, dp, dp, C.POINTER(C.c_int32)]
-            L.orc_piola.restype = C.c_double
-            L.orc_piola.argtypes = [dp, C.c_double, C.c_double, dp]
-            L.orc_strain_energy.restype = C.c_double
-            L.orc_strain_energy.argtypes = [dp, C.c_double, C.c_double]
-            L.orc_poisson_stress.argtypes = [dp, C.c_double, dp]
-            L.orc_threads.restype = C.c_int
-            _lib = L
+            _lib = load(build())
     return _lib
 
 
@@ -215,10 +221,10 @@ def make_problem(nx, ny, dX, lam, mu, rho0, omega, body, edges,
 class Solver:
     """The oracle state for one body; mirrors the library's create/step/read."""
 
-    def __init__(self, problem: OracleProblem, u0=None, v0=None):
+    def __init__(self, problem: OracleProblem, u0=None, v0=None, library=None):
         self.p = problem
         ny, nx = problem.ny, problem.nx
-        L = lib()
+        self._L = L = library if library is not None else lib()
         code = L.orc_check(C.byref(problem))
         if code != 0:
             raise ValueError(f"invalid oracle problem (code {code})")
@@ -232,19 +238,19 @@ class Solver:
         self._h = C.c_void_p(h)
 
     def step(self, n: int) -> None:
-        lib().orc_step(self._h, int(n))
+        self._L.orc_step(self._h, int(n))
 
     @property
     def t(self) -> float:
-        return lib().orc_time(self._h)
+        return self._L.orc_time(self._h)
 
     @property
     def dt(self) -> float:
-        return lib().orc_dt(self._h)
+        return self._L.orc_dt(self._h)
 
     @property
     def steps(self) -> int:
-        return lib().orc_step_count(self._h)
+        return self._L.orc_step_count(self._h)
 
     def read(self) -> dict:
         ny, nx = self.p.ny, self.p.nx
@@ -254,24 +260,24 @@ class Solver:
             "r": np.zeros((ny, nx)), "J": np.zeros((ny, nx)),
             "sigma": np.zeros((ny, nx, 3)),
         }
-        lib().orc_read(self._h, _dp(out["u"]), _dp(out["v"]), _dp(out["P"]),
+        self._L.orc_read(self._h, _dp(out["u"]), _dp(out["v"]), _dp(out["P"]),
                        _dp(out["Pbar"]), _dp(out["r"]), _dp(out["J"]), _dp(out["sigma"]))
         return out
 
     def grad(self) -> np.ndarray:
         """H = Grad u at the current time, [ny][nx][2][2]."""
         out = np.zeros((self.p.ny, self.p.nx, 2, 2))
-        lib().orc_read_grad(self._h, _dp(out))
+        self._L.orc_read_grad(self._h, _dp(out))
         return out
 
     def populations(self) -> np.ndarray:
         out = np.zeros((9, self.p.ny, self.p.nx))
-        lib().orc_read_populations(self._h, _dp(out))
+        self._L.orc_read_populations(self._h, _dp(out))
         return out
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None:
-            lib().orc_destroy(self._h)
+            self._L.orc_destroy(self._h)
             self._h = None
 
     def __del__(self):
