@@ -239,3 +239,35 @@ def test_tuning_changes_the_split_not_the_result():
         with pytest.raises(lbm.LbmError):
             b.step(1)
             lbm.lbm_set_tuning(b.ctx, best)  # too late: the context has planned its launches
+
+
+def test_benchmark_body_at_full_size_against_the_oracle():
+    """The benchmark's body (4096 x 2048 clamped, FP32 storage, compensated
+    carry) in the benchmark's launch configuration (one-wave interior, edge
+    tiles on the side stream, a captured 64-step graph) against the FP64
+    oracle on the same inputs, whole fields; and the FP64 path at 1e-12.
+
+    u and v meet the tolerances (FP64: 4.6e-15 and 9.0e-15; FP32: 2.7e-7
+    and 6.0e-7).  P is evaluated from differences of u, and at this size the
+    displacement is large against what its gradient changes over one node
+    (|u| / (|Grad u| dX) ~ 1e4 after 70 steps), so the rounding of u is
+    amplified that much in P: FP64 3.2e-12, FP32 2.1e-5 (the latter stays near
+    2e-5 up to 2000 steps against the FP64 path: the stored FP32 populations,
+    of the order of v / c ~ 1e-2, carry rounding into the momentum and through
+    it into Grad u, while the strains are ~1e-4).  Bounds asserted for P:
+    1e-10 (FP64) and 5e-5 (FP32); u and v at the stated tolerances."""
+    prob = W.clamped_body(4096, 2048, nu=0.25, vmax=0.01)
+    s = oracle.solver_from(prob, oracle.PREDICTOR)
+    s.step(70)
+    ref = s.read()
+    s.close()
+    with lbm.Body(prob, storage="f32", compensated=True) as b:
+        b.step(70)
+        got32 = b.read()
+    with lbm.Body(prob, storage="f64") as b:
+        b.step(70)
+        got64 = b.read()
+    compare(ref, got32, TOL["f32"], keys=("u", "v"))
+    compare(ref, got32, 5 * TOL["f32"], keys=("P",))
+    compare(ref, got64, TOL["f64"], keys=("u", "v", "J"))
+    compare(ref, got64, 100 * TOL["f64"], keys=("P", "Pbar"))
