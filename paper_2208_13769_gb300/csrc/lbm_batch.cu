@@ -2,9 +2,10 @@
 // lbm_batch_* entry points).
 //
 // Each time step of a batch is one launch of the interior kernel over the
-// work list of every member's interior tiles and one launch of the edge
-// kernel over every member's edge tiles (concurrent, on two streams), each
-// CTA reading its body's parameters from a device table.  So small and
+// work list of every member's interior tiles (a persistent grid of resident
+// CTAs, each taking items in turn) and one launch of the edge kernel over
+// every member's edge tiles (concurrent, on two streams), each CTA reading
+// its body's parameters from a device table.  So small and
 // uneven bodies share the GPU instead of each paying a launch per step, and
 // chunks of 64 steps replay as one CUDA graph.  Every node of every member
 // goes through the same kernels and arithmetic as when the member is
@@ -41,6 +42,7 @@ struct lbm_batch {
     StepParams* dtab = nullptr;  // [2][n]: entry q * n + i = member i at parity base_parity[i] ^ q
     InteriorWork* dwork = nullptr;
     int n_work = 0;
+    int grid = 0;  // persistent CTAs of the interior launch
     EdgeTile* dedge = nullptr;
     int n_edge = 0;
     int chunk_rows = 0;
@@ -86,6 +88,7 @@ cudaError_t batch_launch(lbm_batch* b, int q, bool fields) {
     il.params = b->dtab + size_t(q) * n;
     il.work = b->dwork;
     il.fields = fields ? 1 : 0;
+    il.nwork = b->n_work;
     EdgeLaunch el;
     memset(&el, 0, sizeof(el));
     el.params = b->dtab + size_t(q) * n;
@@ -94,7 +97,7 @@ cudaError_t batch_launch(lbm_batch* b, int q, bool fields) {
     if (b->n_work == 0) return launch_edge(b->fmt, el, b->n_edge, b->stream, 0);
     cudaError_t e = cudaEventRecord(b->ev_fork, b->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
-    if (e == cudaSuccess) e = launch_interior_batch(b->fmt, il, b->n_work, kInteriorRing, b->stream);
+    if (e == cudaSuccess) e = launch_interior_batch(b->fmt, il, b->grid, kInteriorRing, b->stream, nullptr);
     if (e == cudaSuccess) e = launch_edge(b->fmt, el, b->n_edge, b->side, 0);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
@@ -274,11 +277,14 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
         e = cudaMemcpyAsync(b->dedge, tiles.data(), sizeof(EdgeTile) * tiles.size(), cudaMemcpyHostToDevice,
                             b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host tables die with this scope
-    // sets the interior batch kernel's shared-memory limit outside any capture
+    // sets the interior batch kernel's shared-memory limit outside any
+    // capture, and sizes its persistent grid: every resident CTA slot
     if (e == cudaSuccess) {
         InteriorLaunch il;
         memset(&il, 0, sizeof(il));
-        e = launch_interior_batch(b->fmt, il, 0, kInteriorRing, b->stream);
+        int resident = 0;
+        e = launch_interior_batch(b->fmt, il, 0, kInteriorRing, b->stream, &resident);
+        b->grid = std::min(b->n_work, b->m[0]->num_sms * std::max(1, resident));
     }
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -67,9 +67,13 @@ __host__ __device__ constexpr size_t interior_row_bytes() {
 
 }  // namespace
 
-// One tile (column strip bx, row chunk by of p.rect) of one body.
+// One tile (column strip bx, row chunk by of p.rect) of one body.  Returns
+// false if a wait gave up or a copy was refused (reported in p.flag).
+// reuse: the CTA runs more tiles after this one, so the ring's mbarriers are
+// invalidated at the end (every copy has completed by then) for the next
+// tile to initialise them afresh.
 template <class TS, class TC, class UT, int NT>
-__device__ __forceinline__ void interior_tile(const StepParams& p, int bx, int by, double* fields) {
+__device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int by, double* fields, bool reuse) {
     using CT = typename UT::Elem;
     const int W = p.strip_w;
     constexpr int SEG = seg_elems<TS, NT>();
@@ -94,7 +98,7 @@ __device__ __forceinline__ void interior_tile(const StepParams& p, int bx, int b
     // strip bx of the strip grid, clipped to the rectangle
     const int x0 = p.strip_x0 + bx * W;
     const int x_lo = max(rx0, x0), x_hi = min(rx1, x0 + W);
-    if (x_lo >= x_hi || by * p.chunk_rows >= ry1 - ry0) return;
+    if (x_lo >= x_hi || by * p.chunk_rows >= ry1 - ry0) return true;
     int y_begin = ry0 + by * p.chunk_rows;
     if (y_begin > ry1 - p.chunk_rows) y_begin = ry1 - p.chunk_rows > ry0 ? ry1 - p.chunk_rows : ry0;
     const int y_end = min(ry1, y_begin + p.chunk_rows);
@@ -145,6 +149,9 @@ __device__ __forceinline__ void interior_tile(const StepParams& p, int bx, int b
     __syncthreads();
     const int D = R - 3;
     uint32_t phase = 0, issued = 0;
+    if (t == 0) {
+        fence_proxy_async();  // a previous tile's reads of the ring precede these copies
+    }
     if (t == 0)
         for (int j = 0; j < D && j < niter; ++j) {
             if (issue_row(a0 + j, j)) issued |= 1u << j;
@@ -323,31 +330,46 @@ __device__ __forceinline__ void interior_tile(const StepParams& p, int bx, int b
         off_a += pitch32;
     }
     if (bad) atomicOr(p.flag, 1);
-    if (s_abort && t == 0) {
-        atomicOr(p.flag, s_abort == 2 ? 8 : 4);
-        for (int s = 0; s < R; ++s)
-            if (issued & (1u << s)) (void)mbar_wait(&bars[s], (phase >> s) & 1u);
+    if (s_abort) {
+        if (t == 0) {
+            atomicOr(p.flag, s_abort == 2 ? 8 : 4);
+            for (int s = 0; s < R; ++s)
+                if (issued & (1u << s)) (void)mbar_wait(&bars[s], (phase >> s) & 1u);
+        }
+        return false;
     }
+    if (reuse) {
+        __syncthreads();  // every thread has finished with the ring and the row buffers
+        if (t == 0)
+            for (int s = 0; s < R; ++s) mbar_inval(&bars[s]);
+        __syncthreads();
+    }
+    return true;
 }
 
 template <class TS, class TC, class UT, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) interior_step_kernel(const __grid_constant__ StepParams p) {
-    interior_tile<TS, TC, UT, NT>(p, int(blockIdx.x), int(blockIdx.y), p.fields);
+    interior_tile<TS, TC, UT, NT>(p, int(blockIdx.x), int(blockIdx.y), p.fields, false);
 }
 
-// A batch of bodies: one CTA per work item (body, strip, chunk); the body's
-// parameters come from the device table into shared memory.
+// A batch of bodies: a persistent grid of resident CTAs, each running the
+// work items (body, strip, chunk) blockIdx.x, blockIdx.x + gridDim.x, ... in
+// turn (the list is ordered longest first); each item's parameters come from
+// the device table into shared memory.
 template <class TS, class TC, class UT, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) interior_batch_kernel(const __grid_constant__ InteriorLaunch L) {
     __shared__ __align__(16) StepParams sp;
-    const InteriorWork w = L.work[blockIdx.x];
-    {
-        const int4* src = reinterpret_cast<const int4*>(L.params + w.inst);
-        int4* dst = reinterpret_cast<int4*>(&sp);
-        for (int q = int(threadIdx.x); q < int(sizeof(StepParams) / 16); q += NT) dst[q] = src[q];
+    for (int wi = int(blockIdx.x); wi < L.nwork; wi += int(gridDim.x)) {
+        const InteriorWork w = L.work[wi];
+        __syncthreads();  // the previous item is done with sp
+        {
+            const int4* src = reinterpret_cast<const int4*>(L.params + w.inst);
+            int4* dst = reinterpret_cast<int4*>(&sp);
+            for (int q = int(threadIdx.x); q < int(sizeof(StepParams) / 16); q += NT) dst[q] = src[q];
+        }
+        __syncthreads();
+        if (!interior_tile<TS, TC, UT, NT>(sp, w.bx, w.by, L.fields ? sp.fields : nullptr, true)) break;
     }
-    __syncthreads();
-    interior_tile<TS, TC, UT, NT>(sp, w.bx, w.by, L.fields ? sp.fields : nullptr);
 }
 
 template <class TS, class TC, class UT, int NT>
@@ -371,7 +393,8 @@ cudaError_t launch_interior_t(const StepParams& p, cudaStream_t s) {
 }
 
 template <class TS, class TC, class UT, int NT, int MINB>
-cudaError_t launch_interior_batch_t(const InteriorLaunch& L, int nwork, int ring_slots, cudaStream_t s) {
+cudaError_t launch_interior_batch_t(const InteriorLaunch& L, int grid, int ring_slots, cudaStream_t s,
+                                    int* resident) {
     auto kern = interior_batch_kernel<TS, TC, UT, NT, MINB>;
     const size_t sm = interior_smem_bytes<TS, TC, UT, NT>(ring_slots);
     static size_t configured = 0;
@@ -380,19 +403,27 @@ cudaError_t launch_interior_batch_t(const InteriorLaunch& L, int nwork, int ring
         if (e != cudaSuccess) return e;
         configured = sm;
     }
-    if (nwork <= 0) return cudaSuccess;
-    kern<<<nwork, NT, sm, s>>>(L);
+    if (resident) {  // CTAs per SM of this kernel with this ring
+        *resident = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, kern, NT, sm);
+        if (e != cudaSuccess) return e;
+    }
+    if (grid <= 0 || L.nwork <= 0) return cudaSuccess;
+    kern<<<grid, NT, sm, s>>>(L);
     return cudaGetLastError();
 }
 
-cudaError_t launch_interior_batch(int fmt, const InteriorLaunch& L, int nwork, int ring_slots, cudaStream_t s) {
+cudaError_t launch_interior_batch(int fmt, const InteriorLaunch& L, int grid, int ring_slots, cudaStream_t s,
+                                  int* resident) {
     switch (fmt) {
-        case kFmtF64: return launch_interior_batch_t<double, double, UPlain<double>, 128, 2>(L, nwork, ring_slots, s);
-        case kFmtF32: return launch_interior_batch_t<float, float, UPlain<float>, 128, 4>(L, nwork, ring_slots, s);
-        case kFmtF32C: return launch_interior_batch_t<float, float, UComp, 128, 4>(L, nwork, ring_slots, s);
-        case kFmtF16: return launch_interior_batch_t<__half, float, UComp, 128, 4>(L, nwork, ring_slots, s);
+        case kFmtF64:
+            return launch_interior_batch_t<double, double, UPlain<double>, 128, 2>(L, grid, ring_slots, s, resident);
+        case kFmtF32:
+            return launch_interior_batch_t<float, float, UPlain<float>, 128, 4>(L, grid, ring_slots, s, resident);
+        case kFmtF32C: return launch_interior_batch_t<float, float, UComp, 128, 4>(L, grid, ring_slots, s, resident);
+        case kFmtF16: return launch_interior_batch_t<__half, float, UComp, 128, 4>(L, grid, ring_slots, s, resident);
         case kFmtBF16:
-            return launch_interior_batch_t<__nv_bfloat16, float, UComp, 128, 4>(L, nwork, ring_slots, s);
+            return launch_interior_batch_t<__nv_bfloat16, float, UComp, 128, 4>(L, grid, ring_slots, s, resident);
     }
     return cudaErrorInvalidValue;
 }

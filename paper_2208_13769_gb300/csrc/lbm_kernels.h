@@ -40,13 +40,16 @@ struct InteriorWork {
 };
 struct InteriorLaunch {
     const StepParams* params;  // device table, indexed by InteriorWork::inst
-    const InteriorWork* work;  // device work list, one CTA each
+    const InteriorWork* work;  // device work list
     int32_t fields;            // also write u, v, r to params.fields
-    int32_t pad;
+    int32_t nwork;             // items in the work list
 };
-// The setting of the dynamic shared-memory limit happens on the first call
-// (also with nwork == 0), which must precede any stream capture.
-cudaError_t launch_interior_batch(int fmt, const InteriorLaunch& L, int nwork, int ring_slots, cudaStream_t s);
+// A persistent grid of `grid` CTAs runs the work list.  The setting of the
+// dynamic shared-memory limit happens on the first call (also with grid ==
+// 0), which must precede any stream capture; resident (may be NULL) receives
+// the kernel's CTAs per SM with this ring.
+cudaError_t launch_interior_batch(int fmt, const InteriorLaunch& L, int grid, int ring_slots, cudaStream_t s,
+                                  int* resident);
 
 // The edge kernel (lbm_edge.cu): small 2-D tiles with every boundary rule.
 // A tile's threads cover its output nodes and a 2-node halo: tw x th nodes
