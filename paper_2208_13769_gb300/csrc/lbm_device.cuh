@@ -122,23 +122,25 @@ struct Codec<float, float> {
     __device__ __forceinline__ static float st(float v, int, const StepParams&) { return v; }
 };
 // 16-bit storage keeps h_i = f_i / (w_i 2^-s); the scale pair per direction
-// (w_i 2^-s and its inverse) is precomputed on the host.
+// (w_i 2^-s and its inverse) is precomputed on the host.  The scaling
+// products are rounded on their own (never fused into a neighbouring add), so
+// a decoded population has one value wherever and whenever it is decoded.
 template <>
 struct Codec<__half, float> {
     __device__ __forceinline__ static float ld(__half s, int i, const StepParams& p) {
-        return __half2float(s) * p.dec_scale[i];
+        return __fmul_rn(__half2float(s), p.dec_scale[i]);
     }
     __device__ __forceinline__ static __half st(float v, int i, const StepParams& p) {
-        return __float2half_rn(v * p.enc_scale[i]);
+        return __float2half_rn(__fmul_rn(v, p.enc_scale[i]));
     }
 };
 template <>
 struct Codec<__nv_bfloat16, float> {
     __device__ __forceinline__ static float ld(__nv_bfloat16 s, int i, const StepParams& p) {
-        return __bfloat162float(s) * p.dec_scale[i];
+        return __fmul_rn(__bfloat162float(s), p.dec_scale[i]);
     }
     __device__ __forceinline__ static __nv_bfloat16 st(float v, int i, const StepParams& p) {
-        return __float2bfloat16_rn(v * p.enc_scale[i]);
+        return __float2bfloat16_rn(__fmul_rn(v, p.enc_scale[i]));
     }
 };
 

@@ -71,8 +71,10 @@ __host__ __device__ constexpr size_t interior_row_bytes() {
 // false if a wait gave up or a copy was refused (reported in p.flag).
 // reuse: the CTA runs more tiles after this one, so the ring's mbarriers are
 // invalidated at the end (every copy has completed by then) for the next
-// tile to initialise them afresh.
-template <class TS, class TC, class UT, int NT>
+// tile to initialise them afresh.  KEEP: stage C takes populations 1..8 of
+// its row from registers that stage A filled two rows earlier (16 more
+// registers, 8 fewer shared-memory loads per node) instead of the ring.
+template <class TS, class TC, class UT, int NT, bool KEEP>
 __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int by, double* fields, bool reuse) {
     using CT = typename UT::Elem;
     const int W = p.strip_w;
@@ -184,7 +186,13 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
 
     bool bad = false;
     int sA = 0, ra = 0;
+    // populations 1..8 of this column as stage A pulled them for rows a - 1
+    // and a - 2: stage C of row a - 2 takes them from here, not the ring
+    TC fp1[8], fp2[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) fp1[i] = fp2[i] = TC(0);
     for (int q = 0; q < niter; ++q) {
+        TC gcur[8];
         const int sB = sA == 0 ? 2 : sA - 1;  // slot of row a - 1
         const int sC = sA == 2 ? 0 : sA + 1;  // slot of row a - 2 (and Q of row a - 3 in sq[sA])
         const int rc = ra >= 2 ? ra - 2 : ra - 2 + R;
@@ -199,6 +207,8 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
             TC g[9];
 #pragma unroll
             for (int i = 1; i < 9; ++i) g[i] = Codec<TS, TC>::ld(pf[i * SEG - ex(i)], i, p);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) gcur[i - 1] = g[i];
             const TC m0 = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
             const TC m1 = (g[2] - g[4]) + (g[5] - g[8]) + (g[6] - g[7]);
             su[(sA * 2) * NT + t] = an0.add(k.ku * m0);
@@ -255,8 +265,14 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
 
             const TS* pf = reinterpret_cast<const TS*>(ring + size_t(rc) * ROW_BYTES) + e_own;
             TC f[9];
+            if (KEEP) {
+                f[0] = Codec<TS, TC>::ld(pf[0], 0, p);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = Codec<TS, TC>::ld(pf[i * SEG - ex(i)], i, p);
+                for (int i = 1; i < 9; ++i) f[i] = fp2[i - 1];
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) f[i] = Codec<TS, TC>::ld(pf[i * SEG - ex(i)], i, p);
+            }
             const TC r = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
             const TC m0 = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
             const TC m1 = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
@@ -325,6 +341,13 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
                 if (!(fabs(double(j0)) + fabs(double(j1)) < 1e300)) bad = true;
             }
         }
+        if (KEEP) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                fp2[i] = fp1[i];
+                fp1[i] = gcur[i];
+            }
+        }
         sA = sA == 2 ? 0 : sA + 1;
         ra = ra + 1 == R ? 0 : ra + 1;
         off_a += pitch32;
@@ -349,7 +372,7 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
 
 template <class TS, class TC, class UT, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) interior_step_kernel(const __grid_constant__ StepParams p) {
-    interior_tile<TS, TC, UT, NT>(p, int(blockIdx.x), int(blockIdx.y), p.fields, false);
+    interior_tile<TS, TC, UT, NT, true>(p, int(blockIdx.x), int(blockIdx.y), p.fields, false);
 }
 
 // A batch of bodies: a persistent grid of resident CTAs, each running the
@@ -368,7 +391,7 @@ __global__ void __launch_bounds__(NT, MINB) interior_batch_kernel(const __grid_c
             for (int q = int(threadIdx.x); q < int(sizeof(StepParams) / 16); q += NT) dst[q] = src[q];
         }
         __syncthreads();
-        if (!interior_tile<TS, TC, UT, NT>(sp, w.bx, w.by, L.fields ? sp.fields : nullptr, true)) break;
+        if (!interior_tile<TS, TC, UT, NT, false>(sp, w.bx, w.by, L.fields ? sp.fields : nullptr, true)) break;
     }
 }
 
