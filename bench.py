@@ -468,21 +468,33 @@ def run_native(a):
     # K steps, read u (D2H)
     e2e = None
     if not a.no_e2e:
+        import dataclasses
+
+        # inputs in pinned host memory before the clock starts; the upload,
+        # the whole solve and the read-back of u into pinned memory inside it
+        u0_h = torch.empty((prob.ny, prob.nx, 2), dtype=torch.float64, pin_memory=True)
+        v0_h = torch.empty((prob.ny, prob.nx, 2), dtype=torch.float64, pin_memory=True)
+        u_h = torch.empty((prob.ny, prob.nx, 2), dtype=torch.float64, pin_memory=True)
+        u0, v0 = prob.initial()
+        u0_h.numpy()[...] = u0
+        v0_h.numpy()[...] = v0
+        pprob = dataclasses.replace(prob, u0=u0_h.numpy(), v0=v0_h.numpy(), make_initial=None)
         barrier()
         t0 = time.perf_counter()
-        b = lbm.Body(prob, storage=a.storage, compensated=a.compensated, stream=stream.cuda_stream,
+        b = lbm.Body(pprob, storage=a.storage, compensated=a.compensated, stream=stream.cuda_stream,
                      device=local, tuning=tuning)
         b.step(a.steps)
-        out = b.read(lbm.LBM_FIELD_U, allow_unstable=True)
+        st, _ = lbm.lbm_read_fields(b.ctx, lbm.LBM_FIELD_U, u_h.numpy().reshape(-1), allow_unstable=True)
         t1 = time.perf_counter()
         b.close()
         e_secs = max_over_ranks(t1 - t0)
-        h2d = 2 * nodes * 2 * 8
-        d2h = out["u"].nbytes
+        h2d = u0_h.numel() * 8 + v0_h.numel() * 8
+        d2h = u_h.numel() * 8
         e2e = {"value": world * nodes * a.steps / e_secs / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / a.steps, "d2h_bytes_per_step": d2h / a.steps,
                "h2d_bytes_total": h2d, "d2h_bytes_total": d2h, "seconds": e_secs,
-               "includes": "context creation, u0/v0 upload, initialisation, K steps, u read-back"}
+               "includes": "context creation, u0/v0 upload from pinned memory, initialisation, K steps, "
+                           "u read-back into pinned memory"}
 
     cpu = None
     if rank == 0 and not a.no_cpu:
