@@ -71,9 +71,10 @@ __host__ __device__ constexpr size_t interior_row_bytes() {
 // false if a wait gave up or a copy was refused (reported in p.flag).
 // reuse: the CTA runs more tiles after this one, so the ring's mbarriers are
 // invalidated at the end (every copy has completed by then) for the next
-// tile to initialise them afresh.  KEEP: stage C takes populations 1..8 of
-// its row from registers that stage A filled two rows earlier (16 more
-// registers, 8 fewer shared-memory loads per node) instead of the ring.
+// tile to initialise them afresh.  KEEP: stage C takes the populations of
+// its row from registers that stage A filled two rows earlier (18 more
+// registers, 9 fewer shared-memory loads per node) instead of the ring, and
+// the ring keeps every slot in flight.
 template <class TS, class TC, class UT, int NT, bool KEEP>
 __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int by, double* fields, bool reuse) {
     using CT = typename UT::Elem;
@@ -149,7 +150,11 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
         fence_mbar_init();
     }
     __syncthreads();
-    const int D = R - 3;
+    // rows of lookahead: with KEEP a row's ring slot is free once stage A has
+    // read it (stage C takes the row's populations from registers), so every
+    // slot holds a row in flight; otherwise it also serves stage C two rows
+    // later
+    const int D = KEEP ? R : R - 3;
     uint32_t phase = 0, issued = 0;
     if (t == 0) {
         fence_proxy_async();  // a previous tile's reads of the ring precede these copies
@@ -188,11 +193,11 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
     int sA = 0, ra = 0;
     // populations 1..8 of this column as stage A pulled them for rows a - 1
     // and a - 2: stage C of row a - 2 takes them from here, not the ring
-    TC fp1[8], fp2[8];
+    TC fp1[9], fp2[9];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) fp1[i] = fp2[i] = TC(0);
+    for (int i = 0; i < 9; ++i) fp1[i] = fp2[i] = TC(0);
     for (int q = 0; q < niter; ++q) {
-        TC gcur[8];
+        TC gcur[9];
         const int sB = sA == 0 ? 2 : sA - 1;  // slot of row a - 1
         const int sC = sA == 2 ? 0 : sA + 1;  // slot of row a - 2 (and Q of row a - 3 in sq[sA])
         const int rc = ra >= 2 ? ra - 2 : ra - 2 + R;
@@ -207,8 +212,11 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
             TC g[9];
 #pragma unroll
             for (int i = 1; i < 9; ++i) g[i] = Codec<TS, TC>::ld(pf[i * SEG - ex(i)], i, p);
+            if (KEEP) {
+                gcur[0] = Codec<TS, TC>::ld(pf[0], 0, p);
 #pragma unroll
-            for (int i = 1; i < 9; ++i) gcur[i - 1] = g[i];
+                for (int i = 1; i < 9; ++i) gcur[i] = g[i];
+            }
             const TC m0 = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
             const TC m1 = (g[2] - g[4]) + (g[5] - g[8]) + (g[6] - g[7]);
             su[(sA * 2) * NT + t] = an0.add(k.ku * m0);
@@ -221,7 +229,8 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
         __syncthreads();
         if (s_abort) break;
         if (t == 0 && q + D < niter) {
-            const int rn = ra + D < R ? ra + D : ra + D - R;  // slot of row a - 3, done
+            // KEEP: the slot row a just left; else the slot of row a - 3, done
+            const int rn = KEEP ? ra : (ra + D < R ? ra + D : ra + D - R);
             fence_proxy_async();
             if (issue_row(a0 + q + D, rn)) issued |= 1u << rn;
             else s_abort = 2;
@@ -266,9 +275,8 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
             const TS* pf = reinterpret_cast<const TS*>(ring + size_t(rc) * ROW_BYTES) + e_own;
             TC f[9];
             if (KEEP) {
-                f[0] = Codec<TS, TC>::ld(pf[0], 0, p);
 #pragma unroll
-                for (int i = 1; i < 9; ++i) f[i] = fp2[i - 1];
+                for (int i = 0; i < 9; ++i) f[i] = fp2[i];
             } else {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) f[i] = Codec<TS, TC>::ld(pf[i * SEG - ex(i)], i, p);
@@ -343,7 +351,7 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
         }
         if (KEEP) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
+            for (int i = 0; i < 9; ++i) {
                 fp2[i] = fp1[i];
                 fp1[i] = gcur[i];
             }
