@@ -171,11 +171,11 @@ static cudaError_t build_plan(lbm_ctx* c) {
         c->nband = 1;
     }
     int n = 0;
-    for (int b = 0; b < c->nband; ++b) n += edge_tiles_of_rect(c->brect[b], 0, nullptr, 0, false);
+    for (int b = 0; b < c->nband; ++b) n += edge_tiles_of_rect(c->brect[b], 0, nullptr, 0, false, kEdgeThreads);
     EdgeTile* h = new (std::nothrow) EdgeTile[size_t(n)];
     if (!h) return cudaErrorMemoryAllocation;
     int m = 0;
-    for (int b = 0; b < c->nband; ++b) m += edge_tiles_of_rect(c->brect[b], 0, h + m, n - m, m == 0);
+    for (int b = 0; b < c->nband; ++b) m += edge_tiles_of_rect(c->brect[b], 0, h + m, n - m, m == 0, kEdgeThreads);
     StepParams hp[2] = {make_params(c, 0), make_params(c, 1)};
     cudaError_t e = cudaMalloc(&c->dtiles, sizeof(EdgeTile) * size_t(n));
     if (e == cudaSuccess) e = cudaMalloc(&c->dparams, sizeof(hp));

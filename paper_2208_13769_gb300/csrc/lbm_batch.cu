@@ -1,13 +1,12 @@
 // lbm_batch.cu -- many bodies advanced by shared launches (the C ABI's
 // lbm_batch_* entry points).
 //
-// Each time step of a batch is one launch of the interior kernel over the
-// work list of every member's interior tiles (a persistent grid of resident
-// CTAs, each taking items in turn) and one launch of the edge kernel over
-// every member's edge tiles (concurrent, on two streams), each CTA reading
-// its body's parameters from a device table.  So small and
-// uneven bodies share the GPU instead of each paying a launch per step, and
-// chunks of 64 steps replay as one CUDA graph.  Every node of every member
+// Each time step of a batch is one launch of a persistent kernel over a
+// work list of every member's interior tiles and edge tiles (its resident
+// CTAs take the items one at a time from a device queue), each CTA reading
+// its body's parameters from a device table.  So small and uneven bodies
+// share the GPU instead of each paying launches per step, and chunks of 64
+// steps replay as one CUDA graph.  Every node of every member
 // goes through the same kernels and arithmetic as when the member is
 // stepped alone, so the results are bit-identical.
 #include <cuda_runtime.h>
@@ -26,7 +25,11 @@ using namespace lbm;
 namespace {
 
 constexpr int kBatchGraphChunk = 64;  // steps per captured graph (even)
-constexpr int kBatchStripW = 120;     // output columns per interior strip (sizing only)
+
+// An interior tile of a member while the work list is built.
+struct InteriorWork {
+    int32_t inst, bx, by;
+};
 
 }  // namespace
 
@@ -34,17 +37,16 @@ struct lbm_batch {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool owns_stream = false;
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_sync = nullptr;
+    cudaEvent_t ev_sync = nullptr;
     std::vector<lbm_ctx*> m;
     std::vector<int> base_parity;  // member parity when the batch step count is even
     int fmt = 0;
     StepParams* dtab = nullptr;  // [2][n]: entry q * n + i = member i at parity base_parity[i] ^ q
-    InteriorWork* dwork = nullptr;
-    int n_work = 0;
-    int grid = 0;  // persistent CTAs of the interior launch
-    EdgeTile* dedge = nullptr;
-    int n_edge = 0;
+    EdgeTile* ditems = nullptr;  // work list: interior tiles (tw == 0) and edge tiles, interleaved
+    int32_t* dqueue = nullptr;   // {next item, CTAs done} of the persistent kernel
+    int n_work = 0;              // interior tiles in the list
+    int n_edge = 0;              // edge tiles in the list
+    int grid = 0;                // persistent CTAs
     int chunk_rows = 0;
     int64_t steps = 0;
     bool warm = false;
@@ -71,37 +73,23 @@ void batch_free(lbm_batch* b) {
     for (int k = 0; k < 2; ++k)
         if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
     cudaFree(b->dtab);
-    cudaFree(b->dwork);
-    cudaFree(b->dedge);
-    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    cudaFree(b->ditems);
+    cudaFree(b->dqueue);
     if (b->ev_sync) cudaEventDestroy(b->ev_sync);
-    if (b->side) cudaStreamDestroy(b->side);
     if (b->owns_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
 // One batch time step from table parity q.
 cudaError_t batch_launch(lbm_batch* b, int q, bool fields) {
     const int n = int(b->m.size());
-    InteriorLaunch il;
-    memset(&il, 0, sizeof(il));
-    il.params = b->dtab + size_t(q) * n;
-    il.work = b->dwork;
-    il.fields = fields ? 1 : 0;
-    il.nwork = b->n_work;
-    EdgeLaunch el;
-    memset(&el, 0, sizeof(el));
-    el.params = b->dtab + size_t(q) * n;
-    el.tiles = b->dedge;
-    el.fields = fields ? 1 : 0;
-    if (b->n_work == 0) return launch_edge(b->fmt, el, b->n_edge, b->stream, 0);
-    cudaError_t e = cudaEventRecord(b->ev_fork, b->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
-    if (e == cudaSuccess) e = launch_interior_batch(b->fmt, il, b->grid, kInteriorRing, b->stream, nullptr);
-    if (e == cudaSuccess) e = launch_edge(b->fmt, el, b->n_edge, b->side, 0);
-    if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->side);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
-    return e;
+    BatchLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.params = b->dtab + size_t(q) * n;
+    L.items = b->ditems;
+    L.queue = b->dqueue;
+    L.fields = fields ? 1 : 0;
+    L.nitems = b->n_work + b->n_edge;
+    return launch_batch_step(b->fmt, L, b->grid, kInteriorRing, b->stream, nullptr);
 }
 
 void advance_members(lbm_batch* b, int64_t k) {
@@ -192,9 +180,6 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
         e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
         b->owns_stream = e == cudaSuccess;
     }
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_sync, cudaEventDisableTiming);
 
     // interior tiles: rows per chunk so that the batch holds about eight
@@ -204,11 +189,11 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
         if (c->has_interior)
             interior_nodes += int64_t(c->irect[1] - c->irect[0]) * (c->irect[3] - c->irect[2]);
     const int64_t wave = int64_t(b->m[0]->num_sms) * std::max(1, interior_occupancy(b->fmt, kInteriorRing));
-    b->chunk_rows =
-        int(std::min<int64_t>(256, std::max<int64_t>(32, interior_nodes / (int64_t(kBatchStripW) * wave * 8))));
+    b->chunk_rows = int(std::min<int64_t>(256, std::max<int64_t>(32, interior_nodes / (int64_t(120) * wave * 8))));
     std::vector<StepParams> tab;
     std::vector<InteriorWork> work;
     std::vector<EdgeTile> tiles;
+    std::vector<EdgeTile> items;
     std::vector<int> sx0, sw, ns;  // strip grid of each member's interior
     try {
         sx0.assign(size_t(n), 0);
@@ -238,14 +223,14 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
                 const int h = c->irect[3] - c->irect[2];
                 const int sx = ns[size_t(i)], sy = (h + b->chunk_rows - 1) / b->chunk_rows;
                 for (int by = 0; by < sy; ++by)
-                    for (int bx = 0; bx < sx; ++bx) work.push_back(InteriorWork{i, bx, by, 0});
+                    for (int bx = 0; bx < sx; ++bx) work.push_back(InteriorWork{i, bx, by});
             }
             bool first = true;
             for (int r = 0; r < c->nband; ++r) {
-                const int cnt = edge_tiles_of_rect(c->brect[r], i, nullptr, 0, false);
+                const int cnt = edge_tiles_of_rect(c->brect[r], i, nullptr, 0, false, kInteriorThreads);
                 const size_t at = tiles.size();
                 tiles.resize(at + size_t(cnt));
-                edge_tiles_of_rect(c->brect[r], i, tiles.data() + at, cnt, first);
+                edge_tiles_of_rect(c->brect[r], i, tiles.data() + at, cnt, first, kInteriorThreads);
                 first = first && cnt == 0;
             }
         }
@@ -257,34 +242,49 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
         };
         std::stable_sort(work.begin(), work.end(),
                          [&](const InteriorWork& x, const InteriorWork& y) { return rows_of(x) > rows_of(y); });
+        // the work list: the interior tiles in that order, with the edge
+        // tiles spread evenly between them
+        const size_t ni = work.size(), ne = tiles.size();
+        items.reserve(ni + ne);
+        size_t next_edge = 0;
+        for (size_t k = 0; k < ni; ++k) {
+            EdgeTile it;
+            memset(&it, 0, sizeof(it));
+            it.inst = work[k].inst;
+            it.x0 = work[k].bx;
+            it.y0 = work[k].by;
+            it.tw = 0;  // an interior tile
+            items.push_back(it);
+            const size_t upto = ne * (k + 1) / ni;
+            for (; next_edge < upto; ++next_edge) items.push_back(tiles[next_edge]);
+        }
+        for (; next_edge < ne; ++next_edge) items.push_back(tiles[next_edge]);
     } catch (...) {
         batch_free(b);
         delete b;
         return LBM_E_OOM;
     }
-    if (work.size() > 0x7fffffff || tiles.size() > 0x7fffffff) e = cudaErrorInvalidValue;
+    if (items.size() > 0x7fffffff) e = cudaErrorInvalidValue;
     b->n_work = int(work.size());
     b->n_edge = int(tiles.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->dtab, sizeof(StepParams) * tab.size());
-    if (e == cudaSuccess && b->n_work) e = cudaMalloc(&b->dwork, sizeof(InteriorWork) * work.size());
-    if (e == cudaSuccess && b->n_edge) e = cudaMalloc(&b->dedge, sizeof(EdgeTile) * tiles.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->ditems, sizeof(EdgeTile) * items.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->dqueue, 2 * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->dqueue, 0, 2 * sizeof(int32_t), b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->dtab, tab.data(), sizeof(StepParams) * tab.size(), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess && b->n_work)
-        e = cudaMemcpyAsync(b->dwork, work.data(), sizeof(InteriorWork) * work.size(), cudaMemcpyHostToDevice,
-                            b->stream);
-    if (e == cudaSuccess && b->n_edge)
-        e = cudaMemcpyAsync(b->dedge, tiles.data(), sizeof(EdgeTile) * tiles.size(), cudaMemcpyHostToDevice,
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->ditems, items.data(), sizeof(EdgeTile) * items.size(), cudaMemcpyHostToDevice,
                             b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host tables die with this scope
-    // sets the interior batch kernel's shared-memory limit outside any
-    // capture, and sizes its persistent grid: every resident CTA slot
+    // sets the batch kernel's shared-memory limit outside any capture, and
+    // sizes its persistent grid: every resident CTA slot
     if (e == cudaSuccess) {
-        InteriorLaunch il;
-        memset(&il, 0, sizeof(il));
+        BatchLaunch L;
+        memset(&L, 0, sizeof(L));
         int resident = 0;
-        e = launch_interior_batch(b->fmt, il, 0, kInteriorRing, b->stream, &resident);
-        b->grid = std::min(b->n_work, b->m[0]->num_sms * std::max(1, resident));
+        e = launch_batch_step(b->fmt, L, 0, kInteriorRing, b->stream, &resident);
+        b->grid = int(std::min<int64_t>(int64_t(items.size()), int64_t(b->m[0]->num_sms) * std::max(1, resident)));
     }
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -1,23 +1,12 @@
 // lbm_edge.cu -- the fused step on the edge bands of a body, and the
-// initialisation of the whole body, as small two-dimensional tiles.
+// initialisation of the whole body, as small two-dimensional tiles (the tile
+// itself is edge_tile_body of lbm_edge_tile.cuh).
 //
-// Nodes within 2 of a bounded edge (3 of a periodic seam) need the boundary
-// machinery of Sec. 6: ghost values in Grad u and Div Q, bounced populations
-// and periodic images.  These bands hold few nodes, so what bounds their cost
-// is latency, not bandwidth.  Each CTA of 256 threads owns an output tile of
-// (tw - 4) x (th - 4) nodes (tw x th <= 256: tiles exactly as thick as a
-// band, 28 x 4 over larger areas) and one thread per node of the tile and its
-// 2-node halo:
-//   stage A (every thread)      : pull-stream, first moment, predicted u*
-//   stage B (1-node inner ring) : H = Grad u* with the ghost rules,
-//                                 Q = P(F) + Pbar(H)
-//   stage C (output nodes)      : 1S = rho0 b + Div Q, moments, corrected j
-//                                 and u, equilibrium, BGK collision with He
-//                                 forcing, stores, boundary rules of Sec. 6
-// with a barrier between stages.  Every global load is issued in stage A, so
-// a tile costs one memory latency plus its arithmetic, and hundreds of tiles
-// run at once.  The arithmetic is that of the interior kernel (lattice
-// units, Q expanded without cancellation, collision by opposite pairs).
+// The bands hold few nodes, so what bounds their cost is latency, not
+// bandwidth.  Each CTA of 256 threads runs one tile of (tw - 4) x (th - 4)
+// output nodes (tw x th <= 256: tiles exactly as thick as a band, 28 x 4 over
+// larger areas), one thread per node of the tile and its 2-node halo, and
+// hundreds of tiles run at once.
 //
 // Tiles come from a list (instance, output rectangle, shape), and each
 // instance's parameters from a table in device memory, so one launch serves
@@ -27,92 +16,15 @@
 
 #include "lbm_device.cuh"
 #include "lbm_kernels.h"
+#include "lbm_edge_tile.cuh"
 #include "lbm_pipeline.cuh"
 
 namespace lbm {
 
 static_assert(sizeof(StepParams) % 16 == 0, "StepParams is copied to shared memory in 16-byte words");
 
-// Rare paths, kept out of line so the kernel's code stays small: stores of a
-// node on a periodic axis shorter than 6 nodes, and the boundary rules of a
-// node on a bounded edge.
-template <class T>
-__device__ __noinline__ void store_img_slow(T* base, Geo g, int x, int y, T v) {
-    store_img(base, g, x, y, v);
-}
-
-template <class TC>
-struct Pops {
-    TC v[9];
-};
-
-// Links of node (gx, gy) that leave the body through a bounded edge: the
-// boundary rules of Sec. 6, written into the first ghost row/column.  fc:
-// the node's post-collision populations; r, pxx, pxy, pyy: its moments;
-// q: its Q = P + Pbar.
-template <class TS, class TC, class UT>
-__device__ __noinline__ void boundary_links(TS* fdst, Geo g, const StepParams& p, const EdgeNow<TC, UT>* s_edge,
-                                            int gx, int gy, Pops<TC> fc, TC r, TC pxx, TC pxy, TC pyy, TC q11,
-                                            TC q12, TC q21, TC q22, TC inv_c2) {
-    const int nx = g.nx, ny = g.ny;
-#pragma unroll 1
-    for (int i = 1; i < 9; ++i) {
-        const int dx = gx + ex(i), dy = gy + ey(i);
-        const bool bx2 = !g.perx && (dx < 0 || dx >= nx);
-        const bool by2 = !g.pery && (dy < 0 || dy >= ny);
-        if (!bx2 && !by2) continue;
-        const int oi = opp(i);
-        const EdgeNow<TC, UT>* ea = bx2 ? &s_edge[dx < 0 ? 0 : 1] : nullptr;
-        const EdgeNow<TC, UT>* eb = by2 ? &s_edge[dy < 0 ? 2 : 3] : nullptr;
-        const bool da = ea && ea->kind == kDirichlet, db = eb && eb->kind == kDirichlet;
-        TC val;
-        if (da || db) {
-            // Eq. (bbcon) with jh* = rho0 v* / c (averaged over the Dirichlet
-            // edges of a corner link)
-            TC a0c, a1c;
-            if (da && db) {
-                a0c = TC(0.5) * (ea->jh[0] + eb->jh[0]);
-                a1c = TC(0.5) * (ea->jh[1] + eb->jh[1]);
-            } else {
-                const EdgeNow<TC, UT>* e = da ? ea : eb;
-                a0c = e->jh[0];
-                a1c = e->jh[1];
-            }
-            val = fc.v[i] - TC(2) * wgt<TC>(i) * eq_odd<TC>(i, a0c, a1c);
-        } else {
-            // Eq. (abbcon) with Pbar* of Sec. 6 in the wall-normal frame; a
-            // corner link: N = (N1 + N2)/sqrt(2), T* = (T1 + T2)/sqrt(2)
-            const int sx = bx2 ? (dx < 0 ? -1 : 1) : 0, sy = by2 ? (dy < 0 ? -1 : 1) : 0;
-            const TC inv_len = (sx != 0 && sy != 0) ? TC(0.70710678118654752440) : TC(1);
-            TC T0 = TC(0), T1 = TC(0);
-            if (ea) {
-                T0 += ea->T[0];
-                T1 += ea->T[1];
-            }
-            if (eb) {
-                T0 += eb->T[0];
-                T1 += eb->T[1];
-            }
-            const TC N0 = TC(sx) * inv_len, N1 = TC(sy) * inv_len;
-            const TC g0 = -T0 * inv_len + q11 * N0 + q12 * N1;
-            const TC g1 = -T1 * inv_len + q21 * N0 + q22 * N1;
-            const TC t0 = -N1, t1 = N0;
-            const TC pnn = (N0 * g0 + N1 * g1) * inv_c2;
-            const TC pnt = (t0 * g0 + t1 * g1) * inv_c2;
-            const TC ptt = t0 * t0 * pxx + TC(2) * t0 * t1 * pxy + t1 * t1 * pyy;
-            const TC sxx = pnn * N0 * N0 + TC(2) * pnt * N0 * t0 + ptt * t0 * t0;
-            const TC syy = pnn * N1 * N1 + TC(2) * pnt * N1 * t1 + ptt * t1 * t1;
-            const TC sxy = pnn * N0 * N1 + pnt * (N0 * t1 + t0 * N1) + ptt * t0 * t1;
-            val = -fc.v[i] + TC(2) * wgt<TC>(i) * eq_even<TC>(i, r, sxx, sxy, syy);
-        }
-        store_img(fdst + oi * g.plane, g, dx, dy, Codec<TS, TC>::st(val, oi, p));
-    }
-}
-
 template <class TS, class TC, class UT, int MODE>
 __global__ void __launch_bounds__(kEdgeThreads, 3) edge_tile_kernel(const __grid_constant__ EdgeLaunch L) {
-    using CT = typename UT::Elem;
-    constexpr int UP = UT::planes;
     constexpr int N = kEdgeThreads;
     __shared__ __align__(16) StepParams sp;
     __shared__ EdgeNow<TC, UT> s_edge[4];
@@ -142,259 +54,7 @@ __global__ void __launch_bounds__(kEdgeThreads, 3) edge_tile_kernel(const __grid
         for (int q = int(threadIdx.x); q < int(sizeof(StepParams) / 16); q += N) dst[q] = src[q];
     }
     __syncthreads();
-    const StepParams& p = sp;
-    const int t = threadIdx.x;
-
-    int64_t n_now = 0;  // the collision of this launch is at t_now = n_now dt
-    if (MODE == 0) n_now = p.counter[p.parity] + 1;
-    if (tile.lead && t == 0) p.counter[p.parity ^ 1] = n_now;
-    const double t_now = double(n_now) * p.dt;
-    if (t < 4) edge_now<TC, UT>(s_edge[t], p.bc[t], t_now, p.lat_d[kLatRho0OverC]);
-
-    LatConsts<TC> k;
-    k.load(p);
-    Geo g;
-    g.nx = p.nx;
-    g.ny = p.ny;
-    g.pitch = p.pitch;
-    g.plane = p.plane;
-    g.perx = p.periodic_x != 0;
-    g.pery = p.periodic_y != 0;
-    const int nx = g.nx, ny = g.ny;
-    const int64_t pitch = g.pitch, plane = g.plane;
-    const TS* __restrict__ fsrc = static_cast<const TS*>(p.f_src);
-    TS* __restrict__ fdst = static_cast<TS*>(p.f_dst);
-    const CT* __restrict__ a_src = static_cast<const CT*>(p.a_src);
-    CT* __restrict__ a_dst = static_cast<CT*>(p.a_dst);
-    const TC* __restrict__ s_src = static_cast<const TC*>(p.s_src);
-    TC* __restrict__ s_dst = static_cast<TC*>(p.s_dst);
-
-    // ---- this thread's node: raw coordinates (an image beyond a periodic
-    // seam) and node coordinates
-    const int tw = tile.tw, th = tile.th;
-    const int tx = t % tw, ty = t / tw;  // ty >= th: an idle thread
-    const int nxo = tile.x1 - tile.x0, nyo = tile.y1 - tile.y0;  // output extent
-    const int gxr = tile.x0 - 2 + tx, gyr = tile.y0 - 2 + ty;
-    const bool okx = g.perx ? (gxr >= -2 && gxr < nx + 2) : (gxr >= 0 && gxr < nx);
-    const bool oky = g.pery ? (gyr >= -2 && gyr < ny + 2) : (gyr >= 0 && gyr < ny);
-    const bool inA = okx && oky && ty < th;
-    const bool inB = inA && tx >= 1 && tx <= nxo + 2 && ty >= 1 && ty <= nyo + 2;
-    const bool inC = tx >= 2 && tx < nxo + 2 && ty >= 2 && ty < nyo + 2;
-    const int gx = g.perx ? wrap_coord(gxr, nx) : gxr;
-    const int gy = g.pery ? wrap_coord(gyr, ny) : gyr;
-    const bool gxl = !g.perx && gx == 0, gxh = !g.perx && gx == nx - 1;
-    const bool gyl = !g.pery && gy == 0, gyh = !g.pery && gy == ny - 1;
-    // first and second inward neighbours (used only by a ghost rule)
-    const int tx1 = gxl ? min(tx + 1, tw - 1) : max(tx - 1, 0);
-    const int tx2 = gxl ? min(tx + 2, tw - 1) : max(tx - 2, 0);
-    const int ty1 = gyl ? min(ty + 1, th - 1) : max(ty - 1, 0);
-    const int ty2 = gyl ? min(ty + 2, th - 1) : max(ty - 2, 0);
-    const int txm = max(tx - 1, 0), txp = min(tx + 1, tw - 1);
-    const int tym = max(ty - 1, 0), typ = min(ty + 1, th - 1);
-    const int64_t o = g.at(gxr, gyr);  // raw position in the planes
-
-    // ---------------- stage A: pull-stream, first moment, predicted u*
-    TC f[9];
-    TC so0 = TC(0), so1 = TC(0);  // source carry of the node (stage C)
-#pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = TC(0);
-    if (MODE == 0 && inA) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i)
-            f[i] = Codec<TS, TC>::ld(fsrc[int64_t(i) * plane + o - ex(i) - int64_t(ey(i)) * pitch], i, p);
-        const UT A0 = UT::ld_global(a_src, o, plane);
-        const UT A1 = UT::ld_global(a_src + UP * plane, o, plane);
-        if (inC) {
-            so0 = s_src[o];
-            so1 = s_src[o + plane];
-        }
-        const TC m0 = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-        const TC m1 = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
-        su[(ty * 2) * tw + tx] = A0.add(k.ku * m0);
-        su[(ty * 2 + 1) * tw + tx] = A1.add(k.ku * m1);
-    } else if (MODE == 1 && inA) {
-        const int64_t hh = (int64_t(gy) * nx + gx) * 2;
-        su[(ty * 2) * tw + tx] = UT::from_double(p.u0 ? p.u0[hh] : 0.0);
-        su[(ty * 2 + 1) * tw + tx] = UT::from_double(p.u0 ? p.u0[hh + 1] : 0.0);
-    }
-    __syncthreads();
-
-    // ---------------- stage B: H = Grad u*, Q = P(F) + Pbar(H)
-    bool bad = false;
-    if (inB) {
-        const EdgeNow<TC, UT>& ebx = s_edge[gxl ? 0 : 1];
-        const EdgeNow<TC, UT>& eby = s_edge[gyl ? 2 : 3];
-        TC hh[2][2];
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const UT* r0 = su + (ty * 2 + c) * tw;
-            const UT u0 = r0[tx];
-            hh[c][0] = du_axis<TC, UT>(r0[txm], u0, r0[txp], r0[tx1], r0[tx2], gxl, gxh, ebx, c) * k.inv_2dx;
-            hh[c][1] = du_axis<TC, UT>(su[(tym * 2 + c) * tw + tx], u0, su[(typ * 2 + c) * tw + tx],
-                                       su[(ty1 * 2 + c) * tw + tx], su[(ty2 * 2 + c) * tw + tx], gyl, gyh, eby,
-                                       c) *
-                       k.inv_2dx;
-        }
-        TC q11, q12, q21, q22;
-        const TC J =
-            stress_remainder<TC>(hh[0][0], hh[0][1], hh[1][0], hh[1][1], k.lam, k.mu, q11, q12, q21, q22);
-        bad |= !(J > TC(0)) || !(fabs(q11) + fabs(q12) + fabs(q21) + fabs(q22) < TC(1e30));
-        TC* qr = sq + (ty * 4) * tw + tx;
-        qr[0] = q11;
-        qr[tw] = q12;
-        qr[2 * tw] = q21;
-        qr[3 * tw] = q22;
-        if (MODE == 1) {
-            const TC tr = hh[0][0] + hh[1][1];
-            TC* ir = sinit + (ty * 4) * tw + tx;
-            ir[0] = -k.rho0 * tr;
-            ir[tw] = -k.mu * (TC(2) * hh[0][0] + tr) * k.inv_c2;
-            ir[2 * tw] = -k.mu * (hh[0][1] + hh[1][0]) * k.inv_c2;
-            ir[3 * tw] = -k.mu * (TC(2) * hh[1][1] + tr) * k.inv_c2;
-        }
-    }
-    __syncthreads();
-
-    // ---------------- stage C: source, moments, collision, stores
-    if (inC) {
-        // s = (dt / c) 1S, 1S = rho0 b + Div(P + Pbar)   (Eq. source1)
-        TC dQ[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const TC* r0 = sq + (ty * 4 + c) * tw;
-            if ((c & 1) == 0)  // Q_a1: derivative along x
-                dQ[c] = dq_axis<TC>(r0[txm], r0[tx], r0[txp], r0[tx1], r0[tx2], gxl, gxh);
-            else  // Q_a2: derivative along y
-                dQ[c] = dq_axis<TC>(sq[(tym * 4 + c) * tw + tx], r0[tx], sq[(typ * 4 + c) * tw + tx],
-                                    sq[(ty1 * 4 + c) * tw + tx], sq[(ty2 * 4 + c) * tw + tx], gyl, gyh);
-        }
-        const TC sn0 = k.sb0 + k.sq_scale * (dQ[0] + dQ[1]);
-        const TC sn1 = k.sb1 + k.sq_scale * (dQ[2] + dQ[3]);
-
-        const UT ux = su[(ty * 2) * tw + tx], uy = su[(ty * 2 + 1) * tw + tx];
-        TC r, j0, j1, pxx, pxy, pyy;
-        TC du0 = TC(0), du1 = TC(0);  // predictor correction of u*
-        if (MODE == 0) {
-            r = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-            const TC m0 = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-            const TC m1 = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
-            const TC dg = (f[5] + f[6]) + (f[7] + f[8]);
-            pxx = (f[1] + f[3]) + dg;
-            pyy = (f[2] + f[4]) + dg;
-            pxy = (f[5] - f[6]) + (f[7] - f[8]);
-            if (p.scheme == 1) {
-                j0 = m0 + TC(0.5) * sn0;
-                j1 = m1 + TC(0.5) * sn1;
-                du0 = k.ku * (TC(0.5) * (sn0 - so0));
-                du1 = k.ku * (TC(0.5) * (sn1 - so1));
-            } else {
-                j0 = m0 + TC(0.5) * so0;
-                j1 = m1 + TC(0.5) * so1;
-            }
-        } else {
-            // initialisation of Algorithm 1: r = -rho0 Div u0, j = rho0 v0,
-            // Pbar = Pbar(Grad u0) (from stage B), f = f^eq
-            const TC* ir = sinit + (ty * 4) * tw + tx;
-            r = ir[0];
-            pxx = ir[tw];
-            pxy = ir[2 * tw];
-            pyy = ir[3 * tw];
-            const int64_t hh = (int64_t(gy) * nx + gx) * 2;
-            j0 = k.rho0_over_c * TC(p.v0 ? p.v0[hh] : 0.0);
-            j1 = k.rho0_over_c * TC(p.v0 ? p.v0[hh + 1] : 0.0);
-        }
-
-        // equilibrium (Sec. 5), He forcing (Eq. source), BGK collision
-        // (Eq. col), by opposite pairs: f^col_i = (1 - omega) f_i
-        //   + w_i (omega E_i + 3 e_i.(omega jh + (1 - omega/2) s)),
-        // E_i the even part of f^eq_i / w_i (equal for i and its opposite)
-        const TC tr15 = TC(1.5) * (pxx + pyy);
-        const TC E0 = TC(2) * r - tr15;
-        const TC Ex = TC(0.5) * r + TC(4.5) * pxx - tr15;
-        const TC Ey = TC(0.5) * r + TC(4.5) * pyy - tr15;
-        const TC Ed = -r + TC(4.5) * (pxx + pyy) - tr15;
-        const TC Ep = Ed + TC(9) * pxy, Em = Ed - TC(9) * pxy;
-        const TC w0 = wgt<TC>(0), w1 = wgt<TC>(1), w5 = wgt<TC>(5);
-        if (MODE == 1) {
-            const TC o0 = TC(3) * j0, o1 = TC(3) * j1;
-            f[0] = w0 * E0;
-            f[1] = w1 * (Ex + o0);
-            f[3] = w1 * (Ex - o0);
-            f[2] = w1 * (Ey + o1);
-            f[4] = w1 * (Ey - o1);
-            f[5] = w5 * (Ep + o0 + o1);
-            f[7] = w5 * (Ep - o0 - o1);
-            f[6] = w5 * (Em - o0 + o1);
-            f[8] = w5 * (Em + o0 - o1);
-        }
-        const TC b0 = TC(3) * (k.omega * j0 + k.force_pref * sn0);
-        const TC b1 = TC(3) * (k.omega * j1 + k.force_pref * sn1);
-        const TC ax = w1 * (k.omega * Ex), ay = w1 * (k.omega * Ey);
-        const TC ap = w5 * (k.omega * Ep), am = w5 * (k.omega * Em);
-        const TC bx = w1 * b0, by = w1 * b1;
-        const TC bp = w5 * (b0 + b1), bm = w5 * (b1 - b0);
-        TC fc[9];
-        fc[0] = k.one_m_omega * f[0] + w0 * (k.omega * E0);
-        fc[1] = k.one_m_omega * f[1] + (ax + bx);
-        fc[3] = k.one_m_omega * f[3] + (ax - bx);
-        fc[2] = k.one_m_omega * f[2] + (ay + by);
-        fc[4] = k.one_m_omega * f[4] + (ay - by);
-        fc[5] = k.one_m_omega * f[5] + (ap + bp);
-        fc[7] = k.one_m_omega * f[7] + (ap - bp);
-        fc[6] = k.one_m_omega * f[6] + (am + bm);
-        fc[8] = k.one_m_omega * f[8] + (am - bm);
-
-        // stores, with the periodic images of nodes near a seam
-        const bool short_x = g.perx && nx < 6, short_y = g.pery && ny < 6;
-        const int64_t img_x = (!g.perx || short_x) ? 0 : (gx < 3 ? nx : (gx >= nx - 3 ? -nx : 0));
-        const int64_t img_y =
-            (!g.pery || short_y) ? 0 : (gy < 3 ? int64_t(ny) * pitch : (gy >= ny - 3 ? -int64_t(ny) * pitch : 0));
-        const bool slow = short_x || short_y;
-        auto put = [&](auto* base, auto v) {
-            if (slow) {
-                store_img_slow(base, g, gx, gy, v);
-                return;
-            }
-            base[o] = v;
-            if (img_x) base[o + img_x] = v;
-            if (img_y) base[o + img_y] = v;
-            if (img_x && img_y) base[o + img_y + img_x] = v;
-        };
-#pragma unroll
-        for (int i = 0; i < 9; ++i) put(fdst + i * plane, Codec<TS, TC>::st(fc[i], i, p));
-
-        // links that leave the body through a bounded edge
-        if (gxl || gxh || gyl || gyh) {
-            const TC* qr = sq + (ty * 4) * tw + tx;
-            Pops<TC> pc;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) pc.v[i] = fc[i];
-            boundary_links<TS, TC, UT>(fdst, g, p, s_edge, gx, gy, pc, r, pxx, pxy, pyy, qr[0], qr[tw], qr[2 * tw],
-                                       qr[3 * tw], k.inv_c2);
-        }
-
-        // carries for the next step: A' = u + ku (jh + s/2), u = u* + du
-        const UT A0 = ux.add(du0 + k.ku * (j0 + TC(0.5) * sn0)).renorm();
-        const UT A1 = uy.add(du1 + k.ku * (j1 + TC(0.5) * sn1)).renorm();
-#pragma unroll
-        for (int c = 0; c < UP; ++c) {
-            put(a_dst + c * plane, A0.part(c));
-            put(a_dst + (UP + c) * plane, A1.part(c));
-        }
-        put(s_dst, sn0);
-        put(s_dst + plane, sn1);
-        if (L.fields && p.fields != nullptr) {
-            const int64_t fo = int64_t(gy) * nx + gx;
-            const int64_t np = int64_t(nx) * ny;
-            p.fields[fo] = ux.add(du0).to_double();
-            p.fields[np + fo] = uy.add(du1).to_double();
-            p.fields[2 * np + fo] = double(j0 * k.c_over_rho0);
-            p.fields[3 * np + fo] = double(j1 * k.c_over_rho0);
-            p.fields[4 * np + fo] = double(r);
-            if (!(fabs(double(j0)) + fabs(double(j1)) < 1e300)) bad = true;
-        }
-    }
-    if (bad) atomicOr(p.flag, 1);
+    edge_tile_body<TS, TC, UT, MODE>(tile, sp, L.fields != 0, su, sq, MODE == 1 ? sinit : nullptr, s_edge);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -420,29 +80,30 @@ cudaError_t launch_edge(int fmt, const EdgeLaunch& L, int ntiles, cudaStream_t s
     return cudaErrorInvalidValue;
 }
 
-// Tiles of one rectangle.  A band at most 3 nodes thick gets tiles exactly
-// as thick (th = thickness + 4 rows of threads, tw = 256 / th columns), so
-// few threads compute halo only; a larger rectangle gets wide tiles of 28 x 4
-// output nodes.  Every tile has the full extent min(rectangle, tile) along
-// both axes (the last one of a row or column is shifted back, recomputing
-// its neighbour's nodes bit for bit), so each output node on a bounded edge
-// (bodies and bands are at least 2 nodes thick) finds the Q of its two
-// inward neighbours, which stage B computes for the output nodes and their
-// 1-node ring, inside the tile.  Returns the number of tiles (written to out,
-// at most cap, when out is not NULL).
-int edge_tiles_of_rect(const int rect[4], int inst, EdgeTile* out, int cap, bool lead_first) {
+// Tiles of one rectangle for CTAs of nthreads threads.  A band at most 3
+// nodes thick gets tiles exactly as thick (th = thickness + 4 rows of
+// threads, tw = nthreads / th columns), so few threads compute halo only; a
+// larger rectangle gets wide tiles (32 x 8 threads for 256, 16 x 8 for 128).
+// Every tile has the full extent min(rectangle, tile) along both axes (the
+// last one of a row or column is shifted back, recomputing its neighbour's
+// nodes bit for bit), so each output node on a bounded edge (bodies and
+// bands are at least 2 nodes thick) finds the Q of its two inward
+// neighbours, which stage B computes for the output nodes and their 1-node
+// ring, inside the tile.  Returns the number of tiles (written to out, at
+// most cap, when out is not NULL).
+int edge_tiles_of_rect(const int rect[4], int inst, EdgeTile* out, int cap, bool lead_first, int nthreads) {
     const int w = rect[1] - rect[0], h = rect[3] - rect[2];
-    if (w <= 0 || h <= 0) return 0;
+    if (w <= 0 || h <= 0 || nthreads < 128) return 0;
     int tw, th;
     if (h <= 3) {
         th = h + 4;
-        tw = kEdgeThreads / th;
+        tw = nthreads / th;
     } else if (w <= 3) {
         tw = w + 4;
-        th = kEdgeThreads / tw;
+        th = nthreads / tw;
     } else {
-        tw = 32;
-        th = kEdgeThreads / 32;
+        th = 8;
+        tw = nthreads / th >= 32 ? 32 : nthreads / th;
     }
     const int ow = tw - 4, oh = th - 4;
     int n = 0;

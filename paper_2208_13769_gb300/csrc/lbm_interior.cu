@@ -39,6 +39,7 @@
 #include <stdint.h>
 
 #include "lbm_device.cuh"
+#include "lbm_edge_tile.cuh"
 #include "lbm_kernels.h"
 #include "lbm_pipeline.cuh"
 
@@ -383,23 +384,58 @@ __global__ void __launch_bounds__(NT, MINB) interior_step_kernel(const __grid_co
     interior_tile<TS, TC, UT, NT, true>(p, int(blockIdx.x), int(blockIdx.y), p.fields, false);
 }
 
-// A batch of bodies: a persistent grid of resident CTAs, each running the
-// work items (body, strip, chunk) blockIdx.x, blockIdx.x + gridDim.x, ... in
-// turn (the list is ordered longest first); each item's parameters come from
-// the device table into shared memory.
+// One time step of a batch of bodies in one launch: a persistent grid of
+// resident CTAs, each taking the next item of the work list from a device
+// queue when it is done with the last one, until none is left.  Items are interior tiles (body, strip, chunk)
+// and edge tiles (shapes for NT threads) of every member, interleaved in the
+// list, so that the latency-bound edge tiles of some CTAs run beside the
+// bandwidth-bound interior tiles of others.  Each item's parameters come
+// from the device table into shared memory; an edge tile uses the shared
+// buffers of the interior tile (u*, Q, and the edges' boundary data after
+// the u* rows it needs).  The queue {next item, CTAs done} is zero when the
+// launch starts; the last CTA to finish sets it back to zero.
 template <class TS, class TC, class UT, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) interior_batch_kernel(const __grid_constant__ InteriorLaunch L) {
+__global__ void __launch_bounds__(NT, MINB) batch_step_kernel(const __grid_constant__ BatchLaunch L) {
     __shared__ __align__(16) StepParams sp;
-    for (int wi = int(blockIdx.x); wi < L.nwork; wi += int(gridDim.x)) {
-        const InteriorWork w = L.work[wi];
-        __syncthreads();  // the previous item is done with sp
-        {
-            const int4* src = reinterpret_cast<const int4*>(L.params + w.inst);
-            int4* dst = reinterpret_cast<int4*>(&sp);
-            for (int q = int(threadIdx.x); q < int(sizeof(StepParams) / 16); q += NT) dst[q] = src[q];
+    __shared__ EdgeTile s_tile;
+    extern __shared__ __align__(128) unsigned char smem[];
+    UT* su = reinterpret_cast<UT*>(smem + 256);
+    TC* sq = reinterpret_cast<TC*>(smem + 256 + sizeof(UT) * 6 * NT);
+    EdgeNow<TC, UT>* s_edge = reinterpret_cast<EdgeNow<TC, UT>*>(su + 2 * NT);
+    static_assert(4 * sizeof(EdgeNow<TC, UT>) <= 4 * NT * sizeof(UT), "edge data fits after the u* rows");
+    const int t = int(threadIdx.x);
+    for (;;) {
+        __syncthreads();  // every thread is done with the previous item
+        if (t == 0) {
+            const int k = atomicAdd(L.queue, 1);
+            if (k < L.nitems) {
+                s_tile = L.items[k];
+            } else {
+                s_tile.tw = 255;  // none left
+                s_tile.th = 0;
+            }
         }
         __syncthreads();
-        if (!interior_tile<TS, TC, UT, NT, false>(sp, w.bx, w.by, L.fields ? sp.fields : nullptr, true)) break;
+        const EdgeTile it = s_tile;
+        if (it.tw == 255 && it.th == 0) break;
+        {
+            const int4* src = reinterpret_cast<const int4*>(L.params + it.inst);
+            int4* dst = reinterpret_cast<int4*>(&sp);
+            for (int q = t; q < int(sizeof(StepParams) / 16); q += NT) dst[q] = src[q];
+        }
+        __syncthreads();
+        if (it.tw == 0) {
+            if (!interior_tile<TS, TC, UT, NT, false>(sp, it.x0, it.y0, L.fields ? sp.fields : nullptr, true)) break;
+        } else {
+            edge_tile_body<TS, TC, UT, 0>(it, sp, L.fields != 0, su, sq, nullptr, s_edge);
+        }
+    }
+    if (t == 0) {
+        __threadfence();
+        if (atomicAdd(L.queue + 1, 1) == int(gridDim.x) - 1) {  // the last CTA: no item is taken any more
+            L.queue[0] = 0;
+            L.queue[1] = 0;
+        }
     }
 }
 
@@ -424,9 +460,8 @@ cudaError_t launch_interior_t(const StepParams& p, cudaStream_t s) {
 }
 
 template <class TS, class TC, class UT, int NT, int MINB>
-cudaError_t launch_interior_batch_t(const InteriorLaunch& L, int grid, int ring_slots, cudaStream_t s,
-                                    int* resident) {
-    auto kern = interior_batch_kernel<TS, TC, UT, NT, MINB>;
+cudaError_t launch_batch_step_t(const BatchLaunch& L, int grid, int ring_slots, cudaStream_t s, int* resident) {
+    auto kern = batch_step_kernel<TS, TC, UT, NT, MINB>;
     const size_t sm = interior_smem_bytes<TS, TC, UT, NT>(ring_slots);
     static size_t configured = 0;
     if (sm > configured) {
@@ -439,22 +474,25 @@ cudaError_t launch_interior_batch_t(const InteriorLaunch& L, int grid, int ring_
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, kern, NT, sm);
         if (e != cudaSuccess) return e;
     }
-    if (grid <= 0 || L.nwork <= 0) return cudaSuccess;
+    if (grid <= 0 || L.nitems <= 0) return cudaSuccess;
     kern<<<grid, NT, sm, s>>>(L);
     return cudaGetLastError();
 }
 
-cudaError_t launch_interior_batch(int fmt, const InteriorLaunch& L, int grid, int ring_slots, cudaStream_t s,
-                                  int* resident) {
+// Six CTAs per SM (the interior tile's shared memory allows six with the
+// default ring): the edge tile's code would otherwise take more registers.
+cudaError_t launch_batch_step(int fmt, const BatchLaunch& L, int grid, int ring_slots, cudaStream_t s,
+                              int* resident) {
+    constexpr int NT = kInteriorThreads;
     switch (fmt) {
         case kFmtF64:
-            return launch_interior_batch_t<double, double, UPlain<double>, 128, 2>(L, grid, ring_slots, s, resident);
+            return launch_batch_step_t<double, double, UPlain<double>, NT, 2>(L, grid, ring_slots, s, resident);
         case kFmtF32:
-            return launch_interior_batch_t<float, float, UPlain<float>, 128, 4>(L, grid, ring_slots, s, resident);
-        case kFmtF32C: return launch_interior_batch_t<float, float, UComp, 128, 4>(L, grid, ring_slots, s, resident);
-        case kFmtF16: return launch_interior_batch_t<__half, float, UComp, 128, 4>(L, grid, ring_slots, s, resident);
+            return launch_batch_step_t<float, float, UPlain<float>, NT, 6>(L, grid, ring_slots, s, resident);
+        case kFmtF32C: return launch_batch_step_t<float, float, UComp, NT, 6>(L, grid, ring_slots, s, resident);
+        case kFmtF16: return launch_batch_step_t<__half, float, UComp, NT, 6>(L, grid, ring_slots, s, resident);
         case kFmtBF16:
-            return launch_interior_batch_t<__nv_bfloat16, float, UComp, 128, 4>(L, grid, ring_slots, s, resident);
+            return launch_batch_step_t<__nv_bfloat16, float, UComp, NT, 6>(L, grid, ring_slots, s, resident);
     }
     return cudaErrorInvalidValue;
 }
@@ -462,15 +500,18 @@ cudaError_t launch_interior_batch(int fmt, const InteriorLaunch& L, int grid, in
 void interior_strips(int fmt, int rx0, int rx1, bool aligned, int* strip_x0, int* strip_w, int* nstrips) {
     int W = 124, xg = rx0;  // 128 threads: the strip and its 2-column halo on each side
     if (aligned) {
-        // strips on the grid of 32-byte sectors (8 columns of a 4- or 8-byte
-        // plane, 16 of a 2-byte plane; column x sits at x + kPadCols of a plane
-        // row and rows start 256-byte aligned), so that no two CTAs store into
-        // one sector even when they run far apart in time
+        // the fewest strips of equal width on the grid of 32-byte sectors (8
+        // columns of a 4- or 8-byte plane, 16 of a 2-byte plane; column x sits
+        // at x + kPadCols of a plane row and rows start 256-byte aligned), so
+        // that no two CTAs store into one sector even when they run far apart
+        // in time
         const bool half = fmt == kFmtF16 || fmt == kFmtBF16;
-        W = half ? 112 : 120;
+        const int sec = half ? 16 : 8, wmax = half ? 112 : 120;
         const int g0 = half ? -8 : 0;  // g0 + kPadCols is a multiple of the sector's columns
         auto fdiv = [](int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
-        xg = g0 + fdiv(rx0 - g0, W) * W;
+        xg = g0 + fdiv(rx0 - g0, sec) * sec;
+        const int span = rx1 - xg, n = (span + wmax - 1) / wmax;
+        W = ((span + n - 1) / n + sec - 1) / sec * sec;
     }
     *strip_x0 = xg;
     *strip_w = W;

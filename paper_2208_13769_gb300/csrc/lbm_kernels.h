@@ -18,38 +18,45 @@ enum Format : int {
 
 
 // The interior kernel (lbm_interior.cu): nodes of p.rect[0] only, which must
-// lie at least 2 nodes from bounded edges and 3 from periodic seams.
+// lie at least 2 nodes from bounded edges and 3 from periodic seams.  A CTA
+// has kInteriorThreads threads, one per column of its strip and halo.
+constexpr int kInteriorThreads = 128;
 size_t interior_smem(int fmt, int ring_slots);
 // CTAs of the interior kernel resident per SM with this ring (0 on error);
 // also sets the kernel's dynamic shared-memory limit, so call it before any
 // stream capture.
 int interior_occupancy(int fmt, int ring_slots);
-// Rows of the interior kernel's bulk-copy ring (lookahead = ring - 3 rows).
+// Rows of the interior kernel's bulk-copy ring (the single-body kernel keeps
+// them all in flight; the batch kernel, which re-reads a row in stage C, all
+// but 3).
 constexpr int kInteriorRing = 5;
 // The strip grid of the interior kernel over columns [rx0, rx1): origin of
-// strip 0, output columns per strip, number of strips.  aligned: strips on
+// strip 0, output columns per strip, number of strips.  aligned: the fewest
+// strips of equal width (at most 120 columns, 112 for 16-bit storage) on
 // 32-byte sector boundaries (for CTAs of one body that may run in different
 // waves), else 124-column strips from rx0 (one wave).
 void interior_strips(int fmt, int rx0, int rx1, bool aligned, int* strip_x0, int* strip_w, int* nstrips);
 cudaError_t launch_interior(int fmt, const StepParams& p, cudaStream_t s, bool fields);
 
-// Interior tiles of a batch of bodies: work item = (entry of the parameter
-// table, column strip, row chunk) of that body's rect / chunk_rows.
-struct InteriorWork {
-    int32_t inst, bx, by, pad;
-};
-struct InteriorLaunch {
-    const StepParams* params;  // device table, indexed by InteriorWork::inst
-    const InteriorWork* work;  // device work list
+// One time step of a batch of bodies in one launch: a persistent grid whose
+// CTAs take the items of a work list one at a time from a device queue.  An
+// item is an EdgeTile record: an edge tile (shape for kInteriorThreads
+// threads), or, with tw == 0, the interior tile (strip x0, chunk y0) of body
+// inst (its rect / chunk_rows / strip grid in the parameter table).
+struct EdgeTile;
+struct BatchLaunch {
+    const StepParams* params;  // device table, indexed by EdgeTile::inst
+    const EdgeTile* items;     // device work list, in the order it is taken
+    int32_t* queue;            // device {next item, CTAs done}: zero between launches
     int32_t fields;            // also write u, v, r to params.fields
-    int32_t nwork;             // items in the work list
+    int32_t nitems;            // items in the list
 };
-// A persistent grid of `grid` CTAs runs the work list.  The setting of the
+// A persistent grid of `grid` CTAs runs the items.  The setting of the
 // dynamic shared-memory limit happens on the first call (also with grid ==
 // 0), which must precede any stream capture; resident (may be NULL) receives
 // the kernel's CTAs per SM with this ring.
-cudaError_t launch_interior_batch(int fmt, const InteriorLaunch& L, int grid, int ring_slots, cudaStream_t s,
-                                  int* resident);
+cudaError_t launch_batch_step(int fmt, const BatchLaunch& L, int grid, int ring_slots, cudaStream_t s,
+                              int* resident);
 
 // The edge kernel (lbm_edge.cu): small 2-D tiles with every boundary rule.
 // A tile's threads cover its output nodes and a 2-node halo: tw x th nodes
@@ -75,8 +82,10 @@ struct EdgeLaunch {
 // One step (mode 0) or the initialisation (mode 1) over ntiles tiles.
 cudaError_t launch_edge(int fmt, const EdgeLaunch& L, int ntiles, cudaStream_t s, int mode);
 
-// Tiles of one band rectangle (count only when out is NULL).
-int edge_tiles_of_rect(const int rect[4], int inst, EdgeTile* out, int cap, bool lead_first);
+// Tiles of one band rectangle for CTAs of `nthreads` threads (kEdgeThreads
+// for the edge kernel, kInteriorThreads for the batch kernel); count only
+// when out is NULL.
+int edge_tiles_of_rect(const int rect[4], int inst, EdgeTile* out, int cap, bool lead_first, int nthreads);
 
 // Read-out parameters: stresses from the FP64 displacement field.
 struct ReadoutParams {

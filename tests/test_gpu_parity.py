@@ -213,23 +213,27 @@ def test_bounded_wait_gives_up_and_the_context_survives():
 
 def test_tuning_changes_the_split_not_the_result():
     """Every decomposition of the interior launch (ring depth, rows per CTA,
-    strip grid) gives bit-identical fields; the autotuner returns one of the
-    candidates and the tuning in use is reported."""
+    strip grid) gives bit-identical fields in every storage format; the
+    autotuner returns one of the candidates and the tuning in use is
+    reported."""
     prob, _ = CASES["clamped_96x50"]
     big = W.smooth_random(400, 300, W.clamped_free_edges(), seed=23, amp=0.01, vamp=0.004, lam=0.3, mu=0.3)
-    for pr in (prob, big):
-        with lbm.Body(pr, storage="f32") as b:
-            b.step(140)
-            ref = b.read(lbm.LBM_FIELD_U | lbm.LBM_FIELD_V | lbm.LBM_FIELD_R)
-        for ring, chunk, aligned in ((4, 0, 0), (6, 32, 1), (8, 9, 0), (5, 256, 1)):
-            t = lbm.lbm_tuning(ring, chunk, aligned)
-            with lbm.Body(pr, storage="f32", tuning=t) as b:
+    wide = W.smooth_random(700, 90, W.all_periodic(), seed=29, amp=0.01, vamp=0.004, lam=0.3, mu=0.3)
+    tunings = ((4, 0, 0), (6, 32, 1), (8, 9, 0), (5, 256, 1), (7, 40, 0))
+    for storage in ("f32", "f64", "f16"):
+        for pr in (prob, big, wide):
+            with lbm.Body(pr, storage=storage) as b:
                 b.step(140)
-                got = b.read(lbm.LBM_FIELD_U | lbm.LBM_FIELD_V | lbm.LBM_FIELD_R)
-                used = lbm.lbm_get_tuning(b.ctx)
-            assert used.ring_slots == ring and used.aligned == aligned
-            for k in ("u", "v", "r"):
-                assert np.array_equal(got[k], ref[k]), (pr.name, ring, chunk, aligned, k)
+                ref = b.read(lbm.LBM_FIELD_U | lbm.LBM_FIELD_V | lbm.LBM_FIELD_R)
+            for ring, chunk, aligned in tunings:
+                t = lbm.lbm_tuning(ring, chunk, aligned)
+                with lbm.Body(pr, storage=storage, tuning=t) as b:
+                    b.step(140)
+                    got = b.read(lbm.LBM_FIELD_U | lbm.LBM_FIELD_V | lbm.LBM_FIELD_R)
+                    used = lbm.lbm_get_tuning(b.ctx)
+                assert used.ring_slots == ring and used.aligned == aligned
+                for k in ("u", "v", "r"):
+                    assert np.array_equal(got[k], ref[k]), (storage, pr.name, ring, chunk, aligned, k)
     d = lbm.lbm_desc()
     d.nx, d.ny, d.dX, d.storage, d.u_carry, d.scheme = 400, 300, 1.0, lbm.LBM_F32, 1, 1
     best, ms = lbm.lbm_autotune(d, [e.kind for e in big.edges], 65)
