@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--forms", default="f32n,f16,bf16",
                     help="extra population formats timed on the same body ('' to skip)")
     ap.add_argument("--form-steps", type=int, default=500)
+    ap.add_argument("--c3-steps", type=int, default=1000,
+                    help="steps of the 8192 x 8192 16-bit storage run (0 to skip)")
     ap.add_argument("--batch", type=int, default=256,
                     help="bodies of the batched workload (seeded, sides 64..1024; 0 to skip)")
     ap.add_argument("--batch-steps", type=int, default=256)
@@ -401,6 +403,37 @@ def run_native(a):
                     "achieved_gbs": ach, "frac": ach / peak, "steps": a.form_steps, "stable": ok,
                     "u_rel_err_vs_f64": uerr}
 
+    # the 8192 x 8192 clamped body with 16-bit population storage, timed, and
+    # its displacement error against the FP64 path on the same inputs (the
+    # full field and the stride-16 downsample, 512 x 512 points); the FP64
+    # path stands in for the oracle, which this size would keep busy for an
+    # hour; the body stays inside the method's stable horizon
+    c3 = None
+    if a.c3_steps > 0 and world == 1:
+        from paper_2208_13769_gb300 import workloads as W
+
+        big = W.clamped_body(nx=8192, ny=8192, mu=0.3, nu=a.nu, vmax=a.vmax)
+        with lbm.Body(big, storage="f64", stream=stream.cuda_stream, device=local) as b64:
+            b64.step(a.c3_steps)
+            u64 = b64.read(lbm.LBM_FIELD_U, allow_unstable=True)["u"]
+        c3 = {"workload": f"clamped neo-Hooke body 8192x8192, {a.c3_steps} steps, nu {a.nu}, v_max {a.vmax}",
+              "reference": "FP64 GPU path (oracle-validated), same inputs"}
+        for st in ("f16", "bf16"):
+            b = lbm.Body(big, storage=st, stream=stream.cuda_stream, device=local)
+            _, bpn = lbm.lbm_memory_info(b.ctx)
+            b.step(a.warmup)
+            s = time_steps(b, stream, a.c3_steps - a.warmup)
+            out = b.read(lbm.LBM_FIELD_U, allow_unstable=True)
+            b.close()
+            du = out["u"] - u64
+            ds = du[::16, ::16]
+            ach = bpn * big.nodes / (s / (a.c3_steps - a.warmup)) / 1e9
+            c3[st] = {"mlups": big.nodes * (a.c3_steps - a.warmup) / s / 1e6, "bytes_per_node_update": bpn,
+                      "achieved_gbs": ach, "frac": ach / peak, "stable": out["status"] == lbm.LBM_OK,
+                      "u_rel_err_vs_f64": float(np.linalg.norm(du) / np.linalg.norm(u64)),
+                      "u_rel_err_vs_f64_512x512": float(np.linalg.norm(ds) / np.linalg.norm(u64[::16, ::16]))}
+        del u64
+
     # batched workload: many uneven bodies advanced by shared launches, and
     # the same bodies stepped one after another
     batched = None
@@ -511,7 +544,8 @@ def run_native(a):
         "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "f16": "f16", "bf16": "bf16"}[a.storage],
         "data": "synthetic", "config": config_of(a, prob), "roofline": roof, "cpu_baseline": cpu,
-        "e2e": e2e, "gpu_launches": 2 * a.steps, "clocks": clk, "forms": forms, "batched": batched, "serving": serving, "tuning": tuning_info,
+        "e2e": e2e, "gpu_launches": 2 * a.steps, "clocks": clk, "forms": forms, "c3_8192": c3, "batched": batched,
+        "serving": serving, "tuning": tuning_info,
         "status": lbm.status_string(status),
     }
     print(json.dumps(line), flush=True)

@@ -47,9 +47,13 @@ namespace lbm {
 
 namespace {
 
+// Shared memory of the interior tile: a 128-byte header (the ring's
+// mbarriers, at most 8), the u* rows [3][2][NT] and the Q rows [3][4][NT],
+// then the ring.
+constexpr int kSmemHeader = 128;
 template <class UT, class TC, int NT>
 __host__ __device__ constexpr size_t interior_smem_fixed() {
-    return (256 + sizeof(UT) * 6 * NT + sizeof(TC) * 12 * NT + 127) / 128 * 128;
+    return (kSmemHeader + sizeof(UT) * 6 * NT + sizeof(TC) * 12 * NT + 127) / 128 * 128;
 }
 
 // Elements of one bulk-copied row segment: a strip of W <= NT - 4 output
@@ -89,8 +93,8 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
     extern __shared__ __align__(128) unsigned char smem[];
     const int R = p.ring_slots;  // row slots: lookahead + 3
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    UT* su = reinterpret_cast<UT*>(smem + 256);                          // [3][2][NT]
-    TC* sq = reinterpret_cast<TC*>(smem + 256 + sizeof(UT) * 6 * NT);   // [3][4][NT]
+    UT* su = reinterpret_cast<UT*>(smem + kSmemHeader);                          // [3][2][NT]
+    TC* sq = reinterpret_cast<TC*>(smem + kSmemHeader + sizeof(UT) * 6 * NT);   // [3][4][NT]
     unsigned char* ring = smem + interior_smem_fixed<UT, TC, NT>();
     __shared__ int s_abort;
 
@@ -110,6 +114,10 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
     int seg0 = x0 - 3;
     seg0 = (seg0 >= 0 ? seg0 : seg0 - (ALIGN_COLS - 1)) / ALIGN_COLS * ALIGN_COLS;
     if (seg0 < -kPadCols) seg0 = -kPadCols;
+    // elements of each segment this tile copies: through column x_hi + 2 (the
+    // last one stage A pulls from), in whole 16-byte units (a strip narrower
+    // than the widest copies less)
+    const int seg_n = min(SEG, (x_hi + 3 - seg0 + ALIGN_COLS - 1) / ALIGN_COLS * ALIGN_COLS);
 
     const TS* __restrict__ fsrc = static_cast<const TS*>(p.f_src);
     TS* __restrict__ fdst = static_cast<TS*>(p.f_dst);
@@ -135,13 +143,15 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
     auto issue_row = [&](int a, int s) -> bool {
         unsigned char* base = ring + size_t(s) * ROW_BYTES;
         const uintptr_t acc = reinterpret_cast<uintptr_t>(base) | reinterpret_cast<uintptr_t>(src_seg) |
-                              uintptr_t(pitch * int64_t(sizeof(TS))) | uintptr_t(plane * int64_t(sizeof(TS)));
+                              uintptr_t(pitch * int64_t(sizeof(TS))) | uintptr_t(plane * int64_t(sizeof(TS))) |
+                              uintptr_t(seg_n * int(sizeof(TS)));
         if (acc & 15) return false;
-        mbar_expect_tx(&bars[s], uint32_t(ROW_BYTES));
+        mbar_expect_tx(&bars[s], uint32_t(9 * seg_n * int(sizeof(TS))));
         TS* dst = reinterpret_cast<TS*>(base);
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-            bulk_load(dst + i * SEG, src_seg + i * plane + int64_t(a - ey(i)) * pitch, SEG * sizeof(TS), &bars[s]);
+            bulk_load(dst + i * SEG, src_seg + i * plane + int64_t(a - ey(i)) * pitch, uint32_t(seg_n * sizeof(TS)),
+                      &bars[s]);
         return true;
     };
 
@@ -399,8 +409,8 @@ __global__ void __launch_bounds__(NT, MINB) batch_step_kernel(const __grid_const
     __shared__ __align__(16) StepParams sp;
     __shared__ EdgeTile s_tile;
     extern __shared__ __align__(128) unsigned char smem[];
-    UT* su = reinterpret_cast<UT*>(smem + 256);
-    TC* sq = reinterpret_cast<TC*>(smem + 256 + sizeof(UT) * 6 * NT);
+    UT* su = reinterpret_cast<UT*>(smem + kSmemHeader);
+    TC* sq = reinterpret_cast<TC*>(smem + kSmemHeader + sizeof(UT) * 6 * NT);
     EdgeNow<TC, UT>* s_edge = reinterpret_cast<EdgeNow<TC, UT>*>(su + 2 * NT);
     static_assert(4 * sizeof(EdgeNow<TC, UT>) <= 4 * NT * sizeof(UT), "edge data fits after the u* rows");
     const int t = int(threadIdx.x);
