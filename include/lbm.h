@@ -151,7 +151,7 @@ LBM_API lbm_status lbm_profile_steps(lbm_ctx* ctx, int64_t nsteps, double out[4]
  * changes how the work is split, never the result: every setting gives
  * bit-identical fields). */
 typedef struct {
-    int32_t ring_slots; /* rows of the bulk-copy ring, 4..8 (all of them in flight); 0: default (5) */
+    int32_t ring_slots; /* rows of the bulk-copy ring, 4..8 (all of them in flight); 0: default (4) */
     int32_t chunk_rows; /* rows per CTA, >= 8; 0: one wave of CTAs over the SMs (default) */
     int32_t aligned;    /* 1: the fewest strips of equal width on 32-byte sector boundaries (at
                            most 120 columns; 112 for 16-bit storage); 0: 124-column strips;

@@ -89,7 +89,7 @@ cudaError_t batch_launch(lbm_batch* b, int q, bool fields) {
     L.queue = b->dqueue;
     L.fields = fields ? 1 : 0;
     L.nitems = b->n_work + b->n_edge;
-    return launch_batch_step(b->fmt, L, b->grid, kInteriorRing, b->stream, nullptr);
+    return launch_batch_step(b->fmt, L, b->grid, kBatchRing, b->stream, nullptr);
 }
 
 void advance_members(lbm_batch* b, int64_t k) {
@@ -188,7 +188,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
     for (lbm_ctx* c : b->m)
         if (c->has_interior)
             interior_nodes += int64_t(c->irect[1] - c->irect[0]) * (c->irect[3] - c->irect[2]);
-    const int64_t wave = int64_t(b->m[0]->num_sms) * std::max(1, interior_occupancy(b->fmt, kInteriorRing));
+    const int64_t wave = int64_t(b->m[0]->num_sms) * std::max(1, interior_occupancy(b->fmt, kBatchRing));
     b->chunk_rows = int(std::min<int64_t>(256, std::max<int64_t>(32, interior_nodes / (int64_t(120) * wave * 8))));
     std::vector<StepParams> tab;
     std::vector<InteriorWork> work;
@@ -212,7 +212,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
                 StepParams p = make_params(c, b->base_parity[size_t(i)] ^ q);
                 for (int k = 0; k < 4; ++k) p.rect[k] = c->irect[k];
                 p.chunk_rows = b->chunk_rows;
-                p.ring_slots = kInteriorRing;
+                p.ring_slots = kBatchRing;
                 p.strip_x0 = sx0[size_t(i)];
                 p.strip_w = sw[size_t(i)];
                 tab[size_t(q) * n + i] = p;
@@ -283,7 +283,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
         BatchLaunch L;
         memset(&L, 0, sizeof(L));
         int resident = 0;
-        e = launch_batch_step(b->fmt, L, 0, kInteriorRing, b->stream, &resident);
+        e = launch_batch_step(b->fmt, L, 0, kBatchRing, b->stream, &resident);
         b->grid = int(std::min<int64_t>(int64_t(items.size()), int64_t(b->m[0]->num_sms) * std::max(1, resident)));
     }
     if (e != cudaSuccess) {

@@ -87,9 +87,17 @@ __device__ __forceinline__ T feq_odd_over_w(int i, T j0, T j1, T inv_c) {
 //   J Q12 = -H21 d (mu + lambda/2 (2 + d)),  J Q21 = -H12 d (mu + lambda/2 (2 + d)).
 // No term of order mu cancels, so the rounding error of Q is relative to
 // mu |H| rather than to mu.  Returns J.
-// Correctly rounded reciprocal (no division slow path).
-__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+// 1 / J, J = det F near 1 for any admissible deformation.  FP32: the
+// hardware's approximate reciprocal, one instruction on the critical path of
+// stage B (its error, about an ulp, is far inside the FP32 path's
+// tolerance); FP64: the correctly rounded reciprocal, for the FP64 path's
+// parity with the oracle.
+__device__ __forceinline__ float rcp_j(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp_j(double x) { return __drcp_rn(x); }
 
 template <class T>
 __device__ __forceinline__ T stress_remainder(T h11, T h12, T h21, T h22, T lam, T mu, T& q11, T& q12,
@@ -97,7 +105,7 @@ __device__ __forceinline__ T stress_remainder(T h11, T h12, T h21, T h22, T lam,
     const T D = h11 * h22 - h12 * h21;
     const T d = (h11 + h22) + D;
     const T J = T(1) + d;
-    const T invJ = rcp_rn(J);
+    const T invJ = rcp_j(J);
     const T vol = T(0.5) * lam * d * (T(2) + d);
     q11 = (mu * (T(2) * D - d * (T(1) + T(2) * h11 + h22)) + vol * (T(1) + h22)) * invJ;
     q22 = (mu * (T(2) * D - d * (T(1) + T(2) * h22 + h11)) + vol * (T(1) + h11)) * invJ;

@@ -26,10 +26,11 @@ size_t interior_smem(int fmt, int ring_slots);
 // also sets the kernel's dynamic shared-memory limit, so call it before any
 // stream capture.
 int interior_occupancy(int fmt, int ring_slots);
-// Rows of the interior kernel's bulk-copy ring (the single-body kernel keeps
-// them all in flight; the batch kernel, which re-reads a row in stage C, all
-// but 3).
-constexpr int kInteriorRing = 5;
+// Rows of the interior kernel's bulk-copy ring by default: the single-body
+// kernel keeps them all in flight (4 measured fastest); the batch kernel,
+// which re-reads a row in stage C, keeps all but 3 in flight.
+constexpr int kInteriorRing = 4;
+constexpr int kBatchRing = 5;
 // The strip grid of the interior kernel over columns [rx0, rx1): origin of
 // strip 0, output columns per strip, number of strips.  aligned: the fewest
 // strips of equal width (at most 120 columns, 112 for 16-bit storage) on
