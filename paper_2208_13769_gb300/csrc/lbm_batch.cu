@@ -42,10 +42,12 @@ struct lbm_batch {
     std::vector<int> base_parity;  // member parity when the batch step count is even
     int fmt = 0;
     StepParams* dtab = nullptr;  // [2][n]: entry q * n + i = member i at parity base_parity[i] ^ q
-    EdgeTile* ditems = nullptr;  // work list: interior tiles (tw == 0) and edge tiles, interleaved
-    int32_t* dqueue = nullptr;   // {next item, CTAs done} of the persistent kernel
-    int n_work = 0;              // interior tiles in the list
-    int n_edge = 0;              // edge tiles in the list
+    BatchItem* ditems = nullptr;  // work list: interior tiles and groups of edge tiles, interleaved
+    EdgeTile* dtiles = nullptr;   // edge tiles of the groups
+    int32_t* dqueue = nullptr;    // {next item, CTAs done} of the persistent kernel
+    int n_work = 0;               // interior tiles
+    int n_edge = 0;               // edge tiles
+    int n_items = 0;              // items of the work list
     int grid = 0;                // persistent CTAs
     int chunk_rows = 0;
     int64_t steps = 0;
@@ -74,6 +76,7 @@ void batch_free(lbm_batch* b) {
         if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
     cudaFree(b->dtab);
     cudaFree(b->ditems);
+    cudaFree(b->dtiles);
     cudaFree(b->dqueue);
     if (b->ev_sync) cudaEventDestroy(b->ev_sync);
     if (b->owns_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -86,9 +89,10 @@ cudaError_t batch_launch(lbm_batch* b, int q, bool fields) {
     memset(&L, 0, sizeof(L));
     L.params = b->dtab + size_t(q) * n;
     L.items = b->ditems;
+    L.tiles = b->dtiles;
     L.queue = b->dqueue;
     L.fields = fields ? 1 : 0;
-    L.nitems = b->n_work + b->n_edge;
+    L.nitems = b->n_items;
     return launch_batch_step(b->fmt, L, b->grid, kBatchRing, b->stream, nullptr);
 }
 
@@ -193,7 +197,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
     std::vector<StepParams> tab;
     std::vector<InteriorWork> work;
     std::vector<EdgeTile> tiles;
-    std::vector<EdgeTile> items;
+    std::vector<BatchItem> items;
     std::vector<int> sx0, sw, ns;  // strip grid of each member's interior
     try {
         sx0.assign(size_t(n), 0);
@@ -242,39 +246,46 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
         };
         std::stable_sort(work.begin(), work.end(),
                          [&](const InteriorWork& x, const InteriorWork& y) { return rows_of(x) > rows_of(y); });
-        // the work list: the interior tiles in that order, with the edge
-        // tiles spread evenly between them
-        const size_t ni = work.size(), ne = tiles.size();
-        items.reserve(ni + ne);
-        size_t next_edge = 0;
-        for (size_t k = 0; k < ni; ++k) {
-            EdgeTile it;
-            memset(&it, 0, sizeof(it));
-            it.inst = work[k].inst;
-            it.x0 = work[k].bx;
-            it.y0 = work[k].by;
-            it.tw = 0;  // an interior tile
-            items.push_back(it);
-            const size_t upto = ne * (k + 1) / ni;
-            for (; next_edge < upto; ++next_edge) items.push_back(tiles[next_edge]);
+        // groups of up to kEdgeGroup consecutive edge tiles of one body
+        std::vector<BatchItem> groups;
+        for (size_t k = 0; k < tiles.size();) {
+            size_t e = k + 1;
+            while (e < tiles.size() && e - k < size_t(kEdgeGroup) && tiles[e].inst == tiles[k].inst) ++e;
+            groups.push_back(BatchItem{tiles[k].inst, int32_t(k), int32_t(e - k), 1});
+            k = e;
         }
-        for (; next_edge < ne; ++next_edge) items.push_back(tiles[next_edge]);
+        // the work list: the interior tiles in that order, with the edge
+        // groups spread evenly between them
+        const size_t ni = work.size(), ng = groups.size();
+        items.reserve(ni + ng);
+        size_t next_group = 0;
+        for (size_t k = 0; k < ni; ++k) {
+            items.push_back(BatchItem{work[k].inst, work[k].bx, work[k].by, 0});
+            const size_t upto = ng * (k + 1) / ni;
+            for (; next_group < upto; ++next_group) items.push_back(groups[next_group]);
+        }
+        for (; next_group < ng; ++next_group) items.push_back(groups[next_group]);
     } catch (...) {
         batch_free(b);
         delete b;
         return LBM_E_OOM;
     }
-    if (items.size() > 0x7fffffff) e = cudaErrorInvalidValue;
+    if (items.size() > 0x7fffffff || tiles.size() > 0x7fffffff) e = cudaErrorInvalidValue;
     b->n_work = int(work.size());
     b->n_edge = int(tiles.size());
+    b->n_items = int(items.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->dtab, sizeof(StepParams) * tab.size());
-    if (e == cudaSuccess) e = cudaMalloc(&b->ditems, sizeof(EdgeTile) * items.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->ditems, sizeof(BatchItem) * items.size());
+    if (e == cudaSuccess && !tiles.empty()) e = cudaMalloc(&b->dtiles, sizeof(EdgeTile) * tiles.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->dqueue, 2 * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemsetAsync(b->dqueue, 0, 2 * sizeof(int32_t), b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->dtab, tab.data(), sizeof(StepParams) * tab.size(), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->ditems, items.data(), sizeof(EdgeTile) * items.size(), cudaMemcpyHostToDevice,
+        e = cudaMemcpyAsync(b->ditems, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess && !tiles.empty())
+        e = cudaMemcpyAsync(b->dtiles, tiles.data(), sizeof(EdgeTile) * tiles.size(), cudaMemcpyHostToDevice,
                             b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host tables die with this scope
     // sets the batch kernel's shared-memory limit outside any capture, and

@@ -396,48 +396,58 @@ __global__ void __launch_bounds__(NT, MINB) interior_step_kernel(const __grid_co
 
 // One time step of a batch of bodies in one launch: a persistent grid of
 // resident CTAs, each taking the next item of the work list from a device
-// queue when it is done with the last one, until none is left.  Items are interior tiles (body, strip, chunk)
-// and edge tiles (shapes for NT threads) of every member, interleaved in the
-// list, so that the latency-bound edge tiles of some CTAs run beside the
-// bandwidth-bound interior tiles of others.  Each item's parameters come
-// from the device table into shared memory; an edge tile uses the shared
-// buffers of the interior tile (u*, Q, and the edges' boundary data after
-// the u* rows it needs).  The queue {next item, CTAs done} is zero when the
-// launch starts; the last CTA to finish sets it back to zero.
+// queue when it is done with the last one, until none is left.  Items are
+// interior tiles (body, strip, chunk) and groups of edge tiles (shapes for NT
+// threads) of every member, interleaved in the list, so that the
+// latency-bound edge tiles of some CTAs run beside the bandwidth-bound
+// interior tiles of others; a group pays for one parameter load, and each of
+// its tiles for one memory round trip.  Each item's parameters come from the
+// device table into shared memory; an edge tile uses the shared buffers of
+// the interior tile (u*, Q, then the edges' boundary data and the group's
+// tile records after the u* rows it needs).  The queue {next item, CTAs
+// done} is zero when the launch starts; the last CTA to finish sets it back
+// to zero.
 template <class TS, class TC, class UT, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) batch_step_kernel(const __grid_constant__ BatchLaunch L) {
     __shared__ __align__(16) StepParams sp;
-    __shared__ EdgeTile s_tile;
+    __shared__ BatchItem s_item;
     extern __shared__ __align__(128) unsigned char smem[];
     UT* su = reinterpret_cast<UT*>(smem + kSmemHeader);
     TC* sq = reinterpret_cast<TC*>(smem + kSmemHeader + sizeof(UT) * 6 * NT);
+    // an edge tile uses the first 2 of the 6 u* rows; its boundary data and
+    // the group's tile records follow
     EdgeNow<TC, UT>* s_edge = reinterpret_cast<EdgeNow<TC, UT>*>(su + 2 * NT);
-    static_assert(4 * sizeof(EdgeNow<TC, UT>) <= 4 * NT * sizeof(UT), "edge data fits after the u* rows");
+    EdgeTile* s_tiles = reinterpret_cast<EdgeTile*>(su + 4 * NT);
+    static_assert(4 * sizeof(EdgeNow<TC, UT>) <= 2 * NT * sizeof(UT), "edge data fits after the u* rows");
+    static_assert(kEdgeGroup * sizeof(EdgeTile) <= 2 * NT * sizeof(UT), "tile records fit in the last u* rows");
     const int t = int(threadIdx.x);
     for (;;) {
         __syncthreads();  // every thread is done with the previous item
         if (t == 0) {
             const int k = atomicAdd(L.queue, 1);
             if (k < L.nitems) {
-                s_tile = L.items[k];
+                s_item = L.items[k];
             } else {
-                s_tile.tw = 255;  // none left
-                s_tile.th = 0;
+                s_item.kind = -1;  // none left
             }
         }
         __syncthreads();
-        const EdgeTile it = s_tile;
-        if (it.tw == 255 && it.th == 0) break;
-        {
+        const BatchItem it = s_item;
+        if (it.kind < 0) break;
+        {  // the body's parameters and a group's tile records, in one round trip
             const int4* src = reinterpret_cast<const int4*>(L.params + it.inst);
             int4* dst = reinterpret_cast<int4*>(&sp);
             for (int q = t; q < int(sizeof(StepParams) / 16); q += NT) dst[q] = src[q];
+            if (it.kind == 1 && t < it.b) s_tiles[t] = L.tiles[it.a + t];
         }
         __syncthreads();
-        if (it.tw == 0) {
-            if (!interior_tile<TS, TC, UT, NT, false>(sp, it.x0, it.y0, L.fields ? sp.fields : nullptr, true)) break;
+        if (it.kind == 0) {
+            if (!interior_tile<TS, TC, UT, NT, false>(sp, it.a, it.b, L.fields ? sp.fields : nullptr, true)) break;
         } else {
-            edge_tile_body<TS, TC, UT, 0>(it, sp, L.fields != 0, su, sq, nullptr, s_edge);
+            for (int g = 0; g < it.b; ++g) {
+                if (g > 0) __syncthreads();  // the previous tile is done with the shared buffers
+                edge_tile_body<TS, TC, UT, 0>(s_tiles[g], sp, L.fields != 0, su, sq, nullptr, s_edge);
+            }
         }
     }
     if (t == 0) {

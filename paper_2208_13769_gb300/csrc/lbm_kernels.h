@@ -41,13 +41,19 @@ cudaError_t launch_interior(int fmt, const StepParams& p, cudaStream_t s, bool f
 
 // One time step of a batch of bodies in one launch: a persistent grid whose
 // CTAs take the items of a work list one at a time from a device queue.  An
-// item is an EdgeTile record: an edge tile (shape for kInteriorThreads
-// threads), or, with tw == 0, the interior tile (strip x0, chunk y0) of body
-// inst (its rect / chunk_rows / strip grid in the parameter table).
+// item of body inst (its rect / chunk_rows / strip grid in the parameter
+// table) is either its interior tile (strip a, chunk b), or a group of b <=
+// kEdgeGroup edge tiles (shapes for kInteriorThreads threads) at tiles[a ..].
+constexpr int kEdgeGroup = 8;
+struct BatchItem {
+    int32_t inst, a, b;
+    int32_t kind;  // 0: interior tile, 1: group of edge tiles
+};
 struct EdgeTile;
 struct BatchLaunch {
-    const StepParams* params;  // device table, indexed by EdgeTile::inst
-    const EdgeTile* items;     // device work list, in the order it is taken
+    const StepParams* params;  // device table, indexed by BatchItem::inst
+    const BatchItem* items;    // device work list, in the order it is taken
+    const EdgeTile* tiles;     // device edge tiles of the groups
     int32_t* queue;            // device {next item, CTAs done}: zero between launches
     int32_t fields;            // also write u, v, r to params.fields
     int32_t nitems;            // items in the list
