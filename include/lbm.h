@@ -221,6 +221,27 @@ LBM_API lbm_status lbm_get_info(const lbm_ctx* ctx, int64_t* steps, double* dt);
  * node update moves (populations plus carries, read once and written once). */
 LBM_API lbm_status lbm_memory_info(const lbm_ctx* ctx, int64_t* device_bytes, int64_t* bytes_per_node_update);
 
+/* Checkpoint and resume (no counterpart in the paper).  The state of a
+ * context after its last step, in the library's own layout: the
+ * populations, the displacement and source carries (whole planes, with the
+ * ghost and image rows and columns), the read-out fields and the step
+ * count, behind a header naming the format, size, scheme and time step.
+ * lbm_state_size: bytes of a saved state (0 for NULL).
+ * lbm_read_state: writes the state into the caller's host buffer `out`
+ * (out_len >= lbm_state_size); runs the initialisation first if no step has
+ * run; synchronises.  Errors as lbm_read_fields.
+ * lbm_write_state: replaces the context's state by a saved one (from a
+ * context created with the same size, storage, carry and scheme, and with
+ * the same material, hence time step); the boundaries and material must be
+ * set, and should be those the state was computed with.  The next lbm_step
+ * continues from the saved step exactly as the saved context would have
+ * (bit-identical fields).  The caller owns `in`; it is only read during the
+ * call, which synchronises.  Errors: LBM_E_INVALID (a header that does not
+ * match this context, in_len), LBM_E_STATE, LBM_E_CUDA. */
+LBM_API int64_t lbm_state_size(const lbm_ctx* ctx);
+LBM_API lbm_status lbm_read_state(lbm_ctx* ctx, void* out, int64_t out_len);
+LBM_API lbm_status lbm_write_state(lbm_ctx* ctx, const void* in, int64_t in_len);
+
 /* Frees the context and its device memory (NULL is allowed). */
 LBM_API lbm_status lbm_destroy(lbm_ctx* ctx);
 

@@ -738,6 +738,129 @@ lbm_status lbm_sync(lbm_ctx* c) {
     return ctx_check_flag(c);
 }
 
+// ---------------------------------------------------------------- checkpoint
+// A saved state: this header, then the population planes, the u-carry
+// planes and the source-carry planes of the current parity (whole planes:
+// their ghost rows and columns hold the populations the boundary rules sent
+// back and the periodic images), then the five read-out planes.
+namespace {
+
+struct StateHeader {
+    char magic[8];
+    int32_t fmt, nx, ny, scheme;
+    int64_t pitch, plane, steps;
+    double dt;
+    int64_t bytes;  // the whole state, header included
+};
+constexpr char kStateMagic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', '1'};
+
+struct StateParts {
+    size_t f, a, s, fields;
+};
+
+StateParts state_parts(const lbm_ctx* c) {
+    StateParts p;
+    p.f = size_t(9) * size_t(c->plane) * elem_size_storage(c->fmt);
+    p.a = size_t(2 * ucarry_planes(c->fmt)) * size_t(c->plane) * elem_size_ucarry(c->fmt);
+    p.s = size_t(2) * size_t(c->plane) * elem_size_compute(c->fmt);
+    p.fields = size_t(5) * size_t(c->nx) * size_t(c->ny) * sizeof(double);
+    return p;
+}
+
+StateHeader state_header(const lbm_ctx* c) {
+    StateHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, kStateMagic, sizeof(h.magic));
+    h.fmt = c->fmt;
+    h.nx = c->nx;
+    h.ny = c->ny;
+    h.scheme = c->scheme;
+    h.pitch = c->pitch;
+    h.plane = c->plane;
+    h.steps = c->steps;
+    h.dt = c->dt;
+    const StateParts p = state_parts(c);
+    h.bytes = int64_t(sizeof(StateHeader) + p.f + p.a + p.s + p.fields);
+    return h;
+}
+
+}  // namespace
+
+int64_t lbm_state_size(const lbm_ctx* c) {
+    if (!c) return 0;
+    return state_header(c).bytes;
+}
+
+lbm_status lbm_read_state(lbm_ctx* c, void* out, int64_t out_len) {
+    lbm_status st = ctx_ready(c);
+    if (st != LBM_OK) return st;
+    const StateHeader h = state_header(c);
+    if (!out || out_len < h.bytes) return LBM_E_INVALID;
+    DeviceGuard guard(c->device);
+    if (!guard.ok) return ctx_fail_cuda(c, cudaErrorInvalidDevice);
+    st = ctx_ensure_initialized(c);
+    if (st != LBM_OK) return st;
+    const StateParts p = state_parts(c);
+    unsigned char* o = static_cast<unsigned char*>(out);
+    memcpy(o, &h, sizeof(h));
+    size_t at = sizeof(h);
+    const int q = c->parity;
+    LBM_CUDA(c, cudaMemcpyAsync(o + at, c->f[q], p.f, cudaMemcpyDeviceToHost, c->stream));
+    at += p.f;
+    LBM_CUDA(c, cudaMemcpyAsync(o + at, c->a[q], p.a, cudaMemcpyDeviceToHost, c->stream));
+    at += p.a;
+    LBM_CUDA(c, cudaMemcpyAsync(o + at, c->s[q], p.s, cudaMemcpyDeviceToHost, c->stream));
+    at += p.s;
+    LBM_CUDA(c, cudaMemcpyAsync(o + at, c->fields, p.fields, cudaMemcpyDeviceToHost, c->stream));
+    return ctx_check_flag(c);  // synchronises: out is complete
+}
+
+lbm_status lbm_write_state(lbm_ctx* c, const void* in, int64_t in_len) {
+    lbm_status st = ctx_ready(c);
+    if (st != LBM_OK) return st;
+    if (!in || in_len < int64_t(sizeof(StateHeader))) return LBM_E_INVALID;
+    StateHeader h;
+    memcpy(&h, in, sizeof(h));
+    const StateHeader mine = state_header(c);
+    if (memcmp(h.magic, kStateMagic, sizeof(h.magic)) != 0 || h.fmt != mine.fmt || h.nx != mine.nx ||
+        h.ny != mine.ny || h.scheme != mine.scheme || h.pitch != mine.pitch || h.plane != mine.plane ||
+        h.dt != mine.dt || h.bytes != mine.bytes || in_len < h.bytes || h.steps < 0)
+        return LBM_E_INVALID;
+    DeviceGuard guard(c->device);
+    if (!guard.ok) return ctx_fail_cuda(c, cudaErrorInvalidDevice);
+    if (!c->planned) LBM_CUDA(c, build_plan(c));
+    // the work queued so far is done before its buffers are overwritten, and
+    // the copies are done before `in` may be released
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    const StateParts p = state_parts(c);
+    const unsigned char* src = static_cast<const unsigned char*>(in);
+    size_t at = sizeof(h);
+    const int q = c->parity;
+    LBM_CUDA(c, cudaMemcpyAsync(c->f[q], src + at, p.f, cudaMemcpyHostToDevice, c->stream));
+    at += p.f;
+    LBM_CUDA(c, cudaMemcpyAsync(c->a[q], src + at, p.a, cudaMemcpyHostToDevice, c->stream));
+    at += p.a;
+    LBM_CUDA(c, cudaMemcpyAsync(c->s[q], src + at, p.s, cudaMemcpyHostToDevice, c->stream));
+    at += p.s;
+    LBM_CUDA(c, cudaMemcpyAsync(c->fields, src + at, p.fields, cudaMemcpyHostToDevice, c->stream));
+    // the edge kernel evaluates the boundary data at the step counter of
+    // this parity
+    LBM_CUDA(c, cudaMemcpyAsync(c->counter + q, &h.steps, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    LBM_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->steps = h.steps;
+    if (!c->initialized) {  // the restored state replaces the initialisation
+        c->initialized = true;
+        const int64_t ubytes = int64_t(2) * c->nx * c->ny * int64_t(sizeof(double));
+        if (c->u0) c->device_bytes -= ubytes;
+        if (c->v0) c->device_bytes -= ubytes;
+        cudaFree(c->u0);
+        cudaFree(c->v0);
+        c->u0 = c->v0 = nullptr;
+    }
+    return LBM_OK;
+}
+
 lbm_status lbm_get_info(const lbm_ctx* c, int64_t* steps, double* dt) {
     if (!c) return LBM_E_INVALID;
     if (steps) *steps = c->steps;

@@ -82,6 +82,9 @@ _SIGNATURES = {
     "lbm_sync": (C.c_int, [C.c_void_p]),
     "lbm_get_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "lbm_memory_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "lbm_state_size": (C.c_int64, [C.c_void_p]),
+    "lbm_read_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "lbm_write_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "lbm_destroy": (C.c_int, [C.c_void_p]),
     "lbm_status_string": (C.c_char_p, [C.c_int]),
     "lbm_last_cuda_error": (C.c_char_p, [C.c_void_p]),
@@ -182,6 +185,24 @@ def lbm_read_fields(ctx, mask: int, out: np.ndarray, allow_unstable: bool = Fals
                                C.byref(t))
     _check(st, "lbm_read_fields", allow=(LBM_E_UNSTABLE,) if allow_unstable else ())
     return st, t.value
+
+
+def lbm_state_size(ctx) -> int:
+    return int(lib().lbm_state_size(ctx))
+
+
+def lbm_read_state(ctx, allow_unstable: bool = False) -> np.ndarray:
+    """The context's state (a uint8 host array in the library's layout)."""
+    out = np.empty(lbm_state_size(ctx), dtype=np.uint8)
+    st = lib().lbm_read_state(ctx, out.ctypes.data_as(C.c_void_p), out.size)
+    _check(st, "lbm_read_state", allow=(LBM_E_UNSTABLE,) if allow_unstable else ())
+    return out
+
+
+def lbm_write_state(ctx, state: np.ndarray) -> None:
+    """Replaces the context's state by one lbm_read_state returned."""
+    buf = np.ascontiguousarray(state, dtype=np.uint8)
+    _check(lib().lbm_write_state(ctx, buf.ctypes.data_as(C.c_void_p), buf.size), "lbm_write_state")
 
 
 def lbm_diagnostics(ctx, allow_unstable: bool = False) -> tuple:
@@ -377,6 +398,15 @@ class Body:
 
     def diagnostics(self, allow_unstable: bool = False):
         return lbm_diagnostics(self.ctx, allow_unstable)[1]
+
+    def save_state(self, allow_unstable: bool = False) -> np.ndarray:
+        """Checkpoint: the body's state after its last step (host bytes)."""
+        return lbm_read_state(self.ctx, allow_unstable)
+
+    def load_state(self, state: np.ndarray) -> None:
+        """Resume from a checkpoint of a body of the same size, format,
+        scheme and material."""
+        lbm_write_state(self.ctx, state)
 
     def info(self):
         return lbm_get_info(self.ctx)

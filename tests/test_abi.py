@@ -62,3 +62,11 @@ def test_null_context_calls_fail_cleanly():
     assert L.lbm_fields_size(None, 1) == 0
     assert L.lbm_destroy(None) == lbm.LBM_OK
     assert L.lbm_sync(None) == lbm.LBM_E_INVALID
+
+
+def test_checkpoint_calls_reject_null_arguments_without_touching_the_gpu():
+    L = lbm.lib()
+    assert L.lbm_state_size(None) == 0
+    buf = (C.c_uint8 * 64)()
+    assert L.lbm_read_state(None, buf, 64) == lbm.LBM_E_INVALID
+    assert L.lbm_write_state(None, buf, 64) == lbm.LBM_E_INVALID
