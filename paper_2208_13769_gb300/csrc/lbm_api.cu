@@ -33,6 +33,11 @@ int ucarry_planes(int fmt) { return (fmt == kFmtF64 || fmt == kFmtF32) ? 1 : 2; 
 
 }  // namespace
 
+bool lbm::fault_injected(const char* call) {
+    const char* v = getenv("LBM_FAULT");
+    return v != nullptr && strcmp(v, call) == 0;
+}
+
 lbm_status lbm::ctx_fail_cuda(lbm_ctx* ctx, cudaError_t e) {
     if (ctx) {
         ctx->sticky = true;
@@ -345,6 +350,7 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
     // sizes: 64-bit element counts, 32-bit node coordinates
     const int64_t nodes = int64_t(d->nx) * d->ny;
     if (d->nx > (1 << 30) || d->ny > (1 << 30) || nodes > (int64_t(1) << 40)) return LBM_E_INVALID;
+    if (fault_injected("alloc")) return LBM_E_OOM;  // before any CUDA call
 
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return LBM_E_OOM;
@@ -504,6 +510,7 @@ lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
     lbm_status st = ctx_ready(c);
     if (st != LBM_OK) return st;
     if (nsteps < 0) return LBM_E_INVALID;
+    if (fault_injected("step")) return ctx_fail_cuda(c, cudaErrorLaunchFailure);
     DeviceGuard guard(c->device);
     if (!guard.ok) return ctx_fail_cuda(c, cudaErrorInvalidDevice);
     st = ctx_ensure_initialized(c);

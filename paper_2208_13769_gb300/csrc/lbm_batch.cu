@@ -311,6 +311,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
     if (!b) return LBM_E_INVALID;
     if (b->sticky) return LBM_E_CUDA;
     if (nsteps < 0) return LBM_E_INVALID;
+    if (fault_injected("batch_step")) return batch_fail(b, cudaErrorLaunchFailure);
     const int n = int(b->m.size());
     for (int i = 0; i < n; ++i) {
         lbm_ctx* c = b->m[size_t(i)];

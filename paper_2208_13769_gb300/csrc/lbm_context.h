@@ -88,6 +88,12 @@ struct lbm_ctx {
 
 namespace lbm {
 
+// Host-side fault injection for tests of failure handling (nothing faults on
+// the GPU): true when the environment variable LBM_FAULT names `call`
+// ("alloc": lbm_create fails as if device memory were exhausted, before any
+// CUDA call; "step": lbm_step fails as if a launch had failed, leaving the
+// context unusable; "batch_step": the same for lbm_batch_step).
+bool fault_injected(const char* call);
 // Marks the context unusable after a CUDA error; returns LBM_E_CUDA.
 lbm_status ctx_fail_cuda(lbm_ctx* c, cudaError_t e);
 // Parameters of one step from parity `parity` (source buffers of that parity).

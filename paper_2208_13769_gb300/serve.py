@@ -7,7 +7,9 @@ chunks that end exactly when the next admitted request completes (so each
 request gets exactly its step count), reads each finished request's
 displacement back to the host, frees it, and admits the next ones.  The
 batch is rebuilt whenever its membership changes.  Latency of a request =
-completion (its result on the host) minus arrival.
+completion (its result on the host) minus arrival.  A request that fails
+(its body cannot be created, its batch's step fails, or its result cannot
+be read) completes with the error's status while the others go on.
 
 The GPU work goes through lbm.Body / lbm.Batch only; the scheduling logic
 talks to a small backend interface, so it also runs on the host with a
@@ -21,6 +23,8 @@ import time
 from typing import Callable, Dict, List, Optional
 
 import numpy as np
+
+from .lbm import LBM_E_UNSTABLE
 
 
 @dataclasses.dataclass
@@ -136,8 +140,12 @@ class Server:
                 if used + need > self.budget:
                     break
                 waiting.popleft()
-                body = self.be.create(requests[i].problem)
-                mem = float(self.be.memory(body))
+                try:
+                    body = self.be.create(requests[i].problem)
+                    mem = float(self.be.memory(body))
+                except Exception as e:  # this request fails alone
+                    records.append(self._failed(requests, i, t0, e))
+                    continue
                 used += mem
                 peak_used = max(peak_used, used)
                 active.append({"i": i, "body": body, "left": int(requests[i].steps), "mem": mem,
@@ -159,8 +167,19 @@ class Server:
                 n = min(n, max(16, int(self.target_chunk_s / sec_per_step)))
             n = max(1, min(n, self.max_chunk))
             ts = self.clock()
-            self.be.step(batch, n)
-            statuses = self.be.sync(batch)
+            try:
+                self.be.step(batch, n)
+                statuses = self.be.sync(batch)
+            except Exception as e:
+                # the batch is unusable: its members fail with its status,
+                # the server goes on with the next requests
+                for a in active:
+                    records.append(self._failed(requests, a["i"], t0, e, a["admitted"]))
+                    self._quiet(self.be.close, a["body"])
+                    used -= a["mem"]
+                self._quiet(self.be.close_batch, batch)
+                batch, active, dirty = None, [], False
+                continue
             dt = self.clock() - ts
             busy += dt
             chunks += 1
@@ -171,14 +190,17 @@ class Server:
                 if a["left"] > 0:
                     still.append(a)
                     continue
-                u = self.be.result(a["body"])  # the response reaches the host
+                try:
+                    u = self.be.result(a["body"])  # the response reaches the host
+                except Exception as e:
+                    u, st = None, self._status(e)
                 done_t = self.clock() - t0
                 r = requests[a["i"]]
                 records.append(Record(a["i"], r.arrival, a["admitted"], done_t, r.problem.nx * r.problem.ny,
                                       int(r.steps), int(st)))
-                if self.keep_results:
+                if self.keep_results and u is not None:
                     self.results[a["i"]] = u
-                self.be.close(a["body"])
+                self._quiet(self.be.close, a["body"])
                 used -= a["mem"]
                 dirty = True
             active = still
@@ -187,15 +209,33 @@ class Server:
         makespan = self.clock() - t0
         return self._stats(requests, records, rejected, makespan, busy, peak_used, chunks, rebuilds, max_active)
 
+    @staticmethod
+    def _status(e) -> int:
+        return int(getattr(e, "status", -1))
+
+    @staticmethod
+    def _quiet(fn, *args) -> None:
+        try:
+            fn(*args)
+        except Exception:
+            pass
+
+    def _failed(self, requests, i, t0, e, admitted=None) -> Record:
+        now = self.clock() - t0
+        r = requests[i]
+        return Record(i, r.arrival, now if admitted is None else admitted, now, r.problem.nx * r.problem.ny,
+                      int(r.steps), self._status(e))
+
     def _stats(self, requests, records, rejected, makespan, busy, peak_used, chunks, rebuilds, max_active):
         lat = np.array([r.latency for r in records]) if records else np.zeros(0)
-        work = sum(r.nodes * r.steps for r in records)
+        work = sum(r.nodes * r.steps for r in records if r.status in (0, LBM_E_UNSTABLE))
         arrivals = [q.arrival for q in requests]
         window = (max(arrivals) - min(arrivals)) if len(arrivals) > 1 else 0.0
         offered = sum(q.problem.nx * q.problem.ny * q.steps for q in requests)
         return {
             "requests": len(requests), "completed": len(records), "rejected": len(rejected),
-            "unstable": int(sum(1 for r in records if r.status != 0)),
+            "unstable": int(sum(1 for r in records if r.status == LBM_E_UNSTABLE)),
+            "failed": int(sum(1 for r in records if r.status not in (0, LBM_E_UNSTABLE))),
             "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
             "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
             "mean_s": float(lat.mean()) if len(lat) else None,

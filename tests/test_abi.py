@@ -70,3 +70,14 @@ def test_checkpoint_calls_reject_null_arguments_without_touching_the_gpu():
     buf = (C.c_uint8 * 64)()
     assert L.lbm_read_state(None, buf, 64) == lbm.LBM_E_INVALID
     assert L.lbm_write_state(None, buf, 64) == lbm.LBM_E_INVALID
+
+
+def test_injected_allocation_failure_is_reported_before_any_cuda_call(monkeypatch):
+    """LBM_FAULT=alloc makes lbm_create fail as if device memory were
+    exhausted; it needs no GPU and leaves no context behind."""
+    monkeypatch.setenv("LBM_FAULT", "alloc")
+    L = lbm.lib()
+    d = lbm.lbm_desc()
+    d.nx, d.ny, d.dX = 16, 16, 1.0
+    h = C.c_void_p()
+    assert L.lbm_create(C.byref(d), C.byref(h)) == lbm.LBM_E_OOM and not h.value

@@ -142,3 +142,64 @@ def test_trace_at_rate_keeps_requests_and_sets_poisson_arrivals():
     assert [q.steps for q in out] == [q.steps for q in reqs]
     gaps = np.diff([0.0] + [q.arrival for q in out])
     assert (gaps > 0).all() and abs(gaps.mean() - 1 / 50.0) < 0.3 / 50.0
+
+
+class _Failure(RuntimeError):
+    def __init__(self, status):
+        super().__init__(f"injected failure {status}")
+        self.status = status
+
+
+class FailingBackend(FakeBackend):
+    """FakeBackend whose k-th create, k-th batch step and k-th result read
+    raise (host-side fault injection: nothing runs on a GPU)."""
+
+    def __init__(self, clock, fail_create=3, fail_step=6, fail_result=2, **kw):
+        super().__init__(clock, **kw)
+        self.fail = {"create": fail_create, "step": fail_step, "result": fail_result}
+        self.calls = {"create": 0, "step": 0, "result": 0}
+        self.failed_ids = set()
+        self.creates_tried = 0
+
+    def _maybe(self, what, status):
+        self.calls[what] += 1
+        if self.calls[what] == self.fail[what]:
+            raise _Failure(status)
+
+    def create(self, prob):
+        self._maybe("create", 2)  # as lbm_create's LBM_E_OOM
+        return super().create(prob)
+
+    def step(self, batch, n):
+        try:
+            self._maybe("step", 3)  # as a failed launch: LBM_E_CUDA
+        except _Failure:
+            self.failed_ids.update(h["id"] for h in batch)
+            raise
+        super().step(batch, n)
+
+    def result(self, h):
+        self._maybe("result", 3)
+        return super().result(h)
+
+
+def test_failed_requests_complete_with_their_status_and_the_others_go_on():
+    clock = FakeClock()
+    be = FailingBackend(clock)
+    reqs = _trace(40, seed=9)
+    st = serve.Server(be, hbm_budget=1e12, clock=clock, sleep=clock.sleep).run(reqs)
+    assert st["completed"] == len(reqs) and st["rejected"] == 0  # every request got an answer
+    recs = {r.index: r for r in st["records"]}
+    order = sorted(range(len(reqs)), key=lambda i: reqs[i].arrival)
+    failed_create = order[be.fail["create"] - 1]
+    assert recs[failed_create].status == 2
+    bad = [i for i, r in recs.items() if r.status != 0]
+    n_step = len(be.failed_ids)
+    assert n_step >= 1  # the failed batch step took its members with it
+    assert len(bad) == 1 + n_step + 1 and st["failed"] == len(bad)
+    # the requests that did not fail got exactly their steps
+    created = [i for i in order if i != failed_create]
+    for k, i in zip(be.admit_order, created):
+        if recs[i].status == 0:
+            assert be.steps_of[k] == reqs[i].steps
+    assert st["p50_s"] is not None
