@@ -339,6 +339,7 @@ static bool finite_pair(const double* v) { return v == nullptr || (isfinite(v[0]
 extern "C" {
 
 lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
+    NvtxRange range_("lbm_create");
     if (!out) return LBM_E_INVALID;
     *out = nullptr;
     if (!d) return LBM_E_INVALID;
@@ -507,6 +508,7 @@ lbm_status lbm_set_boundary(lbm_ctx* c, int32_t edge, int32_t kind, const double
 }
 
 lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
+    NvtxRange range_("lbm_step");
     lbm_status st = ctx_ready(c);
     if (st != LBM_OK) return st;
     if (nsteps < 0) return LBM_E_INVALID;
@@ -619,6 +621,7 @@ lbm_status lbm_get_tuning(const lbm_ctx* c, lbm_tuning* t) {
 
 lbm_status lbm_autotune(const lbm_desc* d, const int32_t edge_kind[4], int64_t steps, lbm_tuning* best,
                         double* best_ms) {
+    NvtxRange range_("lbm_autotune");
     if (!d || !edge_kind || !best || steps < 1 || steps > 100000) return LBM_E_INVALID;
     for (int e = 0; e < 4; ++e)
         if (edge_kind[e] < LBM_PERIODIC || edge_kind[e] > LBM_NEUMANN) return LBM_E_INVALID;
@@ -692,6 +695,7 @@ int64_t lbm_fields_size(const lbm_ctx* c, uint32_t mask) {
 }
 
 lbm_status lbm_read_fields(lbm_ctx* c, uint32_t mask, double* out, int64_t out_len, double* t_out) {
+    NvtxRange range_("lbm_read_fields");
     lbm_status st = ctx_ready(c);
     if (st != LBM_OK) return st;
     const int64_t need = lbm_fields_size(c, mask);
@@ -721,6 +725,7 @@ lbm_status lbm_read_fields(lbm_ctx* c, uint32_t mask, double* out, int64_t out_l
 }
 
 lbm_status lbm_diagnostics(lbm_ctx* c, double out[6]) {
+    NvtxRange range_("lbm_diagnostics");
     lbm_status st = ctx_ready(c);
     if (st != LBM_OK) return st;
     if (!out) return LBM_E_INVALID;
@@ -799,6 +804,7 @@ int64_t lbm_state_size(const lbm_ctx* c) {
 }
 
 lbm_status lbm_read_state(lbm_ctx* c, void* out, int64_t out_len) {
+    NvtxRange range_("lbm_read_state");
     lbm_status st = ctx_ready(c);
     if (st != LBM_OK) return st;
     const StateHeader h = state_header(c);
@@ -823,6 +829,7 @@ lbm_status lbm_read_state(lbm_ctx* c, void* out, int64_t out_len) {
 }
 
 lbm_status lbm_write_state(lbm_ctx* c, const void* in, int64_t in_len) {
+    NvtxRange range_("lbm_write_state");
     lbm_status st = ctx_ready(c);
     if (st != LBM_OK) return st;
     if (!in || in_len < int64_t(sizeof(StateHeader))) return LBM_E_INVALID;

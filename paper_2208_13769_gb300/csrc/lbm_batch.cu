@@ -141,6 +141,7 @@ cudaError_t stream_after(cudaStream_t waiter, cudaStream_t s, cudaEvent_t ev) {
 extern "C" {
 
 lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_stream, lbm_batch** out) {
+    NvtxRange range_("lbm_batch_create");
     if (!out) return LBM_E_INVALID;
     *out = nullptr;
     if (!members || n < 1) return LBM_E_INVALID;
@@ -308,6 +309,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
 }
 
 lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
+    NvtxRange range_("lbm_batch_step");
     if (!b) return LBM_E_INVALID;
     if (b->sticky) return LBM_E_CUDA;
     if (nsteps < 0) return LBM_E_INVALID;

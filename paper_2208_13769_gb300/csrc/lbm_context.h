@@ -4,12 +4,23 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "lbm.h"
 #include "lbm_kernels.h"
 
 namespace lbm {
+
+// An NVTX range named after the entry point, for the scope: profilers
+// (nsys, ncu --nvtx-include) attribute the launches to the call; without a
+// profiler attached it costs a check of a function pointer.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Makes `dev` current for the scope, restoring the previous device after.
 struct DeviceGuard {
