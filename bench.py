@@ -362,8 +362,11 @@ def run_native(a):
     clk = clocks.stop()
     barrier()
     secs = max_over_ranks(secs)
-    # per-launch durations (CUDA events on the library's stream around each
-    # of a step's two launches) for the roofline of the dominant kernel
+    # the dominant kernel's duration: 200 interior launches back to back
+    # between CUDA events on the library's stream (the state is saved and
+    # restored around them); and each of a step's two launches timed by
+    # events around it (the shares of the step)
+    _, iprof = lbm.lbm_profile_interior(body.ctx, 200, allow_unstable=True)
     _, prof = lbm.lbm_profile_steps(body.ctx, min(a.steps, 300), allow_unstable=True)
     status = body.read(lbm.LBM_FIELD_U, allow_unstable=True)["status"]
     body.close()
@@ -371,7 +374,8 @@ def run_native(a):
     ms_per_step = 1e3 * secs / a.steps
     value = weak_scaling_value(world, nodes, a.steps, secs)
     peak, peak_kind = measured_peak()
-    interior_ms, band_ms, serial_ms, interior_nodes = (float(x) for x in prof)
+    interior_step_ms, band_ms, serial_ms, interior_nodes = (float(x) for x in prof)
+    interior_ms = float(iprof[0])
     achieved = bytes_per_node * interior_nodes / (interior_ms * 1e-3) / 1e9
     step_gbs = bytes_per_node * nodes / (secs / a.steps) / 1e9
     traffic = ncu_traffic(a.storage, a.compensated, interior_nodes)
@@ -379,6 +383,8 @@ def run_native(a):
             "traffic": traffic, "peak_kind": peak_kind, "kernel": "interior_step_kernel",
             "algorithmic_bytes_per_node": bytes_per_node, "units_per_launch": interior_nodes,
             "launch_ms": interior_ms,
+            "launch_timing": "200 launches back to back between CUDA events on the library's stream",
+            "launch_ms_in_step": interior_step_ms,
             "step": {"achieved": step_gbs, "frac": step_gbs / peak,
                      "note": "whole time step (interior + edge-band launch) at the same bytes per node"},
             "edge_band_kernel": {"launch_ms": band_ms, "nodes": nodes - interior_nodes}}
@@ -449,7 +455,14 @@ def run_native(a):
         bnodes = sum(p.nx * p.ny for p in spec.problems)
         bodies = [lbm.Body(p, storage=a.storage, compensated=a.compensated, stream=stream.cuda_stream,
                            device=local) for p in spec.problems]
-        bt = lbm.Batch(bodies, stream=stream.cuda_stream)
+        # the batch autotuner picks ring depth and rows per interior tile on
+        # scratch copies of the members
+        btune, bt_ms, bt_s = None, None, None
+        if a.tune:
+            t0 = time.perf_counter()
+            btune, bt_ms = lbm.lbm_batch_autotune([b.ctx for b in bodies], 128)
+            bt_s = time.perf_counter() - t0
+        bt = lbm.Batch(bodies, stream=stream.cuda_stream, tuning=btune)
         bt.step(a.warmup)
         bsec = time_steps(bt, stream, a.batch_steps)
         info = bt.info()
@@ -474,6 +487,8 @@ def run_native(a):
             "ms_per_step": 1e3 * bsec / a.batch_steps, "achieved_gbs": bach, "frac": bach / peak,
             "one_by_one_mlups": bnodes * osteps / osec / 1e6, "one_by_one_steps": osteps,
             "interior_ctas": info["interior_ctas"], "edge_ctas": info["edge_ctas"],
+            "tuning": (dict(btune.as_dict(), candidate_ms_per_step=bt_ms, seconds=bt_s) if btune is not None
+                       else "library defaults"),
             "unstable_members": int(sum(1 for x in statuses if x != lbm.LBM_OK)),
             "note": "members outside the method's stable range (nu > 0.25 with traction-free edges, "
                     "nu > 0.40 periodic) report LBM_E_UNSTABLE; their cost is the same"}

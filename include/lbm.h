@@ -147,6 +147,20 @@ LBM_API lbm_status lbm_step(lbm_ctx* ctx, int64_t nsteps);
  * LBM_E_OOM, LBM_E_CUDA, and LBM_E_UNSTABLE / LBM_E_TIMEOUT as lbm_sync. */
 LBM_API lbm_status lbm_profile_steps(lbm_ctx* ctx, int64_t nsteps, double out[4]);
 
+/* Measurement aid (no counterpart in the paper): the interior kernel alone,
+ * `nlaunches` launches back to back on the context's stream between two CUDA
+ * events, after one untimed launch; out[0] is the mean duration of a launch
+ * in milliseconds, out[1] the number of nodes one launch advances.  The edge
+ * bands are not advanced meanwhile, so these launches compute no solution:
+ * the state the next step reads (and the device's instability flag) is
+ * saved on the device before them and restored after, and the context
+ * continues exactly as if the call had not been made.  Allocates a device
+ * copy of that state (the population and carry planes of one parity) for
+ * the call.  Synchronises.  Errors: LBM_E_INVALID (nlaunches outside
+ * 1..4096, out NULL, a body too small to have an interior), LBM_E_STATE,
+ * LBM_E_OOM, LBM_E_CUDA. */
+LBM_API lbm_status lbm_profile_interior(lbm_ctx* ctx, int64_t nlaunches, double out[2]);
+
 /* Decomposition of the interior launch (no counterpart in the paper; it
  * changes how the work is split, never the result: every setting gives
  * bit-identical fields). */
@@ -270,6 +284,30 @@ typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
  * member, mixed devices or formats), LBM_E_STATE (a member not ready),
  * LBM_E_OOM, LBM_E_CUDA. */
 LBM_API lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_stream, lbm_batch** out);
+
+/* lbm_batch_create with a decomposition of the batch's interior tiles (no
+ * counterpart in the paper; it changes the split of the work, never the
+ * results): tuning->ring_slots, rows of the bulk-copy ring (4..8; 0: 5),
+ * and tuning->chunk_rows, rows per interior tile (>= 8; 0: about eight
+ * waves of resident CTAs over the batch, 32..256 rows); aligned is ignored
+ * (a batch's strips always lie on 32-byte sectors).  NULL: the defaults.
+ * Errors as lbm_batch_create, and LBM_E_INVALID for a tuning out of range. */
+LBM_API lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda_stream,
+                                          const lbm_tuning* tuning, lbm_batch** out);
+
+/* Batch autotuner (no counterpart in the paper): builds scratch contexts
+ * with the sizes, storage, carry, scheme, device and edge kinds of
+ * `members` (zero initial fields, lambda = mu = 0.3), times `steps`
+ * graph-replayed steps of a scratch batch of them for each candidate
+ * decomposition (ring 4, 5, 6 x rows per tile default, 32, 64, 128, 256) on
+ * a stream of its own, and returns the fastest in *best (its time per step
+ * in *best_ms, may be NULL).  The time of a step does not depend on the
+ * field values, so the choice holds for the members.  The members are not
+ * touched.  Holds as much device memory as the members, for the call.
+ * Synchronises.  Errors: LBM_E_INVALID (n < 1, NULL member, steps outside
+ * 1..100000, best NULL), and those of lbm_create / lbm_batch_create. */
+LBM_API lbm_status lbm_batch_autotune(lbm_ctx* const* members, int32_t n, int64_t steps, lbm_tuning* best,
+                                      double* best_ms);
 
 /* Advances every member by nsteps time steps (its step count and time too);
  * the last step also refreshes each member's read-out fields, so

@@ -591,6 +591,59 @@ lbm_status lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double out[4]) {
     return ctx_check_flag(c);
 }
 
+lbm_status lbm_profile_interior(lbm_ctx* c, int64_t nlaunches, double out[2]) {
+    lbm_status st = ctx_ready(c);
+    if (st != LBM_OK) return st;
+    if (nlaunches < 1 || nlaunches > 4096 || !out) return LBM_E_INVALID;
+    DeviceGuard guard(c->device);
+    if (!guard.ok) return ctx_fail_cuda(c, cudaErrorInvalidDevice);
+    st = ctx_ensure_initialized(c);
+    if (st != LBM_OK) return st;
+    if (!c->planned) LBM_CUDA(c, build_plan(c));
+    if (!c->has_interior) return LBM_E_INVALID;
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    // the state the next step reads, and the device flag, saved on the device
+    const int q = c->parity;
+    const size_t fb = size_t(9) * size_t(c->plane) * elem_size_storage(c->fmt);
+    const size_t ab = size_t(2 * ucarry_planes(c->fmt)) * size_t(c->plane) * elem_size_ucarry(c->fmt);
+    const size_t sb = size_t(2) * size_t(c->plane) * elem_size_compute(c->fmt);
+    unsigned char* save = nullptr;
+    cudaError_t err = cudaMalloc(&save, fb + ab + sb + sizeof(int32_t));
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return err == cudaErrorMemoryAllocation ? LBM_E_OOM : ctx_fail_cuda(c, err);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    err = cudaMemcpyAsync(save, c->f[q], fb, cudaMemcpyDeviceToDevice, c->stream);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(save + fb, c->a[q], ab, cudaMemcpyDeviceToDevice, c->stream);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(save + fb + ab, c->s[q], sb, cudaMemcpyDeviceToDevice, c->stream);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(save + fb + ab + sb, c->flag, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
+    if (err == cudaSuccess) err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    if (err == cudaSuccess) err = launch_interior_part(c, make_params(c, q), false);  // warm
+    if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+    for (int64_t k = 0; k < nlaunches && err == cudaSuccess; ++k)
+        err = launch_interior_part(c, make_params(c, q ^ int((k + 1) & 1)), false);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+    // restore: the context continues from the saved state
+    if (err == cudaSuccess) err = cudaMemcpyAsync(c->f[q], save, fb, cudaMemcpyDeviceToDevice, c->stream);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(c->a[q], save + fb, ab, cudaMemcpyDeviceToDevice, c->stream);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(c->s[q], save + fb + ab, sb, cudaMemcpyDeviceToDevice, c->stream);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(c->flag, save + fb + ab + sb, sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+    float ms = 0;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(save);
+    if (err != cudaSuccess) return ctx_fail_cuda(c, err);
+    out[0] = double(ms) / double(nlaunches);
+    out[1] = double(c->irect[1] - c->irect[0]) * double(c->irect[3] - c->irect[2]);
+    return ctx_check_flag(c);
+}
+
 lbm_status lbm_set_tuning(lbm_ctx* c, const lbm_tuning* t) {
     if (!c || !t) return LBM_E_INVALID;
     if (c->sticky) return LBM_E_CUDA;

@@ -50,6 +50,7 @@ struct lbm_batch {
     int n_items = 0;              // items of the work list
     int grid = 0;                // persistent CTAs
     int chunk_rows = 0;
+    int ring = kBatchRing;
     int64_t steps = 0;
     bool warm = false;
     bool sticky = false;
@@ -93,7 +94,7 @@ cudaError_t batch_launch(lbm_batch* b, int q, bool fields) {
     L.queue = b->dqueue;
     L.fields = fields ? 1 : 0;
     L.nitems = b->n_items;
-    return launch_batch_step(b->fmt, L, b->grid, kBatchRing, b->stream, nullptr);
+    return launch_batch_step(b->fmt, L, b->grid, b->ring, b->stream, nullptr);
 }
 
 void advance_members(lbm_batch* b, int64_t k) {
@@ -141,10 +142,18 @@ cudaError_t stream_after(cudaStream_t waiter, cudaStream_t s, cudaEvent_t ev) {
 extern "C" {
 
 lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_stream, lbm_batch** out) {
+    return lbm_batch_create_tuned(members, n, cuda_stream, nullptr, out);
+}
+
+lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda_stream, const lbm_tuning* tuning,
+                                  lbm_batch** out) {
     NvtxRange range_("lbm_batch_create");
     if (!out) return LBM_E_INVALID;
     *out = nullptr;
     if (!members || n < 1) return LBM_E_INVALID;
+    if (tuning && ((tuning->ring_slots != 0 && (tuning->ring_slots < 4 || tuning->ring_slots > 8)) ||
+                   (tuning->chunk_rows != 0 && (tuning->chunk_rows < 8 || tuning->chunk_rows > (1 << 20)))))
+        return LBM_E_INVALID;
     for (int i = 0; i < n; ++i) {
         if (!members[i]) return LBM_E_INVALID;
         for (int j = 0; j < i; ++j)
@@ -193,8 +202,11 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
     for (lbm_ctx* c : b->m)
         if (c->has_interior)
             interior_nodes += int64_t(c->irect[1] - c->irect[0]) * (c->irect[3] - c->irect[2]);
-    const int64_t wave = int64_t(b->m[0]->num_sms) * std::max(1, interior_occupancy(b->fmt, kBatchRing));
-    b->chunk_rows = int(std::min<int64_t>(256, std::max<int64_t>(32, interior_nodes / (int64_t(120) * wave * 8))));
+    b->ring = tuning && tuning->ring_slots ? tuning->ring_slots : kBatchRing;
+    const int64_t wave = int64_t(b->m[0]->num_sms) * std::max(1, interior_occupancy(b->fmt, b->ring));
+    b->chunk_rows = tuning && tuning->chunk_rows
+                        ? tuning->chunk_rows
+                        : int(std::min<int64_t>(256, std::max<int64_t>(32, interior_nodes / (int64_t(120) * wave * 8))));
     std::vector<StepParams> tab;
     std::vector<InteriorWork> work;
     std::vector<EdgeTile> tiles;
@@ -217,7 +229,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
                 StepParams p = make_params(c, b->base_parity[size_t(i)] ^ q);
                 for (int k = 0; k < 4; ++k) p.rect[k] = c->irect[k];
                 p.chunk_rows = b->chunk_rows;
-                p.ring_slots = kBatchRing;
+                p.ring_slots = b->ring;
                 p.strip_x0 = sx0[size_t(i)];
                 p.strip_w = sw[size_t(i)];
                 tab[size_t(q) * n + i] = p;
@@ -295,7 +307,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_strea
         BatchLaunch L;
         memset(&L, 0, sizeof(L));
         int resident = 0;
-        e = launch_batch_step(b->fmt, L, 0, kBatchRing, b->stream, &resident);
+        e = launch_batch_step(b->fmt, L, 0, b->ring, b->stream, &resident);
         b->grid = int(std::min<int64_t>(int64_t(items.size()), int64_t(b->m[0]->num_sms) * std::max(1, resident)));
     }
     if (e != cudaSuccess) {
@@ -384,6 +396,93 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
         batch_free(b);
     }
     delete b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_ctx* const* members, int32_t n, int64_t steps, lbm_tuning* best,
+                              double* best_ms) {
+    NvtxRange range_("lbm_batch_autotune");
+    if (!members || n < 1 || !best || steps < 1 || steps > 100000) return LBM_E_INVALID;
+    for (int i = 0; i < n; ++i)
+        if (!members[i]) return LBM_E_INVALID;
+    DeviceGuard guard(members[0]->device);
+    if (!guard.ok) return LBM_E_INVALID;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_E_CUDA;
+    }
+    // scratch members: the same shapes and formats, zero fields
+    std::vector<lbm_ctx*> scratch;
+    lbm_status status = LBM_OK;
+    try {
+        scratch.assign(size_t(n), nullptr);
+    } catch (...) {
+        cudaStreamDestroy(st);
+        return LBM_E_OOM;
+    }
+    for (int i = 0; i < n && status == LBM_OK; ++i) {
+        const lbm_ctx* c = members[i];
+        lbm_desc d;
+        memset(&d, 0, sizeof(d));
+        d.nx = c->nx;
+        d.ny = c->ny;
+        d.dX = c->dX;
+        d.storage = c->fmt == kFmtF64 ? LBM_F64 : (c->fmt == kFmtF16 ? LBM_F16 : (c->fmt == kFmtBF16 ? LBM_BF16 : LBM_F32));
+        d.u_carry = c->fmt == kFmtF32 ? LBM_UCARRY_NATIVE : LBM_UCARRY_COMPENSATED;
+        d.scheme = c->scheme;
+        d.f16_scale_log2 = c->f16_scale_log2;
+        d.cuda_stream = st;
+        d.device = c->device;
+        status = lbm_create(&d, &scratch[size_t(i)]);
+        if (status == LBM_OK) status = lbm_set_material(scratch[size_t(i)], 0.3, 0.3, 1.0, 1.0, nullptr);
+        for (int e = 0; e < 4 && status == LBM_OK; ++e)
+            status = lbm_set_boundary(scratch[size_t(i)], e, c->bc[e].kind, nullptr, nullptr, nullptr);
+    }
+    // candidates: ring depth x rows per interior tile (0: the default)
+    const int rings[3] = {4, 5, 6};
+    const int chunks[5] = {0, 32, 64, 128, 256};
+    double best_t = INFINITY;
+    lbm_tuning bt = {0, 0, 1};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (status == LBM_OK &&
+        (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+        cudaGetLastError();
+        status = LBM_E_CUDA;
+    }
+    for (int ri = 0; ri < 3 && status == LBM_OK; ++ri)
+        for (int ci = 0; ci < 5 && status == LBM_OK; ++ci) {
+            const lbm_tuning t = {rings[ri], chunks[ci], 1};
+            lbm_batch* b = nullptr;
+            status = lbm_batch_create_tuned(scratch.data(), n, st, &t, &b);
+            // warm: a plain step and the graphs of both parities
+            if (status == LBM_OK) status = lbm_batch_step(b, 2 * kBatchGraphChunk + 2);
+            if (status == LBM_OK) status = lbm_batch_sync(b, nullptr);
+            double ms = INFINITY;
+            if (status == LBM_OK) {
+                cudaError_t err = cudaEventRecord(e0, st);
+                if (err == cudaSuccess) status = lbm_batch_step(b, steps);
+                if (err == cudaSuccess && status == LBM_OK) err = cudaEventRecord(e1, st);
+                if (err == cudaSuccess && status == LBM_OK) err = cudaEventSynchronize(e1);
+                float f = 0;
+                if (err == cudaSuccess && status == LBM_OK && cudaEventElapsedTime(&f, e0, e1) == cudaSuccess)
+                    ms = double(f) / double(steps);
+                if (err != cudaSuccess) status = LBM_E_CUDA;
+            }
+            if (b) lbm_batch_destroy(b);
+            if (status == LBM_OK && ms < best_t) {
+                best_t = ms;
+                bt = t;
+            }
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (lbm_ctx* c : scratch) lbm_destroy(c);
+    cudaStreamDestroy(st);
+    if (status != LBM_OK) return status;
+    if (!(best_t < INFINITY)) return LBM_E_CUDA;
+    *best = bt;
+    if (best_ms) *best_ms = best_t;
     return LBM_OK;
 }
 

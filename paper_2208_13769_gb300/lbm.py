@@ -75,6 +75,7 @@ _SIGNATURES = {
                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "lbm_profile_steps": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
+    "lbm_profile_interior": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
     "lbm_fields_size": (C.c_int64, [C.c_void_p, C.c_uint32]),
     "lbm_read_fields": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_double), C.c_int64,
                                   C.POINTER(C.c_double)]),
@@ -90,6 +91,10 @@ _SIGNATURES = {
     "lbm_last_cuda_error": (C.c_char_p, [C.c_void_p]),
     "lbm_diagnostics_noalloc": (C.c_int, [C.POINTER(lbm_field_geometry), C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "lbm_batch_create_tuned": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, C.POINTER(lbm_tuning),
+                                         C.POINTER(C.c_void_p)]),
+    "lbm_batch_autotune": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int64, C.POINTER(lbm_tuning),
+                                     C.POINTER(C.c_double)]),
     "lbm_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "lbm_batch_sync": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "lbm_batch_get_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
@@ -173,6 +178,15 @@ def lbm_profile_steps(ctx, nsteps: int, allow_unstable: bool = False) -> tuple:
     return st, out
 
 
+def lbm_profile_interior(ctx, nlaunches: int, allow_unstable: bool = False) -> tuple:
+    """Times nlaunches back-to-back interior launches (the state is saved
+    and restored around them); returns (status, [ms per launch, nodes])."""
+    out = np.zeros(2)
+    st = lib().lbm_profile_interior(ctx, int(nlaunches), out.ctypes.data_as(C.POINTER(C.c_double)))
+    _check(st, "lbm_profile_interior", allow=(LBM_E_UNSTABLE,) if allow_unstable else ())
+    return st, out
+
+
 def lbm_fields_size(ctx, mask: int) -> int:
     return int(lib().lbm_fields_size(ctx, int(mask)))
 
@@ -239,11 +253,28 @@ def lbm_diagnostics_noalloc(geo: lbm_field_geometry, fields_dev: int, out_dev: i
                                              C.c_void_p(stream or None)))
 
 
-def lbm_batch_create(ctxs, stream: int = 0) -> C.c_void_p:
-    arr = (C.c_void_p * len(ctxs))(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+def _ctx_array(ctxs):
+    return (C.c_void_p * len(ctxs))(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+
+
+def lbm_batch_create(ctxs, stream: int = 0, tuning: Optional["lbm_tuning"] = None) -> C.c_void_p:
+    arr = _ctx_array(ctxs)
     h = C.c_void_p()
-    _check(lib().lbm_batch_create(arr, len(ctxs), C.c_void_p(stream or None), C.byref(h)), "lbm_batch_create")
+    if tuning is None:
+        st = lib().lbm_batch_create(arr, len(ctxs), C.c_void_p(stream or None), C.byref(h))
+    else:
+        st = lib().lbm_batch_create_tuned(arr, len(ctxs), C.c_void_p(stream or None), C.byref(tuning), C.byref(h))
+    _check(st, "lbm_batch_create")
     return h
+
+
+def lbm_batch_autotune(ctxs, steps: int = 128) -> tuple:
+    """(best lbm_tuning, its ms per step) for a batch of contexts shaped like
+    ctxs, timed on scratch copies (ctxs are not touched)."""
+    t, ms = lbm_tuning(), C.c_double()
+    _check(lib().lbm_batch_autotune(_ctx_array(ctxs), len(ctxs), int(steps), C.byref(t), C.byref(ms)),
+           "lbm_batch_autotune")
+    return t, ms.value
 
 
 def lbm_batch_step(batch, nsteps: int):
@@ -433,9 +464,9 @@ class Batch:
     """Several Body objects (one storage format) advanced by shared launches;
     each member's results are bit-identical to stepping it alone."""
 
-    def __init__(self, bodies, stream: int = 0):
+    def __init__(self, bodies, stream: int = 0, tuning: Optional["lbm_tuning"] = None):
         self.bodies = list(bodies)
-        self.handle = lbm_batch_create([b.ctx for b in self.bodies], stream)
+        self.handle = lbm_batch_create([b.ctx for b in self.bodies], stream, tuning)
 
     def step(self, n: int) -> None:
         lbm_batch_step(self.handle, n)

@@ -92,3 +92,20 @@ def test_states_of_another_body_are_refused():
                 be.load_state(bad)
             be.load_state(state)  # the good one still loads
             be.step(5)
+
+
+def test_interior_profiling_leaves_the_state_as_it_was():
+    """lbm_profile_interior runs interior launches that compute no solution,
+    between a device-side save and restore of the state: the body then
+    continues bit for bit as if the call had not been made."""
+    prob = W.smooth_random(150, 90, W.clamped_free_edges(), seed=31, amp=0.01, vamp=0.004, lam=0.3, mu=0.3)
+    for storage in ("f32", "f16"):
+        with lbm.Body(prob, storage=storage) as whole:
+            whole.step(140)
+            ref = whole.read(MASK)
+        with lbm.Body(prob, storage=storage) as b:
+            b.step(70)
+            st, out = lbm.lbm_profile_interior(b.ctx, 33)
+            assert st == lbm.LBM_OK and out[0] > 0 and out[1] == (150 - 4) * (90 - 4)
+            b.step(70)
+            _same(b.read(MASK), ref, (storage, "after profiling"))
