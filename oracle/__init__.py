@@ -53,6 +53,8 @@ class OracleProblem(C.Structure):
         ("rate", (C.c_double * 2) * 4),
         ("times", (C.c_double * 3) * 4),
         ("scheme", C.c_int32),
+        ("hole", C.c_int32 * 4),
+        ("hole_T", (C.c_double * 2) * 4),
     ]
 
 
@@ -120,7 +122,8 @@ def _dp(a: np.ndarray):
 def problem_from(wp, scheme: int = PREDICTOR) -> OracleProblem:
     """OracleProblem from a workloads.Problem-like object."""
     return make_problem(wp.nx, wp.ny, wp.dX, wp.lam, wp.mu, wp.rho0, wp.omega, wp.body,
-                        wp.edge_dicts(), scheme)
+                        wp.edge_dicts(), scheme, hole=getattr(wp, "hole", None),
+                        hole_traction=getattr(wp, "hole_traction", None))
 
 
 def solver_from(wp, scheme: int = PREDICTOR) -> "Solver":
@@ -195,11 +198,14 @@ def threads() -> int:
 # ---------------------------------------------------------------- solver
 
 def make_problem(nx, ny, dX, lam, mu, rho0, omega, body, edges,
-                 scheme: int = PREDICTOR) -> OracleProblem:
+                 scheme: int = PREDICTOR, hole=None, hole_traction=None) -> OracleProblem:
     """edges: four dicts {kind, value, rate, times} in order x-, x+, y-, y+.
 
     scheme: EXPLICIT (Algorithm 1's time-t source in collision and moment) or
-    PREDICTOR (the footnote's predictor-corrector for u)."""
+    PREDICTOR (the footnote's predictor-corrector for u).
+    hole: (x0, x1, y0, y1), the removed nodes of a rectangular hole, or None;
+    hole_traction: the constant traction on its faces at x0, x1, y0, y1 (four
+    pairs; None: traction-free)."""
     p = OracleProblem()
     p.scheme = int(scheme)
     p.nx, p.ny = int(nx), int(ny)
@@ -215,6 +221,11 @@ def make_problem(nx, ny, dX, lam, mu, rho0, omega, body, edges,
             p.rate[k][a] = float(rate[a])
         for a in range(3):
             p.times[k][a] = float(times[a])
+    if hole is not None:
+        for k in range(4):
+            p.hole[k] = int(hole[k])
+        for k, tr in enumerate(hole_traction or [(0.0, 0.0)] * 4):
+            p.hole_T[k][0], p.hole_T[k][1] = float(tr[0]), float(tr[1])
     return p
 
 

@@ -71,6 +71,15 @@
  *       is neutrally stable up to lambda = 4 mu (Poisson ratio 0.4).
  *   R15 Read-out stresses (P, Pbar, sigma, J) are evaluated from the read-out
  *       displacement u(t_n) by the same central differences and ghost rules.
+ *   R16 A rectangular hole (the plate with a square hole of Sec. 7) removes the
+ *       nodes x0 <= x < x1, y0 <= y < y1; its four faces lie half-way between
+ *       the last node of the body and the first removed one (R5) and carry a
+ *       constant traction each (zero: traction-free).  A face is a Neumann
+ *       boundary: the quadratic ghost of R6 for Grad u and Div Q, and
+ *       anti-bounce-back (R7, R8) with the face's outward normal for a link
+ *       that enters the hole through it; a diagonal link that enters the hole
+ *       through its corner takes N = (N1 + N2)/sqrt(2) and
+ *       T* = (T1 + T2)/sqrt(2), as at the body's corners (R10).
  */
 #include <math.h>
 #include <stdint.h>
@@ -103,6 +112,8 @@ typedef struct {
     double rate[4][2];
     double times[4][3];
     int32_t scheme; /* 0 = EXPLICIT (Algorithm 1), 1 = PREDICTOR (R14) */
+    int32_t hole[4];   /* x0, x1, y0, y1 of a removed rectangle (R16); x0 >= x1: none */
+    double hole_T[4][2]; /* traction on the hole's faces: x0 face, x1 face, y0 face, y1 face */
 } orc_problem;
 
 typedef struct {
@@ -263,6 +274,14 @@ static int axis_periodic(const orc_state* s, int axis) { return s->p.kind[2 * ax
 
 static int wrap(int k, int n) { return ((k % n) + n) % n; }
 
+static int has_hole(const orc_problem* p) { return p->hole[0] < p->hole[1] && p->hole[2] < p->hole[3]; }
+
+/* (x, y) is a removed node of the hole (R16). */
+static int in_hole(const orc_state* s, int x, int y) {
+    const int32_t* h = s->p.hole;
+    return h[0] < h[1] && x >= h[0] && x < h[1] && y >= h[2] && y < h[3];
+}
+
 /* Displacement at (x, y), which may lie one node outside along one axis
  * (reading R6). */
 static double u_at(const orc_state* s, double* const U[2], int x, int y, int a, double t) {
@@ -322,12 +341,25 @@ static double q_at(const orc_state* s, int x, int y, int k) {
     return 3.0 * v0 - 3.0 * v1 + v2;
 }
 
+/* Value at the removed neighbour (x + dx, y + dy) of the body node (x, y)
+ * across a hole face: the quadratic ghost 3 v0 - 3 v1 + v2 from the node and
+ * its two neighbours away from the face (R16). */
+static double hole_ghost(double v0, double v1, double v2) { return 3.0 * v0 - 3.0 * v1 + v2; }
+
 /* Eq. (defgrad) with central differences: H_ab = d_b u_a. */
+/* Displacement at the neighbour (x + dx, y + dy) of the body node (x, y):
+ * across a hole face the hole's ghost (R16), else u_at. */
+static double u_nb(const orc_state* s, double* const U[2], int x, int y, int dx, int dy, int a, double t) {
+    if (in_hole(s, x + dx, y + dy))
+        return hole_ghost(U[a][IDX(s, x, y)], U[a][IDX(s, x - dx, y - dy)], U[a][IDX(s, x - 2 * dx, y - 2 * dy)]);
+    return u_at(s, U, x + dx, y + dy, a, t);
+}
+
 static void grad_u(const orc_state* s, double* const U[2], int x, int y, double t, double H[4]) {
     double h2 = 2.0 * s->p.dX;
     for (int a = 0; a < 2; a++) {
-        H[2 * a + 0] = (u_at(s, U, x + 1, y, a, t) - u_at(s, U, x - 1, y, a, t)) / h2;
-        H[2 * a + 1] = (u_at(s, U, x, y + 1, a, t) - u_at(s, U, x, y - 1, a, t)) / h2;
+        H[2 * a + 0] = (u_nb(s, U, x, y, 1, 0, a, t) - u_nb(s, U, x, y, -1, 0, a, t)) / h2;
+        H[2 * a + 1] = (u_nb(s, U, x, y, 0, 1, a, t) - u_nb(s, U, x, y, 0, -1, a, t)) / h2;
     }
 }
 
@@ -338,6 +370,7 @@ static void update_stress(orc_state* s, double* const U[2], double t) {
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
+            if (in_hole(s, x, y)) continue; /* removed nodes keep zero stresses */
             double H[4], P[4], Pb[4];
             grad_u(s, U, x, y, t, H);
             orc_piola(H, s->p.lambda, s->p.mu, P);
@@ -350,6 +383,14 @@ static void update_stress(orc_state* s, double* const U[2], double t) {
         }
 }
 
+/* Q component k at the neighbour (x + dx, y + dy) of the body node (x, y):
+ * across a hole face the hole's ghost (R16), else q_at. */
+static double q_nb(const orc_state* s, int x, int y, int dx, int dy, int k) {
+    if (in_hole(s, x + dx, y + dy))
+        return hole_ghost(q_at(s, x, y, k), q_at(s, x - dx, y - dy, k), q_at(s, x - 2 * dx, y - 2 * dy, k));
+    return q_at(s, x + dx, y + dy, k);
+}
+
 /* Eq. (source1): 1S = rho0 b + Div(P + Pbar), central differences. */
 static void compute_source(orc_state* s) {
     int nx = s->p.nx, ny = s->p.ny;
@@ -358,15 +399,18 @@ static void compute_source(orc_state* s) {
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
             long id = IDX(s, x, y);
+            if (in_hole(s, x, y)) continue;
             for (int a = 0; a < 2; a++) {
-                double d1 = (q_at(s, x + 1, y, 2 * a + 0) - q_at(s, x - 1, y, 2 * a + 0)) / h2;
-                double d2 = (q_at(s, x, y + 1, 2 * a + 1) - q_at(s, x, y - 1, 2 * a + 1)) / h2;
+                double d1 = (q_nb(s, x, y, 1, 0, 2 * a + 0) - q_nb(s, x, y, -1, 0, 2 * a + 0)) / h2;
+                double d2 = (q_nb(s, x, y, 0, 1, 2 * a + 1) - q_nb(s, x, y, 0, -1, 2 * a + 1)) / h2;
                 s->S[a][id] = s->p.rho0 * s->p.body[a] + (d1 + d2);
             }
         }
 }
 
 /* ------------------------------------------------------------------ */
+static double abb_rule(const orc_state* s, int x, int y, int i, const double N[2], const double T[2]);
+
 /* Boundary rules of Sec. 6 for the link i of node (x, y) that leaves the body.
  * Returns the value of f_{opp(i)}(X, t + dt).  ex/ey: the bounded edges the
  * link crosses (-1 if none).  Time-t data: f (streamed), f^col, P, Pbar. */
@@ -413,6 +457,14 @@ static double boundary_rule(const orc_state* s, int x, int y, int i, int ex, int
     /* one edge: T = T*; corner: T = (T1 + T2)/sqrt(2) (reading R10) */
     T[0] /= nlen;
     T[1] /= nlen;
+    return abb_rule(s, x, y, i, N, T);
+}
+
+/* Eq. (abbcon): anti-bounce-back for the link i of node (x, y) across a wall
+ * of outward unit normal N carrying the traction T (time-t data). */
+static double abb_rule(const orc_state* s, int x, int y, int i, const double N[2], const double T[2]) {
+    long id = IDX(s, x, y);
+    double fc = s->fcol[i][id];
     /* wall values of the edge node at time t (reading R7) */
     double rw = 0.0, Pfw[4] = {0.0, 0.0, 0.0, 0.0}, Pw[4], Pbw[4];
     for (int k = 0; k < 9; k++) {
@@ -449,6 +501,34 @@ static double boundary_rule(const orc_state* s, int x, int y, int i, int ex, int
 
 /* ------------------------------------------------------------------ */
 
+/* The link i of body node (x, y) enters the hole (R16): anti-bounce-back with
+ * the normal and traction of the face it crosses, or of the hole's corner. */
+static double hole_rule(const orc_state* s, int x, int y, int i) {
+    int ex = s->e[i][0], ey = s->e[i][1];
+    int cx = ex != 0 && in_hole(s, x + ex, y); /* crosses the face normal to x */
+    int cy = ey != 0 && in_hole(s, x, y + ey); /* crosses the face normal to y */
+    if (!cx && !cy) cx = cy = 1;              /* through the hole's corner */
+    double N[2] = {cx ? (double)ex : 0.0, cy ? (double)ey : 0.0};
+    double T[2] = {0.0, 0.0};
+    /* faces: 0 at x0 (normal +x from the body), 1 at x1 (-x), 2 at y0 (+y), 3 at y1 (-y) */
+    if (cx) {
+        const double* tf = s->p.hole_T[ex > 0 ? 0 : 1];
+        T[0] += tf[0];
+        T[1] += tf[1];
+    }
+    if (cy) {
+        const double* tf = s->p.hole_T[ey > 0 ? 2 : 3];
+        T[0] += tf[0];
+        T[1] += tf[1];
+    }
+    double nlen = sqrt(N[0] * N[0] + N[1] * N[1]);
+    N[0] /= nlen;
+    N[1] /= nlen;
+    T[0] /= nlen;
+    T[1] /= nlen;
+    return abb_rule(s, x, y, i, N, T);
+}
+
 static double* zalloc(long n) { return (double*)calloc((size_t)n, sizeof(double)); }
 
 void orc_destroy(orc_state* s);
@@ -464,6 +544,10 @@ int orc_check(const orc_problem* p) {
         if ((a == ORC_PERIODIC) != (b == ORC_PERIODIC)) return 4;
     }
     if (p->scheme != ORC_EXPLICIT && p->scheme != ORC_PREDICTOR) return 6;
+    if (has_hole(p)) {
+        /* at least 3 body nodes between the hole and each edge or seam */
+        if (p->hole[0] < 3 || p->hole[1] > p->nx - 3 || p->hole[2] < 3 || p->hole[3] > p->ny - 3) return 7;
+    }
     return 0;
 }
 
@@ -497,14 +581,16 @@ orc_state* orc_create(const orc_problem* p, const double* u0, const double* v0) 
     }
     for (long id = 0; id < s->n; id++)
         for (int a = 0; a < 2; a++) {
-            s->u[a][id] = u0 ? u0[2 * id + a] : 0.0;
-            s->j[a][id] = p->rho0 * (v0 ? v0[2 * id + a] : 0.0);
+            const int removed = in_hole(s, (int)(id % p->nx), (int)(id / p->nx));
+            s->u[a][id] = u0 && !removed ? u0[2 * id + a] : 0.0;
+            s->j[a][id] = p->rho0 * (v0 && !removed ? v0[2 * id + a] : 0.0);
         }
     update_stress(s, s->u, 0.0);
     int nx = p->nx, ny = p->ny;
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
+            if (in_hole(s, x, y)) continue; /* removed nodes hold nothing */
             double H[4];
             grad_u(s, s->u, x, y, 0.0, H);
             long id = IDX(s, x, y);
@@ -557,8 +643,13 @@ static void step_once(orc_state* s) {
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
             long id = IDX(s, x, y);
+            if (in_hole(s, x, y)) continue;
             for (int i = 0; i < 9; i++) {
                 int dx = x + s->e[i][0], dy = y + s->e[i][1];
+                if (in_hole(s, dx, dy)) {
+                    s->fnew[s->opp[i]][id] = hole_rule(s, x, y, i);
+                    continue;
+                }
                 int ex = -1, ey = -1;
                 if (dx < 0 || dx >= nx) {
                     if (px)
@@ -660,8 +751,8 @@ void orc_read(const orc_state* s, double* u, double* v, double* P, double* Pb, d
             if (v)
                 for (int a = 0; a < 2; a++) v[2 * id + a] = s->j[a][id] / s->p.rho0;
             if (r) r[id] = s->r[id];
-            double H[4], PP[4], PB[4];
-            grad_u(s, s->u, x, y, t, H);
+            double H[4] = {0.0, 0.0, 0.0, 0.0}, PP[4], PB[4];
+            if (!in_hole(s, x, y)) grad_u(s, s->u, x, y, t, H); /* removed nodes read as undeformed */
             double Jv = orc_piola(H, s->p.lambda, s->p.mu, PP);
             orc_poisson_stress(H, s->p.mu, PB);
             if (P)
@@ -689,7 +780,13 @@ void orc_read(const orc_state* s, double* u, double* v, double* P, double* Pb, d
 void orc_read_grad(const orc_state* s, double* H) {
     double t = s->step * s->dt;
     for (int y = 0; y < s->p.ny; y++)
-        for (int x = 0; x < s->p.nx; x++) grad_u(s, s->u, x, y, t, H + 4 * IDX(s, x, y));
+        for (int x = 0; x < s->p.nx; x++) {
+            double* h = H + 4 * IDX(s, x, y);
+            if (in_hole(s, x, y))
+                h[0] = h[1] = h[2] = h[3] = 0.0;
+            else
+                grad_u(s, s->u, x, y, t, h);
+        }
 }
 
 /* Raw populations f_i(X, t) (after streaming), [9][ny][nx]. */

@@ -58,6 +58,10 @@ class Problem:
     name: str = ""
     # built on demand instead of u0 / v0 (long request traces): () -> (u0, v0)
     make_initial: Optional[Callable[[], Tuple[np.ndarray, np.ndarray]]] = None
+    # a rectangular hole: removed nodes x0 <= x < x1, y0 <= y < y1, and the
+    # constant traction on its faces at x0, x1, y0, y1 (None: traction-free)
+    hole: Optional[Tuple[int, int, int, int]] = None
+    hole_traction: Optional[List[Tuple[float, float]]] = None
 
     def initial(self) -> Tuple[Optional[np.ndarray], Optional[np.ndarray]]:
         """(u0, v0), built now if the problem holds a recipe instead."""
@@ -67,7 +71,20 @@ class Problem:
 
     @property
     def nodes(self) -> int:
-        return self.nx * self.ny
+        """Nodes of the body (those of a hole removed)."""
+        n = self.nx * self.ny
+        if self.hole is not None:
+            x0, x1, y0, y1 = self.hole
+            n -= max(0, x1 - x0) * max(0, y1 - y0)
+        return n
+
+    def active(self) -> np.ndarray:
+        """[ny][nx] mask of the body's nodes."""
+        m = np.ones((self.ny, self.nx), dtype=bool)
+        if self.hole is not None:
+            x0, x1, y0, y1 = self.hole
+            m[y0:y1, x0:x1] = False
+        return m
 
     def edge_dicts(self) -> list:
         return [e.as_dict() for e in self.edges]
@@ -199,6 +216,24 @@ def tension_block(n: int = 40, T1: float = 1.0, lam: float = 1.0, mu: float = 1.
     z = np.zeros((n, n, 2))
     return Problem(nx=n, ny=n, lam=lam, mu=mu, dX=dX, edges=edges, u0=z, v0=z.copy(),
                    name=f"tension_{n}")
+
+
+def plate_with_hole(n: int = 80, hole_frac: float = 0.4, T: float = 0.1, mu: float = 1.0, lam: float = 1.0,
+                    t_off: float = 1.0) -> Problem:
+    """Square plate of side l = 1 (dX = 1/n) with a centred square hole of
+    side hole_frac l, traction-free except for a sudden traction of T along
+    x2 on the top and bottom edges (outward on both) from t = 0 to t_off
+    (Sec. 7's plate with a hole: n = 80, hole 0.4 l, T = 0.1 mu, off at
+    t = 1)."""
+    dX = 1.0 / n
+    h = int(round(hole_frac * n))
+    a = (n - h) // 2
+    pull = dict(value=(0.0, 0.0), times=(0.0, 0.0, t_off))
+    edges = [Edge(NEUMANN), Edge(NEUMANN), Edge(NEUMANN, rate=(0.0, -T), **pull),
+             Edge(NEUMANN, rate=(0.0, T), **pull)]
+    z = np.zeros((n, n, 2))
+    return Problem(nx=n, ny=n, lam=lam, mu=mu, dX=dX, edges=edges, u0=z, v0=z.copy(),
+                   hole=(a, a + h, a, a + h), name=f"plate_hole_{n}")
 
 
 # ----------------------------------------------------------------- batches

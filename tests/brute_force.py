@@ -4,6 +4,10 @@ equations and the readings listed in the oracle's header (not from the
 oracle's code).  It pins the C oracle on 3 x 3 .. 6 x 5 bodies, where every
 node is a boundary node or next to one, so the boundary rules of Sec. 6,
 the ghost values of the differences and the corner links are all exercised.
+A rectangular hole (removed nodes, faces with a constant traction each)
+follows reading R16: a removed neighbour takes the quadratic ghost, a link
+into the hole the anti-bounce-back rule with the crossed face's normal (a
+link through the hole's corner: both faces, as at the body's corners).
 
 Notation: direction k has integer offset E[k] and lattice velocity
 C_k = c E[k]; weights 4/9, 1/9, 1/36; Cs^2 = mu / rho0 = c^2 / 3.
@@ -29,7 +33,9 @@ class BruteForce:
         self.c = self.dX / self.dt
         self.n = 0
         u0, v0 = prob.initial() if hasattr(prob, "initial") else (prob.u0, prob.v0)
-        nodes = [(x, y) for y in range(self.ny) for x in range(self.nx)]
+        self.hole = getattr(prob, "hole", None)
+        self.hole_T = getattr(prob, "hole_traction", None) or [(0.0, 0.0)] * 4
+        nodes = [(x, y) for y in range(self.ny) for x in range(self.nx) if not self.removed((x, y))]
         self.nodes = nodes
         self.u = {p: [float(u0[p[1], p[0], 0]), float(u0[p[1], p[0], 1])] for p in nodes}
         self.j = {p: [self.rho0 * float(v0[p[1], p[0], 0]), self.rho0 * float(v0[p[1], p[0], 1])]
@@ -45,6 +51,12 @@ class BruteForce:
         self.S = {p: self.source(p) for p in nodes}
 
     # ---------------------------------------------------------------- pieces
+    def removed(self, p):
+        if self.hole is None:
+            return False
+        x0, x1, y0, y1 = self.hole
+        return x0 <= p[0] < x1 and y0 <= p[1] < y1
+
     def periodic(self, axis):
         return self.edges[2 * axis].kind == PER
 
@@ -93,6 +105,14 @@ class BruteForce:
         """field at p + side along axis; beyond a bounded edge the ghost value
         (Dirichlet: 2 u*(t) - u_edge for u; otherwise 3 v0 - 3 v1 + v2)."""
         x, y = p
+        step = (side, 0) if axis == 0 else (0, side)
+        if self.removed((x + step[0], y + step[1])):
+            # across a face of the hole: quadratic ghost from p and the two
+            # nodes behind it
+            vals = [field[(x - m * step[0], y - m * step[1])] for m in range(3)]
+            if isinstance(vals[0], float):
+                return 3 * vals[0] - 3 * vals[1] + vals[2]
+            return [3 * vals[0][a] - 3 * vals[1][a] + vals[2][a] for a in range(len(vals[0]))]
         n = self.nx if axis == 0 else self.ny
         k = (x if axis == 0 else y) + side
         if 0 <= k < n or self.periodic(axis):
@@ -151,6 +171,30 @@ class BruteForce:
         norm = math.hypot(sx, sy)
         N = (sx / norm, sy / norm)
         T = [sum(self.tstar(e, t)[a] for e in crossed) / norm for a in range(2)]
+        return self.anti_bounce(p, k, N, T, fcol)
+
+    def hole_rule(self, p, k, fcol):
+        """f_opp(k) at p after a link k that enters the hole: anti-bounce-back
+        across the face(s) it crosses (the hole's corner: both faces)."""
+        ex, ey = E[k]
+        faces = []
+        if ex and self.removed((p[0] + ex, p[1])):
+            faces.append((0, ex))
+        if ey and self.removed((p[0], p[1] + ey)):
+            faces.append((1, ey))
+        if not faces:
+            faces = [(0, ex), (1, ey)]
+        s = [0, 0]
+        T = [0.0, 0.0]
+        for axis, sign in faces:
+            s[axis] = sign
+            face = 2 * axis + (0 if sign > 0 else 1)  # faces at x0, x1, y0, y1
+            T = [T[a] + self.hole_T[face][a] for a in range(2)]
+        norm = math.hypot(s[0], s[1])
+        return self.anti_bounce(p, k, (s[0] / norm, s[1] / norm), [T[a] / norm for a in range(2)], fcol)
+
+    def anti_bounce(self, p, k, N, T, fcol):
+        ck = self.C(k)
         fw = self.f[p]  # wall values: the edge node at time t
         rw = sum(fw)
         Pf = [[sum(self.C(i)[a] * self.C(i)[b] * fw[i] for i in range(9)) for b in range(2)] for a in range(2)]
@@ -196,7 +240,9 @@ class BruteForce:
                         y %= self.ny
                     else:
                         crossed.append(2 if y < 0 else 3)
-                if crossed:
+                if self.removed((x, y)):
+                    new[p][OPPOSITE[k]] = self.hole_rule(p, k, fcol[p])
+                elif crossed:
                     new[p][OPPOSITE[k]] = self.wall_rule(p, k, crossed, fcol[p], t)
                 else:
                     new[(x, y)][k] = fcol[p][k]

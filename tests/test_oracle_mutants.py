@@ -33,6 +33,10 @@ MUTANTS = [
      "double FiT[4] = {F[3] / J, -F[1] / J, -F[2] / J, F[0] / J};", 0),
     ("diagonal weight", "1.0 / 9.0 : 1.0 / 36.0", "1.0 / 9.0 : 1.0 / 32.0", 0),
     ("initial r sign", "s->r[id] = -p->rho0 * (H[0] + H[3]);", "s->r[id] = p->rho0 * (H[0] + H[3]);", 0),
+    # the hole of reading R16
+    ("hole ghost", "return 3.0 * v0 - 3.0 * v1 + v2;", "return 2.0 * v0 - v1;", 2),
+    ("hole corner normal", "if (!cx && !cy) cx = cy = 1;", "if (!cx && !cy) cx = 1;", 0),
+    ("hole face traction", "s->p.hole_T[ex > 0 ? 0 : 1]", "s->p.hole_T[ex > 0 ? 1 : 0]", 0),
 ]
 
 

@@ -367,6 +367,13 @@ def _tiny_cases():
         "3x5_periodic": W.smooth_random(3, 5, [Pp] * 4, seed=35, amp=0.02, lam=0.45),
         "6x5_body_force": dataclasses.replace(
             W.smooth_random(6, 5, [N0, D0, N0, N0], seed=36, amp=0.01, lam=0.3, mu=0.3), body=(0.01, -0.02)),
+        # a rectangular hole (reading R16): loaded faces, then a traction-free
+        # hole in a body periodic along x
+        "9x8_hole_loaded": dataclasses.replace(
+            W.smooth_random(9, 8, [N0, D0, ramp, N0], seed=37, amp=0.01, lam=0.3, mu=0.3), hole=(3, 6, 3, 5),
+            hole_traction=[(0.01, 0.0), (0.0, -0.01), (0.005, 0.002), (-0.003, 0.004)]),
+        "10x9_xperiodic_hole": dataclasses.replace(
+            W.smooth_random(10, 9, [Pp, Pp, N0, moving], seed=38, amp=0.01, lam=0.45), hole=(3, 7, 3, 6)),
     }
 
 
@@ -386,3 +393,77 @@ def test_oracle_matches_a_brute_force_restatement(name, scheme):
             scale = max(np.abs(ref[k]).max(), 1e-30)
             assert np.abs(got[k] - ref[k]).max() <= 1e-12 * scale, (name, scheme, steps, k)
     s.close()
+
+
+# ---------------------------------------------------------------- the hole (R16)
+
+def _holed(p, hole, traction=None):
+    return dataclasses.replace(p, hole=hole, hole_traction=traction)
+
+
+@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR])
+def test_patch_test_with_a_loaded_hole_stays_static(scheme):
+    """Affine u = H0 X with T* = P(I + H0) N on the four edges and on the
+    four faces of a hole (N the body's outward normal, into the hole): a
+    homogeneous state, so the body must stay at rest; this holds only if the
+    hole's ghost values, its anti-bounce-back with the face normals and its
+    corner links (N = (N1 + N2)/sqrt(2)) are consistent."""
+    H0 = np.array([[0.02, 0.01], [-0.015, 0.03]])
+    P, _ = oracle.piola(H0, 1.0, 1.0)
+    T = [tuple(P @ np.array(n)) for n in ([-1, 0], [1, 0], [0, -1], [0, 1])]
+    TH = [tuple(P @ np.array(n)) for n in ([1, 0], [-1, 0], [0, 1], [0, -1])]
+    p = _holed(W.affine_patch(20, 18, H0, tractions=T), (6, 12, 5, 11), TH)
+    m = p.active()
+    s = oracle.solver_from(p, scheme)
+    o0 = s.read()
+    s.step(500)
+    o = s.read()
+    assert np.abs(o["u"] - o0["u"])[m].max() < 1e-11
+    assert np.abs(o["v"])[m].max() < 1e-12
+    np.testing.assert_allclose(o["P"].reshape(-1, 2, 2)[m.ravel()], np.broadcast_to(P, (p.nodes, 2, 2)), atol=1e-12)
+
+
+def test_rigid_rotation_with_a_hole_stays_put():
+    R = _rot(0.1)
+    p = _holed(W.affine_patch(20, 18, R - np.eye(2)), (6, 12, 5, 11))
+    m = p.active()
+    s = oracle.solver_from(p)
+    o0 = s.read()
+    s.step(400)
+    o = s.read()
+    assert np.abs(o["u"] - o0["u"])[m].max() < 1e-10
+    assert np.abs(o["P"].reshape(-1, 4)[m.ravel()]).max() < 1e-10
+
+
+def test_plate_with_hole_keeps_its_mirror_symmetries():
+    """Sec. 7's plate with a centred square hole, pulled equally at top and
+    bottom: the response is mirror-symmetric about both centre lines (u_y odd
+    and u_x even in y; u_x odd and u_y even in x), to rounding."""
+    p = W.plate_with_hole(40, T=0.01)
+    s = oracle.solver_from(p)
+    s.step(150)
+    u = s.read()["u"]
+    scale = np.abs(u).max()
+    assert scale > 1e-4
+    for a, (fx, fy) in enumerate(((-1, 1), (1, -1))):  # component: sign under x mirror, under y mirror
+        np.testing.assert_allclose(u[:, ::-1, a], fx * u[:, :, a], atol=1e-11 * scale)
+        np.testing.assert_allclose(u[::-1, :, a], fy * u[:, :, a], atol=1e-11 * scale)
+
+
+def test_plate_with_hole_small_load_is_stable_and_elongates():
+    """The plate of Sec. 7 (80 x 80 nodes, hole 0.4 l) under a sudden
+    traction of 0.02 mu until t = 1, run to t = 3: stable, the plate
+    lengthens along x2 while loaded (a few per cent) and swings back after."""
+    p = W.plate_with_hole(80, T=0.02)
+    s = oracle.solver_from(p)
+    steps = int(round(3.0 / s.dt))
+    peak, last = 0.0, None
+    for k in range(0, steps, 16):
+        s.step(16)
+        u = s.read()["u"]
+        el = u[-1, :, 1].mean() - u[0, :, 1].mean()  # (l + elongation) - l, l = 1
+        assert np.isfinite(el)
+        peak = max(peak, el)
+        last = el
+    assert 0.015 < peak < 0.04
+    assert abs(last) < peak
