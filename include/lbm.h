@@ -125,6 +125,22 @@ enum { LBM_PERIODIC = 0, LBM_DIRICHLET = 1, LBM_NEUMANN = 2 };
 LBM_API lbm_status lbm_set_boundary(lbm_ctx* ctx, int32_t edge, int32_t kind, const double value[2],
                             const double rate[2], const double times[3]);
 
+/* A rectangular hole in the body (Sec. 7's plate with a square hole): the
+ * nodes x0 <= x < x1, y0 <= y < y1 (hole = {x0, x1, y0, y1}) are removed.
+ * Its faces lie half-way between the body's last node and the first removed
+ * one and are Neumann boundaries with a constant traction each: traction
+ * holds (Tx, Ty) for the faces at x0, x1, y0, y1 in that order (NULL:
+ * traction-free).  A face takes the quadratic ghost of the differences and
+ * anti-bounce-back (Eq. abbcon) with its outward normal (pointing into the
+ * hole); a link through a corner of the hole takes both faces, N = (N1 +
+ * N2)/sqrt(2), T* = (T1 + T2)/sqrt(2).  Only before the first lbm_step /
+ * lbm_read_fields / lbm_diagnostics, after the boundaries of both axes are
+ * set.  The hole keeps 4 nodes from bounded edges and 5 from periodic seams
+ * (so that its band of boundary nodes clears the body's).  Errors:
+ * LBM_E_INVALID (hole out of range or empty, traction not finite),
+ * LBM_E_STATE. */
+LBM_API lbm_status lbm_set_hole(lbm_ctx* ctx, const int32_t hole[4], const double traction[8]);
+
 /* Advances nsteps (>= 0) time steps: one fused stream-collide-constitutive
  * kernel launch per step on the context's stream (replayed as CUDA graphs for
  * long runs).  The observable fields (u, v, r) are captured at the last step.

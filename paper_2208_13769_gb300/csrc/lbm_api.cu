@@ -108,6 +108,8 @@ StepParams lbm::make_params(const lbm_ctx* c, int parity) {
     L[kLatRho0OverC] = p.rho0 / p.c;
     L[kLatRho0] = p.rho0;
     for (int k = 0; k < kLatCount; ++k) p.lat_f[k] = float(L[k]);
+    for (int k = 0; k < 4; ++k) p.hole[k] = c->hole[k];
+    for (int k = 0; k < 8; ++k) p.hole_T[k] = c->hole_T[k];
     return p;
 }
 
@@ -125,6 +127,7 @@ static ReadoutParams make_readout(const lbm_ctx* c) {
     r.t = double(c->steps) * c->dt;
     r.fields = c->fields;
     for (int e = 0; e < 4; ++e) r.bc[e] = c->bc[e];
+    for (int k = 0; k < 4; ++k) r.hole[k] = c->hole[k];
     return r;
 }
 
@@ -137,75 +140,134 @@ lbm_status lbm::ctx_ready(const lbm_ctx* c) {
     return LBM_OK;
 }
 
-// Interior rectangle (nodes >= 2 from bounded edges, >= 3 from periodic
-// seams) for the lean kernel, the bands around it as tiles of the edge
-// kernel; the parameter table of both parities and the tile list go to the
-// device.
+int64_t lbm::interior_nodes(const lbm_ctx* c) {
+    int64_t n = 0;
+    for (int k = 0; k < c->n_irect; ++k)
+        n += int64_t(c->irect[k][1] - c->irect[k][0]) * (c->irect[k][3] - c->irect[k][2]);
+    return n;
+}
+
+// The interior (nodes >= 2 from bounded edges and from a hole's faces, >= 3
+// from periodic seams) as up to 4 rectangles for the lean kernel; the bands
+// around the body and around the hole as tiles of the edge kernel; the
+// parameter table of both parities and the tile list go to the device.
 static cudaError_t build_plan(lbm_ctx* c) {
     const bool perx = c->bc[0].kind == kPeriodic, pery = c->bc[2].kind == kPeriodic;
     const int bx = perx ? 3 : 2, by = pery ? 3 : 2;
     const int nx = c->nx, ny = c->ny;
-    c->has_interior = nx - 2 * bx >= 8 && ny - 2 * by >= 8;
+    const int32_t* H = c->hole;
+    const bool hole = H[0] < H[1];
+    const bool small = !(nx - 2 * bx >= 8 && ny - 2 * by >= 8);  // too small for the interior kernel
     c->nband = 0;
-    if (c->has_interior) {
-        const int r[4] = {bx, nx - bx, by, ny - by};
-        for (int k = 0; k < 4; ++k) c->irect[k] = r[k];
-        const int h = r[3] - r[2];
-        c->i_ring = c->tune_ring ? c->tune_ring : kInteriorRing;
-        const int per_sm = std::max(1, interior_occupancy(c->fmt, c->i_ring));
-        interior_strips(c->fmt, r[0], r[1], c->tune_aligned == 1, &c->i_strip_x0, &c->i_strip_w, &c->i_tiles_x);
-        int64_t rows;
-        if (c->tune_chunk > 0) {
-            rows = c->tune_chunk;
+    c->n_irect = 0;
+    const int bands[4][4] = {{0, nx, 0, by}, {0, nx, ny - by, ny}, {0, bx, by, ny - by}, {nx - bx, nx, by, ny - by}};
+    if (!hole) {
+        if (small) {
+            const int all[4] = {0, nx, 0, ny};
+            for (int k = 0; k < 4; ++k) c->brect[0][k] = all[k];
+            c->nband = 1;
         } else {
-            // exactly one wave of equal CTAs: strips x chunks <= SMs x per_sm
-            const int64_t slots = int64_t(c->num_sms) * per_sm;
-            const int64_t chunks = std::max<int64_t>(1, slots / c->i_tiles_x);
-            rows = std::max<int64_t>((h + chunks - 1) / chunks, 16);
+            const int R[4] = {bx, nx - bx, by, ny - by};
+            for (int k = 0; k < 4; ++k) c->irect[0][k] = R[k];
+            c->n_irect = 1;
+            for (int b = 0; b < 4; ++b)
+                for (int k = 0; k < 4; ++k) c->brect[b][k] = bands[b][k];
+            c->nband = 4;
         }
-        rows = std::min<int64_t>(rows, h);
-        c->i_chunk = int(rows);
-        c->i_tiles_y = int((h + rows - 1) / rows);
-        const int bands[4][4] = {{0, nx, 0, by}, {0, nx, ny - by, ny}, {0, bx, by, ny - by}, {nx - bx, nx, by, ny - by}};
+    } else {
+        // the bands of the edges and the 2-node band around the hole (the
+        // hole keeps clear of the edges' bands, lbm_set_hole); the rest of
+        // the body below, above, left and right of the hole's band goes to
+        // the interior kernel, or, for a body too small for it, to tiles of
+        // the edge kernel as well
         for (int b = 0; b < 4; ++b)
             for (int k = 0; k < 4; ++k) c->brect[b][k] = bands[b][k];
-        c->nband = 4;
-    } else {
-        const int all[4] = {0, nx, 0, ny};
-        for (int k = 0; k < 4; ++k) c->brect[0][k] = all[k];
-        c->nband = 1;
+        const int hb[4][4] = {{H[0] - 2, H[0], H[2] - 2, H[3] + 2},
+                              {H[1], H[1] + 2, H[2] - 2, H[3] + 2},
+                              {H[0], H[1], H[2] - 2, H[2]},
+                              {H[0], H[1], H[3], H[3] + 2}};
+        for (int b = 0; b < 4; ++b)
+            for (int k = 0; k < 4; ++k) c->brect[4 + b][k] = hb[b][k];
+        c->nband = 8;
+        const int R[4] = {bx, nx - bx, by, ny - by};
+        const int B[4] = {H[0] - 2, H[1] + 2, H[2] - 2, H[3] + 2};
+        const int parts[4][4] = {{R[0], R[1], R[2], B[2]},
+                                 {R[0], R[1], B[3], R[3]},
+                                 {R[0], B[0], std::max(R[2], B[2]), std::min(R[3], B[3])},
+                                 {B[1], R[1], std::max(R[2], B[2]), std::min(R[3], B[3])}};
+        for (int q = 0; q < 4; ++q) {
+            if (!(parts[q][0] < parts[q][1] && parts[q][2] < parts[q][3])) continue;
+            int* dst = small ? c->brect[c->nband++] : c->irect[c->n_irect++];
+            for (int k = 0; k < 4; ++k) dst[k] = parts[q][k];
+        }
     }
+    if (c->n_irect > 0) {
+        c->i_ring = c->tune_ring ? c->tune_ring : kInteriorRing;
+        const int per_sm = std::max(1, interior_occupancy(c->fmt, c->i_ring));
+        const int64_t slots = int64_t(c->num_sms) * per_sm;
+        const int64_t total = std::max<int64_t>(1, interior_nodes(c));
+        for (int q = 0; q < c->n_irect; ++q) {
+            const int* r = c->irect[q];
+            const int h = r[3] - r[2];
+            interior_strips(c->fmt, r[0], r[1], c->tune_aligned == 1, &c->i_strip_x0[q], &c->i_strip_w[q],
+                            &c->i_tiles_x[q]);
+            int64_t rows;
+            if (c->tune_chunk > 0) {
+                rows = c->tune_chunk;
+            } else {
+                // one wave of equal CTAs: strips x chunks <= the rectangle's
+                // share of SMs x per_sm
+                const int64_t share = std::max<int64_t>(1, slots * (int64_t(r[1] - r[0]) * h) / total);
+                const int64_t chunks = std::max<int64_t>(1, share / c->i_tiles_x[q]);
+                rows = std::max<int64_t>((h + chunks - 1) / chunks, 16);
+            }
+            rows = std::min<int64_t>(rows, h);
+            c->i_chunk[q] = int(rows);
+            c->i_tiles_y[q] = int((h + rows - 1) / rows);
+        }
+    }
+    c->has_interior = c->n_irect > 0;  // a hole may leave the bands only
     int n = 0;
     for (int b = 0; b < c->nband; ++b) n += edge_tiles_of_rect(c->brect[b], 0, nullptr, 0, false, kEdgeThreads);
-    EdgeTile* h = new (std::nothrow) EdgeTile[size_t(n)];
+    int ni = n;  // the initialisation's tiles: with a hole, the interior rectangles' too
+    if (hole)
+        for (int q = 0; q < c->n_irect; ++q) ni += edge_tiles_of_rect(c->irect[q], 0, nullptr, 0, false, kEdgeThreads);
+    EdgeTile* h = new (std::nothrow) EdgeTile[size_t(ni)];
     if (!h) return cudaErrorMemoryAllocation;
     int m = 0;
     for (int b = 0; b < c->nband; ++b) m += edge_tiles_of_rect(c->brect[b], 0, h + m, n - m, m == 0, kEdgeThreads);
+    if (hole)
+        for (int q = 0; q < c->n_irect; ++q) m += edge_tiles_of_rect(c->irect[q], 0, h + m, ni - m, false, kEdgeThreads);
     StepParams hp[2] = {make_params(c, 0), make_params(c, 1)};
-    cudaError_t e = cudaMalloc(&c->dtiles, sizeof(EdgeTile) * size_t(n));
+    cudaError_t e = cudaMalloc(&c->dtiles, sizeof(EdgeTile) * size_t(ni));
     if (e == cudaSuccess) e = cudaMalloc(&c->dparams, sizeof(hp));
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->dtiles, h, sizeof(EdgeTile) * size_t(n), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->dtiles, h, sizeof(EdgeTile) * size_t(ni), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->dparams, hp, sizeof(hp), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // h is freed below
     delete[] h;
     if (e != cudaSuccess) return e;
     c->n_etiles = n;
+    c->n_itiles = hole ? ni : 0;
     c->planned = true;
     return cudaSuccess;
 }
 
-// The interior launch of one time step (nothing if the body has no interior).
+// The interior launches of one time step, one per interior rectangle
+// (nothing if the body has no interior).
 static cudaError_t launch_interior_part(lbm_ctx* c, const StepParams& p, bool fields) {
-    if (!c->has_interior) return cudaSuccess;
-    StepParams pi = p;
-    for (int k = 0; k < 4; ++k) pi.rect[k] = c->irect[k];
-    pi.tiles_x = c->i_tiles_x;
-    pi.tiles_y = c->i_tiles_y;
-    pi.chunk_rows = c->i_chunk;
-    pi.ring_slots = c->i_ring;
-    pi.strip_x0 = c->i_strip_x0;
-    pi.strip_w = c->i_strip_w;
-    return launch_interior(c->fmt, pi, c->stream, fields);
+    for (int q = 0; q < c->n_irect; ++q) {
+        StepParams pi = p;
+        for (int k = 0; k < 4; ++k) pi.rect[k] = c->irect[q][k];
+        pi.tiles_x = c->i_tiles_x[q];
+        pi.tiles_y = c->i_tiles_y[q];
+        pi.chunk_rows = c->i_chunk[q];
+        pi.ring_slots = c->i_ring;
+        pi.strip_x0 = c->i_strip_x0[q];
+        pi.strip_w = c->i_strip_w[q];
+        const cudaError_t e = launch_interior(c->fmt, pi, c->stream, fields);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // The edge-band launch of one time step (the whole body without an interior).
@@ -220,6 +282,14 @@ static cudaError_t launch_band_part(lbm_ctx* c, int parity, bool fields, cudaStr
 
 // Launches of one time step (mode 0) or the initialisation (mode 1).
 static cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int parity) {
+    if (mode == 1 && c->n_itiles > 0) {  // a holed body: the plan's tiles
+        EdgeLaunch L;
+        memset(&L, 0, sizeof(L));
+        L.params = c->dparams + parity;
+        L.tiles = c->dtiles;
+        L.fields = fields ? 1 : 0;
+        return launch_edge(c->fmt, L, c->n_itiles, c->stream, 1);
+    }
     if (mode == 1) {
         EdgeLaunch L;
         memset(&L, 0, sizeof(L));
@@ -507,6 +577,28 @@ lbm_status lbm_set_boundary(lbm_ctx* c, int32_t edge, int32_t kind, const double
     return LBM_OK;
 }
 
+lbm_status lbm_set_hole(lbm_ctx* c, const int32_t hole[4], const double traction[8]) {
+    if (!c || !hole) return LBM_E_INVALID;
+    if (c->sticky) return LBM_E_CUDA;
+    if (c->initialized) return LBM_E_STATE;
+    if (!c->bc_set[0] || !c->bc_set[2]) return LBM_E_STATE;  // the margins depend on the axes' kinds
+    // the hole's 2-node band must clear the bands of the body's edges (2
+    // nodes at a bounded edge, 3 at a periodic seam) and its images
+    const int mx = c->bc[0].kind == kPeriodic ? 5 : 4, my = c->bc[2].kind == kPeriodic ? 5 : 4;
+    if (!(hole[0] < hole[1] && hole[2] < hole[3]) || hole[0] < mx || hole[1] > c->nx - mx || hole[2] < my ||
+        hole[3] > c->ny - my)
+        return LBM_E_INVALID;
+    double T[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (traction)
+        for (int k = 0; k < 8; ++k) {
+            if (!isfinite(traction[k])) return LBM_E_INVALID;
+            T[k] = traction[k];
+        }
+    for (int k = 0; k < 4; ++k) c->hole[k] = hole[k];
+    for (int k = 0; k < 8; ++k) c->hole_T[k] = T[k];
+    return LBM_OK;
+}
+
 lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
     NvtxRange range_("lbm_step");
     lbm_status st = ctx_ready(c);
@@ -587,7 +679,7 @@ lbm_status lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double out[4]) {
     delete[] ev;
     if (err != cudaSuccess) return ctx_fail_cuda(c, err);
     for (int q = 0; q < 3; ++q) out[q] = sum[q] / double(counted);
-    out[3] = c->has_interior ? double(c->irect[1] - c->irect[0]) * double(c->irect[3] - c->irect[2]) : 0.0;
+    out[3] = double(interior_nodes(c));
     return ctx_check_flag(c);
 }
 
@@ -640,7 +732,7 @@ lbm_status lbm_profile_interior(lbm_ctx* c, int64_t nlaunches, double out[2]) {
     cudaFree(save);
     if (err != cudaSuccess) return ctx_fail_cuda(c, err);
     out[0] = double(ms) / double(nlaunches);
-    out[1] = double(c->irect[1] - c->irect[0]) * double(c->irect[3] - c->irect[2]);
+    out[1] = double(interior_nodes(c));
     return ctx_check_flag(c);
 }
 
@@ -662,7 +754,7 @@ lbm_status lbm_get_tuning(const lbm_ctx* c, lbm_tuning* t) {
     if (!c || !t) return LBM_E_INVALID;
     if (c->planned && c->has_interior) {
         t->ring_slots = c->i_ring;
-        t->chunk_rows = c->i_chunk;
+        t->chunk_rows = c->i_chunk[0];
         t->aligned = c->tune_aligned == 1 ? 1 : 0;
     } else {
         t->ring_slots = c->tune_ring;

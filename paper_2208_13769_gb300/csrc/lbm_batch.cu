@@ -41,7 +41,8 @@ struct lbm_batch {
     std::vector<lbm_ctx*> m;
     std::vector<int> base_parity;  // member parity when the batch step count is even
     int fmt = 0;
-    StepParams* dtab = nullptr;  // [2][n]: entry q * n + i = member i at parity base_parity[i] ^ q
+    int n_entries = 0;           // parameter-table entries per parity
+    StepParams* dtab = nullptr;  // [2][n_entries]: entry q * n_entries + e at parity base_parity ^ q
     BatchItem* ditems = nullptr;  // work list: interior tiles and groups of edge tiles, interleaved
     EdgeTile* dtiles = nullptr;   // edge tiles of the groups
     int32_t* dqueue = nullptr;    // {next item, CTAs done} of the persistent kernel
@@ -88,7 +89,7 @@ cudaError_t batch_launch(lbm_batch* b, int q, bool fields) {
     const int n = int(b->m.size());
     BatchLaunch L;
     memset(&L, 0, sizeof(L));
-    L.params = b->dtab + size_t(q) * n;
+    L.params = b->dtab + size_t(q) * size_t(b->n_entries);
     L.items = b->ditems;
     L.tiles = b->dtiles;
     L.queue = b->dqueue;
@@ -198,64 +199,80 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
 
     // interior tiles: rows per chunk so that the batch holds about eight
     // waves of resident CTAs (at least 32 rows, at most 256)
-    int64_t interior_nodes = 0;
-    for (lbm_ctx* c : b->m)
-        if (c->has_interior)
-            interior_nodes += int64_t(c->irect[1] - c->irect[0]) * (c->irect[3] - c->irect[2]);
+    int64_t all_interior = 0;
+    for (lbm_ctx* c : b->m) all_interior += interior_nodes(c);
     b->ring = tuning && tuning->ring_slots ? tuning->ring_slots : kBatchRing;
     const int64_t wave = int64_t(b->m[0]->num_sms) * std::max(1, interior_occupancy(b->fmt, b->ring));
     b->chunk_rows = tuning && tuning->chunk_rows
                         ? tuning->chunk_rows
-                        : int(std::min<int64_t>(256, std::max<int64_t>(32, interior_nodes / (int64_t(120) * wave * 8))));
+                        : int(std::min<int64_t>(256, std::max<int64_t>(32, all_interior / (int64_t(120) * wave * 8))));
     std::vector<StepParams> tab;
     std::vector<InteriorWork> work;
     std::vector<EdgeTile> tiles;
     std::vector<BatchItem> items;
-    std::vector<int> sx0, sw, ns;  // strip grid of each member's interior
     try {
-        sx0.assign(size_t(n), 0);
-        sw.assign(size_t(n), 0);
-        ns.assign(size_t(n), 0);
-        for (int i = 0; i < n; ++i) {
-            const lbm_ctx* c = b->m[size_t(i)];
-            if (c->has_interior)
-                interior_strips(b->fmt, c->irect[0], c->irect[1], true, &sx0[size_t(i)], &sw[size_t(i)],
-                                &ns[size_t(i)]);
-        }
-        tab.resize(size_t(2) * n);
-        for (int q = 0; q < 2; ++q)
-            for (int i = 0; i < n; ++i) {
-                lbm_ctx* c = b->m[size_t(i)];
-                StepParams p = make_params(c, b->base_parity[size_t(i)] ^ q);
-                for (int k = 0; k < 4; ++k) p.rect[k] = c->irect[k];
-                p.chunk_rows = b->chunk_rows;
-                p.ring_slots = b->ring;
-                p.strip_x0 = sx0[size_t(i)];
-                p.strip_w = sw[size_t(i)];
-                tab[size_t(q) * n + i] = p;
-            }
+        // parameter table: one entry per interior rectangle of each member
+        // (at least one per member; its edge tiles use the first), for both
+        // parities: entry e of parity q at q * b->n_entries + e
+        std::vector<int> first_entry(size_t(n), 0), strips, owner;
+        std::vector<StepParams> ent;
         for (int i = 0; i < n; ++i) {
             lbm_ctx* c = b->m[size_t(i)];
-            if (c->has_interior) {
-                const int h = c->irect[3] - c->irect[2];
-                const int sx = ns[size_t(i)], sy = (h + b->chunk_rows - 1) / b->chunk_rows;
-                for (int by = 0; by < sy; ++by)
-                    for (int bx = 0; bx < sx; ++bx) work.push_back(InteriorWork{i, bx, by});
+            first_entry[size_t(i)] = int(ent.size());
+            const int nr = std::max(1, c->n_irect);
+            for (int q = 0; q < nr; ++q) {
+                StepParams p = make_params(c, b->base_parity[size_t(i)]);
+                int ns = 0;
+                if (q < c->n_irect) {
+                    for (int k = 0; k < 4; ++k) p.rect[k] = c->irect[q][k];
+                    interior_strips(b->fmt, p.rect[0], p.rect[1], true, &p.strip_x0, &p.strip_w, &ns);
+                }
+                p.chunk_rows = b->chunk_rows;
+                p.ring_slots = b->ring;
+                ent.push_back(p);
+                strips.push_back(ns);
+                owner.push_back(i);
+                if (q < c->n_irect) {
+                    const int e = int(ent.size()) - 1;
+                    const int h = p.rect[3] - p.rect[2];
+                    const int sy = (h + b->chunk_rows - 1) / b->chunk_rows;
+                    for (int by = 0; by < sy; ++by)
+                        for (int bx = 0; bx < ns; ++bx) work.push_back(InteriorWork{e, bx, by});
+                }
             }
+        }
+        b->n_entries = int(ent.size());
+        tab.resize(size_t(2) * ent.size());
+        for (size_t e = 0; e < ent.size(); ++e) {
+            tab[e] = ent[e];
+            // the other parity: the member's parameters of that parity with
+            // this entry's plan
+            const int i = owner[e];
+            StepParams p = make_params(b->m[size_t(i)], b->base_parity[size_t(i)] ^ 1);
+            for (int k = 0; k < 4; ++k) p.rect[k] = ent[e].rect[k];
+            p.strip_x0 = ent[e].strip_x0;
+            p.strip_w = ent[e].strip_w;
+            p.chunk_rows = ent[e].chunk_rows;
+            p.ring_slots = ent[e].ring_slots;
+            tab[ent.size() + e] = p;
+        }
+        for (int i = 0; i < n; ++i) {
+            lbm_ctx* c = b->m[size_t(i)];
             bool first = true;
+            const int e = first_entry[size_t(i)];
             for (int r = 0; r < c->nband; ++r) {
-                const int cnt = edge_tiles_of_rect(c->brect[r], i, nullptr, 0, false, kInteriorThreads);
+                const int cnt = edge_tiles_of_rect(c->brect[r], e, nullptr, 0, false, kInteriorThreads);
                 const size_t at = tiles.size();
                 tiles.resize(at + size_t(cnt));
-                edge_tiles_of_rect(c->brect[r], i, tiles.data() + at, cnt, first, kInteriorThreads);
+                edge_tiles_of_rect(c->brect[r], e, tiles.data() + at, cnt, first, kInteriorThreads);
                 first = first && cnt == 0;
             }
         }
         // longest tiles first: the short tiles of small bodies fill the tail
         // of the last wave
         auto rows_of = [&](const InteriorWork& w) {
-            const lbm_ctx* c = b->m[size_t(w.inst)];
-            return std::min(b->chunk_rows, c->irect[3] - c->irect[2]);
+            const StepParams& p = tab[size_t(w.inst)];
+            return std::min(b->chunk_rows, p.rect[3] - p.rect[2]);
         };
         std::stable_sort(work.begin(), work.end(),
                          [&](const InteriorWork& x, const InteriorWork& y) { return rows_of(x) > rows_of(y); });

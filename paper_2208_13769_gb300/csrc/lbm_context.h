@@ -82,19 +82,31 @@ struct lbm_ctx {
     bool sticky = false;
     bool variant_warm = false;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    // launch plan (built at initialisation, once the boundaries are known)
+    // a rectangular hole: removed nodes x0 <= x < x1, y0 <= y < y1 (none
+    // while x0 >= x1), and the traction on its faces at x0, x1, y0, y1
+    int32_t hole[4] = {0, 0, 0, 0};
+    double hole_T[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // launch plan (built at initialisation, once the boundaries are known):
+    // the interior as up to 4 rectangles (a hole splits it), each with its
+    // strip grid and row chunks; the bands around the body and the hole
     bool planned = false;
-    bool has_interior = false;
-    int irect[4] = {0, 0, 0, 0};
-    int i_tiles_x = 0, i_tiles_y = 0, i_chunk = 0, i_ring = 0, i_strip_x0 = 0, i_strip_w = 0;
+    bool has_interior = false;  // n_irect > 0
+    int n_irect = 0;
+    int irect[4][4];
+    int i_tiles_x[4], i_tiles_y[4], i_chunk[4], i_strip_x0[4], i_strip_w[4];
+    int i_ring = 0;
     // requested decomposition of the interior launch (lbm_set_tuning); 0 / -1:
     // the library's defaults
     int tune_ring = 0, tune_chunk = 0, tune_aligned = -1;
     int nband = 0;
-    int brect[4][4];
+    int brect[12][4];
     lbm::StepParams* dparams = nullptr;  // device: make_params(parity 0), make_params(parity 1)
     lbm::EdgeTile* dtiles = nullptr;     // device: tiles of the edge bands
     int n_etiles = 0;
+    // with a hole, the initialisation runs over the bands' tiles and tiles of
+    // the interior rectangles (then after the band tiles in dtiles), so that
+    // every face of the hole sees a tile as thick as its band
+    int n_itiles = 0;
 };
 
 namespace lbm {
@@ -112,6 +124,8 @@ StepParams make_params(const lbm_ctx* c, int parity);
 // LBM_OK once material and all four boundaries are set and no CUDA error
 // occurred; LBM_E_STATE / LBM_E_CUDA / LBM_E_INVALID otherwise.
 lbm_status ctx_ready(const lbm_ctx* c);
+// Nodes the interior launches advance (all interior rectangles).
+int64_t interior_nodes(const lbm_ctx* c);
 // Plans the launches and runs the initialisation of Algorithm 1 once.
 lbm_status ctx_ensure_initialized(lbm_ctx* c);
 // Synchronises the context's stream and maps its device flag to a status.

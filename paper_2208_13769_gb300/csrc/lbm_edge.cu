@@ -27,7 +27,7 @@ template <class TS, class TC, class UT, int MODE>
 __global__ void __launch_bounds__(kEdgeThreads, 3) edge_tile_kernel(const __grid_constant__ EdgeLaunch L) {
     constexpr int N = kEdgeThreads;
     __shared__ __align__(16) StepParams sp;
-    __shared__ EdgeNow<TC, UT> s_edge[4];
+    __shared__ EdgeNow<TC, UT> s_edge[5];
     __shared__ UT su[2 * N];                      // u*: [th][2 comps][tw]
     __shared__ TC sq[4 * N];                      // Q:  [th][4 comps][tw]
     __shared__ TC sinit[MODE == 1 ? 4 * N : 1];  // initialisation: r0, Pbar0 / c^2

@@ -42,6 +42,27 @@ struct Pops {
     TC v[9];
 };
 
+// Eq. (abbcon) for link i with the node's post-collision population fci
+// across a wall of outward normal (sx, sy) inv_len (inv_len = 1/sqrt(2) at a
+// corner) carrying the traction (T0, T1) inv_len; Pbar* of Sec. 6 in the
+// wall's frame from the quasi-traction g = -T* + Q N and the tangential
+// entry of the populations' second moment.
+template <class TC>
+__device__ __forceinline__ TC abb_value(int i, TC fci, int sx, int sy, TC inv_len, TC T0, TC T1, TC r, TC pxx,
+                                        TC pxy, TC pyy, TC q11, TC q12, TC q21, TC q22, TC inv_c2) {
+    const TC N0 = TC(sx) * inv_len, N1 = TC(sy) * inv_len;
+    const TC g0 = -T0 * inv_len + q11 * N0 + q12 * N1;
+    const TC g1 = -T1 * inv_len + q21 * N0 + q22 * N1;
+    const TC t0 = -N1, t1 = N0;
+    const TC pnn = (N0 * g0 + N1 * g1) * inv_c2;
+    const TC pnt = (t0 * g0 + t1 * g1) * inv_c2;
+    const TC ptt = t0 * t0 * pxx + TC(2) * t0 * t1 * pxy + t1 * t1 * pyy;
+    const TC sxx = pnn * N0 * N0 + TC(2) * pnt * N0 * t0 + ptt * t0 * t0;
+    const TC syy = pnn * N1 * N1 + TC(2) * pnt * N1 * t1 + ptt * t1 * t1;
+    const TC sxy = pnn * N0 * N1 + pnt * (N0 * t1 + t0 * N1) + ptt * t0 * t1;
+    return -fci + TC(2) * wgt<TC>(i) * eq_even<TC>(i, r, sxx, sxy, syy);
+}
+
 // Links of node (gx, gy) that leave the body through a bounded edge: the
 // boundary rules of Sec. 6, written into the first ghost row/column.  fc:
 // the node's post-collision populations; r, pxx, pxy, pyy: its moments;
@@ -54,6 +75,30 @@ __device__ __noinline__ void boundary_links(TS* fdst, Geo g, const StepParams& p
 #pragma unroll 1
     for (int i = 1; i < 9; ++i) {
         const int dx = gx + ex(i), dy = gy + ey(i);
+        if (in_hole(p.hole, dx, dy)) {
+            // Eq. (abbcon) across the face of the hole the link crosses, or
+            // both faces at the hole's corner
+            const bool cx = ex(i) != 0 && in_hole(p.hole, gx + ex(i), gy);
+            const bool cy = ey(i) != 0 && in_hole(p.hole, gx, gy + ey(i));
+            const int sx = (cx || !cy) ? ex(i) : 0, sy = (cy || !cx) ? ey(i) : 0;
+            TC T0 = TC(0), T1 = TC(0);
+            if (sx != 0) {  // the face at x0 (entered along +x) or at x1
+                const int fa = sx > 0 ? 0 : 1;
+                T0 += TC(p.hole_T[2 * fa]);
+                T1 += TC(p.hole_T[2 * fa + 1]);
+            }
+            if (sy != 0) {  // the face at y0 or at y1
+                const int fa = sy > 0 ? 2 : 3;
+                T0 += TC(p.hole_T[2 * fa]);
+                T1 += TC(p.hole_T[2 * fa + 1]);
+            }
+            const TC inv_len = (sx != 0 && sy != 0) ? TC(0.70710678118654752440) : TC(1);
+            const TC val =
+                abb_value<TC>(i, fc.v[i], sx, sy, inv_len, T0, T1, r, pxx, pxy, pyy, q11, q12, q21, q22, inv_c2);
+            const int oi = opp(i);
+            store_img(fdst + oi * g.plane, g, dx, dy, Codec<TS, TC>::st(val, oi, p));
+            continue;
+        }
         const bool bx2 = !g.perx && (dx < 0 || dx >= nx);
         const bool by2 = !g.pery && (dy < 0 || dy >= ny);
         if (!bx2 && !by2) continue;
@@ -89,17 +134,7 @@ __device__ __noinline__ void boundary_links(TS* fdst, Geo g, const StepParams& p
                 T0 += eb->T[0];
                 T1 += eb->T[1];
             }
-            const TC N0 = TC(sx) * inv_len, N1 = TC(sy) * inv_len;
-            const TC g0 = -T0 * inv_len + q11 * N0 + q12 * N1;
-            const TC g1 = -T1 * inv_len + q21 * N0 + q22 * N1;
-            const TC t0 = -N1, t1 = N0;
-            const TC pnn = (N0 * g0 + N1 * g1) * inv_c2;
-            const TC pnt = (t0 * g0 + t1 * g1) * inv_c2;
-            const TC ptt = t0 * t0 * pxx + TC(2) * t0 * t1 * pxy + t1 * t1 * pyy;
-            const TC sxx = pnn * N0 * N0 + TC(2) * pnt * N0 * t0 + ptt * t0 * t0;
-            const TC syy = pnn * N1 * N1 + TC(2) * pnt * N1 * t1 + ptt * t1 * t1;
-            const TC sxy = pnn * N0 * N1 + pnt * (N0 * t1 + t0 * N1) + ptt * t0 * t1;
-            val = -fc.v[i] + TC(2) * wgt<TC>(i) * eq_even<TC>(i, r, sxx, sxy, syy);
+            val = abb_value<TC>(i, fc.v[i], sx, sy, inv_len, T0, T1, r, pxx, pxy, pyy, q11, q12, q21, q22, inv_c2);
         }
         store_img(fdst + oi * g.plane, g, dx, dy, Codec<TS, TC>::st(val, oi, p));
     }
@@ -109,7 +144,8 @@ __device__ __noinline__ void boundary_links(TS* fdst, Geo g, const StepParams& p
 // mode 1: the initialisation).  Every thread of the CTA calls it (threads
 // beyond tw x th idle through the barriers).  Shared memory: su holds 2 x
 // tw x th u-carry values, sq 4 x tw x th arithmetic values, sinit (mode 1)
-// 4 x tw x th, s_edge the 4 edges' boundary data.  want_fields: also write
+// 4 x tw x th, s_edge the boundary data of the 4 edges and of a hole's faces
+// (5 entries).  want_fields: also write
 // u, v, r to p.fields.
 template <class TS, class TC, class UT, int MODE>
 __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepParams& p, bool want_fields, UT* su,
@@ -150,13 +186,23 @@ __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepP
     const int gxr = tile.x0 - 2 + tx, gyr = tile.y0 - 2 + ty;
     const bool okx = g.perx ? (gxr >= -2 && gxr < nx + 2) : (gxr >= 0 && gxr < nx);
     const bool oky = g.pery ? (gyr >= -2 && gyr < ny + 2) : (gyr >= 0 && gyr < ny);
-    const bool inA = okx && oky && ty < th;
-    const bool inB = inA && tx >= 1 && tx <= nxo + 2 && ty >= 1 && ty <= nyo + 2;
-    const bool inC = tx >= 2 && tx < nxo + 2 && ty >= 2 && ty < nyo + 2;
     const int gx = g.perx ? wrap_coord(gxr, nx) : gxr;
     const int gy = g.pery ? wrap_coord(gyr, ny) : gyr;
-    const bool gxl = !g.perx && gx == 0, gxh = !g.perx && gx == nx - 1;
-    const bool gyl = !g.pery && gy == 0, gyh = !g.pery && gy == ny - 1;
+    // a node of the hole is not part of the body: it holds nothing, and the
+    // cells of the hole next to its faces receive the populations the
+    // anti-bounce-back rule sends back
+    const bool removed = in_hole(p.hole, gx, gy);
+    const bool inA = okx && oky && ty < th && !removed;
+    const bool inB = inA && tx >= 1 && tx <= nxo + 2 && ty >= 1 && ty <= nyo + 2;
+    const bool inC = tx >= 2 && tx < nxo + 2 && ty >= 2 && ty < nyo + 2 && !removed;
+    // a removed neighbour along an axis is a face of the hole: a bounded edge
+    // for the ghost rules
+    const bool hxl = in_hole(p.hole, gx - 1, gy), hxh = in_hole(p.hole, gx + 1, gy);
+    const bool hyl = in_hole(p.hole, gx, gy - 1), hyh = in_hole(p.hole, gx, gy + 1);
+    const bool gxl = (!g.perx && gx == 0) || hxl, gxh = (!g.perx && gx == nx - 1) || hxh;
+    const bool gyl = (!g.pery && gy == 0) || hyl, gyh = (!g.pery && gy == ny - 1) || hyh;
+    // within one node of the hole (a link may enter it)
+    const bool near_hole = gx >= p.hole[0] - 1 && gx <= p.hole[1] && gy >= p.hole[2] - 1 && gy <= p.hole[3];
     // first and second inward neighbours (used only by a ghost rule)
     const int tx1 = gxl ? min(tx + 1, tw - 1) : max(tx - 1, 0);
     const int tx2 = gxl ? min(tx + 2, tw - 1) : max(tx - 2, 0);
@@ -192,13 +238,19 @@ __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepP
     }
     if (tile.lead && t == 0) p.counter[p.parity ^ 1] = n_now;
     if (t < 4) edge_now<TC, UT>(s_edge[t], p.bc[t], double(n_now) * p.dt, p.lat_d[kLatRho0OverC]);
+    if (t == 4) {  // the faces of a hole: Neumann (only the kind is read)
+        EdgeBC hole_bc;
+        memset(&hole_bc, 0, sizeof(hole_bc));
+        hole_bc.kind = kNeumann;
+        edge_now<TC, UT>(s_edge[4], hole_bc, 0.0, p.lat_d[kLatRho0OverC]);
+    }
     __syncthreads();
 
     // ---------------- stage B: H = Grad u*, Q = P(F) + Pbar(H)
     bool bad = false;
     if (inB) {
-        const EdgeNow<TC, UT>& ebx = s_edge[gxl ? 0 : 1];
-        const EdgeNow<TC, UT>& eby = s_edge[gyl ? 2 : 3];
+        const EdgeNow<TC, UT>& ebx = s_edge[(hxl || hxh) ? 4 : (gxl ? 0 : 1)];
+        const EdgeNow<TC, UT>& eby = s_edge[(hyl || hyh) ? 4 : (gyl ? 2 : 3)];
         TC hh[2][2];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
@@ -338,8 +390,8 @@ __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepP
 #pragma unroll
         for (int i = 0; i < 9; ++i) put(fdst + i * plane, Codec<TS, TC>::st(fc[i], i, p));
 
-        // links that leave the body through a bounded edge
-        if (gxl || gxh || gyl || gyh) {
+        // links that leave the body through a bounded edge or enter the hole
+        if (gxl || gxh || gyl || gyh || near_hole) {
             const TC* qr = sq + (ty * 4) * tw + tx;
             Pops<TC> pc;
 #pragma unroll

@@ -23,6 +23,12 @@ __device__ __forceinline__ int wrapc(int g, int n) {
 __device__ double du_fd(const ReadoutParams& p, int x, int y, int dx, int dy, int comp) {
     const double* u = p.fields + int64_t(comp) * p.nx * p.ny;
     auto U = [&](int xx, int yy) { return u[int64_t(yy) * p.nx + xx]; };
+    // across a face of the hole: the quadratic ghost from the node and the
+    // two nodes behind it
+    if (in_hole(p.hole, x + dx, y + dy))
+        return (3.0 * U(x, y) - 3.0 * U(x - dx, y - dy) + U(x - 2 * dx, y - 2 * dy)) - U(x - dx, y - dy);
+    if (in_hole(p.hole, x - dx, y - dy))
+        return U(x + dx, y + dy) - (3.0 * U(x, y) - 3.0 * U(x + dx, y + dy) + U(x + 2 * dx, y + 2 * dy));
     const int n = dx ? p.nx : p.ny;
     const int k = dx ? x : y;
     const bool per = dx ? p.periodic_x : p.periodic_y;
@@ -49,9 +55,10 @@ struct Local {
 
 __device__ void local_state(const ReadoutParams& p, int x, int y, Local& L) {
     const double inv2 = 1.0 / (2.0 * p.dX);
+    const bool removed = in_hole(p.hole, x, y);  // reads as undeformed
     for (int a = 0; a < 2; ++a) {
-        L.H[2 * a] = du_fd(p, x, y, 1, 0, a) * inv2;
-        L.H[2 * a + 1] = du_fd(p, x, y, 0, 1, a) * inv2;
+        L.H[2 * a] = removed ? 0.0 : du_fd(p, x, y, 1, 0, a) * inv2;
+        L.H[2 * a + 1] = removed ? 0.0 : du_fd(p, x, y, 0, 1, a) * inv2;
     }
     const double h11 = L.H[0], h12 = L.H[1], h21 = L.H[2], h22 = L.H[3];
     const double jm1 = h11 + h22 + (h11 * h22 - h12 * h21);
@@ -155,6 +162,7 @@ __global__ void __launch_bounds__(kDiagThreads) diag_partial_kernel(const Readou
     for (int64_t id = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; id < N;
          id += int64_t(gridDim.x) * blockDim.x) {
         const int x = int(id % p.nx), y = int(id / p.nx);
+        if (in_hole(p.hole, x, y)) continue;  // not part of the body
         Local L;
         local_state(p, x, y, L);
         const double j0 = p.rho0 * p.fields[2 * N + id], j1 = p.rho0 * p.fields[3 * N + id];

@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(NT, MINB) batch_step_kernel(const __grid_const
     // the group's tile records follow
     EdgeNow<TC, UT>* s_edge = reinterpret_cast<EdgeNow<TC, UT>*>(su + 2 * NT);
     EdgeTile* s_tiles = reinterpret_cast<EdgeTile*>(su + 4 * NT);
-    static_assert(4 * sizeof(EdgeNow<TC, UT>) <= 2 * NT * sizeof(UT), "edge data fits after the u* rows");
+    static_assert(5 * sizeof(EdgeNow<TC, UT>) <= 2 * NT * sizeof(UT), "edge data fits after the u* rows");
     static_assert(kEdgeGroup * sizeof(EdgeTile) <= 2 * NT * sizeof(UT), "tile records fit in the last u* rows");
     const int t = int(threadIdx.x);
     for (;;) {

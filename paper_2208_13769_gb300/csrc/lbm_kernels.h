@@ -101,6 +101,7 @@ struct ReadoutParams {
     double dX, lambda, mu, rho0, t;
     const double* fields;  // 5 planes [ny][nx]: u_x, u_y, v_x, v_y, r
     EdgeBC bc[4];
+    int32_t hole[4];  // removed nodes of a hole (x0 >= x1: none)
 };
 
 // Writes the fields selected by mask (LBM_FIELD_* bits) into out, each block

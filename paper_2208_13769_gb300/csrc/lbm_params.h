@@ -67,7 +67,17 @@ struct StepParams {
     // lat_f holds the same values rounded to FP32
     double lat_d[16];
     float lat_f[16];
+    // a rectangular hole (Sec. 7's plate with a hole): removed nodes x0 <= x
+    // < x1, y0 <= y < y1 (x0 >= x1: none), and the constant traction on its
+    // faces at x0, x1, y0, y1 (x and y components)
+    int32_t hole[4];
+    double hole_T[8];
 };
+
+// (x, y) is a removed node of the hole.
+__host__ __device__ inline bool in_hole(const int32_t* h, int x, int y) {
+    return x >= h[0] && x < h[1] && y >= h[2] && y < h[3];
+}
 
 // Indices into StepParams::lat_d / lat_f.
 enum LatIndex : int {

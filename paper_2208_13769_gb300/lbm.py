@@ -74,6 +74,7 @@ _SIGNATURES = {
     "lbm_set_boundary": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "lbm_set_hole": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "lbm_profile_steps": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
     "lbm_profile_interior": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
     "lbm_fields_size": (C.c_int64, [C.c_void_p, C.c_uint32]),
@@ -309,6 +310,16 @@ def lbm_selftest_bounded_wait(polls: int, stream: int = 0) -> int:
     return int(out.value)
 
 
+def lbm_set_hole(ctx, hole, traction=None):
+    """A rectangular hole (x0, x1, y0, y1) of removed nodes; traction: four
+    (Tx, Ty) pairs for its faces at x0, x1, y0, y1 (None: traction-free)."""
+    h = (C.c_int32 * 4)(*[int(v) for v in hole])
+    t = None
+    if traction is not None:
+        t = (C.c_double * 8)(*[float(v) for pair in traction for v in pair])
+    _check(lib().lbm_set_hole(ctx, h, t), "lbm_set_hole")
+
+
 def lbm_set_tuning(ctx, tuning: "lbm_tuning"):
     return _check(lib().lbm_set_tuning(ctx, C.byref(tuning)), "lbm_set_tuning")
 
@@ -409,6 +420,8 @@ class Body:
         lbm_set_material(self.ctx, prob.lam, prob.mu, prob.rho0, prob.omega, prob.body)
         for k, e in enumerate(prob.edges):
             lbm_set_boundary(self.ctx, k, e.kind, e.value, e.rate, e.times)
+        if getattr(prob, "hole", None) is not None:
+            lbm_set_hole(self.ctx, prob.hole, prob.hole_traction)
 
     def step(self, n: int) -> None:
         lbm_step(self.ctx, n)

@@ -81,3 +81,9 @@ def test_injected_allocation_failure_is_reported_before_any_cuda_call(monkeypatc
     d.nx, d.ny, d.dX = 16, 16, 1.0
     h = C.c_void_p()
     assert L.lbm_create(C.byref(d), C.byref(h)) == lbm.LBM_E_OOM and not h.value
+
+
+def test_set_hole_rejects_null_arguments_without_touching_the_gpu():
+    L = lbm.lib()
+    hole = (C.c_int32 * 4)(4, 8, 4, 8)
+    assert L.lbm_set_hole(None, hole, None) == lbm.LBM_E_INVALID

@@ -1,0 +1,144 @@
+"""A body with a rectangular hole (Sec. 7's plate with a square hole; the
+hole's faces under the boundary rules of Sec. 6, reading R16) on the GPU:
+element by element against the FP64 oracle, the loaded-hole patch test,
+batches with holed members bit-identical to stepping them alone, and the
+argument checks of lbm_set_hole."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_13769_gb300 import lbm
+from paper_2208_13769_gb300 import workloads as W
+from parity_util import compare, run_both
+
+pytestmark = pytest.mark.gpu
+
+Pp, D0, N0 = W.Edge(W.PERIODIC), W.Edge(W.DIRICHLET), W.Edge(W.NEUMANN)
+ramp = W.Edge(W.NEUMANN, value=(0.0, 0.0), rate=(0.0, 0.01), times=(0.0, 2.0, 1e9))
+LOADED = [(0.004, 0.0), (-0.003, 0.001), (0.0, 0.002), (0.001, -0.004)]
+
+
+def _cases():
+    return {
+        # hole bands, edge bands and four interior rectangles
+        "clamped_40x30": (dataclasses.replace(
+            W.smooth_random(40, 30, W.clamped_free_edges(), seed=41, amp=0.01, vamp=0.004, lam=0.3, mu=0.3),
+            hole=(10, 18, 8, 16)), 200),
+        # a periodic body with loaded hole faces
+        "periodic_48x40_loaded": (dataclasses.replace(
+            W.smooth_random(48, 40, [Pp] * 4, seed=42, amp=0.01, lam=0.3, mu=0.3), hole=(12, 30, 10, 22),
+            hole_traction=LOADED), 200),
+        # periodic along x, walls along y with a ramped traction
+        "mixed_60x37": (dataclasses.replace(
+            W.smooth_random(60, 37, [Pp, Pp, D0, ramp], seed=43, amp=0.01, lam=0.3, mu=0.3),
+            hole=(20, 33, 12, 22)), 200),
+        # one-node-wide interior rectangles around the hole's band (the small
+        # bodies ring down: their velocity falls by orders of magnitude, so
+        # their horizons stop while it is still of its initial order, where
+        # a relative FP64 error of v is rounding, not its shrinking norm)
+        "thin_14x14": (dataclasses.replace(
+            W.smooth_random(14, 14, [N0, D0, N0, N0], seed=44, amp=0.01, lam=0.3, mu=0.3), hole=(5, 9, 5, 9)), 100),
+        # an odd-sized body, the hole's lower band across two rows of the
+        # wide tiles a body without a hole is initialised with
+        "thin_15x15": (dataclasses.replace(
+            W.smooth_random(15, 15, [D0, N0, N0, N0], seed=49, amp=0.01, lam=0.3, mu=0.3), hole=(5, 10, 5, 10)), 150),
+        # too small for the interior kernel: every node in edge tiles
+        "small_11x11": (dataclasses.replace(
+            W.smooth_random(11, 11, [N0, N0, D0, N0], seed=50, amp=0.01, lam=0.3, mu=0.3), hole=(4, 7, 4, 7)), 60),
+        # the hole's band meets the edge bands: no interior rectangle
+        "bands_only_12x12": (dataclasses.replace(
+            W.smooth_random(12, 12, [N0] * 4, seed=45, amp=0.01, lam=0.3, mu=0.3), hole=(4, 8, 4, 8)), 150),
+        # Sec. 7's plate with a hole (80 x 80 nodes, hole 0.4 l) at a load it
+        # stays stable under
+        "plate_80_hole": (W.plate_with_hole(80, T=0.02), 208),
+    }
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp64_holed_body_matches_the_oracle(name, scheme):
+    prob, steps = CASES[name]
+    ref, got = run_both(prob, steps, storage="f64", scheme=scheme, chunks=[1, steps - 1])
+    assert got["status"] == lbm.LBM_OK
+    compare(ref, got, 1e-12, keys=("u", "v", "P", "Pbar", "J", "sigma"))
+    compare(ref, got, 1e-12, keys=("r",), prob=prob)
+    m = prob.active()
+    assert np.all(got["u"][~m] == 0) and np.all(got["J"][~m] == 1)  # removed nodes read as undeformed
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp32_holed_body_matches_the_oracle(name):
+    prob, steps = CASES[name]
+    ref, got = run_both(prob, steps, storage="f32")
+    assert got["status"] == lbm.LBM_OK
+    compare(ref, got, 1e-5, keys=("u", "v", "P"))
+
+
+def test_loaded_hole_patch_test_stays_static_on_the_gpu():
+    """Affine u = H0 X, every edge and every face of the hole loaded by
+    T* = P(I + H0) N: the body stays at rest (FP64)."""
+    H0 = np.array([[0.02, 0.01], [-0.015, 0.03]])
+    P, _ = oracle.piola(H0, 1.0, 1.0)
+    T = [tuple(P @ np.array(n)) for n in ([-1, 0], [1, 0], [0, -1], [0, 1])]
+    TH = [tuple(P @ np.array(n)) for n in ([1, 0], [-1, 0], [0, 1], [0, -1])]
+    p = dataclasses.replace(W.affine_patch(40, 36, H0, tractions=T), hole=(12, 26, 10, 24), hole_traction=TH)
+    m = p.active()
+    with lbm.Body(p, storage="f64") as b:
+        b.step(1)
+        o0 = b.read()
+        b.step(400)
+        o = b.read()
+    assert np.abs(o["u"] - o0["u"])[m].max() < 1e-11
+    assert np.abs(o["v"])[m].max() < 1e-12
+    np.testing.assert_allclose(o["P"].reshape(-1, 2, 2)[m.ravel()], np.broadcast_to(P, (p.nodes, 2, 2)), atol=1e-11)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+def test_batch_with_holed_members_is_bitwise_the_single_body_step(storage):
+    members = [CASES[k][0] for k in ("clamped_40x30", "periodic_48x40_loaded", "thin_14x14", "bands_only_12x12")]
+    members.append(W.smooth_random(50, 30, W.clamped_free_edges(), seed=46, amp=0.01, lam=0.3, mu=0.3))
+    keys = lbm.LBM_FIELD_U | lbm.LBM_FIELD_V | lbm.LBM_FIELD_R | lbm.LBM_FIELD_P
+    alone = []
+    for p in members:
+        with lbm.Body(p, storage=storage) as b:
+            b.step(140)
+            alone.append(b.read(keys))
+    bodies = [lbm.Body(p, storage=storage) for p in members]
+    try:
+        with lbm.Batch(bodies) as batch:
+            batch.step(140)
+            assert all(st == lbm.LBM_OK for st in batch.sync())
+        for k, b in enumerate(bodies):
+            got = b.read(keys)
+            for key in ("u", "v", "r", "P"):
+                assert np.array_equal(got[key], alone[k][key]), (k, key)
+    finally:
+        for b in bodies:
+            b.close()
+
+
+def test_set_hole_checks_its_arguments():
+    p = W.smooth_random(40, 30, W.clamped_free_edges(), seed=47, amp=0.01, lam=0.3, mu=0.3)
+    with lbm.Body(p, storage="f32") as b:
+        for bad in ((3, 10, 8, 16), (10, 37, 8, 16), (10, 18, 3, 16), (10, 18, 8, 27), (10, 10, 8, 16),
+                    (18, 10, 8, 16)):
+            with pytest.raises(lbm.LbmError) as e:
+                lbm.lbm_set_hole(b.ctx, bad)
+            assert e.value.status == lbm.LBM_E_INVALID, bad
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_set_hole(b.ctx, (10, 18, 8, 16), [(float("nan"), 0.0)] + [(0.0, 0.0)] * 3)
+        lbm.lbm_set_hole(b.ctx, (4, 36, 4, 26))  # the widest hole this body allows
+        b.step(2)
+        with pytest.raises(lbm.LbmError) as e:  # too late: the context has run
+            lbm.lbm_set_hole(b.ctx, (10, 18, 8, 16))
+        assert e.value.status == lbm.LBM_E_STATE
+    q = W.smooth_random(40, 30, W.all_periodic(), seed=48, amp=0.01, lam=0.3, mu=0.3)
+    with lbm.Body(q, storage="f32") as b:  # periodic axes keep 5 nodes from the seams
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_set_hole(b.ctx, (4, 20, 8, 16))
+        lbm.lbm_set_hole(b.ctx, (5, 35, 5, 25))
