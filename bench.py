@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--form-steps", type=int, default=500)
     ap.add_argument("--c3-steps", type=int, default=1000,
                     help="steps of the 8192 x 8192 16-bit storage run (0 to skip)")
+    ap.add_argument("--hole-steps", type=int, default=500,
+                    help="steps of the 4096 x 4096 plate with a hole (0 to skip)")
     ap.add_argument("--batch", type=int, default=256,
                     help="bodies of the batched workload (seeded, sides 64..1024; 0 to skip)")
     ap.add_argument("--batch-steps", type=int, default=256)
@@ -445,6 +447,25 @@ def run_native(a):
                       "u_rel_err_vs_f64_512x512": float(np.linalg.norm(ds) / np.linalg.norm(u64[::16, ::16]))}
         del u64
 
+    # the plate with a square hole of Sec. 7 (hole 0.4 l, traction along x2 on
+    # top and bottom) at 4096 x 4096 nodes: four interior rectangles around
+    # the hole and the bands of the edges and of the hole per step
+    hole = None
+    if a.hole_steps > 0 and world == 1:
+        from paper_2208_13769_gb300 import workloads as W
+
+        plate = W.plate_with_hole(4096, T=0.02, t_off=math.inf)
+        b = lbm.Body(plate, storage=a.storage, compensated=a.compensated, stream=stream.cuda_stream, device=local)
+        _, pbpn = lbm.lbm_memory_info(b.ctx)
+        b.step(a.warmup)
+        s = time_steps(b, stream, a.hole_steps)
+        st = b.read(lbm.LBM_FIELD_U, allow_unstable=True)["status"]
+        b.close()
+        ach = pbpn * plate.nodes / (s / a.hole_steps) / 1e9
+        hole = {"workload": "plate with a centred square hole (0.4 l), 4096 x 4096 nodes, traction 0.02 mu along x2",
+                "nodes": plate.nodes, "steps": a.hole_steps, "mlups": plate.nodes * a.hole_steps / s / 1e6,
+                "achieved_gbs": ach, "frac": ach / peak, "stable": st == lbm.LBM_OK}
+
     # batched workload: many uneven bodies advanced by shared launches, and
     # the same bodies stepped one after another
     batched = None
@@ -577,7 +598,7 @@ def run_native(a):
         "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "f16": "f16", "bf16": "bf16"}[a.storage],
         "data": "synthetic", "config": config_of(a, prob), "roofline": roof, "cpu_baseline": cpu,
-        "e2e": e2e, "gpu_launches": 2 * a.steps, "clocks": clk, "forms": forms, "c3_8192": c3, "batched": batched,
+        "e2e": e2e, "gpu_launches": 2 * a.steps, "clocks": clk, "forms": forms, "c3_8192": c3, "plate_hole": hole, "batched": batched,
         "serving": serving, "tuning": tuning_info,
         "status": lbm.status_string(status),
     }

@@ -87,3 +87,16 @@ def test_set_hole_rejects_null_arguments_without_touching_the_gpu():
     L = lbm.lib()
     hole = (C.c_int32 * 4)(4, 8, 4, 8)
     assert L.lbm_set_hole(None, hole, None) == lbm.LBM_E_INVALID
+
+
+def test_measurement_and_batch_tuning_calls_reject_bad_arguments_without_touching_the_gpu():
+    L = lbm.lib()
+    out = (C.c_double * 4)()
+    assert L.lbm_profile_interior(None, 10, out) == lbm.LBM_E_INVALID
+    t, ms = lbm.lbm_tuning(), C.c_double()
+    assert L.lbm_batch_autotune(None, 1, 16, C.byref(t), C.byref(ms)) == lbm.LBM_E_INVALID
+    arr = (C.c_void_p * 1)(None)
+    assert L.lbm_batch_autotune(arr, 1, 16, C.byref(t), C.byref(ms)) == lbm.LBM_E_INVALID  # NULL member
+    assert L.lbm_batch_autotune(arr, 0, 16, C.byref(t), C.byref(ms)) == lbm.LBM_E_INVALID
+    h = C.c_void_p()
+    assert L.lbm_batch_create_tuned(arr, 1, None, C.byref(t), C.byref(h)) == lbm.LBM_E_INVALID
