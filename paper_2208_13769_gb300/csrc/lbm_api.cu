@@ -205,7 +205,6 @@ static cudaError_t build_plan(lbm_ctx* c) {
         c->i_ring = c->tune_ring ? c->tune_ring : kInteriorRing;
         const int per_sm = std::max(1, interior_occupancy(c->fmt, c->i_ring));
         const int64_t slots = int64_t(c->num_sms) * per_sm;
-        const int64_t total = std::max<int64_t>(1, interior_nodes(c));
         for (int q = 0; q < c->n_irect; ++q) {
             const int* r = c->irect[q];
             const int h = r[3] - r[2];
@@ -215,10 +214,9 @@ static cudaError_t build_plan(lbm_ctx* c) {
             if (c->tune_chunk > 0) {
                 rows = c->tune_chunk;
             } else {
-                // one wave of equal CTAs: strips x chunks <= the rectangle's
-                // share of SMs x per_sm
-                const int64_t share = std::max<int64_t>(1, slots * (int64_t(r[1] - r[0]) * h) / total);
-                const int64_t chunks = std::max<int64_t>(1, share / c->i_tiles_x[q]);
+                // one wave of equal CTAs per launch: strips x chunks <= SMs x
+                // per_sm (the rectangles' launches run one after another)
+                const int64_t chunks = std::max<int64_t>(1, slots / c->i_tiles_x[q]);
                 rows = std::max<int64_t>((h + chunks - 1) / chunks, 16);
             }
             rows = std::min<int64_t>(rows, h);
@@ -277,7 +275,7 @@ static cudaError_t launch_band_part(lbm_ctx* c, int parity, bool fields, cudaStr
     L.params = c->dparams + parity;
     L.tiles = c->dtiles;
     L.fields = fields ? 1 : 0;
-    return launch_edge(c->fmt, L, c->n_etiles, st, 0);
+    return launch_edge(c->fmt, L, c->n_etiles, st, 0, c->hole[0] < c->hole[1]);
 }
 
 // Launches of one time step (mode 0) or the initialisation (mode 1).
@@ -288,7 +286,7 @@ static cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int pa
         L.params = c->dparams + parity;
         L.tiles = c->dtiles;
         L.fields = fields ? 1 : 0;
-        return launch_edge(c->fmt, L, c->n_itiles, c->stream, 1);
+        return launch_edge(c->fmt, L, c->n_itiles, c->stream, 1, true);
     }
     if (mode == 1) {
         EdgeLaunch L;
@@ -303,7 +301,7 @@ static cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int pa
         L.rtiles_x = (c->nx + 27) / 28;
         const int64_t ntiles = int64_t(L.rtiles_x) * ((c->ny + 3) / 4);
         if (ntiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
-        return launch_edge(c->fmt, L, int(ntiles), c->stream, 1);
+        return launch_edge(c->fmt, L, int(ntiles), c->stream, 1, true);
     }
     if (!c->has_interior) return launch_band_part(c, parity, fields, c->stream);
     // interior first on the main stream, then the edge tiles on the side

@@ -52,6 +52,7 @@ struct lbm_batch {
     int grid = 0;                // persistent CTAs
     int chunk_rows = 0;
     int ring = kBatchRing;
+    bool holed = false;           // some member has a hole
     int64_t steps = 0;
     bool warm = false;
     bool sticky = false;
@@ -95,7 +96,7 @@ cudaError_t batch_launch(lbm_batch* b, int q, bool fields) {
     L.queue = b->dqueue;
     L.fields = fields ? 1 : 0;
     L.nitems = b->n_items;
-    return launch_batch_step(b->fmt, L, b->grid, b->ring, b->stream, nullptr);
+    return launch_batch_step(b->fmt, L, b->grid, b->ring, b->stream, nullptr, b->holed);
 }
 
 void advance_members(lbm_batch* b, int64_t k) {
@@ -200,7 +201,10 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
     // interior tiles: rows per chunk so that the batch holds about eight
     // waves of resident CTAs (at least 32 rows, at most 256)
     int64_t all_interior = 0;
-    for (lbm_ctx* c : b->m) all_interior += interior_nodes(c);
+    for (lbm_ctx* c : b->m) {
+        all_interior += interior_nodes(c);
+        b->holed = b->holed || c->hole[0] < c->hole[1];
+    }
     b->ring = tuning && tuning->ring_slots ? tuning->ring_slots : kBatchRing;
     const int64_t wave = int64_t(b->m[0]->num_sms) * std::max(1, interior_occupancy(b->fmt, b->ring));
     b->chunk_rows = tuning && tuning->chunk_rows
@@ -324,7 +328,7 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
         BatchLaunch L;
         memset(&L, 0, sizeof(L));
         int resident = 0;
-        e = launch_batch_step(b->fmt, L, 0, b->ring, b->stream, &resident);
+        e = launch_batch_step(b->fmt, L, 0, b->ring, b->stream, &resident, b->holed);
         b->grid = int(std::min<int64_t>(int64_t(items.size()), int64_t(b->m[0]->num_sms) * std::max(1, resident)));
     }
     if (e != cudaSuccess) {
@@ -455,6 +459,8 @@ lbm_status lbm_batch_autotune(lbm_ctx* const* members, int32_t n, int64_t steps,
         if (status == LBM_OK) status = lbm_set_material(scratch[size_t(i)], 0.3, 0.3, 1.0, 1.0, nullptr);
         for (int e = 0; e < 4 && status == LBM_OK; ++e)
             status = lbm_set_boundary(scratch[size_t(i)], e, c->bc[e].kind, nullptr, nullptr, nullptr);
+        if (status == LBM_OK && c->hole[0] < c->hole[1])  // the same plan: bands around the hole
+            status = lbm_set_hole(scratch[size_t(i)], c->hole, c->hole_T);
     }
     // candidates: ring depth x rows per interior tile (0: the default)
     const int rings[3] = {4, 5, 6};

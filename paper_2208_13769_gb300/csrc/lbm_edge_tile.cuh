@@ -66,8 +66,8 @@ __device__ __forceinline__ TC abb_value(int i, TC fci, int sx, int sy, TC inv_le
 // Links of node (gx, gy) that leave the body through a bounded edge: the
 // boundary rules of Sec. 6, written into the first ghost row/column.  fc:
 // the node's post-collision populations; r, pxx, pxy, pyy: its moments;
-// q: its Q = P + Pbar.
-template <class TS, class TC, class UT>
+// q: its Q = P + Pbar.  HOLE: links may also enter a hole.
+template <class TS, class TC, class UT, bool HOLE>
 __device__ __noinline__ void boundary_links(TS* fdst, Geo g, const StepParams& p, const EdgeNow<TC, UT>* s_edge,
                                             int gx, int gy, Pops<TC> fc, TC r, TC pxx, TC pxy, TC pyy, TC q11,
                                             TC q12, TC q21, TC q22, TC inv_c2) {
@@ -75,7 +75,7 @@ __device__ __noinline__ void boundary_links(TS* fdst, Geo g, const StepParams& p
 #pragma unroll 1
     for (int i = 1; i < 9; ++i) {
         const int dx = gx + ex(i), dy = gy + ey(i);
-        if (in_hole(p.hole, dx, dy)) {
+        if (HOLE && in_hole(p.hole, dx, dy)) {
             // Eq. (abbcon) across the face of the hole the link crosses, or
             // both faces at the hole's corner
             const bool cx = ex(i) != 0 && in_hole(p.hole, gx + ex(i), gy);
@@ -145,9 +145,10 @@ __device__ __noinline__ void boundary_links(TS* fdst, Geo g, const StepParams& p
 // beyond tw x th idle through the barriers).  Shared memory: su holds 2 x
 // tw x th u-carry values, sq 4 x tw x th arithmetic values, sinit (mode 1)
 // 4 x tw x th, s_edge the boundary data of the 4 edges and of a hole's faces
-// (5 entries).  want_fields: also write
-// u, v, r to p.fields.
-template <class TS, class TC, class UT, int MODE>
+// (5 entries).  want_fields: also write u, v, r to p.fields.  HOLE: the
+// body may have a hole (false: p.hole is not read, and the tile's code
+// carries none of the hole's tests).
+template <class TS, class TC, class UT, int MODE, bool HOLE>
 __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepParams& p, bool want_fields, UT* su,
                                                TC* sq, TC* sinit, EdgeNow<TC, UT>* s_edge) {
     using CT = typename UT::Elem;
@@ -191,18 +192,20 @@ __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepP
     // a node of the hole is not part of the body: it holds nothing, and the
     // cells of the hole next to its faces receive the populations the
     // anti-bounce-back rule sends back
-    const bool removed = in_hole(p.hole, gx, gy);
+    const bool holed = HOLE && p.hole[0] < p.hole[1];  // the body has a hole (uniform)
+    const bool removed = holed && in_hole(p.hole, gx, gy);
     const bool inA = okx && oky && ty < th && !removed;
     const bool inB = inA && tx >= 1 && tx <= nxo + 2 && ty >= 1 && ty <= nyo + 2;
     const bool inC = tx >= 2 && tx < nxo + 2 && ty >= 2 && ty < nyo + 2 && !removed;
     // a removed neighbour along an axis is a face of the hole: a bounded edge
     // for the ghost rules
-    const bool hxl = in_hole(p.hole, gx - 1, gy), hxh = in_hole(p.hole, gx + 1, gy);
-    const bool hyl = in_hole(p.hole, gx, gy - 1), hyh = in_hole(p.hole, gx, gy + 1);
+    const bool hxl = holed && in_hole(p.hole, gx - 1, gy), hxh = holed && in_hole(p.hole, gx + 1, gy);
+    const bool hyl = holed && in_hole(p.hole, gx, gy - 1), hyh = holed && in_hole(p.hole, gx, gy + 1);
     const bool gxl = (!g.perx && gx == 0) || hxl, gxh = (!g.perx && gx == nx - 1) || hxh;
     const bool gyl = (!g.pery && gy == 0) || hyl, gyh = (!g.pery && gy == ny - 1) || hyh;
     // within one node of the hole (a link may enter it)
-    const bool near_hole = gx >= p.hole[0] - 1 && gx <= p.hole[1] && gy >= p.hole[2] - 1 && gy <= p.hole[3];
+    const bool near_hole =
+        holed && gx >= p.hole[0] - 1 && gx <= p.hole[1] && gy >= p.hole[2] - 1 && gy <= p.hole[3];
     // first and second inward neighbours (used only by a ghost rule)
     const int tx1 = gxl ? min(tx + 1, tw - 1) : max(tx - 1, 0);
     const int tx2 = gxl ? min(tx + 2, tw - 1) : max(tx - 2, 0);
@@ -238,12 +241,7 @@ __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepP
     }
     if (tile.lead && t == 0) p.counter[p.parity ^ 1] = n_now;
     if (t < 4) edge_now<TC, UT>(s_edge[t], p.bc[t], double(n_now) * p.dt, p.lat_d[kLatRho0OverC]);
-    if (t == 4) {  // the faces of a hole: Neumann (only the kind is read)
-        EdgeBC hole_bc;
-        memset(&hole_bc, 0, sizeof(hole_bc));
-        hole_bc.kind = kNeumann;
-        edge_now<TC, UT>(s_edge[4], hole_bc, 0.0, p.lat_d[kLatRho0OverC]);
-    }
+    if (HOLE && t == 4) s_edge[4].kind = kNeumann;  // the faces of a hole (only the kind is read)
     __syncthreads();
 
     // ---------------- stage B: H = Grad u*, Q = P(F) + Pbar(H)
@@ -396,7 +394,7 @@ __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepP
             Pops<TC> pc;
 #pragma unroll
             for (int i = 0; i < 9; ++i) pc.v[i] = fc[i];
-            boundary_links<TS, TC, UT>(fdst, g, p, s_edge, gx, gy, pc, r, pxx, pxy, pyy, qr[0], qr[tw], qr[2 * tw],
+            boundary_links<TS, TC, UT, HOLE>(fdst, g, p, s_edge, gx, gy, pc, r, pxx, pxy, pyy, qr[0], qr[tw], qr[2 * tw],
                                        qr[3 * tw], k.inv_c2);
         }
 

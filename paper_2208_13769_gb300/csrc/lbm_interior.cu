@@ -407,7 +407,9 @@ __global__ void __launch_bounds__(NT, MINB) interior_step_kernel(const __grid_co
 // tile records after the u* rows it needs).  The queue {next item, CTAs
 // done} is zero when the launch starts; the last CTA to finish sets it back
 // to zero.
-template <class TS, class TC, class UT, int NT, int MINB>
+// HOLE: some member has a hole (the edge tiles test for it; a batch without
+// one runs tiles that carry none of the hole's tests).
+template <class TS, class TC, class UT, int NT, int MINB, bool HOLE>
 __global__ void __launch_bounds__(NT, MINB) batch_step_kernel(const __grid_constant__ BatchLaunch L) {
     __shared__ __align__(16) StepParams sp;
     __shared__ BatchItem s_item;
@@ -446,7 +448,7 @@ __global__ void __launch_bounds__(NT, MINB) batch_step_kernel(const __grid_const
         } else {
             for (int g = 0; g < it.b; ++g) {
                 if (g > 0) __syncthreads();  // the previous tile is done with the shared buffers
-                edge_tile_body<TS, TC, UT, 0>(s_tiles[g], sp, L.fields != 0, su, sq, nullptr, s_edge);
+                edge_tile_body<TS, TC, UT, 0, HOLE>(s_tiles[g], sp, L.fields != 0, su, sq, nullptr, s_edge);
             }
         }
     }
@@ -479,9 +481,9 @@ cudaError_t launch_interior_t(const StepParams& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <class TS, class TC, class UT, int NT, int MINB>
-cudaError_t launch_batch_step_t(const BatchLaunch& L, int grid, int ring_slots, cudaStream_t s, int* resident) {
-    auto kern = batch_step_kernel<TS, TC, UT, NT, MINB>;
+template <class TS, class TC, class UT, int NT, int MINB, bool HOLE>
+cudaError_t launch_batch_step_h(const BatchLaunch& L, int grid, int ring_slots, cudaStream_t s, int* resident) {
+    auto kern = batch_step_kernel<TS, TC, UT, NT, MINB, HOLE>;
     const size_t sm = interior_smem_bytes<TS, TC, UT, NT>(ring_slots);
     static size_t configured = 0;
     if (sm > configured) {
@@ -499,20 +501,29 @@ cudaError_t launch_batch_step_t(const BatchLaunch& L, int grid, int ring_slots, 
     return cudaGetLastError();
 }
 
+template <class TS, class TC, class UT, int NT, int MINB>
+cudaError_t launch_batch_step_t(const BatchLaunch& L, int grid, int ring_slots, cudaStream_t s, int* resident,
+                                bool holed) {
+    return holed ? launch_batch_step_h<TS, TC, UT, NT, MINB, true>(L, grid, ring_slots, s, resident)
+                 : launch_batch_step_h<TS, TC, UT, NT, MINB, false>(L, grid, ring_slots, s, resident);
+}
+
 // Six CTAs per SM (the interior tile's shared memory allows six with the
 // default ring): the edge tile's code would otherwise take more registers.
-cudaError_t launch_batch_step(int fmt, const BatchLaunch& L, int grid, int ring_slots, cudaStream_t s,
-                              int* resident) {
+cudaError_t launch_batch_step(int fmt, const BatchLaunch& L, int grid, int ring_slots, cudaStream_t s, int* resident,
+                              bool holed) {
     constexpr int NT = kInteriorThreads;
     switch (fmt) {
         case kFmtF64:
-            return launch_batch_step_t<double, double, UPlain<double>, NT, 2>(L, grid, ring_slots, s, resident);
+            return launch_batch_step_t<double, double, UPlain<double>, NT, 2>(L, grid, ring_slots, s, resident, holed);
         case kFmtF32:
-            return launch_batch_step_t<float, float, UPlain<float>, NT, 6>(L, grid, ring_slots, s, resident);
-        case kFmtF32C: return launch_batch_step_t<float, float, UComp, NT, 6>(L, grid, ring_slots, s, resident);
-        case kFmtF16: return launch_batch_step_t<__half, float, UComp, NT, 6>(L, grid, ring_slots, s, resident);
+            return launch_batch_step_t<float, float, UPlain<float>, NT, 6>(L, grid, ring_slots, s, resident, holed);
+        case kFmtF32C:
+            return launch_batch_step_t<float, float, UComp, NT, 6>(L, grid, ring_slots, s, resident, holed);
+        case kFmtF16:
+            return launch_batch_step_t<__half, float, UComp, NT, 6>(L, grid, ring_slots, s, resident, holed);
         case kFmtBF16:
-            return launch_batch_step_t<__nv_bfloat16, float, UComp, NT, 6>(L, grid, ring_slots, s, resident);
+            return launch_batch_step_t<__nv_bfloat16, float, UComp, NT, 6>(L, grid, ring_slots, s, resident, holed);
     }
     return cudaErrorInvalidValue;
 }

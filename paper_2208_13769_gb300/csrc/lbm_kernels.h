@@ -61,9 +61,10 @@ struct BatchLaunch {
 // A persistent grid of `grid` CTAs runs the items.  The setting of the
 // dynamic shared-memory limit happens on the first call (also with grid ==
 // 0), which must precede any stream capture; resident (may be NULL) receives
-// the kernel's CTAs per SM with this ring.
-cudaError_t launch_batch_step(int fmt, const BatchLaunch& L, int grid, int ring_slots, cudaStream_t s,
-                              int* resident);
+// the kernel's CTAs per SM with this ring.  holed: some member has a hole
+// (the kernel variant whose edge tiles handle one).
+cudaError_t launch_batch_step(int fmt, const BatchLaunch& L, int grid, int ring_slots, cudaStream_t s, int* resident,
+                              bool holed);
 
 // The edge kernel (lbm_edge.cu): small 2-D tiles with every boundary rule.
 // A tile's threads cover its output nodes and a 2-node halo: tw x th nodes
@@ -87,7 +88,7 @@ struct EdgeLaunch {
 };
 
 // One step (mode 0) or the initialisation (mode 1) over ntiles tiles.
-cudaError_t launch_edge(int fmt, const EdgeLaunch& L, int ntiles, cudaStream_t s, int mode);
+cudaError_t launch_edge(int fmt, const EdgeLaunch& L, int ntiles, cudaStream_t s, int mode, bool holed);
 
 // Tiles of one band rectangle for CTAs of `nthreads` threads (kEdgeThreads
 // for the edge kernel, kInteriorThreads for the batch kernel); count only
