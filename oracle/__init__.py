@@ -14,7 +14,9 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
   Solver              -- pinned by conservation, exact shear-wave solution and
                           second-order convergence, longitudinal-wave frequency,
                           patch tests (Neumann, rigid rotation, Dirichlet), the
-                          printed time steps of Sec. 7.  Large-strain clamped
+                          printed time steps of Sec. 7; the extrapolated
+                          scheme by the order of its one-step miss of the
+                          implicit moment.  Large-strain clamped
                           bodies have no closed form: beyond those pins their
                           parity is unpinned.
 """
@@ -35,7 +37,7 @@ _lock = threading.Lock()
 _lib = None
 
 PERIODIC, DIRICHLET, NEUMANN = 0, 1, 2
-EXPLICIT, PREDICTOR = 0, 1
+EXPLICIT, PREDICTOR, EXTRAPOLATED = 0, 1, 2
 
 
 class OracleProblem(C.Structure):
@@ -201,8 +203,9 @@ def make_problem(nx, ny, dX, lam, mu, rho0, omega, body, edges,
                  scheme: int = PREDICTOR, hole=None, hole_traction=None) -> OracleProblem:
     """edges: four dicts {kind, value, rate, times} in order x-, x+, y-, y+.
 
-    scheme: EXPLICIT (Algorithm 1's time-t source in collision and moment) or
-    PREDICTOR (the footnote's predictor-corrector for u).
+    scheme: EXPLICIT (Algorithm 1's time-t source in collision and moment),
+    PREDICTOR (the footnote's predictor-corrector for u) or EXTRAPOLATED
+    (Sec. 5's linear extrapolation of j to t + dt for the moment's source).
     hole: (x0, x1, y0, y1), the removed nodes of a rectangular hole, or None;
     hole_traction: the constant traction on its faces at x0, x1, y0, y1 (four
     pairs; None: traction-free)."""

@@ -80,6 +80,12 @@
  *       that enters the hole through it; a diagonal link that enters the hole
  *       through its corner takes N = (N1 + N2)/sqrt(2) and
  *       T* = (T1 + T2)/sqrt(2), as at the body's corners (R10).
+ *   R17 Scheme 2 (EXTRAPOLATED) is the variant Sec. 5 gives for an O(dt^3)
+ *       error: j(t+dt) is extrapolated linearly from j(t) and j(t-dt), the
+ *       trapezoidal rule turns it into u(t+dt), and 1S(t+dt) from that u
+ *       enters the moment; as in R14, that source is also the next
+ *       collision's, and the step's stresses and wall values are those of the
+ *       extrapolated u.  The first step has no j(-dt): it takes j(-dt) = j(0).
  */
 #include <math.h>
 #include <stdint.h>
@@ -94,6 +100,7 @@
 #define ORC_NEUMANN 2
 #define ORC_EXPLICIT 0
 #define ORC_PREDICTOR 1
+#define ORC_EXTRAPOLATED 2
 
 /* Problem statement (Sec. 4 moment chain, Sec. 6 boundary conditions,
  * Sec. 7 material).  Edge order: 0 = x-, 1 = x+, 2 = y-, 3 = y+.
@@ -111,7 +118,7 @@ typedef struct {
     double value[4][2];
     double rate[4][2];
     double times[4][3];
-    int32_t scheme; /* 0 = EXPLICIT (Algorithm 1), 1 = PREDICTOR (R14) */
+    int32_t scheme; /* 0 = EXPLICIT (Algorithm 1), 1 = PREDICTOR (R14), 2 = EXTRAPOLATED (R17) */
     int32_t hole[4];   /* x0, x1, y0, y1 of a removed rectangle (R16); x0 >= x1: none */
     double hole_T[4][2]; /* traction on the hole's faces: x0 face, x1 face, y0 face, y1 face */
 } orc_problem;
@@ -124,7 +131,7 @@ typedef struct {
     int e[9][2];
     int opp[9];
     double *f[9], *fnew[9], *fcol[9];
-    double *r, *j[2], *jnew[2], *m[2], *u[2], *us[2], *P[4], *Pb[4], *S[2];
+    double *r, *j[2], *jnew[2], *jp[2], *m[2], *u[2], *us[2], *P[4], *Pb[4], *S[2];
     long step;
 } orc_state;
 
@@ -543,7 +550,7 @@ int orc_check(const orc_problem* p) {
         if (a < 0 || a > 2 || b < 0 || b > 2) return 5;
         if ((a == ORC_PERIODIC) != (b == ORC_PERIODIC)) return 4;
     }
-    if (p->scheme != ORC_EXPLICIT && p->scheme != ORC_PREDICTOR) return 6;
+    if (p->scheme != ORC_EXPLICIT && p->scheme != ORC_PREDICTOR && p->scheme != ORC_EXTRAPOLATED) return 6;
     if (has_hole(p)) {
         /* at least 3 body nodes between the hole and each edge or seam */
         if (p->hole[0] < 3 || p->hole[1] > p->nx - 3 || p->hole[2] < 3 || p->hole[3] > p->ny - 3) return 7;
@@ -570,6 +577,7 @@ orc_state* orc_create(const orc_problem* p, const double* u0, const double* v0) 
     for (int a = 0; a < 2; a++) {
         s->j[a] = zalloc(s->n);
         s->jnew[a] = zalloc(s->n);
+        s->jp[a] = zalloc(s->n);
         s->m[a] = zalloc(s->n);
         s->u[a] = zalloc(s->n);
         s->us[a] = zalloc(s->n);
@@ -584,6 +592,7 @@ orc_state* orc_create(const orc_problem* p, const double* u0, const double* v0) 
             const int removed = in_hole(s, (int)(id % p->nx), (int)(id / p->nx));
             s->u[a][id] = u0 && !removed ? u0[2 * id + a] : 0.0;
             s->j[a][id] = p->rho0 * (v0 && !removed ? v0[2 * id + a] : 0.0);
+            s->jp[a][id] = s->j[a][id]; /* R17: j(-dt) = j(0) */
         }
     update_stress(s, s->u, 0.0);
     int nx = p->nx, ny = p->ny;
@@ -704,6 +713,26 @@ static void step_once(orc_state* s) {
             }
         update_stress(s, s->u, t1);
         compute_source(s);
+    } else if (p->scheme == ORC_EXTRAPOLATED) {
+        /* R17: j(t+dt) extrapolated linearly from j(t) and j(t-dt), the
+         * trapezoidal u from it, and 1S(t+dt) from that u */
+#pragma omp parallel for schedule(static)
+        for (long id = 0; id < s->n; id++)
+            for (int a = 0; a < 2; a++) {
+                double je = 2.0 * s->j[a][id] - s->jp[a][id];
+                s->us[a][id] = s->u[a][id] + dt / (2.0 * p->rho0) * (je + s->j[a][id]);
+            }
+        update_stress(s, s->us, t1);
+        compute_source(s);
+        /* j(t+dt) with 1S(t+dt), trapezoidal u (R2) */
+#pragma omp parallel for schedule(static)
+        for (long id = 0; id < s->n; id++)
+            for (int a = 0; a < 2; a++) {
+                double jn = s->m[a][id] + 0.5 * dt * s->S[a][id];
+                s->u[a][id] = s->u[a][id] + dt / (2.0 * p->rho0) * (jn + s->j[a][id]);
+                s->jp[a][id] = s->j[a][id];
+                s->j[a][id] = jn;
+            }
     } else {
         /* predictor (R14): explicit j* and u*(t+dt) */
 #pragma omp parallel for schedule(static)
@@ -805,6 +834,7 @@ void orc_destroy(orc_state* s) {
     for (int a = 0; a < 2; a++) {
         free(s->j[a]);
         free(s->jnew[a]);
+        free(s->jp[a]);
         free(s->m[a]);
         free(s->u[a]);
         free(s->us[a]);

@@ -27,7 +27,9 @@ class BruteForce:
         self.dX = prob.dX
         self.b = tuple(prob.body)
         self.edges = prob.edges
-        self.scheme = scheme  # 0: source of time t in the moment; 1: predicted source
+        # 0: source of time t in the moment; 1: predicted source; 2: source of
+        # the u that j extrapolated to t + dt gives (reading R17)
+        self.scheme = scheme
         self.Cs2 = self.mu / self.rho0
         self.dt = self.dX / math.sqrt(3.0 * self.Cs2)  # Sec. 7's time step
         self.c = self.dX / self.dt
@@ -48,6 +50,7 @@ class BruteForce:
             self.Pstore[p] = (self.piola(H[p]), self.pbar(H[p]))
         self.r = {p: -self.rho0 * (H[p][0][0] + H[p][1][1]) for p in nodes}
         self.f = {p: self.feq(self.r[p], self.j[p], self.pbar(H[p])) for p in nodes}
+        self.j_before = {p: list(self.j[p]) for p in nodes}  # j one step back (none yet: j(0))
         self.S = {p: self.source(p) for p in nodes}
 
     # ---------------------------------------------------------------- pieces
@@ -258,24 +261,48 @@ class BruteForce:
                 H = self.grad(U, p, tt)
                 self.Pstore[p] = (self.piola(H), self.pbar(H))
 
-        if self.scheme == 0:
-            for p in self.nodes:
-                jn = [m[p][a] + 0.5 * dt * self.S[p][a] for a in range(2)]
-                self.u[p] = [self.u[p][a] + dt / (2 * self.rho0) * (jn[a] + self.j[p][a]) for a in range(2)]
-                self.j[p] = jn
+        def trapezoid(jn):
+            return {p: [self.u[p][a] + 0.5 * dt * (jn[p][a] + self.j[p][a]) / self.rho0 for a in range(2)]
+                    for p in self.nodes}
+
+        def moment(S):
+            return {p: [m[p][a] + 0.5 * dt * S[p][a] for a in range(2)] for p in self.nodes}
+
+        scheme = self.scheme
+        if scheme == 0:
+            jn = moment(self.S)
+            self.u = trapezoid(jn)
             stresses(self.u, t1)
             self.S = {p: self.source(p) for p in self.nodes}
+        elif scheme == 3:
+            # not a scheme of the library: the fully implicit moment the
+            # paper's Sec. 5 names as the ideal (the source of u(t + dt)
+            # itself), by fixed-point iteration
+            S = self.S
+            for _ in range(60):
+                jn = moment(S)
+                stresses(trapezoid(jn), t1)
+                S_next = {p: self.source(p) for p in self.nodes}
+                change = max(abs(S_next[p][a] - S[p][a]) for p in self.nodes for a in range(2))
+                S = S_next
+                if change == 0.0:
+                    break
+            self.S = S
+            jn = moment(S)
+            self.u = trapezoid(jn)
         else:
-            us = {}
-            for p in self.nodes:
-                jp = [m[p][a] + 0.5 * dt * self.S[p][a] for a in range(2)]
-                us[p] = [self.u[p][a] + dt / (2 * self.rho0) * (jp[a] + self.j[p][a]) for a in range(2)]
-            stresses(us, t1)
+            if scheme == 2:
+                # j at t + dt on the line through j(t - dt) and j(t); u(t + dt)
+                # by the trapezoid over [t, t + dt]
+                ahead = {p: [2 * self.j[p][a] - self.j_before[p][a] for a in range(2)] for p in self.nodes}
+            else:  # 1: the explicit j of this step
+                ahead = moment(self.S)
+            stresses(trapezoid(ahead), t1)
             self.S = {p: self.source(p) for p in self.nodes}
-            for p in self.nodes:
-                jn = [m[p][a] + 0.5 * dt * self.S[p][a] for a in range(2)]
-                self.u[p] = [self.u[p][a] + dt / (2 * self.rho0) * (jn[a] + self.j[p][a]) for a in range(2)]
-                self.j[p] = jn
+            jn = moment(self.S)
+            self.u = trapezoid(jn)
+        self.j_before = self.j
+        self.j = jn
         self.n += 1
 
     def fields(self):

@@ -37,6 +37,13 @@ MUTANTS = [
     ("hole ghost", "return 3.0 * v0 - 3.0 * v1 + v2;", "return 2.0 * v0 - v1;", 2),
     ("hole corner normal", "if (!cx && !cy) cx = cy = 1;", "if (!cx && !cy) cx = 1;", 0),
     ("hole face traction", "s->p.hole_T[ex > 0 ? 0 : 1]", "s->p.hole_T[ex > 0 ? 1 : 0]", 0),
+    # the extrapolated scheme of reading R17
+    ("extrapolation held constant", "double je = 2.0 * s->j[a][id] - s->jp[a][id];",
+     "double je = s->j[a][id];", 0),
+    ("extrapolation slope reversed", "double je = 2.0 * s->j[a][id] - s->jp[a][id];",
+     "double je = 2.0 * s->jp[a][id] - s->j[a][id];", 0),
+    ("no history before the first step", "s->jp[a][id] = s->j[a][id]; /* R17", "s->jp[a][id] = 0.0; /* R17", 0),
+    ("history not advanced", "s->jp[a][id] = s->j[a][id];\n", "s->jp[a][id] = s->jp[a][id];\n", 0),
 ]
 
 
@@ -79,5 +86,6 @@ def _disagrees(L, scheme):
 @pytest.mark.parametrize("what,old,new,occ", MUTANTS, ids=[m[0] for m in MUTANTS])
 def test_planted_mistake_is_caught(tmp_path, what, old, new, occ):
     L = _build_mutant(tmp_path, old, new, occ)
-    caught = _disagrees(L, oracle.PREDICTOR) or _disagrees(L, oracle.EXPLICIT)
+    caught = (_disagrees(L, oracle.PREDICTOR) or _disagrees(L, oracle.EXPLICIT)
+              or _disagrees(L, oracle.EXTRAPOLATED))
     assert caught is not None, f"planted mistake not caught: {what}"

@@ -166,7 +166,7 @@ def _total_momentum(o):
     return o["v"].sum(axis=(0, 1))
 
 
-@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR])
+@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR, oracle.EXTRAPOLATED])
 def test_periodic_momentum_and_mass_conserved(scheme):
     """Periodic body, b = 0: sum of j and of r are invariants of the scheme
     (collision conserves them, streaming permutes, the periodic divergence
@@ -222,7 +222,7 @@ def _freq_from_zero_crossings(t, a, w_guess=None):
     return res.x
 
 
-@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR])
+@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR, oracle.EXTRAPOLATED])
 def test_shear_wave_exact_solution_second_order(scheme):
     """u_x = A sin(ky) cos(wt), w = k sqrt(mu/rho0) solves the nonlinear
     equations exactly (simple shear: P + Pbar = 0, no source).  The lattice
@@ -268,7 +268,7 @@ def test_pwave_frequency_converges():
     assert all(1.7 < o < 2.5 for o in orders), (errs, orders)
 
 
-@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR])
+@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR, oracle.EXTRAPOLATED])
 def test_neumann_patch_test_static(scheme):
     """Affine u = H0 X, v = 0, tractions T* = P(I + H0) N on all four edges
     (corners included): the body must stay exactly at rest."""
@@ -297,12 +297,15 @@ def test_rigid_rotation_stays_put():
     assert np.abs(o["P"]).max() < 1e-10
 
 
-@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR])
+@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR, oracle.EXTRAPOLATED])
 def test_dirichlet_uniform_motion(scheme):
     """Uniform v0 with all edges moving at v* = v0 (bounce-back, Eq. bbcon):
     u = v0 t exactly, no strain."""
     v = (0.01, -0.02)
-    p = W.uniform_motion(12, 10, v)
+    # the extrapolated scheme is stable only at lambda = mu (see
+    # test_extrapolated_scheme_is_stable_only_at_lambda_eq_mu): there the
+    # rounding noise of the moving walls stays at rounding level
+    p = W.uniform_motion(12, 10, v, lam=0.3) if scheme == oracle.EXTRAPOLATED else W.uniform_motion(12, 10, v)
     s = oracle.solver_from(p, scheme)
     s.step(300)
     o = s.read()
@@ -377,7 +380,7 @@ def _tiny_cases():
     }
 
 
-@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR])
+@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR, oracle.EXTRAPOLATED])
 @pytest.mark.parametrize("name", sorted(_tiny_cases()))
 def test_oracle_matches_a_brute_force_restatement(name, scheme):
     from brute_force import BruteForce
@@ -401,7 +404,7 @@ def _holed(p, hole, traction=None):
     return dataclasses.replace(p, hole=hole, hole_traction=traction)
 
 
-@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR])
+@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR, oracle.EXTRAPOLATED])
 def test_patch_test_with_a_loaded_hole_stays_static(scheme):
     """Affine u = H0 X with T* = P(I + H0) N on the four edges and on the
     four faces of a hole (N the body's outward normal, into the hole): a
@@ -467,3 +470,75 @@ def test_plate_with_hole_small_load_is_stable_and_elongates():
         last = el
     assert 0.015 < peak < 0.04
     assert abs(last) < peak
+
+
+def _one_step_moment_deviation(n, scheme):
+    """j(t + dt) of one step of `scheme` from a mid-run state of the
+    extrapolated scheme, against the fully implicit moment of Sec. 5 (the
+    source of u(t + dt) itself, by fixed-point iteration), relative to max |j|:
+    a small-strain longitudinal wave with lambda != mu along x on an n x 4
+    periodic body."""
+    import copy
+
+    from brute_force import BruteForce
+
+    k = 2 * math.pi / n
+    u0 = np.zeros((4, n, 2))
+    u0[:, :, 0] = 1e-4 * n * np.sin(k * np.arange(n))[None, :]
+    p = W.Problem(nx=n, ny=4, lam=0.35, mu=0.3, edges=W.all_periodic(), u0=u0, v0=np.zeros_like(u0))
+    bf = BruteForce(p, oracle.EXTRAPOLATED)
+    # n / 8 steps: the same phase of the wave for every n (about 1/8 period),
+    # where j and both its first and second time derivatives are far from 0
+    for _ in range(n // 8):
+        bf.step()
+    out = {}
+    for sc in (scheme, 3):
+        b = copy.deepcopy(bf)
+        b.scheme = sc
+        b.step()
+        out[sc] = np.array([b.j[q] for q in b.nodes])
+    return np.abs(out[scheme] - out[3]).max() / np.abs(out[3]).max()
+
+
+def test_extrapolated_moment_is_third_order_in_dt():
+    """Sec. 5: the explicit moment's source (time t) misses the implicit one
+    (time t + dt) by O(dt^2) in j; with j extrapolated linearly to t + dt, the
+    trapezoidal u and its source, the miss in u is O(dt^3) and in j (half a
+    step times the source's miss) O(dt^4).  Refining n (dt proportional to dX)
+    at a fixed wavelength in lattice widths scales the physical problem, so
+    the orders are read from n = 16, 32, 64 at fixed physical time.  A wrong
+    extrapolation (constant, or the slope's sign flipped) falls to order 3."""
+    dev = {sc: [_one_step_moment_deviation(n, sc) for n in (16, 32, 64)]
+           for sc in (oracle.EXPLICIT, oracle.EXTRAPOLATED)}
+    order = {sc: [math.log2(d[i] / d[i + 1]) for i in range(2)] for sc, d in dev.items()}
+    # measured: 1.84, 1.92 and 3.79, 3.88 (a constant extrapolation: 2.6,
+    # 2.8; the slope's sign flipped: 2.8, 2.9)
+    assert all(1.7 < o < 2.3 for o in order[oracle.EXPLICIT]), (dev, order)
+    assert all(o > 3.5 for o in order[oracle.EXTRAPOLATED]), (dev, order)
+
+
+def _noise_growth(nu, scheme, steps=1000, n=16):
+    mu = 0.3
+    lam = 2 * mu * nu / (1 - 2 * nu)
+    p = W.shear_wave(n=n, amp=0.0, lam=lam, mu=mu)
+    rng = np.random.default_rng(5)
+    p.u0 = 1e-8 * rng.standard_normal((n, n, 2))
+    p.v0 = np.zeros((n, n, 2))
+    s = oracle.Solver(oracle.problem_from(p, scheme), p.u0, p.v0)
+    a = np.abs(s.read()["u"]).max()
+    s.step(steps)
+    b = np.abs(s.read()["u"]).max()
+    return b / a if np.isfinite(b) else np.inf
+
+
+def test_extrapolated_scheme_is_stable_only_at_lambda_eq_mu():
+    """The extrapolation feeds a two-step history back into the source: for
+    lambda != mu (a linear part of 1S) small random displacements on a
+    periodic body grow without bound under it, on either side of lambda = mu
+    (nu = 0.23 and 0.26), where the predictor form stays bounded; at
+    lambda = mu (nu = 1/4, the only material Sec. 7 runs) 1S has no linear
+    part and the extrapolated scheme is as stable as the others."""
+    for nu in (0.23, 0.26):
+        assert _noise_growth(nu, oracle.EXTRAPOLATED, steps=2000) > 10.0, nu
+        assert _noise_growth(nu, oracle.PREDICTOR, steps=2000) < 2.0, nu
+    assert _noise_growth(0.25, oracle.EXTRAPOLATED, steps=2000) < 2.0
