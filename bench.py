@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--forms", default="f32n,f16,bf16",
                     help="extra population formats timed on the same body ('' to skip)")
     ap.add_argument("--form-steps", type=int, default=500)
+    ap.add_argument("--schemes", default="explicit,extrapolated",
+                    help="other schemes timed on the same body, FP32 + compensated carry ('' to skip)")
     ap.add_argument("--c3-steps", type=int, default=1000,
                     help="steps of the 8192 x 8192 16-bit storage run (0 to skip)")
     ap.add_argument("--hole-steps", type=int, default=500,
@@ -327,7 +329,7 @@ def run_native(a):
     ranks = Ranks("nccl")
     rank, world, local = ranks.rank, ranks.world, ranks.local
     if world > 1:  # the extra sections run on single-GPU invocations only
-        a.forms, a.batch, a.serve = "", 0, 0
+        a.forms, a.schemes, a.batch, a.serve = "", "", 0, 0
 
     def barrier():
         ranks.barrier()
@@ -415,6 +417,34 @@ def run_native(a):
         forms[f] = {"mlups": nodes * a.form_steps / s / 1e6, "bytes_per_node_update": bpn,
                     "achieved_gbs": ach, "frac": ach / peak, "steps": a.form_steps, "stable": ok,
                     "u_rel_err_vs_f64": uerr}
+
+    # the other time levels of the moment's source (Sec. 5) on the same body,
+    # FP32 with the compensated carry, each with its displacement difference
+    # from the FP64 predictor path after --form-steps steps (the schemes
+    # differ by O(dt^2) in the moment, so this measures how much the choice
+    # matters on this workload, not an error)
+    schemes = {}
+    scheme_ids = {"explicit": lbm.LBM_SCHEME_EXPLICIT, "predictor": lbm.LBM_SCHEME_PREDICTOR,
+                  "extrapolated": lbm.LBM_SCHEME_EXTRAPOLATED}
+    for name in [x for x in a.schemes.split(",") if x]:
+        if ref_u is None:
+            with lbm.Body(prob, storage="f64", stream=stream.cuda_stream, device=local) as b64:
+                b64.step(a.warmup + a.form_steps)
+                ref_u = b64.read(lbm.LBM_FIELD_U, allow_unstable=True)["u"]
+        b = lbm.Body(prob, storage="f32", compensated=True, scheme=scheme_ids[name], stream=stream.cuda_stream,
+                     device=local)
+        _, bpn = lbm.lbm_memory_info(b.ctx)
+        b.step(a.warmup)
+        torch.cuda.synchronize()
+        s = time_steps(b, stream, a.form_steps)
+        out = b.read(lbm.LBM_FIELD_U, allow_unstable=True)
+        b.close()
+        ach = bpn * nodes / (s / a.form_steps) / 1e9
+        schemes[name] = {"mlups": nodes * a.form_steps / s / 1e6, "bytes_per_node_update": bpn,
+                         "achieved_gbs": ach, "frac": ach / peak, "steps": a.form_steps,
+                         "stable": out["status"] == lbm.LBM_OK,
+                         "u_rel_diff_vs_predictor_f64": float(np.linalg.norm(out["u"] - ref_u)
+                                                              / np.linalg.norm(ref_u))}
 
     # the 8192 x 8192 clamped body with 16-bit population storage, timed, and
     # its displacement error against the FP64 path on the same inputs (the
@@ -598,7 +628,7 @@ def run_native(a):
         "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "f16": "f16", "bf16": "bf16"}[a.storage],
         "data": "synthetic", "config": config_of(a, prob), "roofline": roof, "cpu_baseline": cpu,
-        "e2e": e2e, "gpu_launches": 2 * a.steps, "clocks": clk, "forms": forms, "c3_8192": c3, "plate_hole": hole, "batched": batched,
+        "e2e": e2e, "gpu_launches": 2 * a.steps, "clocks": clk, "forms": forms, "schemes": schemes, "c3_8192": c3, "plate_hole": hole, "batched": batched,
         "serving": serving, "tuning": tuning_info,
         "status": lbm.status_string(status),
     }

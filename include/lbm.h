@@ -74,8 +74,14 @@ typedef enum { LBM_UCARRY_NATIVE = 0, LBM_UCARRY_COMPENSATED = 1 } lbm_ucarry;
  * EXPLICIT  -- Algorithm 1: the time-t source enters collision and moment.
  * PREDICTOR -- the predictor-corrector the paper's footnote to Sec. 5 offers:
  *              1S(t+dt) evaluated from the explicitly predicted u*(t+dt)
- *              corrects j and u and is the next collision's source.  Default. */
-typedef enum { LBM_SCHEME_EXPLICIT = 0, LBM_SCHEME_PREDICTOR = 1 } lbm_scheme;
+ *              corrects j and u and is the next collision's source.  Default.
+ * EXTRAPOLATED -- the variant Sec. 5 gives for an O(dt^3) error: 1S(t+dt)
+ *              evaluated from the trapezoidal u(t+dt) of j extrapolated
+ *              linearly from j(t - dt) and j(t) (j(-dt) = j(0)); as above it
+ *              is also the next collision's source.  Stable only for
+ *              lambda = mu; two more carry planes (16 B per node update in
+ *              FP32); single bodies only (lbm_batch_create rejects it). */
+typedef enum { LBM_SCHEME_EXPLICIT = 0, LBM_SCHEME_PREDICTOR = 1, LBM_SCHEME_EXTRAPOLATED = 2 } lbm_scheme;
 
 typedef struct {
     int32_t nx, ny;      /* nodes along x and y; each >= 3 */
@@ -289,16 +295,17 @@ LBM_API lbm_status lbm_destroy(lbm_ctx* ctx);
 typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
 
 /* Groups n existing contexts.  Members must be distinct, on one device, of
- * one storage format and u-carry (scheme, material, boundaries, sizes and
- * step counts may differ), with material and boundaries set; they are
+ * one storage format and u-carry (scheme EXPLICIT or PREDICTOR, material,
+ * boundaries, sizes and step counts may differ), with material and
+ * boundaries set; they are
  * initialised here if they were not, and must outlive the batch.
  * cuda_stream: the batch's stream (NULL: the batch owns a non-blocking one);
  * each lbm_batch_step orders itself after work already enqueued on the
  * members' streams and their later work after itself.  Allocates the batch's
  * parameter table and work lists (a few hundred bytes per member and per
  * tile).  Synchronises.  Errors: LBM_E_INVALID (n < 1, NULL or repeated
- * member, mixed devices or formats), LBM_E_STATE (a member not ready),
- * LBM_E_OOM, LBM_E_CUDA. */
+ * member, mixed devices or formats, a member of scheme EXTRAPOLATED),
+ * LBM_E_STATE (a member not ready), LBM_E_OOM, LBM_E_CUDA. */
 LBM_API lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cuda_stream, lbm_batch** out);
 
 /* lbm_batch_create with a decomposition of the batch's interior tiles (no

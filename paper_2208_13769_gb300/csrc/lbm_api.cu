@@ -28,6 +28,9 @@ size_t elem_size_storage(int fmt) {
     }
 }
 size_t elem_size_compute(int fmt) { return fmt == kFmtF64 ? 8 : 4; }
+// planes of the source carry: the last source, or D and G of the
+// extrapolated scheme
+int source_planes(int scheme) { return scheme == LBM_SCHEME_EXTRAPOLATED ? 4 : 2; }
 size_t elem_size_ucarry(int fmt) { return fmt == kFmtF64 ? 8 : 4; }
 int ucarry_planes(int fmt) { return (fmt == kFmtF64 || fmt == kFmtF32) ? 1 : 2; }
 
@@ -275,7 +278,7 @@ static cudaError_t launch_band_part(lbm_ctx* c, int parity, bool fields, cudaStr
     L.params = c->dparams + parity;
     L.tiles = c->dtiles;
     L.fields = fields ? 1 : 0;
-    return launch_edge(c->fmt, L, c->n_etiles, st, 0, c->hole[0] < c->hole[1]);
+    return launch_edge(c->fmt, L, c->n_etiles, st, 0, c->hole[0] < c->hole[1], c->scheme == LBM_SCHEME_EXTRAPOLATED);
 }
 
 // Launches of one time step (mode 0) or the initialisation (mode 1).
@@ -286,7 +289,7 @@ static cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int pa
         L.params = c->dparams + parity;
         L.tiles = c->dtiles;
         L.fields = fields ? 1 : 0;
-        return launch_edge(c->fmt, L, c->n_itiles, c->stream, 1, true);
+        return launch_edge(c->fmt, L, c->n_itiles, c->stream, 1, true, false);
     }
     if (mode == 1) {
         EdgeLaunch L;
@@ -301,7 +304,7 @@ static cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int pa
         L.rtiles_x = (c->nx + 27) / 28;
         const int64_t ntiles = int64_t(L.rtiles_x) * ((c->ny + 3) / 4);
         if (ntiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
-        return launch_edge(c->fmt, L, int(ntiles), c->stream, 1, true);
+        return launch_edge(c->fmt, L, int(ntiles), c->stream, 1, true, false);
     }
     if (!c->has_interior) return launch_band_part(c, parity, fields, c->stream);
     // interior first on the main stream, then the edge tiles on the side
@@ -414,7 +417,9 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
     if (d->nx < 3 || d->ny < 3 || !(d->dX > 0) || !isfinite(d->dX)) return LBM_E_INVALID;
     if (d->storage < LBM_F64 || d->storage > LBM_BF16) return LBM_E_INVALID;
     if (d->u_carry != LBM_UCARRY_NATIVE && d->u_carry != LBM_UCARRY_COMPENSATED) return LBM_E_INVALID;
-    if (d->scheme != LBM_SCHEME_EXPLICIT && d->scheme != LBM_SCHEME_PREDICTOR) return LBM_E_INVALID;
+    if (d->scheme != LBM_SCHEME_EXPLICIT && d->scheme != LBM_SCHEME_PREDICTOR &&
+        d->scheme != LBM_SCHEME_EXTRAPOLATED)
+        return LBM_E_INVALID;
     if (d->f16_scale_log2 < -60 || d->f16_scale_log2 > 60) return LBM_E_INVALID;
     // sizes: 64-bit element counts, 32-bit node coordinates
     const int64_t nodes = int64_t(d->nx) * d->ny;
@@ -483,7 +488,7 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
 
     const size_t fbytes = size_t(9) * c->plane * elem_size_storage(c->fmt);
     const size_t abytes = size_t(2 * ucarry_planes(c->fmt)) * c->plane * elem_size_ucarry(c->fmt);
-    const size_t sbytes = size_t(2) * c->plane * elem_size_compute(c->fmt);
+    const size_t sbytes = size_t(source_planes(d->scheme)) * c->plane * elem_size_compute(c->fmt);
     const size_t fldbytes = size_t(5) * nodes * sizeof(double);
     const size_t ubytes = size_t(2) * nodes * sizeof(double);
     c->diag_blocks = diagnostics_blocks(nodes);
@@ -696,7 +701,7 @@ lbm_status lbm_profile_interior(lbm_ctx* c, int64_t nlaunches, double out[2]) {
     const int q = c->parity;
     const size_t fb = size_t(9) * size_t(c->plane) * elem_size_storage(c->fmt);
     const size_t ab = size_t(2 * ucarry_planes(c->fmt)) * size_t(c->plane) * elem_size_ucarry(c->fmt);
-    const size_t sb = size_t(2) * size_t(c->plane) * elem_size_compute(c->fmt);
+    const size_t sb = size_t(source_planes(c->scheme)) * size_t(c->plane) * elem_size_compute(c->fmt);
     unsigned char* save = nullptr;
     cudaError_t err = cudaMalloc(&save, fb + ab + sb + sizeof(int32_t));
     if (err != cudaSuccess) {
@@ -917,7 +922,7 @@ StateParts state_parts(const lbm_ctx* c) {
     StateParts p;
     p.f = size_t(9) * size_t(c->plane) * elem_size_storage(c->fmt);
     p.a = size_t(2 * ucarry_planes(c->fmt)) * size_t(c->plane) * elem_size_ucarry(c->fmt);
-    p.s = size_t(2) * size_t(c->plane) * elem_size_compute(c->fmt);
+    p.s = size_t(source_planes(c->scheme)) * size_t(c->plane) * elem_size_compute(c->fmt);
     p.fields = size_t(5) * size_t(c->nx) * size_t(c->ny) * sizeof(double);
     return p;
 }
@@ -1031,7 +1036,7 @@ lbm_status lbm_memory_info(const lbm_ctx* c, int64_t* device_bytes, int64_t* byt
     if (bytes_per_node_update) {
         const int64_t per = int64_t(9 * elem_size_storage(c->fmt)) +
                             int64_t(2 * ucarry_planes(c->fmt) * elem_size_ucarry(c->fmt)) +
-                            int64_t(2 * elem_size_compute(c->fmt));
+                            int64_t(source_planes(c->scheme) * elem_size_compute(c->fmt));
         *bytes_per_node_update = 2 * per;
     }
     return LBM_OK;

@@ -161,6 +161,7 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
         for (int j = 0; j < i; ++j)
             if (members[j] == members[i]) return LBM_E_INVALID;
         if (members[i]->device != members[0]->device || members[i]->fmt != members[0]->fmt) return LBM_E_INVALID;
+        if (members[i]->scheme == LBM_SCHEME_EXTRAPOLATED) return LBM_E_INVALID;  // single bodies only
         const lbm_status st = ctx_ready(members[i]);
         if (st != LBM_OK) return st;
     }
@@ -425,7 +426,7 @@ lbm_status lbm_batch_autotune(lbm_ctx* const* members, int32_t n, int64_t steps,
     NvtxRange range_("lbm_batch_autotune");
     if (!members || n < 1 || !best || steps < 1 || steps > 100000) return LBM_E_INVALID;
     for (int i = 0; i < n; ++i)
-        if (!members[i]) return LBM_E_INVALID;
+        if (!members[i] || members[i]->scheme == LBM_SCHEME_EXTRAPOLATED) return LBM_E_INVALID;
     DeviceGuard guard(members[0]->device);
     if (!guard.ok) return LBM_E_INVALID;
     cudaStream_t st = nullptr;

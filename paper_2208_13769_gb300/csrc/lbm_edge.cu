@@ -23,7 +23,7 @@ namespace lbm {
 
 static_assert(sizeof(StepParams) % 16 == 0, "StepParams is copied to shared memory in 16-byte words");
 
-template <class TS, class TC, class UT, int MODE, bool HOLE>
+template <class TS, class TC, class UT, int MODE, bool HOLE, bool XJ>
 __global__ void __launch_bounds__(kEdgeThreads, 3) edge_tile_kernel(const __grid_constant__ EdgeLaunch L) {
     constexpr int N = kEdgeThreads;
     __shared__ __align__(16) StepParams sp;
@@ -54,31 +54,35 @@ __global__ void __launch_bounds__(kEdgeThreads, 3) edge_tile_kernel(const __grid
         for (int q = int(threadIdx.x); q < int(sizeof(StepParams) / 16); q += N) dst[q] = src[q];
     }
     __syncthreads();
-    edge_tile_body<TS, TC, UT, MODE, HOLE>(tile, sp, L.fields != 0, su, sq, MODE == 1 ? sinit : nullptr, s_edge);
+    edge_tile_body<TS, TC, UT, MODE, HOLE, XJ>(tile, sp, L.fields != 0, su, sq, MODE == 1 ? sinit : nullptr,
+                                                s_edge);
 }
 
 // ---------------------------------------------------------------- launchers
 
 template <class TS, class TC, class UT>
-cudaError_t launch_edge_t(const EdgeLaunch& L, int ntiles, cudaStream_t s, int mode, bool holed) {
+cudaError_t launch_edge_t(const EdgeLaunch& L, int ntiles, cudaStream_t s, int mode, bool holed, bool xj) {
     if (ntiles <= 0) return cudaSuccess;
-    // the initialisation runs once: one variant, which handles a hole
+    // the initialisation runs once: one variant, which handles a hole and
+    // reads the scheme
     if (mode == 1)
-        edge_tile_kernel<TS, TC, UT, 1, true><<<ntiles, kEdgeThreads, 0, s>>>(L);
+        edge_tile_kernel<TS, TC, UT, 1, true, false><<<ntiles, kEdgeThreads, 0, s>>>(L);
+    else if (xj)
+        edge_tile_kernel<TS, TC, UT, 0, true, true><<<ntiles, kEdgeThreads, 0, s>>>(L);
     else if (holed)
-        edge_tile_kernel<TS, TC, UT, 0, true><<<ntiles, kEdgeThreads, 0, s>>>(L);
+        edge_tile_kernel<TS, TC, UT, 0, true, false><<<ntiles, kEdgeThreads, 0, s>>>(L);
     else
-        edge_tile_kernel<TS, TC, UT, 0, false><<<ntiles, kEdgeThreads, 0, s>>>(L);
+        edge_tile_kernel<TS, TC, UT, 0, false, false><<<ntiles, kEdgeThreads, 0, s>>>(L);
     return cudaGetLastError();
 }
 
-cudaError_t launch_edge(int fmt, const EdgeLaunch& L, int ntiles, cudaStream_t s, int mode, bool holed) {
+cudaError_t launch_edge(int fmt, const EdgeLaunch& L, int ntiles, cudaStream_t s, int mode, bool holed, bool xj) {
     switch (fmt) {
-        case kFmtF64: return launch_edge_t<double, double, UPlain<double>>(L, ntiles, s, mode, holed);
-        case kFmtF32: return launch_edge_t<float, float, UPlain<float>>(L, ntiles, s, mode, holed);
-        case kFmtF32C: return launch_edge_t<float, float, UComp>(L, ntiles, s, mode, holed);
-        case kFmtF16: return launch_edge_t<__half, float, UComp>(L, ntiles, s, mode, holed);
-        case kFmtBF16: return launch_edge_t<__nv_bfloat16, float, UComp>(L, ntiles, s, mode, holed);
+        case kFmtF64: return launch_edge_t<double, double, UPlain<double>>(L, ntiles, s, mode, holed, xj);
+        case kFmtF32: return launch_edge_t<float, float, UPlain<float>>(L, ntiles, s, mode, holed, xj);
+        case kFmtF32C: return launch_edge_t<float, float, UComp>(L, ntiles, s, mode, holed, xj);
+        case kFmtF16: return launch_edge_t<__half, float, UComp>(L, ntiles, s, mode, holed, xj);
+        case kFmtBF16: return launch_edge_t<__nv_bfloat16, float, UComp>(L, ntiles, s, mode, holed, xj);
     }
     return cudaErrorInvalidValue;
 }

@@ -147,8 +147,10 @@ __device__ __noinline__ void boundary_links(TS* fdst, Geo g, const StepParams& p
 // 4 x tw x th, s_edge the boundary data of the 4 edges and of a hole's faces
 // (5 entries).  want_fields: also write u, v, r to p.fields.  HOLE: the
 // body may have a hole (false: p.hole is not read, and the tile's code
-// carries none of the hole's tests).
-template <class TS, class TC, class UT, int MODE, bool HOLE>
+// carries none of the hole's tests).  XJ (mode 0): the extrapolated scheme,
+// whose carries are E = u(t) + F (the u* of stage A), D = ku jh(t) and
+// F = ku (3 jh(t) - jh(t - dt)) (the initialisation reads p.scheme instead).
+template <class TS, class TC, class UT, int MODE, bool HOLE, bool XJ>
 __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepParams& p, bool want_fields, UT* su,
                                                TC* sq, TC* sinit, EdgeNow<TC, UT>* s_edge) {
     using CT = typename UT::Elem;
@@ -217,7 +219,8 @@ __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepP
 
     // ---------------- stage A: pull-stream, first moment, predicted u*
     TC f[9];
-    TC so0 = TC(0), so1 = TC(0);  // source carry of the node (stage C)
+    TC so0 = TC(0), so1 = TC(0);  // source carry (XJ: D) of the node (stage C)
+    TC fo0 = TC(0), fo1 = TC(0);  // XJ: F of the node
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = TC(0);
     if (MODE == 0 && inA) {
@@ -230,10 +233,19 @@ __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepP
             so0 = s_src[o];
             so1 = s_src[o + plane];
         }
-        const TC m0 = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-        const TC m1 = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
-        su[(ty * 2) * tw + tx] = A0.add(k.ku * m0);
-        su[(ty * 2 + 1) * tw + tx] = A1.add(k.ku * m1);
+        if (XJ) {  // u* = E
+            if (inC) {
+                fo0 = s_src[o + 2 * plane];
+                fo1 = s_src[o + 3 * plane];
+            }
+            su[(ty * 2) * tw + tx] = A0;
+            su[(ty * 2 + 1) * tw + tx] = A1;
+        } else {
+            const TC m0 = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+            const TC m1 = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
+            su[(ty * 2) * tw + tx] = A0.add(k.ku * m0);
+            su[(ty * 2 + 1) * tw + tx] = A1.add(k.ku * m1);
+        }
     } else if (MODE == 1 && inA) {
         const int64_t hh = (int64_t(gy) * nx + gx) * 2;
         su[(ty * 2) * tw + tx] = UT::from_double(p.u0 ? p.u0[hh] : 0.0);
@@ -307,7 +319,12 @@ __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepP
             pxx = (f[1] + f[3]) + dg;
             pyy = (f[2] + f[4]) + dg;
             pxy = (f[5] - f[6]) + (f[7] - f[8]);
-            if (p.scheme == 1) {
+            if (XJ) {  // u(t + dt) = u(t) + ku (jh(t) + jh) = E - (F - D) + ku jh
+                j0 = m0 + TC(0.5) * sn0;
+                j1 = m1 + TC(0.5) * sn1;
+                du0 = k.ku * j0 - (fo0 - so0);
+                du1 = k.ku * j1 - (fo1 - so1);
+            } else if (p.scheme == 1) {
                 j0 = m0 + TC(0.5) * sn0;
                 j1 = m1 + TC(0.5) * sn1;
                 du0 = k.ku * (TC(0.5) * (sn0 - so0));
@@ -398,16 +415,31 @@ __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepP
                                        qr[3 * tw], k.inv_c2);
         }
 
-        // carries for the next step: A' = u + ku (jh + s/2), u = u* + du
-        const UT A0 = ux.add(du0 + k.ku * (j0 + TC(0.5) * sn0)).renorm();
-        const UT A1 = uy.add(du1 + k.ku * (j1 + TC(0.5) * sn1)).renorm();
+        // carries for the next step: A' = u + ku (jh + s/2), u = u* + du;
+        // the extrapolated scheme: E' = E - F + 4 D', D' = ku jh,
+        // F' = 3 D' - D (before the first step jh(-dt) = jh(0): D = D',
+        // F = 2 D', and E' = u0 + 2 D')
+        const bool xj = XJ || (MODE == 1 && p.scheme == 2);
+        const TC ka0 = xj ? k.ku * j0 : k.ku * (j0 + TC(0.5) * sn0);
+        const TC ka1 = xj ? k.ku * j1 : k.ku * (j1 + TC(0.5) * sn1);
+        const TC f0 = MODE == 1 ? TC(2) * ka0 : fo0, f1 = MODE == 1 ? TC(2) * ka1 : fo1;
+        const UT A0 = xj ? ux.add(TC(4) * ka0 - f0).renorm() : ux.add(du0 + ka0).renorm();
+        const UT A1 = xj ? uy.add(TC(4) * ka1 - f1).renorm() : uy.add(du1 + ka1).renorm();
 #pragma unroll
         for (int c = 0; c < UP; ++c) {
             put(a_dst + c * plane, A0.part(c));
             put(a_dst + (UP + c) * plane, A1.part(c));
         }
-        put(s_dst, sn0);
-        put(s_dst + plane, sn1);
+        if (xj) {
+            const TC d0 = MODE == 1 ? ka0 : so0, d1 = MODE == 1 ? ka1 : so1;
+            put(s_dst, ka0);
+            put(s_dst + plane, ka1);
+            put(s_dst + 2 * plane, TC(3) * ka0 - d0);
+            put(s_dst + 3 * plane, TC(3) * ka1 - d1);
+        } else {
+            put(s_dst, sn0);
+            put(s_dst + plane, sn1);
+        }
         if (want_fields && p.fields != nullptr) {
             const int64_t fo = int64_t(gy) * nx + gx;
             const int64_t np = int64_t(nx) * ny;

@@ -79,8 +79,11 @@ __host__ __device__ constexpr size_t interior_row_bytes() {
 // tile to initialise them afresh.  KEEP: stage C takes the populations of
 // its row from registers that stage A filled two rows earlier (18 more
 // registers, 9 fewer shared-memory loads per node) instead of the ring, and
-// the ring keeps every slot in flight.
-template <class TS, class TC, class UT, int NT, bool KEEP>
+// the ring keeps every slot in flight.  XJ: the extrapolated scheme, whose
+// carries are E = u(t) + F (the u* of stage A, in the u-carry planes),
+// D = ku jh(t) and F = ku (3 jh(t) - jh(t - dt)) (in the source planes);
+// else u* is A + ku m and the source planes hold the last source.
+template <class TS, class TC, class UT, int NT, bool KEEP, bool XJ>
 __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int by, double* fields, bool reuse) {
     using CT = typename UT::Elem;
     const int W = p.strip_w;
@@ -191,10 +194,13 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
     for (int c = 0; c < 2 * UP; ++c) ad[c] = a_dst + int64_t(c) * plane;
     const TC* ss1 = s_src + plane;
     TC* sd1 = s_dst + plane;
+    // the extrapolated scheme's F (planes 2, 3)
+    const TC* sf0 = s_src + 2 * plane;
+    const TC* sf1 = s_src + 3 * plane;
 
     // carries prefetched one row ahead
     UT an0, an1;
-    TC sn_old0 = TC(0), sn_old1 = TC(0);
+    TC sn_old0 = TC(0), sn_old1 = TC(0), f_old0 = TC(0), f_old1 = TC(0);
     if (colA) {
         an0 = UT::ld_global(as0, off_a, plane);
         an1 = UT::ld_global(as1, off_a, plane);
@@ -212,7 +218,8 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
         const int sB = sA == 0 ? 2 : sA - 1;  // slot of row a - 1
         const int sC = sA == 2 ? 0 : sA + 1;  // slot of row a - 2 (and Q of row a - 3 in sq[sA])
         const int rc = ra >= 2 ? ra - 2 : ra - 2 + R;
-        const TC so0 = sn_old0, so1 = sn_old1;  // source carry of stage C's row
+        const TC so0 = sn_old0, so1 = sn_old1;  // source carry (XJ: D) of stage C's row
+        const TC fo0 = f_old0, fo1 = f_old1;    // XJ: F of stage C's row
 
         // ---------------- stage A: row a
         if (!s_abort && !mbar_wait(&bars[ra], (phase >> ra) & 1u)) s_abort = 1;
@@ -228,10 +235,15 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
 #pragma unroll
                 for (int i = 1; i < 9; ++i) gcur[i] = g[i];
             }
-            const TC m0 = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
-            const TC m1 = (g[2] - g[4]) + (g[5] - g[8]) + (g[6] - g[7]);
-            su[(sA * 2) * NT + t] = an0.add(k.ku * m0);
-            su[(sA * 2 + 1) * NT + t] = an1.add(k.ku * m1);
+            if (XJ) {  // u* = u(t) + ku (3 jh(t) - jh(t - dt)) = E
+                su[(sA * 2) * NT + t] = an0;
+                su[(sA * 2 + 1) * NT + t] = an1;
+            } else {
+                const TC m0 = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+                const TC m1 = (g[2] - g[4]) + (g[5] - g[8]) + (g[6] - g[7]);
+                su[(sA * 2) * NT + t] = an0.add(k.ku * m0);
+                su[(sA * 2 + 1) * NT + t] = an1.add(k.ku * m1);
+            }
             if (q + 1 < niter) {
                 an0 = UT::ld_global(as0, off_a + pitch32, plane);
                 an1 = UT::ld_global(as1, off_a + pitch32, plane);
@@ -251,6 +263,10 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
             const int32_t o = off_a - pitch32;  // row a - 1
             sn_old0 = s_src[o];
             sn_old1 = ss1[o];
+            if (XJ) {
+                f_old0 = sf0[o];
+                f_old1 = sf1[o];
+            }
         }
 
         // ---------------- stage B: row a - 1
@@ -300,7 +316,12 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
             const TC pyy = (f[2] + f[4]) + dg;
             const TC pxy = (f[5] - f[6]) + (f[7] - f[8]);
             TC j0, j1, du0 = TC(0), du1 = TC(0);
-            if (p.scheme == 1) {
+            if (XJ) {  // u(t + dt) = u(t) + ku (jh(t) + jh) = E - (F - D) + ku jh
+                j0 = m0 + TC(0.5) * sn0;
+                j1 = m1 + TC(0.5) * sn1;
+                du0 = k.ku * j0 - (fo0 - so0);
+                du1 = k.ku * j1 - (fo1 - so1);
+            } else if (p.scheme == 1) {
                 j0 = m0 + TC(0.5) * sn0;
                 j1 = m1 + TC(0.5) * sn1;
                 du0 = k.ku * (TC(0.5) * (sn0 - so0));
@@ -339,16 +360,27 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
             for (int i = 0; i < 9; ++i) fd[i][o] = Codec<TS, TC>::st(fc[i], i, p);
 
             // carries: A' = u + ku (jh + s/2), u = u* + du;  s' = s
+            // (XJ: E' = u + ku (3 jh - jh(t)) = E - F + 4 D', D' = ku jh,
+            // F' = 3 D' - D)
             const UT ux = su[(sC * 2) * NT + t], uy = su[(sC * 2 + 1) * NT + t];
-            const UT A0 = ux.add(du0 + k.ku * (j0 + TC(0.5) * sn0)).renorm();
-            const UT A1 = uy.add(du1 + k.ku * (j1 + TC(0.5) * sn1)).renorm();
+            const TC ka0 = XJ ? k.ku * j0 : k.ku * (j0 + TC(0.5) * sn0);
+            const TC ka1 = XJ ? k.ku * j1 : k.ku * (j1 + TC(0.5) * sn1);
+            const UT A0 = XJ ? ux.add(TC(4) * ka0 - fo0).renorm() : ux.add(du0 + ka0).renorm();
+            const UT A1 = XJ ? uy.add(TC(4) * ka1 - fo1).renorm() : uy.add(du1 + ka1).renorm();
 #pragma unroll
             for (int c = 0; c < UP; ++c) {
                 ad[c][o] = A0.part(c);
                 ad[UP + c][o] = A1.part(c);
             }
-            s_dst[o] = sn0;
-            sd1[o] = sn1;
+            if (XJ) {
+                s_dst[o] = ka0;
+                sd1[o] = ka1;
+                s_dst[o + 2 * plane] = TC(3) * ka0 - so0;
+                s_dst[o + 3 * plane] = TC(3) * ka1 - so1;
+            } else {
+                s_dst[o] = sn0;
+                sd1[o] = sn1;
+            }
             if (fields != nullptr) {
                 const int64_t fo = int64_t(gy) * p.nx + gx;
                 const int64_t np = int64_t(p.nx) * p.ny;
@@ -389,9 +421,9 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
     return true;
 }
 
-template <class TS, class TC, class UT, int NT, int MINB>
+template <class TS, class TC, class UT, int NT, int MINB, bool XJ>
 __global__ void __launch_bounds__(NT, MINB) interior_step_kernel(const __grid_constant__ StepParams p) {
-    interior_tile<TS, TC, UT, NT, true>(p, int(blockIdx.x), int(blockIdx.y), p.fields, false);
+    interior_tile<TS, TC, UT, NT, true, XJ>(p, int(blockIdx.x), int(blockIdx.y), p.fields, false);
 }
 
 // One time step of a batch of bodies in one launch: a persistent grid of
@@ -444,11 +476,12 @@ __global__ void __launch_bounds__(NT, MINB) batch_step_kernel(const __grid_const
         }
         __syncthreads();
         if (it.kind == 0) {
-            if (!interior_tile<TS, TC, UT, NT, false>(sp, it.a, it.b, L.fields ? sp.fields : nullptr, true)) break;
+            if (!interior_tile<TS, TC, UT, NT, false, false>(sp, it.a, it.b, L.fields ? sp.fields : nullptr, true))
+                break;
         } else {
             for (int g = 0; g < it.b; ++g) {
                 if (g > 0) __syncthreads();  // the previous tile is done with the shared buffers
-                edge_tile_body<TS, TC, UT, 0, HOLE>(s_tiles[g], sp, L.fields != 0, su, sq, nullptr, s_edge);
+                edge_tile_body<TS, TC, UT, 0, HOLE, false>(s_tiles[g], sp, L.fields != 0, su, sq, nullptr, s_edge);
             }
         }
     }
@@ -466,9 +499,9 @@ size_t interior_smem_bytes(int ring_slots) {
     return interior_smem_fixed<UT, TC, NT>() + interior_row_bytes<TS, NT>() * size_t(ring_slots);
 }
 
-template <class TS, class TC, class UT, int NT, int MINB>
-cudaError_t launch_interior_t(const StepParams& p, cudaStream_t s) {
-    auto kern = interior_step_kernel<TS, TC, UT, NT, MINB>;
+template <class TS, class TC, class UT, int NT, int MINB, bool XJ>
+cudaError_t launch_interior_x(const StepParams& p, cudaStream_t s) {
+    auto kern = interior_step_kernel<TS, TC, UT, NT, MINB, XJ>;
     const size_t sm = interior_smem_bytes<TS, TC, UT, NT>(p.ring_slots);
     static size_t configured = 0;
     if (sm > configured) {
@@ -479,6 +512,12 @@ cudaError_t launch_interior_t(const StepParams& p, cudaStream_t s) {
     dim3 grid(p.tiles_x, p.tiles_y, 1);
     kern<<<grid, NT, sm, s>>>(p);
     return cudaGetLastError();
+}
+
+template <class TS, class TC, class UT, int NT, int MINB>
+cudaError_t launch_interior_t(const StepParams& p, cudaStream_t s) {
+    return p.scheme == 2 ? launch_interior_x<TS, TC, UT, NT, MINB, true>(p, s)
+                         : launch_interior_x<TS, TC, UT, NT, MINB, false>(p, s);
 }
 
 template <class TS, class TC, class UT, int NT, int MINB, bool HOLE>
@@ -551,7 +590,7 @@ void interior_strips(int fmt, int rx0, int rx1, bool aligned, int* strip_x0, int
 
 template <class TS, class TC, class UT, int NT, int MINB>
 int interior_occupancy_t(int ring_slots) {
-    auto kern = interior_step_kernel<TS, TC, UT, NT, MINB>;
+    auto kern = interior_step_kernel<TS, TC, UT, NT, MINB, false>;
     const size_t sm = interior_smem_bytes<TS, TC, UT, NT>(ring_slots);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)) != cudaSuccess) return 0;
     int n = 0;

@@ -88,7 +88,9 @@ struct EdgeLaunch {
 };
 
 // One step (mode 0) or the initialisation (mode 1) over ntiles tiles.
-cudaError_t launch_edge(int fmt, const EdgeLaunch& L, int ntiles, cudaStream_t s, int mode, bool holed);
+// holed: the body has a hole; xj: the extrapolated scheme (mode 0; the
+// initialisation reads the scheme from the parameters).
+cudaError_t launch_edge(int fmt, const EdgeLaunch& L, int ntiles, cudaStream_t s, int mode, bool holed, bool xj);
 
 // Tiles of one band rectangle for CTAs of `nthreads` threads (kEdgeThreads
 // for the edge kernel, kInteriorThreads for the batch kernel); count only

@@ -22,7 +22,7 @@ from . import build as _build
 LBM_OK, LBM_E_INVALID, LBM_E_OOM, LBM_E_CUDA, LBM_E_UNSTABLE, LBM_E_TIMEOUT, LBM_E_STATE = range(7)
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = range(4)
 LBM_UCARRY_NATIVE, LBM_UCARRY_COMPENSATED = 0, 1
-LBM_SCHEME_EXPLICIT, LBM_SCHEME_PREDICTOR = 0, 1
+LBM_SCHEME_EXPLICIT, LBM_SCHEME_PREDICTOR, LBM_SCHEME_EXTRAPOLATED = 0, 1, 2
 LBM_PERIODIC, LBM_DIRICHLET, LBM_NEUMANN = 0, 1, 2
 LBM_FIELD_U, LBM_FIELD_V, LBM_FIELD_P, LBM_FIELD_PBAR, LBM_FIELD_R, LBM_FIELD_SIGMA, LBM_FIELD_J = (
     1, 2, 4, 8, 16, 32, 64)
@@ -391,7 +391,8 @@ class Body:
 
     storage: "f64" | "f32" | "f16" | "bf16"; compensated: FP32-pair u-carry
     for "f32" (default True: a plain FP32 u loses Grad u to rounding once
-    |u| >> |H| dX); scheme: LBM_SCHEME_PREDICTOR (default) or LBM_SCHEME_EXPLICIT;
+    |u| >> |H| dX); scheme: LBM_SCHEME_PREDICTOR (default), LBM_SCHEME_EXPLICIT
+    or LBM_SCHEME_EXTRAPOLATED (stable only for lambda = mu);
     stream: an integer cudaStream_t handle (e.g. torch's stream.cuda_stream)."""
 
     def __init__(self, prob, storage: str = "f64", compensated: Optional[bool] = None,

@@ -127,6 +127,10 @@ def test_batch_argument_and_phase_errors():
             lbm.Batch([a, a])  # repeated member
         with pytest.raises(lbm.LbmError):
             lbm.Batch([])
+        with lbm.Body(p1, storage="f32", scheme=lbm.LBM_SCHEME_EXTRAPOLATED) as x:
+            with pytest.raises(lbm.LbmError) as ei:
+                lbm.Batch([a, x])  # the extrapolated scheme runs as a single body only
+            assert ei.value.status == lbm.LBM_E_INVALID
         with lbm.Batch([a, c]) as batch:
             batch.step(2)
             c.step(1)  # a member stepped on its own: out of phase

@@ -50,6 +50,27 @@ def test_resume_in_a_fresh_context_is_bitwise_the_uninterrupted_run(storage):
             _same(second.read(MASK), ref, (prob.name, storage, "resumed"))
 
 
+def test_extrapolated_scheme_resumes_bitwise():
+    """The extrapolated scheme's state holds two more carry planes (j of two
+    time levels); a resumed run continues bit for bit."""
+    n = 75
+    prob = W.smooth_random(150, 90, W.clamped_free_edges(), seed=31, amp=0.01, vamp=0.004, lam=0.3, mu=0.3)
+    xs = lbm.LBM_SCHEME_EXTRAPOLATED
+    with lbm.Body(prob, storage="f32", scheme=xs) as whole:
+        whole.step(2 * n)
+        ref = whole.read(MASK)
+    with lbm.Body(prob, storage="f32", scheme=xs) as first:
+        first.step(n)
+        state = first.save_state()
+    with lbm.Body(prob, storage="f32") as other:  # another scheme: refused
+        with pytest.raises(lbm.LbmError):
+            other.load_state(state)
+    with lbm.Body(prob, storage="f32", scheme=xs) as second:
+        second.load_state(state)
+        second.step(n)
+        _same(second.read(MASK), ref, "extrapolated resumed")
+
+
 def test_rollback_within_one_context():
     prob = W.tension_block(40, T1=0.1)
     with lbm.Body(prob, storage="f32") as b:

@@ -3,7 +3,7 @@
 Tolerances: relative L2 error of u, v and P <= 1e-12 for FP64 storage and
 <= 1e-5 for FP32 storage after the stated step count.  Sizes span several
 fused-kernel tiles (64 x 16 for FP32, 32 x 16 for FP64) with ragged tails,
-periodic axes shorter than a tile, every boundary kind and both schemes.
+periodic axes shorter than a tile, every boundary kind and the three schemes.
 """
 import dataclasses
 import math
@@ -70,6 +70,18 @@ def test_fp64_parity_explicit(name):
     compare(ref, got, TOL["f64"], keys=("u", "v", "P", "Pbar", "r", "J", "sigma"), prob=prob)
 
 
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp64_parity_extrapolated(name):
+    """The extrapolated scheme (j extrapolated to t + dt for the moment's
+    source, two more carry planes).  Stable only at lambda = mu, so its parity
+    is checked there; the tension block ramps its load, which keeps it
+    bounded over its horizon."""
+    prob, steps = CASES[name]
+    prob = dataclasses.replace(prob, lam=prob.mu)
+    ref, got = run_both(prob, steps, "f64", scheme=oracle.EXTRAPOLATED)
+    compare(ref, got, TOL["f64"], keys=("u", "v", "P", "Pbar", "r", "J", "sigma"), prob=prob)
+
+
 # FP32 step counts: the rounding of FP32 populations and arithmetic makes the
 # error grow with the step count (about sqrt(n) for random rounding; in a fully
 # periodic body with a nonzero source the rounded divergence does not
@@ -87,6 +99,35 @@ def test_fp32_parity(name):
     prob, _ = CASES[name]
     ref, got = run_both(prob, FP32_STEPS[name], "f32", compensated=True)
     compare(ref, got, TOL["f32"])
+
+
+@pytest.mark.parametrize("name", sorted(FP32_STEPS))
+def test_fp32_parity_extrapolated(name):
+    """The extrapolated scheme in FP32 with the compensated carry, at
+    lambda = mu (its only stable material)."""
+    prob, _ = CASES[name]
+    prob = dataclasses.replace(prob, lam=prob.mu)
+    ref, got = run_both(prob, FP32_STEPS[name], "f32", compensated=True, scheme=oracle.EXTRAPOLATED)
+    compare(ref, got, TOL["f32"])
+
+
+def test_extrapolated_tuning_and_chunking_are_bit_identical():
+    """Decompositions of the interior launch and graph-chunked stepping give
+    bit-identical fields under the extrapolated scheme as well (FP32 and
+    FP16)."""
+    big = W.smooth_random(400, 300, W.clamped_free_edges(), seed=23, amp=0.01, vamp=0.004, lam=0.3, mu=0.3)
+    xs = lbm.LBM_SCHEME_EXTRAPOLATED
+    for storage in ("f32", "f16"):
+        with lbm.Body(big, storage=storage, scheme=xs) as b:
+            b.step(150)
+            ref = b.read(lbm.LBM_FIELD_U | lbm.LBM_FIELD_V | lbm.LBM_FIELD_R)
+        for ring, chunk, aligned in ((6, 32, 1), (5, 9, 0)):
+            with lbm.Body(big, storage=storage, scheme=xs, tuning=lbm.lbm_tuning(ring, chunk, aligned)) as b:
+                for n in (1, 64, 85):
+                    b.step(n)
+                got = b.read(lbm.LBM_FIELD_U | lbm.LBM_FIELD_V | lbm.LBM_FIELD_R)
+            for k in ("u", "v", "r"):
+                assert np.array_equal(got[k], ref[k]), (storage, ring, chunk, k)
 
 
 def test_fp32_clamped_body_full_horizon():
