@@ -218,6 +218,21 @@ def tension_block(n: int = 40, T1: float = 1.0, lam: float = 1.0, mu: float = 1.
                    name=f"tension_{n}")
 
 
+def shear_block(n: int = 40, T1: float = 0.05, lam: float = 1.0, mu: float = 1.0,
+                t_ramp: float = 1.0) -> Problem:
+    """Square block of side l = 1 (dX = 1/n) under simple shear (Sec. 7): a
+    tangential traction along x1 on y+, ramped from 0 to T1 over t_ramp and
+    held (the paper: T1 = 0.05 mu, to t = 8).  The y- edge is clamped, the x
+    edges are traction-free (the paper's figure is absent; its probe at the
+    centre of the left side moves, so that side is free)."""
+    dX = 1.0 / n
+    edges = [Edge(NEUMANN), Edge(NEUMANN), Edge(DIRICHLET),
+             Edge(NEUMANN, value=(0.0, 0.0), rate=(T1, 0.0), times=(0.0, t_ramp, math.inf))]
+    z = np.zeros((n, n, 2))
+    return Problem(nx=n, ny=n, lam=lam, mu=mu, dX=dX, edges=edges, u0=z, v0=z.copy(),
+                   name=f"shear_{n}")
+
+
 def plate_with_hole(n: int = 80, hole_frac: float = 0.4, T: float = 0.1, mu: float = 1.0, lam: float = 1.0,
                     t_off: float = 1.0) -> Problem:
     """Square plate of side l = 1 (dX = 1/n) with a centred square hole of

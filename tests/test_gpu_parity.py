@@ -46,6 +46,8 @@ def _cases():
     }
     t = W.tension_block(40, T1=0.1)
     cases["tension_ramp_40"] = (t, 208)
+    # Sec. 7's shear block at its load, inside its stable horizon (t = 1.73)
+    cases["shear_ramp_40"] = (W.shear_block(40), 120)
     return cases
 
 
@@ -89,6 +91,7 @@ def test_fp64_parity_extrapolated(name):
 # tolerance is checked at these horizons; the growth itself is measured in
 # test_fp32_error_growth_is_bounded below.
 FP32_STEPS = {"shear_wave_64": 500, "periodic_100x70": 300, "clamped_96x50": 400, "tension_ramp_40": 208,
+              "shear_ramp_40": 120,
               "x_periodic_y_walls_70x37": 300, "periodic_short_20x8": 60, "all_dirichlet_moving_33x40": 300}
 
 
