@@ -183,15 +183,24 @@ LBM_API lbm_status lbm_profile_steps(lbm_ctx* ctx, int64_t nsteps, double out[4]
  * LBM_E_OOM, LBM_E_CUDA. */
 LBM_API lbm_status lbm_profile_interior(lbm_ctx* ctx, int64_t nlaunches, double out[2]);
 
-/* Decomposition of the interior launch (no counterpart in the paper; it
- * changes how the work is split, never the result: every setting gives
- * bit-identical fields). */
+/* Decomposition of the step (no counterpart in the paper; it changes how
+ * the work is split, never the result: the interior settings give
+ * bit-identical fields; the plan decides which kernel advances the nodes
+ * more than two nodes from an edge, whose results agree to rounding).  The
+ * interior kernel's row pipeline has a latency floor per launch (about 20 us
+ * in FP32, 110 us in FP64) that small bodies do not fill, while edge tiles
+ * take one memory round trip each: below the size thresholds of plan 0 the
+ * edge tiles alone are faster (2 to 9 times up to 256 x 256). */
 typedef struct {
     int32_t ring_slots; /* rows of the bulk-copy ring, 4..8 (all of them in flight); 0: default (4) */
     int32_t chunk_rows; /* rows per CTA, >= 8; 0: one wave of CTAs over the SMs (default) */
     int32_t aligned;    /* 1: the fewest strips of equal width on 32-byte sector boundaries (at
                            most 120 columns; 112 for 16-bit storage); 0: 124-column strips;
                            -1: default (0) */
+    int32_t plan;       /* 0: by size (default): a body of fewer than 2^18 nodes (2^19 in FP64)
+                           runs as small tiles of the edge kernel only, a larger one as the
+                           interior kernel plus the edge bands; 1: edge tiles only; 2: the
+                           interior kernel wherever the body allows it */
 } lbm_tuning;
 
 /* Sets the decomposition; only before the first lbm_step / lbm_read_fields /
@@ -205,8 +214,9 @@ LBM_API lbm_status lbm_get_tuning(const lbm_ctx* ctx, lbm_tuning* tuning);
 /* Autotuner: times `steps` graph-replayed steps of scratch contexts with
  * desc's size, storage, carry, scheme, stream and device, zero initial
  * fields, lambda = mu = 0.3, and the given edge kinds (periodic edges in
- * pairs), for each candidate decomposition (ring 4, 5, 6 x rows per CTA one
- * wave, 32, 96, 256 x both strip grids), and returns the fastest in *best
+ * pairs), for each candidate decomposition (the interior kernel with ring 4,
+ * 5, 6 x rows per CTA one wave, 32, 96, 256 x both strip grids, and edge
+ * tiles only), and returns the fastest in *best
  * (its time per step in *best_ms, may be NULL).  The time of a step does not
  * depend on the field values, so the choice holds for any body of that shape.
  * Allocates and frees one scratch context at a time.  Synchronises.
@@ -313,7 +323,8 @@ LBM_API lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cu
  * results): tuning->ring_slots, rows of the bulk-copy ring (4..8; 0: 5),
  * and tuning->chunk_rows, rows per interior tile (>= 8; 0: about eight
  * waves of resident CTAs over the batch, 32..256 rows); aligned is ignored
- * (a batch's strips always lie on 32-byte sectors).  NULL: the defaults.
+ * (a batch's strips always lie on 32-byte sectors), and so is plan (each
+ * member keeps its own).  NULL: the defaults.
  * Errors as lbm_batch_create, and LBM_E_INVALID for a tuning out of range. */
 LBM_API lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda_stream,
                                           const lbm_tuning* tuning, lbm_batch** out);

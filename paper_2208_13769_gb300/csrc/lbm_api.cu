@@ -150,32 +150,30 @@ int64_t lbm::interior_nodes(const lbm_ctx* c) {
     return n;
 }
 
-// The interior (nodes >= 2 from bounded edges and from a hole's faces, >= 3
-// from periodic seams) as up to 4 rectangles for the lean kernel; the bands
-// around the body and around the hole as tiles of the edge kernel; the
-// parameter table of both parities and the tile list go to the device.
-static cudaError_t build_plan(lbm_ctx* c) {
+void lbm::plan_rects(const lbm_ctx* c, bool edge_only, int irect[4][4], int* n_irect, int brect[12][4],
+                     int* nband) {
     const bool perx = c->bc[0].kind == kPeriodic, pery = c->bc[2].kind == kPeriodic;
     const int bx = perx ? 3 : 2, by = pery ? 3 : 2;
     const int nx = c->nx, ny = c->ny;
     const int32_t* H = c->hole;
     const bool hole = H[0] < H[1];
-    const bool small = !(nx - 2 * bx >= 8 && ny - 2 * by >= 8);  // too small for the interior kernel
-    c->nband = 0;
-    c->n_irect = 0;
+    // too small for the interior kernel
+    const bool small = edge_only || !(nx - 2 * bx >= 8 && ny - 2 * by >= 8);
+    *nband = 0;
+    *n_irect = 0;
     const int bands[4][4] = {{0, nx, 0, by}, {0, nx, ny - by, ny}, {0, bx, by, ny - by}, {nx - bx, nx, by, ny - by}};
     if (!hole) {
         if (small) {
             const int all[4] = {0, nx, 0, ny};
-            for (int k = 0; k < 4; ++k) c->brect[0][k] = all[k];
-            c->nband = 1;
+            for (int k = 0; k < 4; ++k) brect[0][k] = all[k];
+            *nband = 1;
         } else {
             const int R[4] = {bx, nx - bx, by, ny - by};
-            for (int k = 0; k < 4; ++k) c->irect[0][k] = R[k];
-            c->n_irect = 1;
+            for (int k = 0; k < 4; ++k) irect[0][k] = R[k];
+            *n_irect = 1;
             for (int b = 0; b < 4; ++b)
-                for (int k = 0; k < 4; ++k) c->brect[b][k] = bands[b][k];
-            c->nband = 4;
+                for (int k = 0; k < 4; ++k) brect[b][k] = bands[b][k];
+            *nband = 4;
         }
     } else {
         // the bands of the edges and the 2-node band around the hole (the
@@ -184,14 +182,14 @@ static cudaError_t build_plan(lbm_ctx* c) {
         // the interior kernel, or, for a body too small for it, to tiles of
         // the edge kernel as well
         for (int b = 0; b < 4; ++b)
-            for (int k = 0; k < 4; ++k) c->brect[b][k] = bands[b][k];
+            for (int k = 0; k < 4; ++k) brect[b][k] = bands[b][k];
         const int hb[4][4] = {{H[0] - 2, H[0], H[2] - 2, H[3] + 2},
                               {H[1], H[1] + 2, H[2] - 2, H[3] + 2},
                               {H[0], H[1], H[2] - 2, H[2]},
                               {H[0], H[1], H[3], H[3] + 2}};
         for (int b = 0; b < 4; ++b)
-            for (int k = 0; k < 4; ++k) c->brect[4 + b][k] = hb[b][k];
-        c->nband = 8;
+            for (int k = 0; k < 4; ++k) brect[4 + b][k] = hb[b][k];
+        *nband = 8;
         const int R[4] = {bx, nx - bx, by, ny - by};
         const int B[4] = {H[0] - 2, H[1] + 2, H[2] - 2, H[3] + 2};
         const int parts[4][4] = {{R[0], R[1], R[2], B[2]},
@@ -200,10 +198,24 @@ static cudaError_t build_plan(lbm_ctx* c) {
                                  {B[1], R[1], std::max(R[2], B[2]), std::min(R[3], B[3])}};
         for (int q = 0; q < 4; ++q) {
             if (!(parts[q][0] < parts[q][1] && parts[q][2] < parts[q][3])) continue;
-            int* dst = small ? c->brect[c->nband++] : c->irect[c->n_irect++];
+            int* dst = small ? brect[(*nband)++] : irect[(*n_irect)++];
             for (int k = 0; k < 4; ++k) dst[k] = parts[q][k];
         }
     }
+}
+
+// The interior (nodes >= 2 from bounded edges and from a hole's faces, >= 3
+// from periodic seams) as up to 4 rectangles for the lean kernel; the bands
+// around the body and around the hole as tiles of the edge kernel; the
+// parameter table of both parities and the tile list go to the device.
+static cudaError_t build_plan(lbm_ctx* c) {
+    // edge tiles only for a body that the interior kernel's per-launch
+    // latency floor would slow down (plan 0), or on request (plan 1)
+    const int64_t nodes = int64_t(c->nx) * c->ny;
+    const int64_t edge_only_below = c->fmt == kFmtF64 ? (int64_t(1) << 19) : (int64_t(1) << 18);
+    const bool edge_only = c->tune_plan == 1 || (c->tune_plan == 0 && nodes < edge_only_below);
+    plan_rects(c, edge_only, c->irect, &c->n_irect, c->brect, &c->nband);
+    const bool hole = c->hole[0] < c->hole[1];
     if (c->n_irect > 0) {
         c->i_ring = c->tune_ring ? c->tune_ring : kInteriorRing;
         const int per_sm = std::max(1, interior_occupancy(c->fmt, c->i_ring));
@@ -745,11 +757,12 @@ lbm_status lbm_set_tuning(lbm_ctx* c, const lbm_tuning* t) {
     if (c->planned) return LBM_E_STATE;
     if ((t->ring_slots != 0 && (t->ring_slots < 4 || t->ring_slots > 8)) ||
         (t->chunk_rows != 0 && (t->chunk_rows < 8 || t->chunk_rows > (1 << 20))) || t->aligned < -1 ||
-        t->aligned > 1)
+        t->aligned > 1 || t->plan < 0 || t->plan > 2)
         return LBM_E_INVALID;
     c->tune_ring = t->ring_slots;
     c->tune_chunk = t->chunk_rows;
     c->tune_aligned = t->aligned;
+    c->tune_plan = t->plan;
     return LBM_OK;
 }
 
@@ -759,10 +772,12 @@ lbm_status lbm_get_tuning(const lbm_ctx* c, lbm_tuning* t) {
         t->ring_slots = c->i_ring;
         t->chunk_rows = c->i_chunk[0];
         t->aligned = c->tune_aligned == 1 ? 1 : 0;
+        t->plan = 2;
     } else {
         t->ring_slots = c->tune_ring;
         t->chunk_rows = c->tune_chunk;
         t->aligned = c->tune_aligned;
+        t->plan = c->planned ? 1 : c->tune_plan;
     }
     return LBM_OK;
 }
@@ -779,54 +794,60 @@ lbm_status lbm_autotune(const lbm_desc* d, const int32_t edge_kind[4], int64_t s
     lbm_desc sd = *d;  // the same body shape and format, zero initial fields
     sd.u0 = nullptr;
     sd.v0 = nullptr;
-    // candidates: ring depth x rows per CTA (0: one wave) x strip grid
+    // candidates: the interior kernel with ring depth x rows per CTA (0: one
+    // wave) x strip grid, and edge tiles only
     const int rings[3] = {4, 5, 6};
     const int chunks[4] = {0, 32, 96, 256};
-    double best_t = INFINITY;
-    lbm_tuning bt = {0, 0, -1};
-    lbm_status last = LBM_OK;
+    lbm_tuning cand[25];
+    int ncand = 0;
     for (int a = 0; a < 2; ++a)
         for (int ri = 0; ri < 3; ++ri)
             for (int ci = 0; ci < 4; ++ci) {
-                const int ch = chunks[ci];
-                if (ch > 0 && ch >= d->ny) continue;  // the same as one chunk of all rows
-                lbm_ctx* c = nullptr;
-                lbm_status st = lbm_create(&sd, &c);
-                if (st != LBM_OK) return st;
-                const lbm_tuning t = {rings[ri], ch, a};
-                st = lbm_set_tuning(c, &t);
-                if (st == LBM_OK) st = lbm_set_material(c, 0.3, 0.3, 1.0, 1.0, nullptr);
-                for (int e = 0; e < 4 && st == LBM_OK; ++e)
-                    st = lbm_set_boundary(c, e, edge_kind[e], nullptr, nullptr, nullptr);
-                // warm: initialisation, a plain step, the graphs of both parities
-                if (st == LBM_OK) st = lbm_step(c, 2 * kGraphChunk + 2);
-                double ms = INFINITY;
-                if (st == LBM_OK) {
-                    DeviceGuard guard(c->device);
-                    cudaEvent_t e0 = nullptr, e1 = nullptr;
-                    cudaError_t err = cudaEventCreate(&e0);
-                    if (err == cudaSuccess) err = cudaEventCreate(&e1);
-                    if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
-                    if (err == cudaSuccess) st = lbm_step(c, steps);
-                    if (err == cudaSuccess && st == LBM_OK) err = cudaEventRecord(e1, c->stream);
-                    if (err == cudaSuccess && st == LBM_OK) err = cudaEventSynchronize(e1);
-                    float f = 0;
-                    if (err == cudaSuccess && st == LBM_OK && cudaEventElapsedTime(&f, e0, e1) == cudaSuccess)
-                        ms = double(f) / double(steps);
-                    if (e0) cudaEventDestroy(e0);
-                    if (e1) cudaEventDestroy(e1);
-                    if (err != cudaSuccess) st = LBM_E_CUDA;
-                }
-                lbm_destroy(c);
-                if (st != LBM_OK) {
-                    last = st;
-                    continue;
-                }
-                if (ms < best_t) {
-                    best_t = ms;
-                    bt = t;
-                }
+                if (chunks[ci] > 0 && chunks[ci] >= d->ny) continue;  // the same as one chunk of all rows
+                cand[ncand++] = lbm_tuning{rings[ri], chunks[ci], a, 2};
             }
+    cand[ncand++] = lbm_tuning{0, 0, -1, 1};
+    double best_t = INFINITY;
+    lbm_tuning bt = {0, 0, -1, 0};
+    lbm_status last = LBM_OK;
+    for (int k = 0; k < ncand; ++k) {
+        lbm_ctx* c = nullptr;
+        lbm_status st = lbm_create(&sd, &c);
+        if (st != LBM_OK) return st;
+        const lbm_tuning t = cand[k];
+        st = lbm_set_tuning(c, &t);
+        if (st == LBM_OK) st = lbm_set_material(c, 0.3, 0.3, 1.0, 1.0, nullptr);
+        for (int e = 0; e < 4 && st == LBM_OK; ++e)
+            st = lbm_set_boundary(c, e, edge_kind[e], nullptr, nullptr, nullptr);
+        // warm: initialisation, a plain step, the graphs of both parities
+        if (st == LBM_OK) st = lbm_step(c, 2 * kGraphChunk + 2);
+        double ms = INFINITY;
+        if (st == LBM_OK) {
+            DeviceGuard guard(c->device);
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            cudaError_t err = cudaEventCreate(&e0);
+            if (err == cudaSuccess) err = cudaEventCreate(&e1);
+            if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+            if (err == cudaSuccess) st = lbm_step(c, steps);
+            if (err == cudaSuccess && st == LBM_OK) err = cudaEventRecord(e1, c->stream);
+            if (err == cudaSuccess && st == LBM_OK) err = cudaEventSynchronize(e1);
+            float f = 0;
+            if (err == cudaSuccess && st == LBM_OK && cudaEventElapsedTime(&f, e0, e1) == cudaSuccess)
+                ms = double(f) / double(steps);
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            if (err != cudaSuccess) st = LBM_E_CUDA;
+        }
+        lbm_destroy(c);
+        if (st != LBM_OK) {
+            last = st;
+            continue;
+        }
+        if (ms < best_t) {
+            best_t = ms;
+            bt = t;
+        }
+    }
     if (!(best_t < INFINITY)) return last != LBM_OK ? last : LBM_E_CUDA;
     *best = bt;
     if (best_ms) *best_ms = best_t;

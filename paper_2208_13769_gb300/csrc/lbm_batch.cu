@@ -199,11 +199,33 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_sync, cudaEventDisableTiming);
 
+    // each member's rectangles: the interior kernel wherever the body allows
+    // it (plan 2), whatever plan the member runs alone with (plan 0 gives
+    // small bodies edge tiles only; in a batch their interior tiles fill the
+    // persistent grid better), unless the member asked for edge tiles only
+    struct Rects {
+        int irect[4][4];
+        int n_irect;
+        int brect[12][4];
+        int nband;
+    };
+    std::vector<Rects> mr;
+    try {
+        mr.resize(size_t(n));
+    } catch (...) {
+        batch_free(b);
+        delete b;
+        return LBM_E_OOM;
+    }
     // interior tiles: rows per chunk so that the batch holds about eight
     // waves of resident CTAs (at least 32 rows, at most 256)
     int64_t all_interior = 0;
-    for (lbm_ctx* c : b->m) {
-        all_interior += interior_nodes(c);
+    for (int i = 0; i < n; ++i) {
+        const lbm_ctx* c = b->m[size_t(i)];
+        Rects& r = mr[size_t(i)];
+        plan_rects(c, c->tune_plan == 1, r.irect, &r.n_irect, r.brect, &r.nband);
+        for (int k = 0; k < r.n_irect; ++k)
+            all_interior += int64_t(r.irect[k][1] - r.irect[k][0]) * (r.irect[k][3] - r.irect[k][2]);
         b->holed = b->holed || c->hole[0] < c->hole[1];
     }
     b->ring = tuning && tuning->ring_slots ? tuning->ring_slots : kBatchRing;
@@ -223,13 +245,14 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
         std::vector<StepParams> ent;
         for (int i = 0; i < n; ++i) {
             lbm_ctx* c = b->m[size_t(i)];
+            const Rects& mri = mr[size_t(i)];
             first_entry[size_t(i)] = int(ent.size());
-            const int nr = std::max(1, c->n_irect);
+            const int nr = std::max(1, mri.n_irect);
             for (int q = 0; q < nr; ++q) {
                 StepParams p = make_params(c, b->base_parity[size_t(i)]);
                 int ns = 0;
-                if (q < c->n_irect) {
-                    for (int k = 0; k < 4; ++k) p.rect[k] = c->irect[q][k];
+                if (q < mri.n_irect) {
+                    for (int k = 0; k < 4; ++k) p.rect[k] = mri.irect[q][k];
                     interior_strips(b->fmt, p.rect[0], p.rect[1], true, &p.strip_x0, &p.strip_w, &ns);
                 }
                 p.chunk_rows = b->chunk_rows;
@@ -237,7 +260,7 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
                 ent.push_back(p);
                 strips.push_back(ns);
                 owner.push_back(i);
-                if (q < c->n_irect) {
+                if (q < mri.n_irect) {
                     const int e = int(ent.size()) - 1;
                     const int h = p.rect[3] - p.rect[2];
                     const int sy = (h + b->chunk_rows - 1) / b->chunk_rows;
@@ -262,14 +285,14 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
             tab[ent.size() + e] = p;
         }
         for (int i = 0; i < n; ++i) {
-            lbm_ctx* c = b->m[size_t(i)];
+            const Rects& mri = mr[size_t(i)];
             bool first = true;
             const int e = first_entry[size_t(i)];
-            for (int r = 0; r < c->nband; ++r) {
-                const int cnt = edge_tiles_of_rect(c->brect[r], e, nullptr, 0, false, kInteriorThreads);
+            for (int r = 0; r < mri.nband; ++r) {
+                const int cnt = edge_tiles_of_rect(mri.brect[r], e, nullptr, 0, false, kInteriorThreads);
                 const size_t at = tiles.size();
                 tiles.resize(at + size_t(cnt));
-                edge_tiles_of_rect(c->brect[r], e, tiles.data() + at, cnt, first, kInteriorThreads);
+                edge_tiles_of_rect(mri.brect[r], e, tiles.data() + at, cnt, first, kInteriorThreads);
                 first = first && cnt == 0;
             }
         }

@@ -97,7 +97,7 @@ struct lbm_ctx {
     int i_ring = 0;
     // requested decomposition of the interior launch (lbm_set_tuning); 0 / -1:
     // the library's defaults
-    int tune_ring = 0, tune_chunk = 0, tune_aligned = -1;
+    int tune_ring = 0, tune_chunk = 0, tune_aligned = -1, tune_plan = 0;
     int nband = 0;
     int brect[12][4];
     lbm::StepParams* dparams = nullptr;  // device: make_params(parity 0), make_params(parity 1)
@@ -126,6 +126,10 @@ StepParams make_params(const lbm_ctx* c, int parity);
 lbm_status ctx_ready(const lbm_ctx* c);
 // Nodes the interior launches advance (all interior rectangles).
 int64_t interior_nodes(const lbm_ctx* c);
+// The rectangles of a step: the interior kernel's (n_irect, up to 4: a hole
+// splits the interior; none for a body too small for it) and the edge
+// tiles' (nband, up to 12).  edge_only: everything as edge tiles.
+void plan_rects(const lbm_ctx* c, bool edge_only, int irect[4][4], int* n_irect, int brect[12][4], int* nband);
 // Plans the launches and runs the initialisation of Algorithm 1 once.
 lbm_status ctx_ensure_initialized(lbm_ctx* c);
 // Synchronises the context's stream and maps its device flag to a status.

@@ -44,10 +44,12 @@ class lbm_desc(C.Structure):
 
 
 class lbm_tuning(C.Structure):
-    _fields_ = [("ring_slots", C.c_int32), ("chunk_rows", C.c_int32), ("aligned", C.c_int32)]
+    _fields_ = [("ring_slots", C.c_int32), ("chunk_rows", C.c_int32), ("aligned", C.c_int32),
+                ("plan", C.c_int32)]
 
     def as_dict(self) -> dict:
-        return {"ring_slots": self.ring_slots, "chunk_rows": self.chunk_rows, "aligned": self.aligned}
+        return {"ring_slots": self.ring_slots, "chunk_rows": self.chunk_rows, "aligned": self.aligned,
+                "plan": self.plan}
 
 
 class lbm_field_geometry(C.Structure):
@@ -339,7 +341,7 @@ def lbm_autotune(desc: lbm_desc, edge_kinds, steps: int = 129) -> tuple:
 
 
 def tuning_from_dict(d: dict) -> lbm_tuning:
-    return lbm_tuning(int(d["ring_slots"]), int(d["chunk_rows"]), int(d["aligned"]))
+    return lbm_tuning(int(d["ring_slots"]), int(d["chunk_rows"]), int(d["aligned"]), int(d.get("plan", 0)))
 
 
 def autotune_cached(prob, storage: str = "f32", compensated: Optional[bool] = None,
@@ -352,7 +354,7 @@ def autotune_cached(prob, storage: str = "f32", compensated: Optional[bool] = No
 
     comp = True if compensated is None else compensated
     kinds = [e.kind for e in prob.edges]
-    key = f"{storage}:{int(comp)}:{scheme}:{prob.nx}x{prob.ny}:{''.join(str(k) for k in kinds)}"
+    key = f"{storage}:{int(comp)}:{scheme}:{prob.nx}x{prob.ny}:{''.join(str(k) for k in kinds)}:p"
     cache = {}
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as fh:

@@ -11,3 +11,31 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: long CPU-oracle run")
+    config.addinivalue_line("markers", "auto_plan: bodies keep the library's size-based plan")
+
+
+@pytest.fixture(autouse=True)
+def _interior_kernel_wherever_possible(request, monkeypatch):
+    """The library advances bodies under 2^18 nodes (2^19 in FP64) with edge
+    tiles only.  The test bodies are mostly that small, and most tests are
+    about the interior kernel's decompositions and its meeting with the edge
+    bands, so every body a test builds takes plan 2 (the interior kernel
+    wherever the body allows it) unless the test is marked auto_plan or
+    names a plan; the size-based plan and the edge-only plan have tests of
+    their own."""
+    if request.node.get_closest_marker("auto_plan"):
+        return
+    try:
+        from paper_2208_13769_gb300 import lbm
+    except Exception:  # the CPU-only tests run without the library
+        return
+    original = lbm.Body.__init__
+
+    def init(self, prob, *args, tuning=None, **kwargs):
+        if tuning is None:
+            tuning = lbm.lbm_tuning(0, 0, -1, 2)
+        elif tuning.plan == 0:
+            tuning = lbm.lbm_tuning(tuning.ring_slots, tuning.chunk_rows, tuning.aligned, 2)
+        original(self, prob, *args, tuning=tuning, **kwargs)
+
+    monkeypatch.setattr(lbm.Body, "__init__", init)

@@ -226,6 +226,8 @@ def test_call_order_and_argument_errors():
     try:
         L = lbm.lib()
         assert L.lbm_step(ctx, 1) == lbm.LBM_E_STATE
+        for bad in ((0, 0, -1, 3), (0, 0, -1, -1), (3, 0, -1, 0), (0, 4, -1, 0), (0, 0, 2, 0)):
+            assert L.lbm_set_tuning(ctx, lbm.C.byref(lbm.lbm_tuning(*bad))) == lbm.LBM_E_INVALID, bad
         assert L.lbm_set_material(ctx, 0.3, -1.0, 1.0, 1.0, None) == lbm.LBM_E_INVALID
         assert L.lbm_set_material(ctx, 0.3, 0.3, 1.0, 2.5, None) == lbm.LBM_E_INVALID
         lbm.lbm_set_material(ctx, 0.3, 0.3, 1.0, 1.0)
@@ -286,7 +288,9 @@ def test_tuning_changes_the_split_not_the_result():
     d = lbm.lbm_desc()
     d.nx, d.ny, d.dX, d.storage, d.u_carry, d.scheme = 400, 300, 1.0, lbm.LBM_F32, 1, 1
     best, ms = lbm.lbm_autotune(d, [e.kind for e in big.edges], 65)
-    assert best.ring_slots in (4, 5, 6) and best.chunk_rows in (0, 32, 96, 256) and best.aligned in (0, 1)
+    # an interior decomposition, or the edge tiles alone (the faster at this size)
+    assert (best.plan == 2 and best.ring_slots in (4, 5, 6) and best.chunk_rows in (0, 32, 96, 256)
+            and best.aligned in (0, 1)) or (best.plan == 1 and best.ring_slots == 0), best.as_dict()
     assert 0 < ms < 1.0
     with lbm.Body(big, storage="f32") as b:
         with pytest.raises(lbm.LbmError):
@@ -324,3 +328,55 @@ def test_benchmark_body_at_full_size_against_the_oracle():
     compare(ref, got32, 5 * TOL["f32"], keys=("P",))
     compare(ref, got64, TOL["f64"], keys=("u", "v", "J"))
     compare(ref, got64, 100 * TOL["f64"], keys=("P", "Pbar"))
+
+
+AUTO_CASES = ["clamped_96x50", "periodic_100x70", "x_periodic_y_walls_70x37", "ragged_33x13_mixed",
+              "tension_ramp_40", "all_dirichlet_moving_33x40"]
+
+
+@pytest.mark.auto_plan
+@pytest.mark.parametrize("name", AUTO_CASES)
+def test_small_bodies_run_as_edge_tiles_and_match_the_oracle(name):
+    """The library's default plan: a body under 2^18 nodes (2^19 in FP64) is
+    advanced by edge tiles alone; FP64 parity at 1e-12 and FP32 at 1e-5."""
+    prob, steps = CASES[name]
+    ref, got = run_both(prob, steps, "f64")
+    compare(ref, got, TOL["f64"], keys=("u", "v", "P", "Pbar", "r", "J", "sigma"), prob=prob)
+    if name in FP32_STEPS:
+        ref, got = run_both(prob, FP32_STEPS[name], "f32", compensated=True)
+        compare(ref, got, TOL["f32"])
+    with lbm.Body(prob, storage="f32") as b:
+        b.step(1)
+        assert lbm.lbm_get_tuning(b.ctx).plan == 1
+
+
+@pytest.mark.auto_plan
+def test_the_plan_switches_at_the_size_thresholds():
+    """Edge tiles alone below 2^18 nodes in FP32 and FP16, below 2^19 in
+    FP64; the interior kernel from there on; plans 1 and 2 as requested."""
+    def plan_of(nx, ny, storage, tuning=None):
+        prob = W.smooth_random(nx, ny, W.clamped_free_edges(), seed=5, amp=0.0, lam=0.3, mu=0.3)
+        with lbm.Body(prob, storage=storage, tuning=tuning) as b:
+            b.step(1)
+            return lbm.lbm_get_tuning(b.ctx).plan
+
+    assert plan_of(512, 511, "f32") == 1 and plan_of(512, 512, "f32") == 2
+    assert plan_of(512, 511, "f16") == 1 and plan_of(512, 512, "f16") == 2
+    assert plan_of(724, 724, "f64") == 1 and plan_of(725, 724, "f64") == 2
+    assert plan_of(64, 64, "f32", lbm.lbm_tuning(0, 0, -1, 2)) == 2
+    assert plan_of(600, 600, "f32", lbm.lbm_tuning(0, 0, -1, 1)) == 1
+
+
+def test_edge_tiles_only_on_a_larger_body_match_the_oracle():
+    """Plan 1 (edge tiles only) on a body large enough for the interior
+    kernel, in FP64 and FP32."""
+    prob = W.smooth_random(400, 300, W.clamped_free_edges(), seed=23, amp=0.01, vamp=0.004, lam=0.3, mu=0.3)
+    s = oracle.solver_from(prob, oracle.PREDICTOR)
+    s.step(100)
+    ref = s.read()
+    for storage, tol in (("f64", TOL["f64"]), ("f32", TOL["f32"])):
+        with lbm.Body(prob, storage=storage, tuning=lbm.lbm_tuning(0, 0, -1, 1)) as b:
+            b.step(100)
+            got = b.read()
+            assert lbm.lbm_get_tuning(b.ctx).plan == 1
+        compare(ref, got, tol)
