@@ -187,17 +187,18 @@ LBM_API lbm_status lbm_profile_interior(lbm_ctx* ctx, int64_t nlaunches, double 
  * the work is split, never the result: the interior settings give
  * bit-identical fields; the plan decides which kernel advances the nodes
  * more than two nodes from an edge, whose results agree to rounding).  The
- * interior kernel's row pipeline has a latency floor per launch (about 20 us
- * in FP32, 110 us in FP64) that small bodies do not fill, while edge tiles
+ * interior kernel's row pipeline has a latency floor per launch (about 13 us
+ * in FP32 with its shortest 8-row tiles) that small bodies do not fill, while edge tiles
  * take one memory round trip each: below the size thresholds of plan 0 the
- * edge tiles alone are faster (2 to 9 times up to 256 x 256). */
+ * edge tiles alone are faster (2 to 5 times up to 256 x 256). */
 typedef struct {
     int32_t ring_slots; /* rows of the bulk-copy ring, 4..8 (all of them in flight); 0: default (4) */
-    int32_t chunk_rows; /* rows per CTA, >= 8; 0: one wave of CTAs over the SMs (default) */
+    int32_t chunk_rows; /* rows per CTA, >= 8; 0: one wave of CTAs over the SMs, at least 8 rows
+                           each (default) */
     int32_t aligned;    /* 1: the fewest strips of equal width on 32-byte sector boundaries (at
                            most 120 columns; 112 for 16-bit storage); 0: 124-column strips;
                            -1: default (0) */
-    int32_t plan;       /* 0: by size (default): a body of fewer than 2^18 nodes (2^19 in FP64)
+    int32_t plan;       /* 0: by size (default): a body of fewer than 2^17 nodes (3 x 2^17 in FP64)
                            runs as small tiles of the edge kernel only, a larger one as the
                            interior kernel plus the edge bands; 1: edge tiles only; 2: the
                            interior kernel wherever the body allows it */

@@ -16,7 +16,7 @@ def pytest_configure(config):
 
 @pytest.fixture(autouse=True)
 def _interior_kernel_wherever_possible(request, monkeypatch):
-    """The library advances bodies under 2^18 nodes (2^19 in FP64) with edge
+    """The library advances bodies under 2^17 nodes (3 x 2^17 in FP64) with edge
     tiles only.  The test bodies are mostly that small, and most tests are
     about the interior kernel's decompositions and its meeting with the edge
     bands, so every body a test builds takes plan 2 (the interior kernel

@@ -337,7 +337,7 @@ AUTO_CASES = ["clamped_96x50", "periodic_100x70", "x_periodic_y_walls_70x37", "r
 @pytest.mark.auto_plan
 @pytest.mark.parametrize("name", AUTO_CASES)
 def test_small_bodies_run_as_edge_tiles_and_match_the_oracle(name):
-    """The library's default plan: a body under 2^18 nodes (2^19 in FP64) is
+    """The library's default plan: a body under 2^17 nodes (3 x 2^17 in FP64) is
     advanced by edge tiles alone; FP64 parity at 1e-12 and FP32 at 1e-5."""
     prob, steps = CASES[name]
     ref, got = run_both(prob, steps, "f64")
@@ -352,7 +352,7 @@ def test_small_bodies_run_as_edge_tiles_and_match_the_oracle(name):
 
 @pytest.mark.auto_plan
 def test_the_plan_switches_at_the_size_thresholds():
-    """Edge tiles alone below 2^18 nodes in FP32 and FP16, below 2^19 in
+    """Edge tiles alone below 2^17 nodes in FP32 and FP16, below 3 x 2^17 in
     FP64; the interior kernel from there on; plans 1 and 2 as requested."""
     def plan_of(nx, ny, storage, tuning=None):
         prob = W.smooth_random(nx, ny, W.clamped_free_edges(), seed=5, amp=0.0, lam=0.3, mu=0.3)
@@ -360,9 +360,9 @@ def test_the_plan_switches_at_the_size_thresholds():
             b.step(1)
             return lbm.lbm_get_tuning(b.ctx).plan
 
-    assert plan_of(512, 511, "f32") == 1 and plan_of(512, 512, "f32") == 2
-    assert plan_of(512, 511, "f16") == 1 and plan_of(512, 512, "f16") == 2
-    assert plan_of(724, 724, "f64") == 1 and plan_of(725, 724, "f64") == 2
+    assert plan_of(362, 362, "f32") == 1 and plan_of(363, 362, "f32") == 2
+    assert plan_of(362, 362, "f16") == 1 and plan_of(363, 362, "f16") == 2
+    assert plan_of(627, 627, "f64") == 1 and plan_of(628, 627, "f64") == 2
     assert plan_of(64, 64, "f32", lbm.lbm_tuning(0, 0, -1, 2)) == 2
     assert plan_of(600, 600, "f32", lbm.lbm_tuning(0, 0, -1, 1)) == 1
 
