@@ -299,9 +299,13 @@ LBM_API lbm_status lbm_destroy(lbm_ctx* ctx);
  * to several independent bodies at once: each time step is one launch over
  * the interior tiles of every member and one over their edge tiles, so small
  * or uneven bodies share the GPU instead of each paying its own launches;
- * chunks of 64 steps replay as one CUDA graph.  Every member goes through
- * the same kernels and arithmetic as when stepped alone: results are
- * bit-identical to lbm_step on each member.
+ * chunks of 64 steps replay as one CUDA graph.  The batch advances every
+ * member with the interior kernel where the body allows it (plan 2 of
+ * lbm_tuning, unless the member asked for plan 1), through the same
+ * arithmetic as a single body: results are bit-identical to lbm_step on a
+ * member that runs plan 2 (every body of 2^17 nodes or more does by
+ * default); a smaller member stepped alone runs edge tiles only, which agree
+ * with the interior kernel to rounding.
  */
 typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
 

@@ -478,7 +478,9 @@ class Body:
 
 class Batch:
     """Several Body objects (one storage format) advanced by shared launches;
-    each member's results are bit-identical to stepping it alone."""
+    each member's results are bit-identical to stepping it alone with the
+    interior kernel (plan 2; to rounding for a small member whose own default
+    plan is edge tiles only)."""
 
     def __init__(self, bodies, stream: int = 0, tuning: Optional["lbm_tuning"] = None):
         self.bodies = list(bodies)
