@@ -177,3 +177,33 @@ def test_batch_tuning_changes_the_split_not_the_result():
     finally:
         for b in bodies:
             b.close()
+
+
+@pytest.mark.auto_plan
+def test_batch_of_small_bodies_agrees_with_their_default_plan():
+    """With the library's default plan a small body stepped alone runs edge
+    tiles only, while the batch advances it with the interior kernel: the
+    two agree to rounding (FP64: 1e-12), and the batch matches the oracle."""
+    members = [m for m in _members() if m[0].nx * m[0].ny < (1 << 17)]
+    steps = 70
+    alone = []
+    for prob, scheme in members:
+        with lbm.Body(prob, storage="f64", scheme=scheme) as b:
+            b.step(steps)
+            alone.append(_fields(b))
+            assert lbm.lbm_get_tuning(b.ctx).plan == 1
+    bodies = [lbm.Body(prob, storage="f64", scheme=scheme) for prob, scheme in members]
+    try:
+        with lbm.Batch(bodies) as batch:
+            batch.step(steps)
+        for (prob, scheme), b, ref in zip(members, bodies, alone):
+            got = _fields(b)
+            for k in ("u", "v", "P"):
+                scale = max(np.linalg.norm(ref[k]), 1e-30)
+                assert np.linalg.norm(got[k] - ref[k]) <= 1e-12 * scale, (prob.name, k)
+            s = oracle.solver_from(prob, scheme)
+            s.step(steps)
+            compare(s.read(), got, 1e-12)
+    finally:
+        for b in bodies:
+            b.close()

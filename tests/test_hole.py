@@ -144,3 +144,16 @@ def test_set_hole_checks_its_arguments():
         with pytest.raises(lbm.LbmError):
             lbm.lbm_set_hole(b.ctx, (4, 20, 8, 16))
         lbm.lbm_set_hole(b.ctx, (5, 35, 5, 25))
+
+
+@pytest.mark.auto_plan
+def test_plate_with_hole_under_the_default_plan_matches_the_oracle():
+    """Sec. 7's 80 x 80 plate with its hole under the library's default plan
+    (edge tiles only at this size), FP64 against the oracle."""
+    prob = W.plate_with_hole(80, T=0.02)
+    ref, got = run_both(prob, 208, storage="f64")
+    assert got["status"] == lbm.LBM_OK
+    compare(ref, got, 1e-12, keys=("u", "v", "P", "Pbar", "J", "sigma"))
+    with lbm.Body(prob, storage="f64") as b:
+        b.step(1)
+        assert lbm.lbm_get_tuning(b.ctx).plan == 1
