@@ -220,6 +220,7 @@ static cudaError_t build_plan(lbm_ctx* c) {
         c->i_ring = c->tune_ring ? c->tune_ring : kInteriorRing;
         const int per_sm = std::max(1, interior_occupancy(c->fmt, c->i_ring));
         const int64_t slots = int64_t(c->num_sms) * per_sm;
+        const int64_t all_area = interior_nodes(c);
         for (int q = 0; q < c->n_irect; ++q) {
             const int* r = c->irect[q];
             const int h = r[3] - r[2];
@@ -229,12 +230,14 @@ static cudaError_t build_plan(lbm_ctx* c) {
             if (c->tune_chunk > 0) {
                 rows = c->tune_chunk;
             } else {
-                // one wave of equal CTAs per launch: strips x chunks <= SMs x
-                // per_sm (the rectangles' launches run one after another), at
+                // one wave of CTAs per launch (strips x chunks <= SMs x
+                // per_sm), the rectangles of a hole sharing it by area, at
                 // least 8 rows each (shorter tiles of mid-size bodies cut the
                 // row pipeline's latency: 512 x 512 FP32 in 17 us with 8-row
                 // tiles against 25 us with 16)
-                const int64_t chunks = std::max<int64_t>(1, slots / c->i_tiles_x[q]);
+                const int64_t area = int64_t(r[1] - r[0]) * h;
+                const int64_t share = std::max<int64_t>(1, slots * area / std::max<int64_t>(1, all_area));
+                const int64_t chunks = std::max<int64_t>(1, share / c->i_tiles_x[q]);
                 rows = std::max<int64_t>((h + chunks - 1) / chunks, 8);
             }
             rows = std::min<int64_t>(rows, h);
@@ -271,19 +274,30 @@ static cudaError_t build_plan(lbm_ctx* c) {
 // The interior launches of one time step, one per interior rectangle
 // (nothing if the body has no interior).
 static cudaError_t launch_interior_part(lbm_ctx* c, const StepParams& p, bool fields) {
-    for (int q = 0; q < c->n_irect; ++q) {
-        StepParams pi = p;
-        for (int k = 0; k < 4; ++k) pi.rect[k] = c->irect[q][k];
-        pi.tiles_x = c->i_tiles_x[q];
-        pi.tiles_y = c->i_tiles_y[q];
-        pi.chunk_rows = c->i_chunk[q];
-        pi.ring_slots = c->i_ring;
-        pi.strip_x0 = c->i_strip_x0[q];
-        pi.strip_w = c->i_strip_w[q];
-        const cudaError_t e = launch_interior(c->fmt, pi, c->stream, fields);
-        if (e != cudaSuccess) return e;
+    if (c->n_irect < 1) return cudaSuccess;
+    // one launch over every interior rectangle
+    InteriorRects R;
+    memset(&R, 0, sizeof(R));
+    int64_t total = 0;
+    for (int q = 0; q < 4; ++q) {
+        if (q < c->n_irect) {
+            for (int k = 0; k < 4; ++k) R.g[q].rect[k] = c->irect[q][k];
+            R.g[q].strip_x0 = c->i_strip_x0[q];
+            R.g[q].strip_w = c->i_strip_w[q];
+            R.g[q].chunk_rows = c->i_chunk[q];
+            R.tiles_x[q] = c->i_tiles_x[q];
+            R.first[q] = int32_t(total);
+            total += int64_t(c->i_tiles_x[q]) * c->i_tiles_y[q];
+        } else {
+            R.tiles_x[q] = 1;
+            R.first[q] = INT32_MAX;
+        }
     }
-    return cudaSuccess;
+    if (total > INT32_MAX - 1) return cudaErrorInvalidConfiguration;
+    R.total = int32_t(total);
+    StepParams pi = p;
+    pi.ring_slots = c->i_ring;
+    return launch_interior(c->fmt, pi, R, c->stream, fields);
 }
 
 // The edge-band launch of one time step (the whole body without an interior).

@@ -74,7 +74,7 @@ __host__ __device__ constexpr size_t interior_row_bytes() {
 
 }  // namespace
 
-// One tile (column strip bx, row chunk by of p.rect) of one body.  Returns
+// One tile (column strip bx, row chunk by of the rectangle tg) of one body.  Returns
 // false if a wait gave up or a copy was refused (reported in p.flag).
 // reuse: the CTA runs more tiles after this one, so the ring's mbarriers are
 // invalidated at the end (every copy has completed by then) for the next
@@ -89,9 +89,10 @@ __host__ __device__ constexpr size_t interior_row_bytes() {
 // D = ku jh(t) and F = ku (3 jh(t) - jh(t - dt)) (in the source planes);
 // else u* is A + ku m and the source planes hold the last source.
 template <class TS, class TC, class UT, int NT, bool KEEP, bool XJ, bool UNROLL3>
-__device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int by, double* fields, bool reuse) {
+__device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeom& tg, int bx, int by, double* fields,
+                                              bool reuse) {
     using CT = typename UT::Elem;
-    const int W = p.strip_w;
+    const int W = tg.strip_w;
     constexpr int SEG = seg_elems<TS, NT>();
     constexpr int UP = UT::planes;
     constexpr int ROW_BYTES = int(interior_row_bytes<TS, NT>());
@@ -110,14 +111,15 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
     k.load(p);
     const int64_t pitch = p.pitch, plane = p.plane;
     const int t = threadIdx.x;
-    const int rx0 = p.rect[0], rx1 = p.rect[1], ry0 = p.rect[2], ry1 = p.rect[3];
+    const int rx0 = tg.rect[0], rx1 = tg.rect[1], ry0 = tg.rect[2], ry1 = tg.rect[3];
     // strip bx of the strip grid, clipped to the rectangle
-    const int x0 = p.strip_x0 + bx * W;
+    const int x0 = tg.strip_x0 + bx * W;
     const int x_lo = max(rx0, x0), x_hi = min(rx1, x0 + W);
-    if (x_lo >= x_hi || by * p.chunk_rows >= ry1 - ry0) return true;
-    int y_begin = ry0 + by * p.chunk_rows;
-    if (y_begin > ry1 - p.chunk_rows) y_begin = ry1 - p.chunk_rows > ry0 ? ry1 - p.chunk_rows : ry0;
-    const int y_end = min(ry1, y_begin + p.chunk_rows);
+    const int chunk_rows = tg.chunk_rows;
+    if (x_lo >= x_hi || by * chunk_rows >= ry1 - ry0) return true;
+    int y_begin = ry0 + by * chunk_rows;
+    if (y_begin > ry1 - chunk_rows) y_begin = ry1 - chunk_rows > ry0 ? ry1 - chunk_rows : ry0;
+    const int y_end = min(ry1, y_begin + chunk_rows);
     // first column of the row segments: 16-byte aligned, inside the plane
     int seg0 = x0 - 3;
     seg0 = (seg0 >= 0 ? seg0 : seg0 - (ALIGN_COLS - 1)) / ALIGN_COLS * ALIGN_COLS;
@@ -447,9 +449,35 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, int bx, int b
     return true;
 }
 
+// One CTA per tile over the launch's rectangles (one 1-D grid; a body
+// without a hole has one rectangle).
 template <class TS, class TC, class UT, int NT, int MINB, bool XJ, bool UNROLL3>
-__global__ void __launch_bounds__(NT, MINB) interior_step_kernel(const __grid_constant__ StepParams p) {
-    interior_tile<TS, TC, UT, NT, true, XJ, UNROLL3>(p, int(blockIdx.x), int(blockIdx.y), p.fields, false);
+__global__ void __launch_bounds__(NT, MINB)
+    interior_step_kernel(const __grid_constant__ StepParams p, const __grid_constant__ InteriorRects R) {
+    const int b = int(blockIdx.x);
+    const int q = (b >= R.first[1]) + (b >= R.first[2]) + (b >= R.first[3]);
+    TileGeom tg;
+    int tx, f;
+    // the rectangle by constant indices (no indexed reads of the parameters)
+    if (q == 0) {
+        tg = R.g[0];
+        tx = R.tiles_x[0];
+        f = R.first[0];
+    } else if (q == 1) {
+        tg = R.g[1];
+        tx = R.tiles_x[1];
+        f = R.first[1];
+    } else if (q == 2) {
+        tg = R.g[2];
+        tx = R.tiles_x[2];
+        f = R.first[2];
+    } else {
+        tg = R.g[3];
+        tx = R.tiles_x[3];
+        f = R.first[3];
+    }
+    const int local = b - f;
+    interior_tile<TS, TC, UT, NT, true, XJ, UNROLL3>(p, tg, local % tx, local / tx, p.fields, false);
 }
 
 // One time step of a batch of bodies in one launch: a persistent grid of
@@ -502,8 +530,10 @@ __global__ void __launch_bounds__(NT, MINB) batch_step_kernel(const __grid_const
         }
         __syncthreads();
         if (it.kind == 0) {
-            if (!interior_tile<TS, TC, UT, NT, false, false, false>(sp, it.a, it.b, L.fields ? sp.fields : nullptr,
-                                                                    true))
+            const TileGeom tg = {{sp.rect[0], sp.rect[1], sp.rect[2], sp.rect[3]}, sp.strip_x0, sp.strip_w,
+                                 sp.chunk_rows};
+            if (!interior_tile<TS, TC, UT, NT, false, false, false>(sp, tg, it.a, it.b,
+                                                                    L.fields ? sp.fields : nullptr, true))
                 break;
         } else {
             for (int g = 0; g < it.b; ++g) {
@@ -527,7 +557,7 @@ size_t interior_smem_bytes(int ring_slots) {
 }
 
 template <class TS, class TC, class UT, int NT, int MINB, bool UNROLL3, bool XJ>
-cudaError_t launch_interior_x(const StepParams& p, cudaStream_t s) {
+cudaError_t launch_interior_x(const StepParams& p, const InteriorRects& R, cudaStream_t s) {
     auto kern = interior_step_kernel<TS, TC, UT, NT, MINB, XJ, UNROLL3>;
     const size_t sm = interior_smem_bytes<TS, TC, UT, NT>(p.ring_slots);
     static size_t configured = 0;
@@ -536,17 +566,17 @@ cudaError_t launch_interior_x(const StepParams& p, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         configured = sm;
     }
-    dim3 grid(p.tiles_x, p.tiles_y, 1);
-    kern<<<grid, NT, sm, s>>>(p);
+    if (R.total <= 0) return cudaSuccess;
+    kern<<<R.total, NT, sm, s>>>(p, R);
     return cudaGetLastError();
 }
 
 // (the extrapolated scheme's variant keeps the rotating loop: its extra
 // carries leave no registers for the unrolled one)
 template <class TS, class TC, class UT, int NT, int MINB, bool UNROLL3>
-cudaError_t launch_interior_t(const StepParams& p, cudaStream_t s) {
-    return p.scheme == 2 ? launch_interior_x<TS, TC, UT, NT, MINB, false, true>(p, s)
-                         : launch_interior_x<TS, TC, UT, NT, MINB, UNROLL3, false>(p, s);
+cudaError_t launch_interior_t(const StepParams& p, const InteriorRects& R, cudaStream_t s) {
+    return p.scheme == 2 ? launch_interior_x<TS, TC, UT, NT, MINB, false, true>(p, R, s)
+                         : launch_interior_x<TS, TC, UT, NT, MINB, UNROLL3, false>(p, R, s);
 }
 
 template <class TS, class TC, class UT, int NT, int MINB, bool HOLE>
@@ -652,15 +682,15 @@ size_t interior_smem(int fmt, int ring_slots) {
     }
 }
 
-cudaError_t launch_interior(int fmt, const StepParams& p0, cudaStream_t s, bool fields) {
+cudaError_t launch_interior(int fmt, const StepParams& p0, const InteriorRects& R, cudaStream_t s, bool fields) {
     StepParams p = p0;
     if (!fields) p.fields = nullptr;
     switch (fmt) {
-        case kFmtF64: return launch_interior_t<double, double, UPlain<double>, 128, 2, false>(p, s);
-        case kFmtF32: return launch_interior_t<float, float, UPlain<float>, 128, 6, true>(p, s);
-        case kFmtF32C: return launch_interior_t<float, float, UComp, 128, 4, false>(p, s);
-        case kFmtF16: return launch_interior_t<__half, float, UComp, 128, 4, true>(p, s);
-        case kFmtBF16: return launch_interior_t<__nv_bfloat16, float, UComp, 128, 4, true>(p, s);
+        case kFmtF64: return launch_interior_t<double, double, UPlain<double>, 128, 2, false>(p, R, s);
+        case kFmtF32: return launch_interior_t<float, float, UPlain<float>, 128, 6, true>(p, R, s);
+        case kFmtF32C: return launch_interior_t<float, float, UComp, 128, 4, false>(p, R, s);
+        case kFmtF16: return launch_interior_t<__half, float, UComp, 128, 4, true>(p, R, s);
+        case kFmtBF16: return launch_interior_t<__nv_bfloat16, float, UComp, 128, 4, true>(p, R, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -37,7 +37,24 @@ constexpr int kBatchRing = 5;
 // 32-byte sector boundaries (for CTAs of one body that may run in different
 // waves), else 124-column strips from rx0 (one wave).
 void interior_strips(int fmt, int rx0, int rx1, bool aligned, int* strip_x0, int* strip_w, int* nstrips);
-cudaError_t launch_interior(int fmt, const StepParams& p, cudaStream_t s, bool fields);
+
+// One interior rectangle of a launch: its nodes [rect[0], rect[1]) x
+// [rect[2], rect[3]), the strip grid over its columns and the rows per tile.
+struct TileGeom {
+    int32_t rect[4];
+    int32_t strip_x0, strip_w, chunk_rows;
+};
+// The rectangles of one interior launch (a hole splits the interior into up
+// to 4): tiles_x x tiles_y tiles each, numbered from first[q] in one 1-D grid
+// of total tiles.
+struct InteriorRects {
+    TileGeom g[4];
+    int32_t tiles_x[4];
+    int32_t first[4];  // unused entries: INT32_MAX
+    int32_t total;
+};
+// One step of the interior: a launch of R.total CTAs over the rectangles.
+cudaError_t launch_interior(int fmt, const StepParams& p, const InteriorRects& R, cudaStream_t s, bool fields);
 
 // One time step of a batch of bodies in one launch: a persistent grid whose
 // CTAs take the items of a work list one at a time from a device queue.  An
