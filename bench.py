@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=256,
                     help="bodies of the batched workload (seeded, sides 64..1024; 0 to skip)")
     ap.add_argument("--batch-steps", type=int, default=256)
+    ap.add_argument("--solves", type=int, default=20,
+                    help="repeated solves of the C1 and C2 workloads for p50 / p99 latency (0 to skip)")
     ap.add_argument("--serve", type=int, default=120,
                     help="requests of the serving trace replayed at 200/s (0 to skip)")
     ap.add_argument("--serve-window", type=float, default=12.0,
@@ -329,7 +331,7 @@ def run_native(a):
     ranks = Ranks("nccl")
     rank, world, local = ranks.rank, ranks.world, ranks.local
     if world > 1:  # the extra sections run on single-GPU invocations only
-        a.forms, a.schemes, a.batch, a.serve = "", "", 0, 0
+        a.forms, a.schemes, a.batch, a.serve, a.solves = "", "", 0, 0, 0
 
     def barrier():
         ranks.barrier()
@@ -597,6 +599,53 @@ def run_native(a):
 
     # end to end through the C ABI from host buffers: create (H2D of u0, v0),
     # K steps, read u (D2H)
+    # solve latency: a solve creates the body from host arrays, initialises
+    # it, runs its steps and reads u back to the host (host clock around
+    # all of it); p50 / p99 over repeated solves of the 64 x 64 FP64 shear
+    # wave (1000 steps), the benchmark's clamped body in its format (2000 steps:
+    # the planned 5000 lie beyond its stable horizon) and the 256-body batch
+    # (256 steps; its members complete together)
+    solves = None
+    if a.solves > 0 and world == 1:
+        from paper_2208_13769_gb300 import workloads as W
+
+        def one_solve(make, steps):
+            t0 = time.perf_counter()
+            bodies = make()
+            if len(bodies) == 1:
+                bodies[0].step(steps)
+            else:
+                with lbm.Batch(bodies, stream=stream.cuda_stream) as bt:
+                    bt.step(steps)
+            for b in bodies:
+                b.read(lbm.LBM_FIELD_U, allow_unstable=True)
+            t1 = time.perf_counter()
+            for b in bodies:
+                b.close()
+            return t1 - t0
+
+        def stats(times, nodes_per_solve, steps):
+            times = sorted(times)
+            q = lambda f: times[min(len(times) - 1, int(round(f * (len(times) - 1))))]
+            return {"solves": len(times), "steps": steps, "p50_s": q(0.5), "p99_s": q(0.99),
+                    "mlups_at_p50": nodes_per_solve * steps / q(0.5) / 1e6}
+
+        c1 = W.shear_wave(64, amp=0.01, lam=0.5, mu=0.3)
+        c2 = W.clamped_body(a.nx, a.ny, mu=0.3, nu=a.nu, vmax=a.vmax)
+        c4 = W.body_batch(256)
+        solves = {}
+        for name, make, steps, n_solves, nodes_per in (
+                ("c1_64x64_f64", lambda: [lbm.Body(c1, storage="f64", stream=stream.cuda_stream, device=local)],
+                 1000, a.solves, 64 * 64),
+                ("c2_%dx%d_%s" % (a.nx, a.ny, a.storage),
+                 lambda: [lbm.Body(c2, storage=a.storage, compensated=a.compensated, stream=stream.cuda_stream,
+                                   device=local, tuning=tuning)], 2000, a.solves, a.nx * a.ny),
+                ("c4_256_bodies_f32", lambda: [lbm.Body(p, storage="f32", stream=stream.cuda_stream, device=local)
+                                               for p in c4.problems], 256, max(1, a.solves // 4),
+                 sum(p.nx * p.ny for p in c4.problems))):
+            one_solve(make, 8)  # warm: kernels loaded, graphs of this shape built once
+            solves[name] = stats([one_solve(make, steps) for _ in range(n_solves)], nodes_per, steps)
+
     e2e = None
     if not a.no_e2e:
         import dataclasses
@@ -642,7 +691,7 @@ def run_native(a):
         "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "f16": "f16", "bf16": "bf16"}[a.storage],
         "data": "synthetic", "config": config_of(a, prob), "roofline": roof, "cpu_baseline": cpu,
-        "e2e": e2e, "gpu_launches": 2 * a.steps, "clocks": clk, "forms": forms, "schemes": schemes, "c3_8192": c3, "plate_hole": hole, "batched": batched,
+        "e2e": e2e, "gpu_launches": 2 * a.steps, "clocks": clk, "forms": forms, "schemes": schemes, "solves": solves, "c3_8192": c3, "plate_hole": hole, "batched": batched,
         "serving": serving, "tuning": tuning_info,
         "status": lbm.status_string(status),
     }
