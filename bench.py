@@ -208,6 +208,23 @@ def oracle_sample(prob, steps):
     return prob.nodes * steps / dt / 1e6, dt, oracle.threads()
 
 
+def oracle_single_thread(a, steps):
+    """The oracle on one core: the reference arm in a child process with
+    OMP_NUM_THREADS=1 (the OpenMP runtime reads it at start-up), on `steps`
+    steps of the same body."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", "1", "--warmup", "0",
+           "--cpu-steps", str(steps), "--nx", str(a.nx), "--ny", str(a.ny), "--nu", str(a.nu),
+           "--vmax", str(a.vmax)]
+    try:
+        r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600, check=True)
+        line = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"value": line["value"], "unit": "MLUPS", "cores": line["cpu_baseline"]["cores"],
+                "sample": line["cpu_baseline"]["sample"]}
+    except Exception as exc:  # reported, not fatal: the all-core figure stands
+        return {"value": None, "error": str(exc)[:200]}
+
+
 def auto_cpu_steps(prob, budget_s=12.0):
     mlups, dt, _ = oracle_sample(prob, 1)
     per = prob.nodes / (mlups * 1e6)
@@ -681,7 +698,8 @@ def run_native(a):
         steps = a.cpu_steps or auto_cpu_steps(prob)
         v, dt, cores = oracle_sample(prob, steps)
         cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-               "sample": f"{steps} time steps of the full {a.nx}x{a.ny} body ({dt:.1f} s, FP64 oracle)"}
+               "sample": f"{steps} time steps of the full {a.nx}x{a.ny} body ({dt:.1f} s, FP64 oracle)",
+               "single_thread": oracle_single_thread(a, max(1, steps // max(1, cores)))}
 
     ranks.close()
     if rank != 0:
