@@ -448,7 +448,7 @@ __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepP
             p.fields[2 * np + fo] = double(j0 * k.c_over_rho0);
             p.fields[3 * np + fo] = double(j1 * k.c_over_rho0);
             p.fields[4 * np + fo] = double(r);
-            if (!(fabs(double(j0)) + fabs(double(j1)) < 1e300)) bad = true;
+            if (!(isfinite(j0) && isfinite(j1))) bad = true;  // in the arithmetic type: no FP64 work
         }
     }
     if (bad) atomicOr(p.flag, 1);

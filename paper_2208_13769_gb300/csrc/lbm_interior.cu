@@ -400,7 +400,7 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeo
                 fields[2 * np + fo] = double(j0 * k.c_over_rho0);
                 fields[3 * np + fo] = double(j1 * k.c_over_rho0);
                 fields[4 * np + fo] = double(r);
-                if (!(fabs(double(j0)) + fabs(double(j1)) < 1e300)) bad = true;
+                if (!(isfinite(j0) && isfinite(j1))) bad = true;  // in the arithmetic type: no FP64 work
             }
         }
         ra = ra + 1 == R ? 0 : ra + 1;
