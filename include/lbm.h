@@ -136,7 +136,7 @@ LBM_API lbm_status lbm_set_boundary(lbm_ctx* ctx, int32_t edge, int32_t kind, co
  * Its faces lie half-way between the body's last node and the first removed
  * one and are Neumann boundaries with a constant traction each: traction
  * holds (Tx, Ty) for the faces at x0, x1, y0, y1 in that order (NULL:
- * traction-free).  A face takes the quadratic ghost of the differences and
+ * traction-free).  A face takes the linear ghost of the differences and
  * anti-bounce-back (Eq. abbcon) with its outward normal (pointing into the
  * hole); a link through a corner of the hole takes both faces, N = (N1 +
  * N2)/sqrt(2), T* = (T1 + T2)/sqrt(2).  Only before the first lbm_step /

@@ -57,7 +57,22 @@ class OracleProblem(C.Structure):
         ("scheme", C.c_int32),
         ("hole", C.c_int32 * 4),
         ("hole_T", (C.c_double * 2) * 4),
+        ("alt_feq_pbar", C.c_int32),
+        ("alt_wall", C.c_int32),
+        ("alt_ghost_u", C.c_int32),
+        ("alt_ghost_q", C.c_int32),
+        ("mu_bar", C.c_double),
     ]
+
+
+# Alternative readings of the paper's open points (all zero: the readings the
+# oracle's header lists).  Keys of the `readings` dict of make_problem:
+#   feq_pbar -- 1: f^eq takes Pbar(H) of Eq. (Plin), as Algorithm 1's listing
+#   wall     -- 1: anti-bounce-back wall values extrapolated linearly to the wall
+#   ghost_u  -- 1: the Neumann ghost of u quadratic instead of linear
+#   ghost_q  -- 1: the ghost of Q = P + Pbar quadratic instead of linear; 2: constant
+#   mu_bar   -- split stiffness: Pbar and C_s built with mu_bar (0: mu)
+READING_KEYS = ("feq_pbar", "wall", "ghost_u", "ghost_q", "mu_bar")
 
 
 def build(force: bool = False) -> str:
@@ -121,16 +136,16 @@ def _dp(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-def problem_from(wp, scheme: int = PREDICTOR) -> OracleProblem:
+def problem_from(wp, scheme: int = PREDICTOR, readings=None) -> OracleProblem:
     """OracleProblem from a workloads.Problem-like object."""
     return make_problem(wp.nx, wp.ny, wp.dX, wp.lam, wp.mu, wp.rho0, wp.omega, wp.body,
                         wp.edge_dicts(), scheme, hole=getattr(wp, "hole", None),
-                        hole_traction=getattr(wp, "hole_traction", None))
+                        hole_traction=getattr(wp, "hole_traction", None), readings=readings)
 
 
-def solver_from(wp, scheme: int = PREDICTOR) -> "Solver":
+def solver_from(wp, scheme: int = PREDICTOR, readings=None) -> "Solver":
     u0, v0 = wp.initial() if hasattr(wp, "initial") else (wp.u0, wp.v0)
-    return Solver(problem_from(wp, scheme), u0, v0)
+    return Solver(problem_from(wp, scheme, readings), u0, v0)
 
 
 def _f64(x, shape=None) -> np.ndarray:
@@ -200,7 +215,7 @@ def threads() -> int:
 # ---------------------------------------------------------------- solver
 
 def make_problem(nx, ny, dX, lam, mu, rho0, omega, body, edges,
-                 scheme: int = PREDICTOR, hole=None, hole_traction=None) -> OracleProblem:
+                 scheme: int = PREDICTOR, hole=None, hole_traction=None, readings=None) -> OracleProblem:
     """edges: four dicts {kind, value, rate, times} in order x-, x+, y-, y+.
 
     scheme: EXPLICIT (Algorithm 1's time-t source in collision and moment),
@@ -208,7 +223,8 @@ def make_problem(nx, ny, dX, lam, mu, rho0, omega, body, edges,
     (Sec. 5's linear extrapolation of j to t + dt for the moment's source).
     hole: (x0, x1, y0, y1), the removed nodes of a rectangular hole, or None;
     hole_traction: the constant traction on its faces at x0, x1, y0, y1 (four
-    pairs; None: traction-free)."""
+    pairs; None: traction-free).  readings: alternative readings (a dict
+    with keys from READING_KEYS; None: the oracle's readings)."""
     p = OracleProblem()
     p.scheme = int(scheme)
     p.nx, p.ny = int(nx), int(ny)
@@ -229,6 +245,13 @@ def make_problem(nx, ny, dX, lam, mu, rho0, omega, body, edges,
             p.hole[k] = int(hole[k])
         for k, tr in enumerate(hole_traction or [(0.0, 0.0)] * 4):
             p.hole_T[k][0], p.hole_T[k][1] = float(tr[0]), float(tr[1])
+    for key, val in (readings or {}).items():
+        if key not in READING_KEYS:
+            raise ValueError(f"unknown reading {key!r}")
+        if key == "mu_bar":
+            p.mu_bar = float(val)
+        else:
+            setattr(p, "alt_" + key, int(val))
     return p
 
 

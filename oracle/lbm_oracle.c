@@ -21,7 +21,10 @@
  *       7.217e-3 at dX = 0.0125 with C_s = 1).  Lower-case c_s in Sec. 5 = C_s.
  *   R2  The trapezoidal displacement update of Sec. 5 carries a factor dt:
  *       u += dt/(2 rho0) (j_new + j_old).
- *   R3  omega = dt/tau is an input (the paper never fixes tau).
+ *   R3  omega = dt/tau is an input (the paper never fixes tau).  With the
+ *       other readings, the three runs of Sec. 7 complete at the paper's loads
+ *       only for omega in about [1.92, 1.99] (at omega = 1 each blows up before
+ *       t = 2.1); the workloads take omega = 1.95.
  *   R4  The Pbar that enters f^eq in the collision is the second moment of the
  *       streamed populations, sum_i C_i C_i f_i (Eq. moment with N = 2 and no
  *       second-order source, Sec. 3: the moments computed after streaming feed
@@ -33,8 +36,11 @@
  *   R5  Nodes of a bounded axis sit at (k+1/2) dX; walls are half-way between
  *       the edge node and the missing ghost node.  Periodic axes wrap.
  *   R6  Central differences everywhere (Sec. 5), with ghost values at bounded
- *       edges: Dirichlet u_g = 2 u*(t) - u_0, Neumann u_g = 3u_0 - 3u_1 + u_2;
- *       for Div(P + Pbar) the quadratic ghost on every bounded edge.
+ *       edges: Dirichlet u_g = 2 u*(t) - u_0, Neumann u_g = 2 u_0 - u_1 (linear
+ *       extrapolation); for Div(P + Pbar) the linear ghost 2 Q_0 - Q_1 on every
+ *       bounded edge.  Both are exact for affine u (the patch tests).  With the
+ *       quadratic extrapolation 3 v_0 - 3 v_1 + v_2 instead, the shear and
+ *       tension blocks of Sec. 7 blow up at every omega.
  *   R7  "Extrapolated to the boundary" (Sec. 6) is taken at zeroth order: the
  *       wall values are those of the edge node at time t (the level of f^col):
  *       r^bd = sum_i f_i, the tangential entry of Pbar* from the populations'
@@ -75,7 +81,7 @@
  *       nodes x0 <= x < x1, y0 <= y < y1; its four faces lie half-way between
  *       the last node of the body and the first removed one (R5) and carry a
  *       constant traction each (zero: traction-free).  A face is a Neumann
- *       boundary: the quadratic ghost of R6 for Grad u and Div Q, and
+ *       boundary: the linear ghost of R6 for Grad u and Div Q, and
  *       anti-bounce-back (R7, R8) with the face's outward normal for a link
  *       that enters the hole through it; a diagonal link that enters the hole
  *       through its corner takes N = (N1 + N2)/sqrt(2) and
@@ -121,6 +127,16 @@ typedef struct {
     int32_t scheme; /* 0 = EXPLICIT (Algorithm 1), 1 = PREDICTOR (R14), 2 = EXTRAPOLATED (R17) */
     int32_t hole[4];   /* x0, x1, y0, y1 of a removed rectangle (R16); x0 >= x1: none */
     double hole_T[4][2]; /* traction on the hole's faces: x0 face, x1 face, y0 face, y1 face */
+    /* Alternative readings of the open points above (zero everywhere selects
+     * the readings R4, R6, R7 as listed), kept switchable so that the runs of
+     * Sec. 7 can be repeated under each of them. */
+    int32_t alt_feq_pbar; /* 1: f^eq takes Pbar(H) of Eq. (Plin), as the listing of Algorithm 1 prints it (R4) */
+    int32_t alt_wall;     /* 1: wall values extrapolated linearly, (3 v_0 - v_1)/2, from the edge node
+                             and its inner neighbour along the wall normal (R7) */
+    int32_t alt_ghost_u;  /* 1: Neumann ghost of u quadratic, 3 u_0 - 3 u_1 + u_2 (R6) */
+    int32_t alt_ghost_q;  /* 1: ghost of Q = P + Pbar quadratic; 2: constant, Q_0 (R6) */
+    double mu_bar;        /* split stiffness: Pbar and C_s = sqrt(mu_bar/rho0) built with mu_bar,
+                             the remainder of P in 1S (0: mu_bar = mu, the paper's split) */
 } orc_problem;
 
 typedef struct {
@@ -283,6 +299,19 @@ static int wrap(int k, int n) { return ((k % n) + n) % n; }
 
 static int has_hole(const orc_problem* p) { return p->hole[0] < p->hole[1] && p->hole[2] < p->hole[3]; }
 
+/* The modulus of the linear split Pbar (Eq. Plin) and of C_s: mu, or mu_bar
+ * for the split-stiffness variant. */
+static double split_mu(const orc_problem* p) { return p->mu_bar > 0.0 ? p->mu_bar : p->mu; }
+
+/* Ghost value one node outside a traction-free or loaded edge from the edge
+ * node v0 and its inner neighbours v1, v2 (R6): linear extrapolation, or the
+ * quadratic / constant alternatives. */
+static double ghost_extrap(int alt, double v0, double v1, double v2) {
+    if (alt == 1) return 3.0 * v0 - 3.0 * v1 + v2;
+    if (alt == 2) return v0;
+    return 2.0 * v0 - v1;
+}
+
 /* (x, y) is a removed node of the hole (R16). */
 static int in_hole(const orc_state* s, int x, int y) {
     const int32_t* h = s->p.hole;
@@ -317,11 +346,11 @@ static double u_at(const orc_state* s, double* const U[2], int x, int y, int a, 
         ustar(&s->p, edge, t, ub);
         return 2.0 * ub[a] - v0;
     }
-    return 3.0 * v0 - 3.0 * v1 + v2;
+    return ghost_extrap(s->p.alt_ghost_u, v0, v1, v2);
 }
 
 /* Q = P + Pbar component k at (x, y), possibly one node outside along one
- * axis: periodic wrap or quadratic extrapolation (reading R6). */
+ * axis: periodic wrap or the ghost of reading R6. */
 static double q_at(const orc_state* s, int x, int y, int k) {
     int nx = s->p.nx, ny = s->p.ny;
     if (x >= 0 && x < nx && y >= 0 && y < ny) {
@@ -345,20 +374,16 @@ static double q_at(const orc_state* s, int x, int y, int k) {
         v1 = q_at(s, x, k0 + step, k);
         v2 = q_at(s, x, k0 + 2 * step, k);
     }
-    return 3.0 * v0 - 3.0 * v1 + v2;
+    return ghost_extrap(s->p.alt_ghost_q, v0, v1, v2);
 }
-
-/* Value at the removed neighbour (x + dx, y + dy) of the body node (x, y)
- * across a hole face: the quadratic ghost 3 v0 - 3 v1 + v2 from the node and
- * its two neighbours away from the face (R16). */
-static double hole_ghost(double v0, double v1, double v2) { return 3.0 * v0 - 3.0 * v1 + v2; }
 
 /* Eq. (defgrad) with central differences: H_ab = d_b u_a. */
 /* Displacement at the neighbour (x + dx, y + dy) of the body node (x, y):
  * across a hole face the hole's ghost (R16), else u_at. */
 static double u_nb(const orc_state* s, double* const U[2], int x, int y, int dx, int dy, int a, double t) {
-    if (in_hole(s, x + dx, y + dy))
-        return hole_ghost(U[a][IDX(s, x, y)], U[a][IDX(s, x - dx, y - dy)], U[a][IDX(s, x - 2 * dx, y - 2 * dy)]);
+    if (in_hole(s, x + dx, y + dy)) /* the hole's ghost (R16): as at a traction-free edge */
+        return ghost_extrap(s->p.alt_ghost_u, U[a][IDX(s, x, y)], U[a][IDX(s, x - dx, y - dy)],
+                            U[a][IDX(s, x - 2 * dx, y - 2 * dy)]);
     return u_at(s, U, x + dx, y + dy, a, t);
 }
 
@@ -381,7 +406,7 @@ static void update_stress(orc_state* s, double* const U[2], double t) {
             double H[4], P[4], Pb[4];
             grad_u(s, U, x, y, t, H);
             orc_piola(H, s->p.lambda, s->p.mu, P);
-            orc_poisson_stress(H, s->p.mu, Pb);
+            orc_poisson_stress(H, split_mu(&s->p), Pb);
             long id = IDX(s, x, y);
             for (int k = 0; k < 4; k++) {
                 s->P[k][id] = P[k];
@@ -394,7 +419,8 @@ static void update_stress(orc_state* s, double* const U[2], double t) {
  * across a hole face the hole's ghost (R16), else q_at. */
 static double q_nb(const orc_state* s, int x, int y, int dx, int dy, int k) {
     if (in_hole(s, x + dx, y + dy))
-        return hole_ghost(q_at(s, x, y, k), q_at(s, x - dx, y - dy, k), q_at(s, x - 2 * dx, y - 2 * dy, k));
+        return ghost_extrap(s->p.alt_ghost_q, q_at(s, x, y, k), q_at(s, x - dx, y - dy, k),
+                            q_at(s, x - 2 * dx, y - 2 * dy, k));
     return q_at(s, x + dx, y + dy, k);
 }
 
@@ -416,7 +442,8 @@ static void compute_source(orc_state* s) {
 }
 
 /* ------------------------------------------------------------------ */
-static double abb_rule(const orc_state* s, int x, int y, int i, const double N[2], const double T[2]);
+static double abb_rule(const orc_state* s, int x, int y, int i, const double N[2], const double T[2], int ox,
+                       int oy);
 
 /* Boundary rules of Sec. 6 for the link i of node (x, y) that leaves the body.
  * Returns the value of f_{opp(i)}(X, t + dt).  ex/ey: the bounded edges the
@@ -464,24 +491,46 @@ static double boundary_rule(const orc_state* s, int x, int y, int i, int ex, int
     /* one edge: T = T*; corner: T = (T1 + T2)/sqrt(2) (reading R10) */
     T[0] /= nlen;
     T[1] /= nlen;
-    return abb_rule(s, x, y, i, N, T);
+    return abb_rule(s, x, y, i, N, T, dx, dy);
 }
 
-/* Eq. (abbcon): anti-bounce-back for the link i of node (x, y) across a wall
- * of outward unit normal N carrying the traction T (time-t data). */
-static double abb_rule(const orc_state* s, int x, int y, int i, const double N[2], const double T[2]) {
-    long id = IDX(s, x, y);
-    double fc = s->fcol[i][id];
-    /* wall values of the edge node at time t (reading R7) */
-    double rw = 0.0, Pfw[4] = {0.0, 0.0, 0.0, 0.0}, Pw[4], Pbw[4];
+/* Time-t values at node id that the anti-bounce-back rule needs at the wall:
+ * r = sum_i f_i, Pf = sum_i C_i C_i f_i, and the stresses P, Pbar. */
+static void wall_data(const orc_state* s, long id, double* rw, double Pfw[4], double Pw[4], double Pbw[4]) {
+    *rw = 0.0;
+    for (int k = 0; k < 4; k++) Pfw[k] = 0.0;
     for (int k = 0; k < 9; k++) {
-        rw += s->f[k][id];
+        *rw += s->f[k][id];
         for (int a = 0; a < 2; a++)
             for (int b = 0; b < 2; b++) Pfw[2 * a + b] += s->C[k][a] * s->C[k][b] * s->f[k][id];
     }
     for (int k = 0; k < 4; k++) {
         Pw[k] = s->P[k][id];
         Pbw[k] = s->Pb[k][id];
+    }
+}
+
+/* Eq. (abbcon): anti-bounce-back for the link i of node (x, y) across a wall
+ * of outward unit normal N carrying the traction T (time-t data); (ox, oy) is
+ * the outward integer offset of the normal, (x - ox, y - oy) the node's inner
+ * neighbour. */
+static double abb_rule(const orc_state* s, int x, int y, int i, const double N[2], const double T[2], int ox,
+                       int oy) {
+    long id = IDX(s, x, y);
+    double fc = s->fcol[i][id];
+    /* wall values at time t: those of the edge node (reading R7), or the
+     * linear extrapolation to the wall from it and its inner neighbour */
+    double rw, Pfw[4], Pw[4], Pbw[4];
+    wall_data(s, id, &rw, Pfw, Pw, Pbw);
+    if (s->p.alt_wall == 1) {
+        double r1, Pf1[4], P1[4], Pb1[4];
+        wall_data(s, IDX(s, x - ox, y - oy), &r1, Pf1, P1, Pb1);
+        rw = 0.5 * (3.0 * rw - r1);
+        for (int k = 0; k < 4; k++) {
+            Pfw[k] = 0.5 * (3.0 * Pfw[k] - Pf1[k]);
+            Pw[k] = 0.5 * (3.0 * Pw[k] - P1[k]);
+            Pbw[k] = 0.5 * (3.0 * Pbw[k] - Pb1[k]);
+        }
     }
     /* quasi-traction g = -T* + (P + Pbar)_w N (Sec. 6) */
     double g[2];
@@ -529,11 +578,12 @@ static double hole_rule(const orc_state* s, int x, int y, int i) {
         T[1] += tf[1];
     }
     double nlen = sqrt(N[0] * N[0] + N[1] * N[1]);
+    int ox = (int)N[0], oy = (int)N[1];
     N[0] /= nlen;
     N[1] /= nlen;
     T[0] /= nlen;
     T[1] /= nlen;
-    return abb_rule(s, x, y, i, N, T);
+    return abb_rule(s, x, y, i, N, T, ox, oy);
 }
 
 static double* zalloc(long n) { return (double*)calloc((size_t)n, sizeof(double)); }
@@ -551,6 +601,9 @@ int orc_check(const orc_problem* p) {
         if ((a == ORC_PERIODIC) != (b == ORC_PERIODIC)) return 4;
     }
     if (p->scheme != ORC_EXPLICIT && p->scheme != ORC_PREDICTOR && p->scheme != ORC_EXTRAPOLATED) return 6;
+    if (p->alt_feq_pbar < 0 || p->alt_feq_pbar > 1 || p->alt_wall < 0 || p->alt_wall > 1 || p->alt_ghost_u < 0 ||
+        p->alt_ghost_u > 1 || p->alt_ghost_q < 0 || p->alt_ghost_q > 2 || !(p->mu_bar >= 0.0))
+        return 8;
     if (has_hole(p)) {
         /* at least 3 body nodes between the hole and each edge or seam */
         if (p->hole[0] < 3 || p->hole[1] > p->nx - 3 || p->hole[2] < 3 || p->hole[3] > p->ny - 3) return 7;
@@ -566,7 +619,7 @@ orc_state* orc_create(const orc_problem* p, const double* u0, const double* v0) 
     orc_state* s = (orc_state*)calloc(1, sizeof(orc_state));
     s->p = *p;
     s->n = (long)p->nx * p->ny;
-    orc_time_step(p->dX, p->mu, p->rho0, &s->dt, &s->c, &s->Cs2);
+    orc_time_step(p->dX, split_mu(p), p->rho0, &s->dt, &s->c, &s->Cs2);
     lattice(s->c, s->C, s->w, s->e, s->opp);
     for (int i = 0; i < 9; i++) {
         s->f[i] = zalloc(s->n);
@@ -632,9 +685,13 @@ static void step_once(orc_state* s) {
             long id = IDX(s, x, y);
             double jj[2] = {s->j[0][id], s->j[1][id]};
             double Pb[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int i = 0; i < 9; i++)
-                for (int a = 0; a < 2; a++)
-                    for (int b = 0; b < 2; b++) Pb[2 * a + b] += s->C[i][a] * s->C[i][b] * s->f[i][id];
+            if (p->alt_feq_pbar == 1) {
+                for (int k = 0; k < 4; k++) Pb[k] = s->Pb[k][id];
+            } else {
+                for (int i = 0; i < 9; i++)
+                    for (int a = 0; a < 2; a++)
+                        for (int b = 0; b < 2; b++) Pb[2 * a + b] += s->C[i][a] * s->C[i][b] * s->f[i][id];
+            }
             double Sv[2] = {s->S[0][id], s->S[1][id]};
             double fe[9], ps[9];
             feq_lat(s->C, s->w, s->Cs2, s->r[id], jj, Pb, fe);
@@ -783,7 +840,7 @@ void orc_read(const orc_state* s, double* u, double* v, double* P, double* Pb, d
             double H[4] = {0.0, 0.0, 0.0, 0.0}, PP[4], PB[4];
             if (!in_hole(s, x, y)) grad_u(s, s->u, x, y, t, H); /* removed nodes read as undeformed */
             double Jv = orc_piola(H, s->p.lambda, s->p.mu, PP);
-            orc_poisson_stress(H, s->p.mu, PB);
+            orc_poisson_stress(H, split_mu(&s->p), PB);
             if (P)
                 for (int k = 0; k < 4; k++) P[4 * id + k] = PP[k];
             if (Pb) {

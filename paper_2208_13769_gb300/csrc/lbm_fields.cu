@@ -23,12 +23,10 @@ __device__ __forceinline__ int wrapc(int g, int n) {
 __device__ double du_fd(const ReadoutParams& p, int x, int y, int dx, int dy, int comp) {
     const double* u = p.fields + int64_t(comp) * p.nx * p.ny;
     auto U = [&](int xx, int yy) { return u[int64_t(yy) * p.nx + xx]; };
-    // across a face of the hole: the quadratic ghost from the node and the
-    // two nodes behind it
-    if (in_hole(p.hole, x + dx, y + dy))
-        return (3.0 * U(x, y) - 3.0 * U(x - dx, y - dy) + U(x - 2 * dx, y - 2 * dy)) - U(x - dx, y - dy);
-    if (in_hole(p.hole, x - dx, y - dy))
-        return U(x + dx, y + dy) - (3.0 * U(x, y) - 3.0 * U(x + dx, y + dy) + U(x + 2 * dx, y + 2 * dy));
+    // across a face of the hole: the linear ghost 2 u_0 - u_1 from the node
+    // and the node behind it
+    if (in_hole(p.hole, x + dx, y + dy)) return (2.0 * U(x, y) - U(x - dx, y - dy)) - U(x - dx, y - dy);
+    if (in_hole(p.hole, x - dx, y - dy)) return U(x + dx, y + dy) - (2.0 * U(x, y) - U(x + dx, y + dy));
     const int n = dx ? p.nx : p.ny;
     const int k = dx ? x : y;
     const bool per = dx ? p.periodic_x : p.periodic_y;
@@ -40,12 +38,12 @@ __device__ double du_fd(const ReadoutParams& p, int x, int y, int dx, int dy, in
     const int edge = (dx ? 0 : 2) + (k == 0 ? 0 : 1);
     const EdgeBC& e = p.bc[edge];
     const int s = (k == 0) ? 1 : -1;  // inward step
-    const double u0 = U(x, y), u1 = U(x + s * dx, y + s * dy), u2 = U(x + 2 * s * dx, y + 2 * s * dy);
+    const double u0 = U(x, y), u1 = U(x + s * dx, y + s * dy);
     double ghost;
     if (e.kind == kDirichlet)
         ghost = 2.0 * (e.value[comp] + e.rate[comp] * p.t) - u0;
     else
-        ghost = 3.0 * u0 - 3.0 * u1 + u2;
+        ghost = 2.0 * u0 - u1;
     return (k == 0) ? (u1 - ghost) : (ghost - u1);
 }
 

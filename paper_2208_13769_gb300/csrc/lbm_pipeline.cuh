@@ -100,9 +100,10 @@ __device__ __forceinline__ void edge_now(EdgeNow<TC, UT>& out, const EdgeBC& e, 
 }
 
 // u(+1) - u(-1) along one axis around u0 with the ghost rules of bounded
-// edges (Dirichlet: u_g = 2 u*(t) - u0; Neumann: quadratic extrapolation).
-// um, up: neighbours below/above; u1, u2: first and second inward neighbours
-// (read only when a ghost is needed).
+// edges (Dirichlet: u_g = 2 u*(t) - u0; Neumann: linear extrapolation,
+// u_g = 2 u0 - u1).  um, up: neighbours below/above; u1: the inward
+// neighbour (read only when a ghost is needed); u2 is not used by these
+// rules.
 template <class TC, class UT>
 __device__ __forceinline__ TC du_axis(const UT& um, const UT& u0, const UT& up, const UT& u1, const UT& u2,
                                       bool ghost_lo, bool ghost_hi, const EdgeNow<TC, UT>& e, int comp) {
@@ -111,15 +112,15 @@ __device__ __forceinline__ TC du_axis(const UT& um, const UT& u0, const UT& up, 
         const TC v = u0.minus(e.us[comp]) + u1.minus(e.us[comp]);
         return ghost_hi ? -v : v;
     }
-    const TC v = TC(3) * u1.minus(u0) - u2.minus(u1);
+    const TC v = TC(2) * u1.minus(u0);
     return ghost_hi ? -v : v;
 }
 
-// Q(+1) - Q(-1) with the quadratic ghost of bounded edges.
+// Q(+1) - Q(-1) with the linear ghost of bounded edges, Q_g = 2 Q0 - Q1.
 template <class TC>
 __device__ __forceinline__ TC dq_axis(TC qm, TC q0, TC qp, TC q1, TC q2, bool ghost_lo, bool ghost_hi) {
     if (!ghost_lo && !ghost_hi) return qp - qm;
-    const TC v = TC(4) * q1 - TC(3) * q0 - q2;
+    const TC v = TC(2) * (q1 - q0);
     return ghost_hi ? -v : v;
 }
 

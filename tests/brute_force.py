@@ -5,7 +5,7 @@ oracle's code).  It pins the C oracle on 3 x 3 .. 6 x 5 bodies, where every
 node is a boundary node or next to one, so the boundary rules of Sec. 6,
 the ghost values of the differences and the corner links are all exercised.
 A rectangular hole (removed nodes, faces with a constant traction each)
-follows reading R16: a removed neighbour takes the quadratic ghost, a link
+follows reading R16: a removed neighbour takes the linear ghost, a link
 into the hole the anti-bounce-back rule with the crossed face's normal (a
 link through the hole's corner: both faces, as at the body's corners).
 
@@ -104,18 +104,19 @@ class BruteForce:
             s = 1.0
         return [E_.value[a] + (E_.rate[a] - E_.value[a]) * s for a in range(2)]
 
-    def neighbour(self, field, p, axis, side, t, quadratic_only):
+    def neighbour(self, field, p, axis, side, t, extrapolate_only):
         """field at p + side along axis; beyond a bounded edge the ghost value
-        (Dirichlet: 2 u*(t) - u_edge for u; otherwise 3 v0 - 3 v1 + v2)."""
+        (Dirichlet: 2 u*(t) - u_edge for u; otherwise the linear extrapolation
+        2 v0 - v1 from the edge node and the node behind it)."""
         x, y = p
         step = (side, 0) if axis == 0 else (0, side)
         if self.removed((x + step[0], y + step[1])):
-            # across a face of the hole: quadratic ghost from p and the two
-            # nodes behind it
-            vals = [field[(x - m * step[0], y - m * step[1])] for m in range(3)]
+            # across a face of the hole: the linear ghost from p and the node
+            # behind it
+            vals = [field[(x - m * step[0], y - m * step[1])] for m in range(2)]
             if isinstance(vals[0], float):
-                return 3 * vals[0] - 3 * vals[1] + vals[2]
-            return [3 * vals[0][a] - 3 * vals[1][a] + vals[2][a] for a in range(len(vals[0]))]
+                return 2 * vals[0] - vals[1]
+            return [2 * vals[0][a] - vals[1][a] for a in range(len(vals[0]))]
         n = self.nx if axis == 0 else self.ny
         k = (x if axis == 0 else y) + side
         if 0 <= k < n or self.periodic(axis):
@@ -125,14 +126,14 @@ class BruteForce:
         edge = 2 * axis + (0 if side < 0 else 1)
         k0 = 0 if side < 0 else n - 1
         inward = 1 if side < 0 else -1
-        pts = [(k0 + m * inward) for m in range(3)]
+        pts = [(k0 + m * inward) for m in range(2)]
         vals = [field[(kk, y) if axis == 0 else (x, kk)] for kk in pts]
-        if not quadratic_only and self.edges[edge].kind == DIR:
+        if not extrapolate_only and self.edges[edge].kind == DIR:
             us = self.ustar(edge, t)
             return [2 * us[a] - vals[0][a] for a in range(2)]
         if isinstance(vals[0], float):
-            return 3 * vals[0] - 3 * vals[1] + vals[2]
-        return [3 * vals[0][a] - 3 * vals[1][a] + vals[2][a] for a in range(len(vals[0]))]
+            return 2 * vals[0] - vals[1]
+        return [2 * vals[0][a] - vals[1][a] for a in range(len(vals[0]))]
 
     def grad(self, U, p, t):
         H = [[0.0, 0.0], [0.0, 0.0]]
@@ -144,7 +145,7 @@ class BruteForce:
         return H
 
     def source(self, p):
-        """1S = rho0 b + Div(P + Pbar), central differences, quadratic ghosts."""
+        """1S = rho0 b + Div(P + Pbar), central differences, linear ghosts."""
         Qf = {q: [self.Pstore[q][0][a][b] + self.Pstore[q][1][a][b] for a in range(2) for b in range(2)]
               for q in self.nodes}
         out = []

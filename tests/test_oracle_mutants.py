@@ -19,8 +19,9 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "lbm_oracle.c")
 MUTANTS = [
     ("bounce-back sign", "return fc - 2.0 / s->Cs2 * s->w[i] * cj;", "return fc + 2.0 / s->Cs2 * s->w[i] * cj;", 0),
     ("Dirichlet ghost value", "return 2.0 * ub[a] - v0;", "return ub[a];", 0),
-    ("Neumann ghost of u", "return 3.0 * v0 - 3.0 * v1 + v2;", "return 2.0 * v0 - v1;", 0),
-    ("ghost of Q", "return 3.0 * v0 - 3.0 * v1 + v2;", "return v0;", 1),
+    ("Neumann ghost of u", "return ghost_extrap(s->p.alt_ghost_u, v0, v1, v2);",
+     "return 3.0 * v0 - 3.0 * v1 + v2;", 0),
+    ("ghost of Q", "return ghost_extrap(s->p.alt_ghost_q, v0, v1, v2);", "return v0;", 0),
     ("forcing prefactor", "dt * (1.0 - 0.5 * omega) * ps[i]", "dt * ps[i]", 0),
     ("tangential wall entry from Pbar(H)", "Ptt += tv[a] * Pfw[2 * a + b] * tv[b];",
      "Ptt += tv[a] * Pbw[2 * a + b] * tv[b];", 0),
@@ -34,7 +35,8 @@ MUTANTS = [
     ("diagonal weight", "1.0 / 9.0 : 1.0 / 36.0", "1.0 / 9.0 : 1.0 / 32.0", 0),
     ("initial r sign", "s->r[id] = -p->rho0 * (H[0] + H[3]);", "s->r[id] = p->rho0 * (H[0] + H[3]);", 0),
     # the hole of reading R16
-    ("hole ghost", "return 3.0 * v0 - 3.0 * v1 + v2;", "return 2.0 * v0 - v1;", 2),
+    ("hole ghost", "return ghost_extrap(s->p.alt_ghost_u, U[a][IDX(s, x, y)]", "return ghost_extrap(1, U[a][IDX(s, x, y)]",
+     0),
     ("hole corner normal", "if (!cx && !cy) cx = cy = 1;", "if (!cx && !cy) cx = 1;", 0),
     ("hole face traction", "s->p.hole_T[ex > 0 ? 0 : 1]", "s->p.hole_T[ex > 0 ? 1 : 0]", 0),
     # the extrapolated scheme of reading R17

@@ -170,7 +170,11 @@ def _total_momentum(o):
 def test_periodic_momentum_and_mass_conserved(scheme):
     """Periodic body, b = 0: sum of j and of r are invariants of the scheme
     (collision conserves them, streaming permutes, the periodic divergence
-    telescopes).  With b != 0 the total momentum grows by rho0 b N dt."""
+    telescopes).  With b != 0 each step adds rho0 b N dt to the total
+    momentum, except the first: Algorithm 1 initialises f = f^eq(r, j, Pbar)
+    with j = rho0 v0, so sum C f holds no half source, and the first
+    collision keeps (1 - omega) of that mismatch, so the first step adds only
+    rho0 b N dt (3 - omega)/2 (all of it at omega = 1)."""
     p = W.smooth_random(20, 14, W.all_periodic(), seed=5, lam=0.3, mu=0.3, amp=0.01)
     s = oracle.solver_from(p, scheme)
     o0 = s.read()
@@ -180,12 +184,14 @@ def test_periodic_momentum_and_mass_conserved(scheme):
     np.testing.assert_allclose(_total_momentum(o1), M0, atol=1e-13)
     assert abs(o1["r"].sum() - R0) < 1e-13
     assert np.abs(o1["u"] - o0["u"]).max() > 1e-4  # the body did move
-    p.body = (1e-4, -2e-4)
-    s = oracle.solver_from(p, scheme)
-    s.step(40)
-    o2 = s.read()
-    expect = M0 + np.array(p.body) * p.nodes * s.t
-    np.testing.assert_allclose(_total_momentum(o2), expect, atol=1e-12)
+    for omega in (1.0, p.omega):
+        p.body = (1e-4, -2e-4)
+        p.omega = omega
+        s = oracle.solver_from(p, scheme)
+        s.step(40)
+        o2 = s.read()
+        expect = M0 + np.array(p.body) * p.nodes * (s.t - s.dt * (omega - 1.0) / 2.0)
+        np.testing.assert_allclose(_total_momentum(o2), expect, atol=1e-12)
 
 
 def _shear_amplitude_series(n, amp, omega, scheme, periods=3.0):
@@ -302,10 +308,10 @@ def test_dirichlet_uniform_motion(scheme):
     """Uniform v0 with all edges moving at v* = v0 (bounce-back, Eq. bbcon):
     u = v0 t exactly, no strain."""
     v = (0.01, -0.02)
-    # the extrapolated scheme is stable only at lambda = mu (see
-    # test_extrapolated_scheme_is_stable_only_at_lambda_eq_mu): there the
-    # rounding noise of the moving walls stays at rounding level
-    p = W.uniform_motion(12, 10, v, lam=0.3) if scheme == oracle.EXTRAPOLATED else W.uniform_motion(12, 10, v)
+    # Algorithm 1's explicit moment and the extrapolated scheme are stable
+    # only at lambda = mu (readings R14, R17): there the rounding noise of the
+    # moving walls stays at rounding level
+    p = W.uniform_motion(12, 10, v, lam=0.3) if scheme != oracle.PREDICTOR else W.uniform_motion(12, 10, v)
     s = oracle.solver_from(p, scheme)
     s.step(300)
     o = s.read()

@@ -1,0 +1,168 @@
+"""The oracle against the runs of Sec. 7, the only outcomes the paper prints
+for the nonlinear path: its simple tension block (T* ramped to mu by t = 1,
+held to t = 3), its simple shear block (T* ramped to 0.05 mu, to t = 8) and
+its plate with a square hole (a sudden 0.1 mu held until t = 1, to t = 3,
+"lengthened by approximately 18 %").  The paper reports that all three run
+to the end and agree with FE; these tests pin that, under the readings the
+oracle adopts, and pin why the alternatives it does not adopt are ruled out
+(each run blows up under them):
+
+  R3  omega = dt / tau near 2 (the paper never fixes tau): at omega = 1 the
+      plate blows up before its peak;
+  R4  the kinetic second moment in f^eq: Algorithm 1's listing read
+      literally (Pbar(H) of Eq. Plin in f^eq) blows up every run within a
+      few dozen steps;
+  R6  linear ghost extrapolation at traction edges: the quadratic one blows
+      up the shear block and the plate.
+
+The tension block at T* = mu (about 80 % elongation) needs the footnote's
+predictor-corrector for u (Sec. 5): with Algorithm 1's explicit moment it
+blows up after t = 2.  The paper says the predictor was not needed in its
+runs; under these readings it is, at that load.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_13769_gb300 import workloads as W
+
+
+def _run(prob, t_end, scheme, readings=None, every=8):
+    """Steps the oracle to t_end.  Returns (time of blow-up or None, history
+    of (t, u) every `every` steps): a blow-up is a non-finite u, |u| beyond
+    5 body lengths or J <= 0 at a node of the body."""
+    s = oracle.solver_from(prob, scheme, readings)
+    n = int(round(t_end / s.dt))
+    act = prob.active()
+    hist = []
+    k = 0
+    while k < n:
+        m = min(every, n - k)
+        s.step(m)
+        k += m
+        o = s.read()
+        u = o["u"]
+        if not np.all(np.isfinite(u)) or np.abs(u).max() > 5.0 or np.where(act, o["J"], 1.0).min() <= 0.0:
+            return s.t, hist
+        hist.append((s.t, u.copy()))
+    return None, hist
+
+
+def _centre_elongation(prob, hist):
+    """Length change along x2 of the centre line (the column of Sec. 7's probe
+    Q2 at x1 = dX/2 from the plate's centre): top node minus bottom node."""
+    c = prob.nx // 2
+    return np.array([(t, u[-1, c, 1] - u[0, c, 1]) for t, u in hist])
+
+
+def test_plate_with_hole_runs_to_completion_and_lengthens_about_18_percent():
+    """Sec. 7: the plate under a sudden 0.1 mu (removed at t = 1) runs to
+    t = 3 with Algorithm 1's explicit moment and is lengthened by about 18 %;
+    the peak comes as the load is removed."""
+    p = W.plate_with_hole()
+    blow, hist = _run(p, 3.0, oracle.EXPLICIT, every=1)
+    assert blow is None
+    e = _centre_elongation(p, hist)
+    i = int(np.argmax(e[:, 1]))
+    assert 0.16 < e[i, 1] < 0.20, e[i]
+    assert 0.9 < e[i, 0] < 1.1, e[i]
+    # after the load is gone the plate swings back past its rest length
+    assert e[e[:, 0] > 1.5, 1].min() < 0.05
+
+
+def test_shear_block_runs_to_completion():
+    """Sec. 7: the shear block (T* along x1 ramped to 0.05 mu by t = 1, held)
+    runs to t = 8 with Algorithm 1's explicit moment; its top-left corner
+    (probe P2) moves with the load and its left side's centre (probe P3)
+    moves horizontally, less than the corner."""
+    p = W.shear_block()
+    blow, hist = _run(p, 8.0, oracle.EXPLICIT)
+    assert blow is None
+    mid = p.ny // 2
+    corner = np.array([u[-1, 0, 0] for _, u in hist])
+    side = np.array([u[mid, 0, 0] for _, u in hist])
+    assert corner.max() > 0.05 and corner.min() > -1e-3
+    assert 0.0 < side.max() < corner.max()
+
+
+def test_tension_block_runs_to_completion_with_the_predictor():
+    """Sec. 7: the tension block (T* along x2 ramped to mu by t = 1, held to
+    t = 3) runs to the end with the footnote's predictor-corrector; its top
+    (probe P1) stretches by more than half the block's length and its side
+    (probe P3) contracts."""
+    p = W.tension_block()
+    blow, hist = _run(p, 3.0, oracle.PREDICTOR)
+    assert blow is None
+    c = p.nx // 2
+    top = np.array([u[-1, c, 1] for _, u in hist])
+    side = np.array([u[p.ny // 2, 0, 0] for _, u in hist])
+    assert top.max() > 0.5
+    assert side.max() > 0.05  # the left side moves inward (+x1)
+
+
+def test_tension_block_blows_up_with_the_explicit_moment():
+    """The finding stated in the module docstring: at T* = mu, Algorithm 1's
+    explicit moment does not carry the tension block to t = 3."""
+    blow, _ = _run(W.tension_block(), 3.0, oracle.EXPLICIT)
+    assert blow is not None and 1.8 < blow < 3.0
+
+
+@pytest.mark.parametrize("scheme", [oracle.EXPLICIT, oracle.PREDICTOR])
+def test_literal_pbar_in_the_equilibrium_blows_up(scheme):
+    """Reading R4: f^eq built with Pbar(H) (Algorithm 1's listing taken
+    literally) amplifies grid modes (by about 1.4 per step); every run of
+    Sec. 7 blows up within 60 steps, at any omega."""
+    for omega in (1.0, W.OMEGA):
+        for make, t_end in ((W.plate_with_hole, 3.0), (W.shear_block, 8.0)):
+            p = make()
+            p.omega = omega
+            blow, hist = _run(p, t_end, scheme, dict(feq_pbar=1), every=4)
+            assert blow is not None and blow < 60 * oracle.solver_from(p).dt
+
+
+def test_omega_one_blows_up_the_plate_before_its_peak():
+    """Reading R3: with omega = 1 the plate blows up before t = 1.2."""
+    p = W.plate_with_hole()
+    p.omega = 1.0
+    blow, _ = _run(p, 3.0, oracle.EXPLICIT)
+    assert blow is not None and blow < 1.2
+
+
+def test_quadratic_ghosts_blow_up_the_shear_block_and_the_plate():
+    """Reading R6: with the quadratic ghost extrapolation at traction edges
+    (for u and for Q) the shear block and the plate blow up, with either
+    scheme."""
+    quad = dict(ghost_u=1, ghost_q=1)
+    for scheme in (oracle.EXPLICIT, oracle.PREDICTOR):
+        blow, _ = _run(W.shear_block(), 8.0, scheme, quad)
+        assert blow is not None
+        blow, _ = _run(W.plate_with_hole(), 3.0, scheme, quad)
+        assert blow is not None
+
+
+def test_split_stiffness_does_not_stabilise_the_method():
+    """The split-stiffness variant (Pbar and C_s built with mu_bar != mu, the
+    linear remainder moved into 1S; an extension, not in the paper) is no
+    remedy for the method's stability limits: of the splits tried, only the
+    paper's own (mu_bar = mu) carries all three runs of Sec. 7 to the end,
+    and none carries a clamped body with Poisson ratio 0.3 (beyond lambda =
+    mu) through 3000 steps."""
+    for ratio in (0.8, 0.9, 2.0):
+        p = W.plate_with_hole()
+        blow, _ = _run(p, 3.0, oracle.EXPLICIT, dict(mu_bar=ratio * p.mu))
+        assert blow is not None and blow < 3.0
+    for ratio in (1.25, 1.5):
+        p = W.tension_block()
+        blow, _ = _run(p, 3.0, oracle.PREDICTOR, dict(mu_bar=ratio * p.mu))
+        assert blow is not None
+    for ratio in (1.0, 1.1, 1.25, 1.5):
+        p = W.clamped_body(128, 64, mu=0.3, nu=0.3, vmax=0.05)
+        s = oracle.solver_from(p, oracle.PREDICTOR, dict(mu_bar=ratio * p.mu))
+        blew = False
+        for _ in range(30):
+            s.step(100)
+            o = s.read()
+            if not np.all(np.isfinite(o["u"])) or o["J"].min() <= 0.0:
+                blew = True
+                break
+        assert blew, ratio
