@@ -400,9 +400,15 @@ LBM_API lbm_status lbm_selftest_bounded_wait(uint32_t polls, void* cuda_stream, 
  *   has finished.
  * Limits: nx, ny >= 3 and nx * ny <= LBM_NOALLOC_MAX_NODES; larger bodies,
  *   null pointers, unknown edge kinds or an unpaired periodic edge return
- *   LBM_E_INVALID without launching anything.
- * The first call on a device looks up the device address of the static array
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   LBM_E_INVALID without launching anything.  The geometry has no hole: for
+ *   a body with one (lbm_set_hole) the removed nodes, whatever the fields
+ *   hold there, count as nodes of the body, where lbm_diagnostics skips them.
+ * The sums equal lbm_diagnostics' to rounding, not bit for bit: the same
+ *   kernels run, but above 1024 x 256 nodes the CTAs here stride over more
+ *   nodes each, so the order of the additions differs.
+ * The first call in each CUDA context of a device looks up the device address
+ * of the static array (cudaGetSymbolAddress); make that first call before any
+ * stream capture (also again after a device reset, which ends the context).
  * All calls share the one array: calls whose work overlaps on the GPU (other
  * streams, other host threads) race and may return wrong sums.  Each call
  * overwrites every partial it reads, so no clearing between calls is needed.

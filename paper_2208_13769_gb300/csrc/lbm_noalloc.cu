@@ -9,6 +9,7 @@
 // static device array instead of context memory.  The array is part of the
 // library image: every GPU that loads the library holds it until the process
 // exits, and every call shares it.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -27,18 +28,53 @@ static __device__ __align__(256) double g_partials[kMaxBlocks * 8];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
+// per device: the address of g_partials and the id of the CUDA context it
+// belongs to (a device reset destroys the context; the module, and with it
+// the array, is loaded afresh, possibly elsewhere, in the next one)
 double* g_ptr[kMaxDevices] = {nullptr};
+unsigned long long g_ctx[kMaxDevices] = {0};
+
+// The unique id of the calling thread's current CUDA context (0 if there is
+// none yet, or if the driver cannot tell), through the driver's entry points
+// (no link against the driver library).
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || c == nullptr || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 // The device address of g_partials on `device` (which must be current).
-// Looked up once per device; the host-side name g_partials is only a
-// stand-in and must never be handed to a kernel.
+// Looked up on the first call in each CUDA context of the device and kept
+// for the calls that follow in that context; the host-side name g_partials
+// is only a stand-in and must never be handed to a kernel.
 cudaError_t partials_address(int device, double** out) {
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_ptr[device]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_ptr[device] || ctx == 0 || ctx != g_ctx[device]) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_partials);
         if (e != cudaSuccess) return e;
         g_ptr[device] = static_cast<double*>(p);
+        g_ctx[device] = current_context_id();  // the lookup made the context current if none was
     }
     *out = g_ptr[device];
     return cudaSuccess;

@@ -33,10 +33,14 @@ def _device_fields(torch, fields):
     return torch.tensor(planes, dtype=torch.float64, device="cuda").contiguous()
 
 
-def test_noalloc_diagnostics_match_context_diagnostics():
+@pytest.mark.parametrize("nx,ny", [(150, 90), (700, 400)])
+def test_noalloc_diagnostics_match_context_diagnostics(nx, ny):
+    """150 x 90 nodes: 53 CTAs of partial sums.  700 x 400 nodes: more than
+    1024 CTAs' worth, so the allocation-free call's CTAs stride over several
+    nodes each (the additions in another order than lbm_diagnostics')."""
     torch = pytest.importorskip("torch")
-    prob = W.smooth_random(150, 90, [W.Edge(W.DIRICHLET, value=(0.0, 0.0), rate=(0.002, -0.001)),
-                                     W.Edge(W.NEUMANN), W.Edge(W.NEUMANN), W.Edge(W.NEUMANN)],
+    prob = W.smooth_random(nx, ny, [W.Edge(W.DIRICHLET, value=(0.0, 0.0), rate=(0.002, -0.001)),
+                                    W.Edge(W.NEUMANN), W.Edge(W.NEUMANN), W.Edge(W.NEUMANN)],
                            seed=21, amp=0.01, vamp=0.004, lam=0.3, mu=0.3)
     stream = torch.cuda.current_stream().cuda_stream
     out = torch.full((8,), float("nan"), dtype=torch.float64, device="cuda")
