@@ -50,10 +50,18 @@ def _cases():
         # the hole's band meets the edge bands: no interior rectangle
         "bands_only_12x12": (dataclasses.replace(
             W.smooth_random(12, 12, [N0] * 4, seed=45, amp=0.01, lam=0.3, mu=0.3), hole=(4, 8, 4, 8)), 150),
-        # Sec. 7's plate with a hole (80 x 80 nodes, hole 0.4 l) at a load it
-        # stays stable under
-        "plate_80_hole": (W.plate_with_hole(80, T=0.02), 208),
+        # Sec. 7's plate with a hole (80 x 80 nodes, hole 0.4 l) at a fifth of
+        # its load and omega = 1
+        "plate_80_hole": (W.plate_with_hole(80, T=0.02, omega=1.0), 208),
+        # the plate as Sec. 7 runs it: 0.1 mu from t = 0 to 1, to t = 3, at
+        # omega = 1.95 (FP64 only: near omega = 2 FP32 storage leaves its
+        # rounding in the populations' slowly decaying non-equilibrium part)
+        "plate_80_paper": (W.plate_with_hole(80), 416),
     }
+
+
+# the extrapolated scheme blows the paper's plate up at t = 1.99 (step 275)
+EXTRAPOLATED_STEPS = {"plate_80_paper": 250}
 
 
 CASES = _cases()
@@ -65,6 +73,7 @@ def test_fp64_holed_body_matches_the_oracle(name, scheme):
     prob, steps = CASES[name]
     if scheme == oracle.EXTRAPOLATED:  # stable only at lambda = mu
         prob = dataclasses.replace(prob, lam=prob.mu)
+        steps = EXTRAPOLATED_STEPS.get(name, steps)
     ref, got = run_both(prob, steps, storage="f64", scheme=scheme, chunks=[1, steps - 1])
     assert got["status"] == lbm.LBM_OK
     compare(ref, got, 1e-12, keys=("u", "v", "P", "Pbar", "J", "sigma"))
@@ -73,7 +82,7 @@ def test_fp64_holed_body_matches_the_oracle(name, scheme):
     assert np.all(got["u"][~m] == 0) and np.all(got["J"][~m] == 1)  # removed nodes read as undeformed
 
 
-@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("name", sorted(n for n in CASES if n != "plate_80_paper"))
 def test_fp32_holed_body_matches_the_oracle(name):
     prob, steps = CASES[name]
     ref, got = run_both(prob, steps, storage="f32")
@@ -148,10 +157,11 @@ def test_set_hole_checks_its_arguments():
 
 @pytest.mark.auto_plan
 def test_plate_with_hole_under_the_default_plan_matches_the_oracle():
-    """Sec. 7's 80 x 80 plate with its hole under the library's default plan
-    (edge tiles only at this size), FP64 against the oracle."""
-    prob = W.plate_with_hole(80, T=0.02)
-    ref, got = run_both(prob, 208, storage="f64")
+    """Sec. 7's 80 x 80 plate with its hole, its load and its horizon
+    (t = 3) under the library's default plan (edge tiles only at this
+    size), FP64 against the oracle."""
+    prob = W.plate_with_hole(80)
+    ref, got = run_both(prob, 416, storage="f64")
     assert got["status"] == lbm.LBM_OK
     compare(ref, got, 1e-12, keys=("u", "v", "P", "Pbar", "J", "sigma"))
     with lbm.Body(prob, storage="f64") as b:

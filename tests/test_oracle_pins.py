@@ -184,7 +184,7 @@ def test_periodic_momentum_and_mass_conserved(scheme):
     np.testing.assert_allclose(_total_momentum(o1), M0, atol=1e-13)
     assert abs(o1["r"].sum() - R0) < 1e-13
     assert np.abs(o1["u"] - o0["u"]).max() > 1e-4  # the body did move
-    for omega in (1.0, p.omega):
+    for omega in (1.0, W.OMEGA_SEC7):
         p.body = (1e-4, -2e-4)
         p.omega = omega
         s = oracle.solver_from(p, scheme)

@@ -112,7 +112,7 @@ def test_literal_pbar_in_the_equilibrium_blows_up(scheme):
     """Reading R4: f^eq built with Pbar(H) (Algorithm 1's listing taken
     literally) amplifies grid modes (by about 1.4 per step); every run of
     Sec. 7 blows up within 60 steps, at any omega."""
-    for omega in (1.0, W.OMEGA):
+    for omega in (1.0, W.OMEGA_SEC7):
         for make, t_end in ((W.plate_with_hole, 3.0), (W.shear_block, 8.0)):
             p = make()
             p.omega = omega

@@ -1,19 +1,28 @@
 """16-bit population storage (FP16 / BF16 with a power-of-two scale per
 direction, FP32 arithmetic, compensated FP32-pair displacement carry):
-error against the FP64 path after many steps, and its structure.
+error against the FP64 oracle and the FP64 path, and its structure.
 
 The populations of this method are of the order of the strains (f^eq at rest
 is zero), and the moments are sums and differences of the nine stored
-values, so the storage rounding of every step enters the momentum directly:
-the displacement error grows like the square root of the step count times
-the format's unit roundoff (2^-11 for FP16, 2^-8 for BF16).  Measured on
-the clamped body (512 x 256, 500 steps): FP16 about 2e-3 in u, BF16 about
-3e-2; FP32 storage stays near 1e-6.  These are the bounds asserted (with
-margin); they are far above the 1e-4 displacement error FP32 storage keeps,
-which is why FP32 is the default form."""
+values, so each step's storage rounding enters the momentum directly.  How
+it reaches the displacement depends on the relaxation: at omega = 1 the
+rounded populations are the next equilibrium, the rounding random-walks into
+u and the error grows like sqrt(steps) times the format's unit roundoff (on
+the clamped body at 4096 x 2048: FP16 1.9e-3 after 500 steps, 1.3e-2 after
+2000).  At the clamped body's omega = 1.9 the rounding lands in the
+populations' non-equilibrium part, which the collision multiplies by
+1 - omega = -0.9 each step: it alternates in sign and cancels in the
+trapezoidal sum that gives u.  The velocity keeps an error of the order of
+the roundoff (FP16 about 1e-3), the displacement does not: FP16 stays near
+6e-5 in u from 500 to 5000 steps at 4096 x 2048, below the 1e-4 the
+reduced-storage form is held to.  On a body 8 times smaller (512 x 256,
+500 steps) the same rounding weighs more against a displacement field of
+fewer nodes: FP16 1.8e-4 against the oracle, so the 1e-4 bound is asserted
+on the benchmark's body.  BF16's 8-bit significand leaves 2e-3 to 7e-3."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2208_13769_gb300 import lbm
 from paper_2208_13769_gb300 import workloads as W
 
@@ -26,14 +35,18 @@ def _rel(a, b):
 
 @pytest.fixture(scope="module")
 def reference():
+    """The clamped body (omega 1.9) at 512 x 256 after 500 steps, from the
+    FP64 oracle."""
     prob = W.clamped_body(512, 256, nu=0.25, vmax=0.01)
-    with lbm.Body(prob, storage="f64") as b:
-        b.step(500)
-        return prob, b.read(lbm.LBM_FIELD_U | lbm.LBM_FIELD_V)
+    s = oracle.solver_from(prob, oracle.PREDICTOR)
+    s.step(500)
+    ref = s.read()
+    s.close()
+    return prob, ref
 
 
-@pytest.mark.parametrize("storage,tol_u,tol_v", [("f32", 2e-5, 5e-5), ("f16", 1e-2, 5e-2), ("bf16", 1e-1, 3e-1)])
-def test_storage_form_error_against_fp64(reference, storage, tol_u, tol_v):
+@pytest.mark.parametrize("storage,tol_u,tol_v", [("f32", 1e-5, 1e-5), ("f16", 3e-4, 5e-3), ("bf16", 2e-2, 5e-2)])
+def test_storage_form_error_against_the_oracle(reference, storage, tol_u, tol_v):
     prob, ref = reference
     with lbm.Body(prob, storage=storage) as b:
         b.step(500)
@@ -42,13 +55,29 @@ def test_storage_form_error_against_fp64(reference, storage, tol_u, tol_v):
     assert eu <= tol_u and ev <= tol_v, (storage, eu, ev)
 
 
-def test_fp16_error_is_ordered_by_the_formats_roundoff(reference):
+def test_fp16_displacement_error_at_full_size_stays_below_1e4():
+    """The benchmark's clamped body (4096 x 2048) with FP16 populations after
+    2000 steps, against the FP64 path on the same inputs (the oracle would
+    take minutes here; the FP64 path meets it to 1e-12 in the parity
+    tests): the displacement error stays below 1e-4."""
+    prob = W.clamped_body(4096, 2048, nu=0.25, vmax=0.01)
+    with lbm.Body(prob, storage="f64") as b:
+        b.step(2000)
+        ref = b.read(lbm.LBM_FIELD_U)["u"]
+    with lbm.Body(prob, storage="f16") as b:
+        b.step(2000)
+        got = b.read(lbm.LBM_FIELD_U)
+    assert got["status"] == lbm.LBM_OK
+    assert _rel(got["u"], ref) <= 1e-4
+
+
+def test_error_is_ordered_by_the_formats_roundoff(reference):
     prob, ref = reference
     errs = {}
     for st in ("f32", "f16", "bf16"):
         with lbm.Body(prob, storage=st) as b:
             b.step(500)
-            errs[st] = _rel(b.read(lbm.LBM_FIELD_U)["u"], ref["u"])
+            errs[st] = _rel(b.read(lbm.LBM_FIELD_V)["v"], ref["v"])
     assert errs["f32"] < errs["f16"] < errs["bf16"]
 
 
