@@ -51,12 +51,15 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--native-ucarry", dest="compensated", action="store_false",
                     help="plain FP32 displacement carry (default: compensated FP32 pair)")
+    ap.add_argument("--scheme", default="explicit", choices=["explicit", "predictor", "extrapolated"],
+                    help="time level of 1S in the moment: Algorithm 1 (explicit), the footnote's "
+                         "predictor-corrector, or the extrapolated j of Sec. 5")
     ap.add_argument("--nu", type=float, default=0.25)
     ap.add_argument("--vmax", type=float, default=0.01)
     ap.add_argument("--forms", default="f32n,f16,bf16",
                     help="extra population formats timed on the same body ('' to skip)")
     ap.add_argument("--form-steps", type=int, default=500)
-    ap.add_argument("--schemes", default="explicit,extrapolated",
+    ap.add_argument("--schemes", default="predictor,extrapolated",
                     help="other schemes timed on the same body, FP32 + compensated carry ('' to skip)")
     ap.add_argument("--c3-steps", type=int, default=1000,
                     help="steps of the 8192 x 8192 16-bit storage run (0 to skip)")
@@ -71,6 +74,8 @@ def parse():
                     help="requests of the serving trace replayed at 200/s (0 to skip)")
     ap.add_argument("--serve-window", type=float, default=12.0,
                     help="arrival window (s) of the sub-capacity serving run")
+    ap.add_argument("--serve-long", type=int, default=2000,
+                    help="requests of the long sub-capacity run (stable materials, steps log-U[50, 2000]; 0 to skip)")
     ap.add_argument("--cpu-steps", type=int, default=0, help="oracle sample steps (0 = auto, ~10-20 s)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -85,13 +90,34 @@ def workload(a):
     return W.clamped_body(nx=a.nx, ny=a.ny, mu=0.3, nu=a.nu, vmax=a.vmax)
 
 
+SCHEME_LABEL = {"explicit": "explicit (Algorithm 1: the time-t source in collision and moment)",
+                "predictor": "predictor-corrector (the footnote to Sec. 5)",
+                "extrapolated": "extrapolated j (Sec. 5, O(dt^3))"}
+
+
+def scheme_id(name):
+    from paper_2208_13769_gb300 import lbm
+
+    return {"explicit": lbm.LBM_SCHEME_EXPLICIT, "predictor": lbm.LBM_SCHEME_PREDICTOR,
+            "extrapolated": lbm.LBM_SCHEME_EXTRAPOLATED}[name]
+
+
+def algorithmic_bytes(storage):
+    """Bytes per node update that must cross HBM (9 populations and 4 carry
+    values, each read and written once): FP64 208, FP32 104; 16-bit
+    populations with an FP64-wide displacement carry and an FP32 source carry
+    84.  A form that moves more (the compensated FP32 carry: 120) is charged
+    these bytes, not its own."""
+    return {"f64": 208, "f32": 104, "f16": 84, "bf16": 84}[storage]
+
+
 def config_of(a, prob):
     return {
         "workload": f"clamped neo-Hooke body {a.nx}x{a.ny} nodes, FP32 populations/arithmetic",
         "nx": a.nx, "ny": a.ny, "mu": prob.mu, "lambda": prob.lam, "nu": a.nu, "rho0": prob.rho0,
         "omega": prob.omega, "v_max": a.vmax, "edges": "x- clamped (Dirichlet), x+/y-/y+ traction-free",
         "storage": a.storage, "u_carry": "compensated" if a.compensated else "native",
-        "scheme": "predictor-corrector",
+        "scheme": SCHEME_LABEL[a.scheme],
         "l2": "no flush: the state (two ping-pong copies, ~1 GB) is 8x the 129 MB L2",
     }
 
@@ -367,15 +393,16 @@ def run_native(a):
         d.nx, d.ny, d.dX = prob.nx, prob.ny, prob.dX
         d.storage = lbm.STORAGE[a.storage]
         d.u_carry = lbm.LBM_UCARRY_COMPENSATED if a.compensated else lbm.LBM_UCARRY_NATIVE
-        d.scheme = lbm.LBM_SCHEME_PREDICTOR
+        d.scheme = scheme_id(a.scheme)
         d.cuda_stream = stream.cuda_stream
         d.device = local
         t0 = time.perf_counter()
         tuning, tms = lbm.lbm_autotune(d, [e.kind for e in prob.edges], 129)
         tuning_info = dict(tuning.as_dict(), candidate_ms_per_step=tms, seconds=time.perf_counter() - t0)
-    body = lbm.Body(prob, storage=a.storage, compensated=a.compensated, stream=stream.cuda_stream,
-                    device=local, tuning=tuning)
-    _, bytes_per_node = lbm.lbm_memory_info(body.ctx)
+    body = lbm.Body(prob, storage=a.storage, compensated=a.compensated, scheme=scheme_id(a.scheme),
+                    stream=stream.cuda_stream, device=local, tuning=tuning)
+    _, moved_per_node = lbm.lbm_memory_info(body.ctx)
+    bytes_per_node = algorithmic_bytes(a.storage)
     body.step(a.warmup)
     body.read(lbm.LBM_FIELD_U, allow_unstable=True)
     clocks = ClockSampler(local)
@@ -409,6 +436,8 @@ def run_native(a):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": "interior_step_kernel",
                 "algorithmic_bytes_per_node": bytes_per_node, "units_per_launch": interior_nodes,
+                "moved_bytes_per_node": moved_per_node,
+                "frac_at_moved_bytes": moved_per_node * interior_nodes / (interior_ms * 1e-3) / 1e9 / peak,
                 "launch_ms": interior_ms,
                 "launch_timing": "200 launches back to back between CUDA events on the library's stream",
                 "launch_ms_in_step": interior_step_ms,
@@ -420,6 +449,7 @@ def run_native(a):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None, "peak_kind": peak_kind, "kernel": "edge_tile_kernel",
                 "algorithmic_bytes_per_node": bytes_per_node, "units_per_launch": nodes,
+                "moved_bytes_per_node": moved_per_node,
                 "launch_ms": band_ms,
                 "launch_timing": "CUDA events around each launch of lbm_profile_steps (the body runs as edge "
                                  "tiles only: fewer than 2^17 nodes)",
@@ -432,12 +462,14 @@ def run_native(a):
     forms = {}
     ref_u = None
     if a.forms:
-        with lbm.Body(prob, storage="f64", stream=stream.cuda_stream, device=local) as b64:
+        with lbm.Body(prob, storage="f64", scheme=scheme_id(a.scheme), stream=stream.cuda_stream,
+                      device=local) as b64:
             b64.step(a.warmup + a.form_steps)
             ref_u = b64.read(lbm.LBM_FIELD_U, allow_unstable=True)["u"]
     for f in [x for x in a.forms.split(",") if x]:
         st, comp = {"f32c": ("f32", True), "f32n": ("f32", False)}.get(f, (f, False))
-        b = lbm.Body(prob, storage=st, compensated=comp, stream=stream.cuda_stream, device=local)
+        b = lbm.Body(prob, storage=st, compensated=comp, scheme=scheme_id(a.scheme), stream=stream.cuda_stream,
+                     device=local)
         _, bpn = lbm.lbm_memory_info(b.ctx)
         b.step(a.warmup)
         torch.cuda.synchronize()
@@ -446,10 +478,12 @@ def run_native(a):
         ok = out["status"] == lbm.LBM_OK
         uerr = float(np.linalg.norm(out["u"] - ref_u) / np.linalg.norm(ref_u))
         b.close()
-        ach = bpn * nodes / (s / a.form_steps) / 1e9
-        forms[f] = {"mlups": nodes * a.form_steps / s / 1e6, "bytes_per_node_update": bpn,
-                    "achieved_gbs": ach, "frac": ach / peak, "steps": a.form_steps, "stable": ok,
-                    "u_rel_err_vs_f64": uerr}
+        alg = algorithmic_bytes(st)
+        ach = alg * nodes / (s / a.form_steps) / 1e9
+        forms[f] = {"mlups": nodes * a.form_steps / s / 1e6, "algorithmic_bytes_per_node": alg,
+                    "moved_bytes_per_node": bpn, "achieved_gbs": ach, "frac": ach / peak,
+                    "frac_at_moved_bytes": bpn * nodes / (s / a.form_steps) / 1e9 / peak,
+                    "steps": a.form_steps, "stable": ok, "u_rel_err_vs_f64": uerr}
 
     # the other time levels of the moment's source (Sec. 5) on the same body,
     # FP32 with the compensated carry, each with its displacement difference
@@ -461,7 +495,8 @@ def run_native(a):
                   "extrapolated": lbm.LBM_SCHEME_EXTRAPOLATED}
     for name in [x for x in a.schemes.split(",") if x]:
         if ref_u is None:
-            with lbm.Body(prob, storage="f64", stream=stream.cuda_stream, device=local) as b64:
+            with lbm.Body(prob, storage="f64", scheme=scheme_id(a.scheme), stream=stream.cuda_stream,
+                          device=local) as b64:
                 b64.step(a.warmup + a.form_steps)
                 ref_u = b64.read(lbm.LBM_FIELD_U, allow_unstable=True)["u"]
         b = lbm.Body(prob, storage="f32", compensated=True, scheme=scheme_ids[name], stream=stream.cuda_stream,
@@ -476,7 +511,7 @@ def run_native(a):
         schemes[name] = {"mlups": nodes * a.form_steps / s / 1e6, "bytes_per_node_update": bpn,
                          "achieved_gbs": ach, "frac": ach / peak, "steps": a.form_steps,
                          "stable": out["status"] == lbm.LBM_OK,
-                         "u_rel_diff_vs_predictor_f64": float(np.linalg.norm(out["u"] - ref_u)
+                         "u_rel_diff_vs_f64_" + a.scheme: float(np.linalg.norm(out["u"] - ref_u)
                                                               / np.linalg.norm(ref_u))}
 
     # the 8192 x 8192 clamped body with 16-bit population storage, timed, and
@@ -613,6 +648,22 @@ def run_native(a):
         serving = {"storage": "f16", "trace": "Poisson 200/s, sides U{128..2048}, steps log-U[500, 20000], seed 7",
                    "overload": dict(over, rate_per_s=200.0), "capacity_requests_per_s": capacity,
                    "sub_capacity": dict(sub, rate_per_s=rate)}
+        # a long sub-capacity run: the literal trace's sizes, arrival process
+        # and initial fields, with Poisson ratios drawn where the method is
+        # stable (0.25 for clamped bodies, U[0.2, 0.4] for periodic ones) and
+        # step counts log-U[50, 2000] (a tenth of the literal trace's, whose
+        # 2000 requests would take over 5 minutes of GPU time), at 0.7 x the
+        # capacity the overload run measured
+        if a.serve_long > 0:
+            ltrace = W.serving_trace(rate=200.0, duration=1e9, seed=8, steps_lo=50, steps_hi=2000,
+                                     max_requests=a.serve_long, stable_materials=True)
+            lwork = float(np.mean([q.problem.nx * q.problem.ny * q.steps for q in ltrace]))
+            lrate = 0.7 * over["served_mlups"] * 1e6 / lwork
+            lrun = strip(serve.Server(be, hbm_budget=150e9).run(serve.trace_at_rate(ltrace, lrate)))
+            serving["long_sub_capacity"] = dict(
+                lrun, rate_per_s=lrate,
+                trace="Poisson at 0.7 x capacity, sides U{128..2048}, steps log-U[50, 2000], Poisson ratio 0.25 "
+                      "(clamped) / U[0.2, 0.4] (periodic), seed 8")
 
     # end to end through the C ABI from host buffers: create (H2D of u0, v0),
     # K steps, read u (D2H)
@@ -655,8 +706,9 @@ def run_native(a):
                 ("c1_64x64_f64", lambda: [lbm.Body(c1, storage="f64", stream=stream.cuda_stream, device=local)],
                  1000, a.solves, 64 * 64),
                 ("c2_%dx%d_%s" % (a.nx, a.ny, a.storage),
-                 lambda: [lbm.Body(c2, storage=a.storage, compensated=a.compensated, stream=stream.cuda_stream,
-                                   device=local, tuning=tuning)], 2000, a.solves, a.nx * a.ny),
+                 lambda: [lbm.Body(c2, storage=a.storage, compensated=a.compensated, scheme=scheme_id(a.scheme),
+                                   stream=stream.cuda_stream, device=local, tuning=tuning)], 2000, a.solves,
+                 a.nx * a.ny),
                 ("c4_256_bodies_f32", lambda: [lbm.Body(p, storage="f32", stream=stream.cuda_stream, device=local)
                                                for p in c4.problems], 256, max(1, a.solves // 4),
                  sum(p.nx * p.ny for p in c4.problems))):
@@ -678,8 +730,8 @@ def run_native(a):
         pprob = dataclasses.replace(prob, u0=u0_h.numpy(), v0=v0_h.numpy(), make_initial=None)
         barrier()
         t0 = time.perf_counter()
-        b = lbm.Body(pprob, storage=a.storage, compensated=a.compensated, stream=stream.cuda_stream,
-                     device=local, tuning=tuning)
+        b = lbm.Body(pprob, storage=a.storage, compensated=a.compensated, scheme=scheme_id(a.scheme),
+                     stream=stream.cuda_stream, device=local, tuning=tuning)
         b.step(a.steps)
         st, _ = lbm.lbm_read_fields(b.ctx, lbm.LBM_FIELD_U, u_h.numpy().reshape(-1), allow_unstable=True)
         t1 = time.perf_counter()
@@ -709,7 +761,11 @@ def run_native(a):
         "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "f16": "f16", "bf16": "bf16"}[a.storage],
         "data": "synthetic", "config": config_of(a, prob), "roofline": roof, "cpu_baseline": cpu,
-        "e2e": e2e, "gpu_launches": 2 * a.steps, "clocks": clk, "forms": forms, "schemes": schemes, "solves": solves, "c3_8192": c3, "plate_hole": hole, "batched": batched,
+        "e2e": e2e, "gpu_launches": 2 * a.steps, "clocks": clk,
+        # the plain-carry FP32 form (104 bytes moved per node, like the survey's count)
+        "plain_carry_f32": ({k: forms["f32n"][k] for k in ("mlups", "frac", "u_rel_err_vs_f64")}
+                            if "f32n" in forms else None),
+        "forms": forms, "schemes": schemes, "solves": solves, "c3_8192": c3, "plate_hole": hole, "batched": batched,
         "serving": serving, "tuning": tuning_info,
         "status": lbm.status_string(status),
     }

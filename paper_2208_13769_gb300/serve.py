@@ -94,7 +94,14 @@ class Server:
 
     target_chunk_s: wall time aimed at per lbm_batch_step call (bounds how
     long an arrival waits before it can be admitted); max_chunk: steps per
-    call at most."""
+    call at most.
+
+    Arrivals join the batch at chunk boundaries, not inside a chunk: a chunk
+    is one lbm_batch_step call, replayed as CUDA graphs over a fixed set of
+    members, and admitting a member inside it would mean rebuilding the
+    batch's graphs while they run.  With chunks of at most target_chunk_s
+    (50 ms by default) an arrival waits at most that long for its turn, far
+    below the solve times."""
 
     def __init__(self, backend, hbm_budget: float = 150e9, target_chunk_s: float = 0.05, max_chunk: int = 2048,
                  clock: Callable[[], float] = time.perf_counter, sleep: Callable[[float], None] = time.sleep,
@@ -228,6 +235,9 @@ class Server:
 
     def _stats(self, requests, records, rejected, makespan, busy, peak_used, chunks, rebuilds, max_active):
         lat = np.array([r.latency for r in records]) if records else np.zeros(0)
+        # the requests whose solve finished (status OK), apart from those that
+        # ended LBM_E_UNSTABLE or failed
+        ok = np.array([r.latency for r in records if r.status == 0]) if records else np.zeros(0)
         work = sum(r.nodes * r.steps for r in records if r.status in (0, LBM_E_UNSTABLE))
         arrivals = [q.arrival for q in requests]
         window = (max(arrivals) - min(arrivals)) if len(arrivals) > 1 else 0.0
@@ -239,13 +249,17 @@ class Server:
             "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
             "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
             "mean_s": float(lat.mean()) if len(lat) else None,
+            "stable_completed": int(len(ok)),
+            "stable_p50_s": float(np.percentile(ok, 50)) if len(ok) else None,
+            "stable_p99_s": float(np.percentile(ok, 99)) if len(ok) else None,
             "makespan_s": makespan, "gpu_busy_s": busy,
             "served_mlups": work / makespan / 1e6 if makespan > 0 else None,
             "offered_mlups": offered / window / 1e6 if window > 0 else None,
             "arrival_window_s": window,
             "peak_hbm_bytes": peak_used, "hbm_budget_bytes": self.budget,
             "chunks": chunks, "batch_rebuilds": rebuilds, "max_active": max_active,
-            "admission": "FCFS, head of line blocks while it does not fit the budget",
+            "admission": "FCFS, head of line blocks while it does not fit the budget; arrivals join at "
+                         "the next chunk boundary (chunks aim at target_chunk_s of GPU time)",
             "records": records,
         }
 

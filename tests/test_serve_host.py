@@ -203,3 +203,35 @@ def test_failed_requests_complete_with_their_status_and_the_others_go_on():
         if recs[i].status == 0:
             assert be.steps_of[k] == reqs[i].steps
     assert st["p50_s"] is not None
+
+
+class UnstableBackend(FakeBackend):
+    """Every third body reports LBM_E_UNSTABLE when its batch is synced."""
+
+    def sync(self, batch):
+        return [4 if h["id"] % 3 == 2 else 0 for h in batch]
+
+
+def test_stable_only_percentiles_leave_out_the_unstable_solves():
+    clock = FakeClock()
+    be = UnstableBackend(clock)
+    reqs = _trace(60, seed=11)
+    st = serve.Server(be, hbm_budget=1e12, clock=clock, sleep=clock.sleep).run(reqs)
+    ok = sorted(r.latency for r in st["records"] if r.status == 0)
+    assert st["unstable"] == 20 and st["stable_completed"] == len(ok) == 40
+    assert abs(st["stable_p50_s"] - float(np.percentile(ok, 50))) < 1e-12
+    assert abs(st["stable_p99_s"] - float(np.percentile(ok, 99))) < 1e-12
+    assert st["p50_s"] is not None and st["completed"] == 60
+
+
+def test_stable_materials_trace_draws_the_stable_poisson_ratios():
+    lit = W.serving_trace(max_requests=200)
+    st = W.serving_trace(max_requests=200, stable_materials=True)
+    assert [q.arrival for q in st] == [q.arrival for q in lit]  # the same draws otherwise
+    assert [q.problem.nx for q in st] == [q.problem.nx for q in lit]
+    for q in st:
+        nu = q.problem.lam / (2.0 * (q.problem.lam + q.problem.mu))
+        if q.problem.periodic(0):
+            assert 0.2 - 1e-12 <= nu <= 0.4 + 1e-12
+        else:
+            assert abs(nu - 0.25) < 1e-12
