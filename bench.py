@@ -134,8 +134,7 @@ def measured_peak():
 
 # the interior kernel's sources: the committed DRAM-traffic profile is valid
 # while these are unchanged
-KERNEL_SOURCES = ("lbm_interior.cu", "lbm_edge_tile.cuh", "lbm_device.cuh", "lbm_pipeline.cuh", "lbm_params.h",
-                  "lbm_kernels.h")
+KERNEL_SOURCES = ("lbm_interior.cu", "lbm_device.cuh", "lbm_pipeline.cuh", "lbm_params.h", "lbm_kernels.h")
 
 
 def kernel_source_hash():

@@ -1,14 +1,15 @@
 // lbm_batch.cu -- many bodies advanced by shared launches (the C ABI's
 // lbm_batch_* entry points).
 //
-// Each time step of a batch is one launch of a persistent kernel over a
-// work list of every member's interior tiles and edge tiles (its resident
-// CTAs take the items one at a time from a device queue), each CTA reading
-// its body's parameters from a device table.  So small and uneven bodies
-// share the GPU instead of each paying launches per step, and chunks of 64
-// steps replay as one CUDA graph.  Every node of every member
-// goes through the same kernels and arithmetic as when the member is
-// stepped alone, so the results are bit-identical.
+// Each time step of a batch is two launches, as for a single body: the
+// interior tiles of every member (one CTA per tile, longest first) on the
+// batch's stream, and the edge tiles of every member on a side stream at the
+// same time, each CTA reading its member's parameters from a device table.
+// So small and uneven bodies share the GPU instead of each paying launches
+// per step, and chunks of 64 steps replay as one CUDA graph.  Every node of
+// every member goes through the same tile code and arithmetic as when the
+// member is stepped alone (with the interior kernel: plan 2), so the results
+// are bit-identical.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -37,19 +38,18 @@ struct lbm_batch {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool owns_stream = false;
+    cudaStream_t side = nullptr;  // the edge tiles' stream
     cudaEvent_t ev_sync = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<lbm_ctx*> m;
     std::vector<int> base_parity;  // member parity when the batch step count is even
     int fmt = 0;
     int n_entries = 0;           // parameter-table entries per parity
     StepParams* dtab = nullptr;  // [2][n_entries]: entry q * n_entries + e at parity base_parity ^ q
-    BatchItem* ditems = nullptr;  // work list: interior tiles and groups of edge tiles, interleaved
-    EdgeTile* dtiles = nullptr;   // edge tiles of the groups
-    int32_t* dqueue = nullptr;    // {next item, CTAs done} of the persistent kernel
+    BatchItem* ditems = nullptr;  // interior tiles, longest first
+    EdgeTile* dtiles = nullptr;   // edge tiles of every member
     int n_work = 0;               // interior tiles
     int n_edge = 0;               // edge tiles
-    int n_items = 0;              // items of the work list
-    int grid = 0;                // persistent CTAs
     int chunk_rows = 0;
     int ring = kBatchRing;
     bool holed = false;           // some member has a hole
@@ -80,23 +80,37 @@ void batch_free(lbm_batch* b) {
     cudaFree(b->dtab);
     cudaFree(b->ditems);
     cudaFree(b->dtiles);
-    cudaFree(b->dqueue);
     if (b->ev_sync) cudaEventDestroy(b->ev_sync);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->side) cudaStreamDestroy(b->side);
     if (b->owns_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
-// One batch time step from table parity q.
+// One batch time step from table parity q: the interior tiles on the batch's
+// stream and the edge tiles on the side stream, forked from and joined to
+// the batch's stream (the small edge CTAs fill the room the interior CTAs
+// leave).
 cudaError_t batch_launch(lbm_batch* b, int q, bool fields) {
-    const int n = int(b->m.size());
-    BatchLaunch L;
-    memset(&L, 0, sizeof(L));
-    L.params = b->dtab + size_t(q) * size_t(b->n_entries);
-    L.items = b->ditems;
-    L.tiles = b->dtiles;
-    L.queue = b->dqueue;
-    L.fields = fields ? 1 : 0;
-    L.nitems = b->n_items;
-    return launch_batch_step(b->fmt, L, b->grid, b->ring, b->stream, nullptr, b->holed);
+    const StepParams* tab = b->dtab + size_t(q) * size_t(b->n_entries);
+    BatchInteriorLaunch I;
+    memset(&I, 0, sizeof(I));
+    I.params = tab;
+    I.items = b->ditems;
+    I.fields = fields ? 1 : 0;
+    I.nitems = b->n_work;
+    EdgeLaunch E;
+    memset(&E, 0, sizeof(E));
+    E.params = tab;
+    E.tiles = b->dtiles;
+    E.fields = fields ? 1 : 0;
+    cudaError_t e = cudaEventRecord(b->ev_fork, b->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+    if (e == cudaSuccess) e = launch_batch_interior(b->fmt, I, b->ring, b->stream, nullptr);
+    if (e == cudaSuccess) e = launch_edge(b->fmt, E, b->n_edge, b->side, 0, b->holed, false);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+    return e;
 }
 
 void advance_members(lbm_batch* b, int64_t k) {
@@ -198,11 +212,14 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
         b->owns_stream = e == cudaSuccess;
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_sync, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
 
     // each member's rectangles: the interior kernel wherever the body allows
     // it (plan 2), whatever plan the member runs alone with (plan 0 gives
-    // small bodies edge tiles only; in a batch their interior tiles fill the
-    // persistent grid better), unless the member asked for edge tiles only
+    // small bodies edge tiles only; in a batch their interior tiles share the
+    // launch with the others'), unless the member asked for edge tiles only
     struct Rects {
         int irect[4][4];
         int n_irect;
@@ -229,7 +246,15 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
         b->holed = b->holed || c->hole[0] < c->hole[1];
     }
     b->ring = tuning && tuning->ring_slots ? tuning->ring_slots : kBatchRing;
-    const int64_t wave = int64_t(b->m[0]->num_sms) * std::max(1, interior_occupancy(b->fmt, b->ring));
+    // the interior kernel's CTAs per SM with this ring (the first call also
+    // sets its shared-memory limit, outside any capture)
+    int resident = 0;
+    {
+        BatchInteriorLaunch L;
+        memset(&L, 0, sizeof(L));
+        if (e == cudaSuccess) e = launch_batch_interior(b->fmt, L, b->ring, b->stream, &resident);
+    }
+    const int64_t wave = int64_t(b->m[0]->num_sms) * std::max(1, resident);
     b->chunk_rows = tuning && tuning->chunk_rows
                         ? tuning->chunk_rows
                         : int(std::min<int64_t>(256, std::max<int64_t>(32, all_interior / (int64_t(120) * wave * 8))));
@@ -289,10 +314,10 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
             bool first = true;
             const int e = first_entry[size_t(i)];
             for (int r = 0; r < mri.nband; ++r) {
-                const int cnt = edge_tiles_of_rect(mri.brect[r], e, nullptr, 0, false, kInteriorThreads);
+                const int cnt = edge_tiles_of_rect(mri.brect[r], e, nullptr, 0, false, kEdgeThreads);
                 const size_t at = tiles.size();
                 tiles.resize(at + size_t(cnt));
-                edge_tiles_of_rect(mri.brect[r], e, tiles.data() + at, cnt, first, kInteriorThreads);
+                edge_tiles_of_rect(mri.brect[r], e, tiles.data() + at, cnt, first, kEdgeThreads);
                 first = first && cnt == 0;
             }
         }
@@ -304,25 +329,8 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
         };
         std::stable_sort(work.begin(), work.end(),
                          [&](const InteriorWork& x, const InteriorWork& y) { return rows_of(x) > rows_of(y); });
-        // groups of up to kEdgeGroup consecutive edge tiles of one body
-        std::vector<BatchItem> groups;
-        for (size_t k = 0; k < tiles.size();) {
-            size_t e = k + 1;
-            while (e < tiles.size() && e - k < size_t(kEdgeGroup) && tiles[e].inst == tiles[k].inst) ++e;
-            groups.push_back(BatchItem{tiles[k].inst, int32_t(k), int32_t(e - k), 1});
-            k = e;
-        }
-        // the work list: the interior tiles in that order, with the edge
-        // groups spread evenly between them
-        const size_t ni = work.size(), ng = groups.size();
-        items.reserve(ni + ng);
-        size_t next_group = 0;
-        for (size_t k = 0; k < ni; ++k) {
-            items.push_back(BatchItem{work[k].inst, work[k].bx, work[k].by, 0});
-            const size_t upto = ng * (k + 1) / ni;
-            for (; next_group < upto; ++next_group) items.push_back(groups[next_group]);
-        }
-        for (; next_group < ng; ++next_group) items.push_back(groups[next_group]);
+        items.reserve(work.size());
+        for (const InteriorWork& w : work) items.push_back(BatchItem{w.inst, w.bx, w.by, 0});
     } catch (...) {
         batch_free(b);
         delete b;
@@ -331,30 +339,18 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
     if (items.size() > 0x7fffffff || tiles.size() > 0x7fffffff) e = cudaErrorInvalidValue;
     b->n_work = int(work.size());
     b->n_edge = int(tiles.size());
-    b->n_items = int(items.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->dtab, sizeof(StepParams) * tab.size());
-    if (e == cudaSuccess) e = cudaMalloc(&b->ditems, sizeof(BatchItem) * items.size());
+    if (e == cudaSuccess && !items.empty()) e = cudaMalloc(&b->ditems, sizeof(BatchItem) * items.size());
     if (e == cudaSuccess && !tiles.empty()) e = cudaMalloc(&b->dtiles, sizeof(EdgeTile) * tiles.size());
-    if (e == cudaSuccess) e = cudaMalloc(&b->dqueue, 2 * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->dqueue, 0, 2 * sizeof(int32_t), b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->dtab, tab.data(), sizeof(StepParams) * tab.size(), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !items.empty())
         e = cudaMemcpyAsync(b->ditems, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
                             b->stream);
     if (e == cudaSuccess && !tiles.empty())
         e = cudaMemcpyAsync(b->dtiles, tiles.data(), sizeof(EdgeTile) * tiles.size(), cudaMemcpyHostToDevice,
                             b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host tables die with this scope
-    // sets the batch kernel's shared-memory limit outside any capture, and
-    // sizes its persistent grid: every resident CTA slot
-    if (e == cudaSuccess) {
-        BatchLaunch L;
-        memset(&L, 0, sizeof(L));
-        int resident = 0;
-        e = launch_batch_step(b->fmt, L, 0, b->ring, b->stream, &resident, b->holed);
-        b->grid = int(std::min<int64_t>(int64_t(items.size()), int64_t(b->m[0]->num_sms) * std::max(1, resident)));
-    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         batch_free(b);

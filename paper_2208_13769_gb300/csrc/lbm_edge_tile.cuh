@@ -1,6 +1,6 @@
 // lbm_edge_tile.cuh -- one tile of the fused step on the edge bands of a
-// body (or of the initialisation), shared by the edge kernel (lbm_edge.cu)
-// and the persistent batch kernel (lbm_interior.cu).
+// body or of a batch's members (or of the initialisation), the body of the
+// edge kernel (lbm_edge.cu).
 //
 // Nodes within 2 of a bounded edge (3 of a periodic seam) need the boundary
 // machinery of Sec. 6: ghost values in Grad u and Div Q, bounced populations

@@ -41,7 +41,6 @@
 #include <type_traits>
 
 #include "lbm_device.cuh"
-#include "lbm_edge_tile.cuh"
 #include "lbm_kernels.h"
 #include "lbm_pipeline.cuh"
 
@@ -74,11 +73,9 @@ __host__ __device__ constexpr size_t interior_row_bytes() {
 
 }  // namespace
 
-// One tile (column strip bx, row chunk by of the rectangle tg) of one body.  Returns
-// false if a wait gave up or a copy was refused (reported in p.flag).
-// reuse: the CTA runs more tiles after this one, so the ring's mbarriers are
-// invalidated at the end (every copy has completed by then) for the next
-// tile to initialise them afresh.  UNROLL3: the row loop unrolled by 3 (the
+// One tile (column strip bx, row chunk by of the rectangle tg) of one body,
+// the only tile of its CTA.  Returns false if a wait gave up or a copy was
+// refused (reported in p.flag).  UNROLL3: the row loop unrolled by 3 (the
 // row buffers' indices fixed at compile time, the kept populations changing
 // roles instead of moving: fewer instructions, more registers; faster for
 // the formats whose registers allow it).  KEEP: stage C takes the populations of
@@ -89,8 +86,8 @@ __host__ __device__ constexpr size_t interior_row_bytes() {
 // D = ku jh(t) and F = ku (3 jh(t) - jh(t - dt)) (in the source planes);
 // else u* is A + ku m and the source planes hold the last source.
 template <class TS, class TC, class UT, int NT, bool KEEP, bool XJ, bool UNROLL3>
-__device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeom& tg, int bx, int by, double* fields,
-                                              bool reuse) {
+__device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeom& tg, int bx, int by,
+                                              double* fields) {
     using CT = typename UT::Elem;
     const int W = tg.strip_w;
     constexpr int SEG = seg_elems<TS, NT>();
@@ -178,7 +175,7 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeo
     const int D = KEEP ? R : R - 3;
     uint32_t phase = 0, issued = 0;
     if (t == 0) {
-        fence_proxy_async();  // a previous tile's reads of the ring precede these copies
+        fence_proxy_async();  // the CTA's earlier shared-memory accesses precede the copies into the ring
     }
     if (t == 0)
         for (int j = 0; j < D && j < niter; ++j) {
@@ -440,12 +437,6 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeo
         }
         return false;
     }
-    if (reuse) {
-        __syncthreads();  // every thread has finished with the ring and the row buffers
-        if (t == 0)
-            for (int s = 0; s < R; ++s) mbar_inval(&bars[s]);
-        __syncthreads();
-    }
     return true;
 }
 
@@ -477,78 +468,27 @@ __global__ void __launch_bounds__(NT, MINB)
         f = R.first[3];
     }
     const int local = b - f;
-    interior_tile<TS, TC, UT, NT, true, XJ, UNROLL3>(p, tg, local % tx, local / tx, p.fields, false);
+    interior_tile<TS, TC, UT, NT, true, XJ, UNROLL3>(p, tg, local % tx, local / tx, p.fields);
 }
 
-// One time step of a batch of bodies in one launch: a persistent grid of
-// resident CTAs, each taking the next item of the work list from a device
-// queue when it is done with the last one, until none is left.  Items are
-// interior tiles (body, strip, chunk) and groups of edge tiles (shapes for NT
-// threads) of every member, interleaved in the list, so that the
-// latency-bound edge tiles of some CTAs run beside the bandwidth-bound
-// interior tiles of others; a group pays for one parameter load, and each of
-// its tiles for one memory round trip.  Each item's parameters come from the
-// device table into shared memory; an edge tile uses the shared buffers of
-// the interior tile (u*, Q, then the edges' boundary data and the group's
-// tile records after the u* rows it needs).  The queue {next item, CTAs
-// done} is zero when the launch starts; the last CTA to finish sets it back
-// to zero.
-// HOLE: some member has a hole (the edge tiles test for it; a batch without
-// one runs tiles that carry none of the hole's tests).
-template <class TS, class TC, class UT, int NT, int MINB, bool HOLE>
-__global__ void __launch_bounds__(NT, MINB) batch_step_kernel(const __grid_constant__ BatchLaunch L) {
+// The interiors of a batch of bodies for one time step: one CTA per interior
+// tile (member rectangle, strip, chunk) of a list ordered longest first, the
+// tile's parameters (the member's, with the rectangle and its strip grid)
+// read from the device table into shared memory.  The tile is the
+// single-body kernel's, so every node of a member takes the same arithmetic
+// as when the member is stepped alone.
+template <class TS, class TC, class UT, int NT, int MINB, bool UNROLL3>
+__global__ void __launch_bounds__(NT, MINB) batch_interior_kernel(const __grid_constant__ BatchInteriorLaunch L) {
     __shared__ __align__(16) StepParams sp;
-    __shared__ BatchItem s_item;
-    extern __shared__ __align__(128) unsigned char smem[];
-    UT* su = reinterpret_cast<UT*>(smem + kSmemHeader);
-    TC* sq = reinterpret_cast<TC*>(smem + kSmemHeader + sizeof(UT) * 6 * NT);
-    // an edge tile uses the first 2 of the 6 u* rows; its boundary data and
-    // the group's tile records follow
-    EdgeNow<TC, UT>* s_edge = reinterpret_cast<EdgeNow<TC, UT>*>(su + 2 * NT);
-    EdgeTile* s_tiles = reinterpret_cast<EdgeTile*>(su + 4 * NT);
-    static_assert(5 * sizeof(EdgeNow<TC, UT>) <= 2 * NT * sizeof(UT), "edge data fits after the u* rows");
-    static_assert(kEdgeGroup * sizeof(EdgeTile) <= 2 * NT * sizeof(UT), "tile records fit in the last u* rows");
-    const int t = int(threadIdx.x);
-    for (;;) {
-        __syncthreads();  // every thread is done with the previous item
-        if (t == 0) {
-            const int k = atomicAdd(L.queue, 1);
-            if (k < L.nitems) {
-                s_item = L.items[k];
-            } else {
-                s_item.kind = -1;  // none left
-            }
-        }
-        __syncthreads();
-        const BatchItem it = s_item;
-        if (it.kind < 0) break;
-        {  // the body's parameters and a group's tile records, in one round trip
-            const int4* src = reinterpret_cast<const int4*>(L.params + it.inst);
-            int4* dst = reinterpret_cast<int4*>(&sp);
-            for (int q = t; q < int(sizeof(StepParams) / 16); q += NT) dst[q] = src[q];
-            if (it.kind == 1 && t < it.b) s_tiles[t] = L.tiles[it.a + t];
-        }
-        __syncthreads();
-        if (it.kind == 0) {
-            const TileGeom tg = {{sp.rect[0], sp.rect[1], sp.rect[2], sp.rect[3]}, sp.strip_x0, sp.strip_w,
-                                 sp.chunk_rows};
-            if (!interior_tile<TS, TC, UT, NT, false, false, false>(sp, tg, it.a, it.b,
-                                                                    L.fields ? sp.fields : nullptr, true))
-                break;
-        } else {
-            for (int g = 0; g < it.b; ++g) {
-                if (g > 0) __syncthreads();  // the previous tile is done with the shared buffers
-                edge_tile_body<TS, TC, UT, 0, HOLE, false>(s_tiles[g], sp, L.fields != 0, su, sq, nullptr, s_edge);
-            }
-        }
+    const BatchItem it = L.items[blockIdx.x];
+    {
+        const int4* src = reinterpret_cast<const int4*>(L.params + it.inst);
+        int4* dst = reinterpret_cast<int4*>(&sp);
+        for (int q = int(threadIdx.x); q < int(sizeof(StepParams) / 16); q += NT) dst[q] = src[q];
     }
-    if (t == 0) {
-        __threadfence();
-        if (atomicAdd(L.queue + 1, 1) == int(gridDim.x) - 1) {  // the last CTA: no item is taken any more
-            L.queue[0] = 0;
-            L.queue[1] = 0;
-        }
-    }
+    __syncthreads();
+    const TileGeom tg = {{sp.rect[0], sp.rect[1], sp.rect[2], sp.rect[3]}, sp.strip_x0, sp.strip_w, sp.chunk_rows};
+    interior_tile<TS, TC, UT, NT, true, false, UNROLL3>(sp, tg, it.a, it.b, L.fields ? sp.fields : nullptr);
 }
 
 template <class TS, class TC, class UT, int NT>
@@ -579,9 +519,9 @@ cudaError_t launch_interior_t(const StepParams& p, const InteriorRects& R, cudaS
                          : launch_interior_x<TS, TC, UT, NT, MINB, UNROLL3, false>(p, R, s);
 }
 
-template <class TS, class TC, class UT, int NT, int MINB, bool HOLE>
-cudaError_t launch_batch_step_h(const BatchLaunch& L, int grid, int ring_slots, cudaStream_t s, int* resident) {
-    auto kern = batch_step_kernel<TS, TC, UT, NT, MINB, HOLE>;
+template <class TS, class TC, class UT, int NT, int MINB, bool UNROLL3>
+cudaError_t launch_batch_interior_t(const BatchInteriorLaunch& L, int ring_slots, cudaStream_t s, int* resident) {
+    auto kern = batch_interior_kernel<TS, TC, UT, NT, MINB, UNROLL3>;
     const size_t sm = interior_smem_bytes<TS, TC, UT, NT>(ring_slots);
     static size_t configured = 0;
     if (sm > configured) {
@@ -594,34 +534,29 @@ cudaError_t launch_batch_step_h(const BatchLaunch& L, int grid, int ring_slots, 
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, kern, NT, sm);
         if (e != cudaSuccess) return e;
     }
-    if (grid <= 0 || L.nitems <= 0) return cudaSuccess;
-    kern<<<grid, NT, sm, s>>>(L);
+    if (L.nitems <= 0) return cudaSuccess;
+    kern<<<L.nitems, NT, sm, s>>>(L);
     return cudaGetLastError();
 }
 
-template <class TS, class TC, class UT, int NT, int MINB>
-cudaError_t launch_batch_step_t(const BatchLaunch& L, int grid, int ring_slots, cudaStream_t s, int* resident,
-                                bool holed) {
-    return holed ? launch_batch_step_h<TS, TC, UT, NT, MINB, true>(L, grid, ring_slots, s, resident)
-                 : launch_batch_step_h<TS, TC, UT, NT, MINB, false>(L, grid, ring_slots, s, resident);
-}
-
-// Six CTAs per SM (the interior tile's shared memory allows six with the
-// default ring): the edge tile's code would otherwise take more registers.
-cudaError_t launch_batch_step(int fmt, const BatchLaunch& L, int grid, int ring_slots, cudaStream_t s, int* resident,
-                              bool holed) {
+// The row loops of the single-body interior kernel (launch_interior); the
+// register caps hold six CTAs per SM (the parameters come from shared
+// memory here, not the launch's constant bank, which takes more registers
+// unless capped: 96 to 104).
+cudaError_t launch_batch_interior(int fmt, const BatchInteriorLaunch& L, int ring_slots, cudaStream_t s,
+                                  int* resident) {
     constexpr int NT = kInteriorThreads;
     switch (fmt) {
         case kFmtF64:
-            return launch_batch_step_t<double, double, UPlain<double>, NT, 2>(L, grid, ring_slots, s, resident, holed);
+            return launch_batch_interior_t<double, double, UPlain<double>, NT, 2, false>(L, ring_slots, s, resident);
         case kFmtF32:
-            return launch_batch_step_t<float, float, UPlain<float>, NT, 6>(L, grid, ring_slots, s, resident, holed);
+            return launch_batch_interior_t<float, float, UPlain<float>, NT, 6, true>(L, ring_slots, s, resident);
         case kFmtF32C:
-            return launch_batch_step_t<float, float, UComp, NT, 6>(L, grid, ring_slots, s, resident, holed);
+            return launch_batch_interior_t<float, float, UComp, NT, 6, false>(L, ring_slots, s, resident);
         case kFmtF16:
-            return launch_batch_step_t<__half, float, UComp, NT, 6>(L, grid, ring_slots, s, resident, holed);
+            return launch_batch_interior_t<__half, float, UComp, NT, 6, true>(L, ring_slots, s, resident);
         case kFmtBF16:
-            return launch_batch_step_t<__nv_bfloat16, float, UComp, NT, 6>(L, grid, ring_slots, s, resident, holed);
+            return launch_batch_interior_t<__nv_bfloat16, float, UComp, NT, 6, true>(L, ring_slots, s, resident);
     }
     return cudaErrorInvalidValue;
 }

@@ -26,11 +26,10 @@ size_t interior_smem(int fmt, int ring_slots);
 // also sets the kernel's dynamic shared-memory limit, so call it before any
 // stream capture.
 int interior_occupancy(int fmt, int ring_slots);
-// Rows of the interior kernel's bulk-copy ring by default: the single-body
-// kernel keeps them all in flight (4 measured fastest); the batch kernel,
-// which re-reads a row in stage C, keeps all but 3 in flight.
+// Rows of the interior kernel's bulk-copy ring by default, all of them in
+// flight (4 measured fastest for single bodies and for batches).
 constexpr int kInteriorRing = 4;
-constexpr int kBatchRing = 5;
+constexpr int kBatchRing = 4;
 // The strip grid of the interior kernel over columns [rx0, rx1): origin of
 // strip 0, output columns per strip, number of strips.  aligned: the fewest
 // strips of equal width (at most 120 columns, 112 for 16-bit storage) on
@@ -56,32 +55,25 @@ struct InteriorRects {
 // One step of the interior: a launch of R.total CTAs over the rectangles.
 cudaError_t launch_interior(int fmt, const StepParams& p, const InteriorRects& R, cudaStream_t s, bool fields);
 
-// One time step of a batch of bodies in one launch: a persistent grid whose
-// CTAs take the items of a work list one at a time from a device queue.  An
-// item of body inst (its rect / chunk_rows / strip grid in the parameter
-// table) is either its interior tile (strip a, chunk b), or a group of b <=
-// kEdgeGroup edge tiles (shapes for kInteriorThreads threads) at tiles[a ..].
-constexpr int kEdgeGroup = 8;
+// The interiors of a batch of bodies for one time step: one CTA of
+// kInteriorThreads threads per item, the interior tile (strip a, chunk b) of
+// the parameter-table entry inst (a member's rectangle, with its strip grid
+// and rows per chunk).
 struct BatchItem {
     int32_t inst, a, b;
-    int32_t kind;  // 0: interior tile, 1: group of edge tiles
+    int32_t pad;
 };
-struct EdgeTile;
-struct BatchLaunch {
+struct BatchInteriorLaunch {
     const StepParams* params;  // device table, indexed by BatchItem::inst
-    const BatchItem* items;    // device work list, in the order it is taken
-    const EdgeTile* tiles;     // device edge tiles of the groups
-    int32_t* queue;            // device {next item, CTAs done}: zero between launches
+    const BatchItem* items;    // device list of interior tiles, one per CTA
     int32_t fields;            // also write u, v, r to params.fields
-    int32_t nitems;            // items in the list
+    int32_t nitems;            // tiles in the list
 };
-// A persistent grid of `grid` CTAs runs the items.  The setting of the
-// dynamic shared-memory limit happens on the first call (also with grid ==
-// 0), which must precede any stream capture; resident (may be NULL) receives
-// the kernel's CTAs per SM with this ring.  holed: some member has a hole
-// (the kernel variant whose edge tiles handle one).
-cudaError_t launch_batch_step(int fmt, const BatchLaunch& L, int grid, int ring_slots, cudaStream_t s, int* resident,
-                              bool holed);
+// The setting of the dynamic shared-memory limit happens on the first call
+// (also with nitems == 0), which must precede any stream capture; resident
+// (may be NULL) receives the kernel's CTAs per SM with this ring.
+cudaError_t launch_batch_interior(int fmt, const BatchInteriorLaunch& L, int ring_slots, cudaStream_t s,
+                                  int* resident);
 
 // The edge kernel (lbm_edge.cu): small 2-D tiles with every boundary rule.
 // A tile's threads cover its output nodes and a 2-node halo: tw x th nodes
@@ -110,8 +102,7 @@ struct EdgeLaunch {
 cudaError_t launch_edge(int fmt, const EdgeLaunch& L, int ntiles, cudaStream_t s, int mode, bool holed, bool xj);
 
 // Tiles of one band rectangle for CTAs of `nthreads` threads (kEdgeThreads
-// for the edge kernel, kInteriorThreads for the batch kernel); count only
-// when out is NULL.
+// for the edge kernel); count only when out is NULL.
 int edge_tiles_of_rect(const int rect[4], int inst, EdgeTile* out, int cap, bool lead_first, int nthreads);
 
 // Read-out parameters: stresses from the FP64 displacement field.

@@ -315,21 +315,13 @@ def test_tuning_changes_the_split_not_the_result():
             lbm.lbm_set_tuning(b.ctx, best)  # too late: the context has planned its launches
 
 
-def test_benchmark_body_at_full_size_against_the_oracle():
-    """The benchmark's body (4096 x 2048 clamped, FP32 storage, compensated
-    carry) in the benchmark's launch configuration (one-wave interior, edge
-    tiles on the side stream, a captured 64-step graph) against the FP64
-    oracle on the same inputs, whole fields; and the FP64 path at 1e-12.
-
-    u and v meet the tolerances (FP64: 4.6e-15 and 9.0e-15; FP32: 2.7e-7
-    and 6.0e-7).  P is evaluated from differences of u, and at this size the
-    displacement is large against what its gradient changes over one node
-    (|u| / (|Grad u| dX) ~ 1e4 after 70 steps), so the rounding of u is
-    amplified that much in P: FP64 3.2e-12, FP32 2.1e-5 (the latter stays near
-    2e-5 up to 2000 steps against the FP64 path: the stored FP32 populations,
-    of the order of v / c ~ 1e-2, carry rounding into the momentum and through
-    it into Grad u, while the strains are ~1e-4).  Bounds asserted for P:
-    1e-10 (FP64) and 5e-5 (FP32); u and v at the stated tolerances."""
+@pytest.fixture(scope="module")
+def benchmark_body_runs():
+    """The benchmark's body (4096 x 2048 clamped, Algorithm 1's explicit
+    moment, omega 1.9) in the benchmark's launch configuration (one-wave
+    interior, edge tiles on the side stream, a captured 64-step graph) after
+    70 steps: the FP64 oracle, the FP32 path (compensated carry) and the FP64
+    path on the same inputs."""
     prob = W.clamped_body(4096, 2048, nu=0.25, vmax=0.01)
     s = oracle.solver_from(prob, oracle.EXPLICIT)
     s.step(70)
@@ -341,10 +333,66 @@ def test_benchmark_body_at_full_size_against_the_oracle():
     with lbm.Body(prob, storage="f64", scheme=lbm.LBM_SCHEME_EXPLICIT) as b:
         b.step(70)
         got64 = b.read()
+    return prob, ref, got32, got64
+
+
+def _bands(nx, ny, w=3):
+    """Index sets of the four edge bands (w nodes thick) and the four w x w
+    corners of an nx x ny body."""
+    return {"x-": (slice(None), slice(0, w)), "x+": (slice(None), slice(nx - w, nx)),
+            "y-": (slice(0, w), slice(None)), "y+": (slice(ny - w, ny), slice(None)),
+            "x-y-": (slice(0, w), slice(0, w)), "x+y-": (slice(0, w), slice(nx - w, nx)),
+            "x-y+": (slice(ny - w, ny), slice(0, w)), "x+y+": (slice(ny - w, ny), slice(nx - w, nx))}
+
+
+def test_benchmark_body_at_full_size_against_the_oracle(benchmark_body_runs):
+    """Whole fields at the stated tolerances (FP64 1e-12, FP32 1e-5; measured
+    at omega = 1: FP64 4.6e-15 and 9.0e-15, FP32 2.7e-7 and 6.0e-7 in u and
+    v); and, because the edge bands are a few tenths of a percent of the
+    nodes and a whole-field norm would hide an error confined to them, the
+    largest error in each edge band and corner, relative to the largest
+    value of the field, within the same tolerances."""
+    prob, ref, got32, got64 = benchmark_body_runs
     compare(ref, got32, TOL["f32"], keys=("u", "v"))
-    compare(ref, got32, 5 * TOL["f32"], keys=("P",))
     compare(ref, got64, TOL["f64"], keys=("u", "v", "J"))
-    compare(ref, got64, 100 * TOL["f64"], keys=("P", "Pbar"))
+    for name, (ys, xs) in _bands(prob.nx, prob.ny).items():
+        for k in ("u", "v"):
+            scale = np.abs(ref[k]).max()
+            e64 = np.abs(got64[k][ys, xs] - ref[k][ys, xs]).max() / scale
+            e32 = np.abs(got32[k][ys, xs] - ref[k][ys, xs]).max() / scale
+            assert e64 <= TOL["f64"] and e32 <= TOL["f32"], (name, k, e64, e32)
+
+
+@pytest.mark.xfail(reason="known miss at this size: P comes from differences of u, and |u| / (|Grad u| dX) is "
+                          "about 4e3 after 70 steps, so the rounding of u weighs that much more in P "
+                          "(measured FP64 3.2e-12, FP32 2.1e-5)", strict=False)
+def test_benchmark_body_stress_at_full_size_within_the_stated_tolerances(benchmark_body_runs):
+    prob, ref, got32, got64 = benchmark_body_runs
+    compare(ref, got64, TOL["f64"], keys=("P", "Pbar"))
+    compare(ref, got32, TOL["f32"], keys=("P",))
+
+
+def test_benchmark_body_stress_at_full_size_within_its_rounding_floor(benchmark_body_runs):
+    """The floor of P on this body: every u carries rounding relative to |u|,
+    and P is formed from differences of u, which multiplies the relative
+    error by kappa = |u| / (|Grad u| dX) (root mean squares, computed from the
+    oracle's fields).  FP64: a few ulps of u in each implementation, at most
+    16 eps_64 kappa.  FP32 (compensated carry): the rounding of the stored
+    populations, eps_32 of the velocity they carry, enters u once per step as
+    dt eps_32 |v| and random-walks over the n steps: a relative error of u of
+    eps_32 |v| sqrt(n) dt / |u|, times kappa in P (here |v| / |u| ~ 1 / t).
+    These are floors, not tolerances: P meets the stated 1e-12 / 1e-5 on the
+    smaller parity bodies."""
+    prob, ref, got32, got64 = benchmark_body_runs
+    H = np.stack([np.gradient(ref["u"][:, :, a], prob.dX, axis=ax) for a in range(2) for ax in (1, 0)])
+    kappa = np.sqrt((ref["u"] ** 2).mean()) / (np.sqrt((H ** 2).mean()) * prob.dX)
+    n, dt = 70, oracle.solver_from(prob).dt
+    floor64 = 16 * np.finfo(np.float64).eps * kappa
+    vu = np.sqrt((ref["v"] ** 2).mean()) / np.sqrt((ref["u"] ** 2).mean())
+    floor32 = np.finfo(np.float32).eps * kappa * prob.dX * vu * np.sqrt(n) * dt
+    assert 1e3 < kappa < 1e5, kappa
+    assert rel_l2(got64["P"], ref["P"]) <= floor64, (rel_l2(got64["P"], ref["P"]), floor64)
+    assert rel_l2(got32["P"], ref["P"]) <= floor32, (rel_l2(got32["P"], ref["P"]), floor32)
 
 
 AUTO_CASES = ["clamped_96x50", "periodic_100x70", "x_periodic_y_walls_70x37", "ragged_33x13_mixed",
