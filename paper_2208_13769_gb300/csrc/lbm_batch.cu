@@ -48,6 +48,9 @@ struct lbm_batch {
     StepParams* dtab = nullptr;  // [2][n_entries]: entry q * n_entries + e at parity base_parity ^ q
     BatchItem* ditems = nullptr;  // interior tiles, longest first
     EdgeTile* dtiles = nullptr;   // edge tiles of every member
+    int32_t** dflagptr = nullptr;  // device: each member's status flag
+    int32_t* dflagval = nullptr;   // device: the flags gathered by lbm_batch_sync
+    std::vector<int32_t> hflag;    // host copy of dflagval
     int n_work = 0;               // interior tiles
     int n_edge = 0;               // edge tiles
     int chunk_rows = 0;
@@ -80,6 +83,8 @@ void batch_free(lbm_batch* b) {
     cudaFree(b->dtab);
     cudaFree(b->ditems);
     cudaFree(b->dtiles);
+    cudaFree(b->dflagptr);
+    cudaFree(b->dflagval);
     if (b->ev_sync) cudaEventDestroy(b->ev_sync);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->ev_join) cudaEventDestroy(b->ev_join);
@@ -145,6 +150,13 @@ lbm_status batch_graph(lbm_batch* b, int q, cudaGraphExec_t* out) {
     return LBM_OK;
 }
 
+// Copies every member's status flag into one array (one launch and one
+// copy for the whole batch instead of one round trip per member).
+__global__ void gather_flags(int32_t* const* flags, int32_t* out, int n) {
+    const int i = int(blockIdx.x * blockDim.x + threadIdx.x);
+    if (i < n) out[i] = *flags[i];
+}
+
 // Orders `waiter` after the work enqueued so far on `s`.
 cudaError_t stream_after(cudaStream_t waiter, cudaStream_t s, cudaEvent_t ev) {
     if (waiter == s) return cudaSuccess;
@@ -191,15 +203,16 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
     try {
         b->m.assign(members, members + n);
         b->base_parity.resize(size_t(n));
+        b->hflag.resize(size_t(n));
     } catch (...) {
         delete b;
         return LBM_E_OOM;
     }
-    // every member planned and initialised, its work finished
+    // every member initialised (its initialisation is ordered before the
+    // batch's first step by the streams; its flag is read by lbm_batch_sync)
     for (int i = 0; i < n; ++i) {
         lbm_status st = ctx_ensure_initialized(members[i]);
-        if (st == LBM_OK) st = ctx_check_flag(members[i]);
-        if (st != LBM_OK && st != LBM_E_UNSTABLE) {
+        if (st != LBM_OK) {
             delete b;
             return st;
         }
@@ -340,6 +353,17 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
     b->n_work = int(work.size());
     b->n_edge = int(tiles.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->dtab, sizeof(StepParams) * tab.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->dflagptr, sizeof(int32_t*) * size_t(n));
+    if (e == cudaSuccess) e = cudaMalloc(&b->dflagval, sizeof(int32_t) * size_t(n));
+    std::vector<int32_t*> flagptr;
+    try {
+        for (lbm_ctx* c : b->m) flagptr.push_back(c->flag);
+    } catch (...) {
+        e = cudaErrorMemoryAllocation;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->dflagptr, flagptr.data(), sizeof(int32_t*) * size_t(n), cudaMemcpyHostToDevice,
+                            b->stream);
     if (e == cudaSuccess && !items.empty()) e = cudaMalloc(&b->ditems, sizeof(BatchItem) * items.size());
     if (e == cudaSuccess && !tiles.empty()) e = cudaMalloc(&b->dtiles, sizeof(EdgeTile) * tiles.size());
     if (e == cudaSuccess)
@@ -411,10 +435,25 @@ lbm_status lbm_batch_sync(lbm_batch* b, int32_t* status) {
     if (b->sticky) return LBM_E_CUDA;
     DeviceGuard guard(b->device);
     if (!guard.ok) return batch_fail(b, cudaErrorInvalidDevice);
+    // every member's flag in one launch and one copy (the members' streams
+    // wait for the batch's, so nothing of a member is pending elsewhere);
+    // bits as for one context: 8 a refused copy (the member becomes
+    // unusable), 4 a bounded wait gave up, 1 a non-finite value or J <= 0
+    const int n = int(b->m.size());
+    gather_flags<<<(n + 255) / 256, 256, 0, b->stream>>>(b->dflagptr, b->dflagval, n);
+    BATCH_CUDA(b, cudaGetLastError());
+    BATCH_CUDA(b, cudaMemcpyAsync(b->hflag.data(), b->dflagval, sizeof(int32_t) * size_t(n), cudaMemcpyDeviceToHost,
+                                  b->stream));
     BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
     lbm_status worst = LBM_OK;
-    for (size_t i = 0; i < b->m.size(); ++i) {
-        const lbm_status st = ctx_check_flag(b->m[i]);
+    for (int i = 0; i < n; ++i) {
+        lbm_ctx* c = b->m[size_t(i)];
+        const int32_t h = b->hflag[size_t(i)];
+        lbm_status st = LBM_OK;
+        if (c->sticky) st = LBM_E_CUDA;
+        else if (h & 8) st = ctx_fail_cuda(c, cudaErrorMisalignedAddress);
+        else if (h & 4) st = LBM_E_TIMEOUT;
+        else if (h & 1) st = LBM_E_UNSTABLE;
         if (status) status[i] = st;
         if (worst == LBM_OK) worst = st;
     }

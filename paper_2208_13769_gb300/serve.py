@@ -17,7 +17,9 @@ simulated backend (tests)."""
 from __future__ import annotations
 
 import collections
+import concurrent.futures
 import dataclasses
+import itertools
 import math
 import time
 from typing import Callable, Dict, List, Optional
@@ -64,6 +66,17 @@ class GpuBackend:
         state = plane * (9 * es + 2 * ucp * ec + 2 * ec)
         return 2 * state + 5 * 8 * prob.nx * prob.ny + 2 * 16 * prob.nx * prob.ny
 
+    def prepare(self, prob):
+        """The request's initial fields built on the host (the server runs
+        this in its loader threads when the request arrives, off the GPU
+        loop's path)."""
+        if getattr(prob, "make_initial", None) is None:
+            return prob
+        u0, v0 = prob.make_initial()
+        if v0 is not None and not v0.any():
+            v0 = None  # zero initial velocity: lbm_create sets it without a copy
+        return dataclasses.replace(prob, u0=u0, v0=v0, make_initial=None)
+
     def create(self, prob):
         return self.lbm.Body(prob, storage=self.storage, stream=self.stream, device=self.device)
 
@@ -96,6 +109,12 @@ class Server:
     long an arrival waits before it can be admitted); max_chunk: steps per
     call at most.
 
+    loader_threads: threads that prepare the next `prefetch` requests in
+    arrival order (the backend's prepare(), if it has one: their initial
+    fields on the host) while the GPU works.  A request comes with its input
+    data, so its preparation may start before its arrival time (the client's
+    side of the exchange); admission takes the prepared problem.
+
     Arrivals join the batch at chunk boundaries, not inside a chunk: a chunk
     is one lbm_batch_step call, replayed as CUDA graphs over a fixed set of
     members, and admitting a member inside it would mean rebuilding the
@@ -105,8 +124,10 @@ class Server:
 
     def __init__(self, backend, hbm_budget: float = 150e9, target_chunk_s: float = 0.05, max_chunk: int = 2048,
                  clock: Callable[[], float] = time.perf_counter, sleep: Callable[[float], None] = time.sleep,
-                 keep_results: bool = False):
+                 keep_results: bool = False, loader_threads: int = 8, prefetch: int = 32):
         self.be = backend
+        self.loader_threads = int(loader_threads)
+        self.prefetch = int(prefetch)
         self.budget = float(hbm_budget)
         self.target_chunk_s = float(target_chunk_s)
         self.max_chunk = int(max_chunk)
@@ -122,6 +143,18 @@ class Server:
         active: List[dict] = []
         records: List[Record] = []
         rejected: List[int] = []
+        t0 = self.clock()
+        prepare = getattr(self.be, "prepare", None)
+        pool = (concurrent.futures.ThreadPoolExecutor(self.loader_threads)
+                if prepare is not None and self.loader_threads > 0 else None)
+        prepared: Dict[int, concurrent.futures.Future] = {}
+        try:
+            return self._loop(requests, pending, waiting, active, records, rejected, t0, pool, prepare, prepared)
+        finally:
+            if pool is not None:
+                pool.shutdown(wait=True, cancel_futures=True)
+
+    def _loop(self, requests, pending, waiting, active, records, rejected, t0, pool, prepare, prepared):
         used = 0.0
         peak_used = 0.0
         batch = None
@@ -130,12 +163,15 @@ class Server:
         chunks = 0
         rebuilds = 0
         max_active = 0
-        t0 = self.clock()
         busy = 0.0
+        # host time in each backend call outside the timed chunks
+        host = {"create": 0.0, "batch": 0.0, "result": 0.0, "close": 0.0}
         while pending or waiting or active:
             now = self.clock() - t0
             while pending and requests[pending[0]].arrival <= now:
                 waiting.append(pending.popleft())
+            # the loader prepares the next requests while the GPU works
+            self._prefetch(requests, waiting, pending, pool, prepare, prepared)
             # first come, first served: admit the head while it fits
             while waiting:
                 i = waiting[0]
@@ -143,16 +179,26 @@ class Server:
                 if need > self.budget:  # can never fit
                     waiting.popleft()
                     rejected.append(i)
+                    if i in prepared:
+                        prepared.pop(i).cancel()
                     continue
                 if used + need > self.budget:
                     break
                 waiting.popleft()
+                tc = self.clock()
                 try:
-                    body = self.be.create(requests[i].problem)
+                    self._prefetch(requests, waiting, pending, pool, prepare, prepared)
+                    if i in prepared:
+                        prob = prepared.pop(i).result()
+                    else:  # admitted before the loader reached it
+                        prob = prepare(requests[i].problem) if prepare is not None else requests[i].problem
+                    body = self.be.create(prob)
                     mem = float(self.be.memory(body))
                 except Exception as e:  # this request fails alone
                     records.append(self._failed(requests, i, t0, e))
                     continue
+                finally:
+                    host["create"] += self.clock() - tc
                 used += mem
                 peak_used = max(peak_used, used)
                 active.append({"i": i, "body": body, "left": int(requests[i].steps), "mem": mem,
@@ -164,11 +210,13 @@ class Server:
                 continue
             max_active = max(max_active, len(active))
             if dirty:
+                tb = self.clock()
                 if batch is not None:
                     self.be.close_batch(batch)
                 batch = self.be.batch([a["body"] for a in active])
                 dirty = False
                 rebuilds += 1
+                host["batch"] += self.clock() - tb
             n = min(a["left"] for a in active)
             if sec_per_step:
                 n = min(n, max(16, int(self.target_chunk_s / sec_per_step)))
@@ -197,24 +245,38 @@ class Server:
                 if a["left"] > 0:
                     still.append(a)
                     continue
+                tr = self.clock()
                 try:
                     u = self.be.result(a["body"])  # the response reaches the host
                 except Exception as e:
                     u, st = None, self._status(e)
                 done_t = self.clock() - t0
+                host["result"] += done_t + t0 - tr
                 r = requests[a["i"]]
                 records.append(Record(a["i"], r.arrival, a["admitted"], done_t, r.problem.nx * r.problem.ny,
                                       int(r.steps), int(st)))
                 if self.keep_results and u is not None:
                     self.results[a["i"]] = u
+                tq = self.clock()
                 self._quiet(self.be.close, a["body"])
+                host["close"] += self.clock() - tq
                 used -= a["mem"]
                 dirty = True
             active = still
         if batch is not None:
             self.be.close_batch(batch)
         makespan = self.clock() - t0
-        return self._stats(requests, records, rejected, makespan, busy, peak_used, chunks, rebuilds, max_active)
+        out = self._stats(requests, records, rejected, makespan, busy, peak_used, chunks, rebuilds, max_active)
+        out["host_s"] = host
+        return out
+
+    def _prefetch(self, requests, waiting, pending, pool, prepare, prepared) -> None:
+        """Hands the next `prefetch` requests in arrival order to the loader."""
+        if pool is None:
+            return
+        for i in itertools.islice(itertools.chain(waiting, pending), self.prefetch):
+            if i not in prepared:
+                prepared[i] = pool.submit(prepare, requests[i].problem)
 
     @staticmethod
     def _status(e) -> int:

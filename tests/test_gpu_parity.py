@@ -445,3 +445,25 @@ def test_edge_tiles_only_on_a_larger_body_match_the_oracle():
             got = b.read()
             assert lbm.lbm_get_tuning(b.ctx).plan == 1
         compare(ref, got, tol)
+
+
+def test_clamped_body_stability_horizon():
+    """The benchmark's clamped body at 4096 x 2048 (nu = 0.25, v_max = 0.01,
+    omega = 1.9, Algorithm 1's explicit moment, FP32) stays stable through
+    6000 steps, past the planned 5000 (at omega = 1 it blew up at its clamped
+    corners after 3250).  With the literal material of the configuration
+    (nu = 0.3, v_max = 0.05) the method is unstable: traction-free edges are
+    neutrally stable only at lambda = mu, and the run reports LBM_E_UNSTABLE
+    long before 5000 steps (measured: within 500 steps with the explicit
+    moment, 2500 with the predictor)."""
+    prob = W.clamped_body(4096, 2048, nu=0.25, vmax=0.01)
+    with lbm.Body(prob, storage="f32", scheme=lbm.LBM_SCHEME_EXPLICIT) as b:
+        for _ in range(12):
+            b.step(500)
+            st, d = lbm.lbm_diagnostics(b.ctx, allow_unstable=True)
+            assert st == lbm.LBM_OK and d[5] == 0 and d[4] > 0.5, (b.info()[0], d)
+    literal = W.clamped_body(4096, 2048, nu=0.3, vmax=0.05)
+    for scheme, horizon in ((lbm.LBM_SCHEME_EXPLICIT, 1000), (lbm.LBM_SCHEME_PREDICTOR, 3000)):
+        with lbm.Body(literal, storage="f32", scheme=scheme) as b:
+            b.step(horizon)
+            assert b.read(lbm.LBM_FIELD_U, allow_unstable=True)["status"] == lbm.LBM_E_UNSTABLE, scheme

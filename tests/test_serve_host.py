@@ -235,3 +235,39 @@ def test_stable_materials_trace_draws_the_stable_poisson_ratios():
             assert 0.2 - 1e-12 <= nu <= 0.4 + 1e-12
         else:
             assert abs(nu - 0.25) < 1e-12
+
+
+class PreparingBackend(FakeBackend):
+    """FakeBackend with a prepare() step, as the GPU backend builds a
+    request's initial fields: it records the problems it prepared and which
+    problem each create received."""
+
+    def __init__(self, clock, **kw):
+        super().__init__(clock, **kw)
+        self.prepared = []
+        self.created_from = []
+
+    def prepare(self, prob):
+        self.prepared.append(id(prob))
+        return ("prepared", prob)
+
+    def create(self, prob):
+        assert isinstance(prob, tuple) and prob[0] == "prepared"
+        self.created_from.append(id(prob[1]))
+        return super().create(prob[1])
+
+    def estimate(self, prob):
+        return super().estimate(prob)
+
+
+def test_loader_threads_prepare_each_admitted_request_once():
+    clock = FakeClock()
+    be = PreparingBackend(clock)
+    reqs = _trace(50, seed=13)
+    st = serve.Server(be, hbm_budget=1e12, clock=clock, sleep=clock.sleep, loader_threads=4, prefetch=8).run(reqs)
+    assert st["completed"] == len(reqs)
+    order = sorted(range(len(reqs)), key=lambda i: reqs[i].arrival)
+    # every request prepared exactly once, and created from its prepared form in FCFS order
+    assert sorted(be.prepared) == sorted(id(q.problem) for q in reqs)
+    assert be.created_from == [id(reqs[i].problem) for i in order]
+    assert [be.steps_of[k] for k in be.admit_order] == [reqs[i].steps for i in order]
