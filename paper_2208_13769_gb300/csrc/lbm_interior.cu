@@ -102,6 +102,8 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeo
     UT* su = reinterpret_cast<UT*>(smem + kSmemHeader);                          // [3][2][NT]
     TC* sq = reinterpret_cast<TC*>(smem + kSmemHeader + sizeof(UT) * 6 * NT);   // [3][4][NT]
     unsigned char* ring = smem + interior_smem_fixed<UT, TC, NT>();
+    // a wait gave up: set in stage A, read after the row's first barrier, so
+    // every thread takes the same decision
     __shared__ int s_abort;
 
     LatConsts<TC> k;
@@ -146,13 +148,18 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeo
     const TS* src_seg = fsrc + int64_t(kPadRows) * pitch + seg0 + kPadCols;  // row 0 of plane 0
 
     // bulk copies of row a into ring slot s (thread 0); the 16-byte alignment
-    // of every address is checked before anything is issued
+    // of every address is checked before anything is issued.  A refused row
+    // is reported in p.flag (bit 8) and never arrives, so the wait for it
+    // gives up and the tile stops at the next barrier
     auto issue_row = [&](int a, int s) -> bool {
         unsigned char* base = ring + size_t(s) * ROW_BYTES;
         const uintptr_t acc = reinterpret_cast<uintptr_t>(base) | reinterpret_cast<uintptr_t>(src_seg) |
                               uintptr_t(pitch * int64_t(sizeof(TS))) | uintptr_t(plane * int64_t(sizeof(TS))) |
                               uintptr_t(seg_n * int(sizeof(TS)));
-        if (acc & 15) return false;
+        if (acc & 15) {
+            atomicOr(p.flag, 8);
+            return false;
+        }
         mbar_expect_tx(&bars[s], uint32_t(9 * seg_n * int(sizeof(TS))));
         TS* dst = reinterpret_cast<TS*>(base);
 #pragma unroll
@@ -180,7 +187,6 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeo
     if (t == 0)
         for (int j = 0; j < D && j < niter; ++j) {
             if (issue_row(a0 + j, j)) issued |= 1u << j;
-            else s_abort = 2;
         }
 
     // 32-bit element offsets inside a plane (a plane holds fewer than 2^31
@@ -264,7 +270,6 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeo
             const int rn = KEEP ? ra : (ra + D < R ? ra + D : ra + D - R);
             fence_proxy_async();
             if (issue_row(a0 + q + D, rn)) issued |= 1u << rn;
-            else s_abort = 2;
         }
         // source carry of the next iteration's stage C row (a - 1)
         if (colC && q >= 3 && q + 1 < niter) {
@@ -431,7 +436,7 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeo
     if (bad) atomicOr(p.flag, 1);
     if (s_abort) {
         if (t == 0) {
-            atomicOr(p.flag, s_abort == 2 ? 8 : 4);
+            atomicOr(p.flag, 4);
             for (int s = 0; s < R; ++s)
                 if (issued & (1u << s)) (void)mbar_wait(&bars[s], (phase >> s) & 1u);
         }
