@@ -601,7 +601,10 @@ def run_native(a):
         # the reduced-storage batched form: the same bodies with FP16
         # populations, the same decomposition
         hbodies = [lbm.Body(p, storage="f16", stream=stream.cuda_stream, device=local) for p in spec.problems]
-        hb = lbm.Batch(hbodies, stream=stream.cuda_stream, tuning=btune)
+        htune, ht_ms = None, None
+        if a.tune:  # its own decomposition: the strip grid that suits 2-byte planes differs
+            htune, ht_ms = lbm.lbm_batch_autotune([b.ctx for b in hbodies], 128)
+        hb = lbm.Batch(hbodies, stream=stream.cuda_stream, tuning=htune)
         hb.step(a.warmup)
         hsec = time_steps(hb, stream, a.batch_steps)
         _, hbpn = lbm.lbm_memory_info(hbodies[0].ctx)
@@ -617,7 +620,9 @@ def run_native(a):
             "ms_per_step": 1e3 * bsec / a.batch_steps, "achieved_gbs": bach, "frac": bach / peak,
             "one_by_one_mlups": bnodes * osteps / osec / 1e6, "one_by_one_steps": osteps,
             "f16_storage": {"mlups": bnodes * a.batch_steps / hsec / 1e6, "ms_per_step": 1e3 * hsec / a.batch_steps,
-                            "bytes_per_node_update": hbpn, "achieved_gbs": hach, "frac": hach / peak},
+                            "bytes_per_node_update": hbpn, "achieved_gbs": hach, "frac": hach / peak,
+                            "tuning": (dict(htune.as_dict(), candidate_ms_per_step=ht_ms) if htune is not None
+                                       else "library defaults")},
             "interior_ctas": info["interior_ctas"], "edge_ctas": info["edge_ctas"],
             "tuning": (dict(btune.as_dict(), candidate_ms_per_step=bt_ms, seconds=bt_s) if btune is not None
                        else "library defaults"),

@@ -196,8 +196,10 @@ typedef struct {
     int32_t chunk_rows; /* rows per CTA, >= 8; 0: one wave of CTAs over the SMs, at least 8 rows
                            each (default) */
     int32_t aligned;    /* 1: the fewest strips of equal width on 32-byte sector boundaries (at
-                           most 120 columns; 112 for 16-bit storage); 0: 124-column strips;
-                           -1: default (0) */
+                           most 120 columns; 112 for 16-bit storage); 2: the same on 16-byte
+                           boundaries (at most 124 columns; 120 for 16-bit storage);
+                           0: 124-column strips; -1: default (0; in a batch: 0 for 16-bit
+                           storage, 1 otherwise) */
     int32_t plan;       /* 0: by size (default): a body of fewer than 2^17 nodes (3 x 2^17 in FP64)
                            runs as small tiles of the edge kernel only, a larger one as the
                            interior kernel plus the edge bands; 1: edge tiles only; 2: the
@@ -325,11 +327,12 @@ LBM_API lbm_status lbm_batch_create(lbm_ctx* const* members, int32_t n, void* cu
 
 /* lbm_batch_create with a decomposition of the batch's interior tiles (no
  * counterpart in the paper; it changes the split of the work, never the
- * results): tuning->ring_slots, rows of the bulk-copy ring (4..8; 0: 5),
- * and tuning->chunk_rows, rows per interior tile (>= 8; 0: about eight
- * waves of resident CTAs over the batch, 32..256 rows); aligned is ignored
- * (a batch's strips always lie on 32-byte sectors), and so is plan (each
- * member keeps its own).  NULL: the defaults.
+ * results): tuning->ring_slots, rows of the bulk-copy ring (4..8; 0: 4),
+ * tuning->chunk_rows, rows per interior tile (>= 8; 0: about eight waves of
+ * resident CTAs over the batch, 32..256 rows), and tuning->aligned, the
+ * strip grid of each member (as for lbm_set_tuning; -1: 124-column strips
+ * for 16-bit storage, strips on 32-byte sectors otherwise); plan is ignored
+ * (each member keeps its own).  NULL: the defaults.
  * Errors as lbm_batch_create, and LBM_E_INVALID for a tuning out of range. */
 LBM_API lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda_stream,
                                           const lbm_tuning* tuning, lbm_batch** out);
@@ -338,9 +341,10 @@ LBM_API lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, vo
  * with the sizes, storage, carry, scheme, device and edge kinds of
  * `members` (zero initial fields, lambda = mu = 0.3), times `steps`
  * graph-replayed steps of a scratch batch of them for each candidate
- * decomposition (ring 4, 5, 6 x rows per tile default, 32, 64, 128, 256) on
- * a stream of its own, and returns the fastest in *best (its time per step
- * in *best_ms, may be NULL).  The time of a step does not depend on the
+ * decomposition (ring 4, 5, 6 x rows per tile default, 32, 64, 128, 256 on
+ * the format's default strip grid, then the other two strip grids at the
+ * best of those) on a stream of its own, and returns the fastest in *best
+ * (its time per step in *best_ms, may be NULL).  The time of a step does not depend on the
  * field values, so the choice holds for the members.  The members are not
  * touched.  Holds as much device memory as the members, for the call.
  * Synchronises.  Errors: LBM_E_INVALID (n < 1, NULL member, steps outside

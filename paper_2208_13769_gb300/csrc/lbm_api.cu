@@ -224,7 +224,7 @@ static cudaError_t build_plan(lbm_ctx* c) {
         for (int q = 0; q < c->n_irect; ++q) {
             const int* r = c->irect[q];
             const int h = r[3] - r[2];
-            interior_strips(c->fmt, r[0], r[1], c->tune_aligned == 1, &c->i_strip_x0[q], &c->i_strip_w[q],
+            interior_strips(c->fmt, r[0], r[1], c->tune_aligned > 0 ? c->tune_aligned : 0, &c->i_strip_x0[q], &c->i_strip_w[q],
                             &c->i_tiles_x[q]);
             int64_t rows;
             if (c->tune_chunk > 0) {
@@ -774,7 +774,7 @@ lbm_status lbm_set_tuning(lbm_ctx* c, const lbm_tuning* t) {
     if (c->planned) return LBM_E_STATE;
     if ((t->ring_slots != 0 && (t->ring_slots < 4 || t->ring_slots > 8)) ||
         (t->chunk_rows != 0 && (t->chunk_rows < 8 || t->chunk_rows > (1 << 20))) || t->aligned < -1 ||
-        t->aligned > 1 || t->plan < 0 || t->plan > 2)
+        t->aligned > 2 || t->plan < 0 || t->plan > 2)
         return LBM_E_INVALID;
     c->tune_ring = t->ring_slots;
     c->tune_chunk = t->chunk_rows;
@@ -788,7 +788,7 @@ lbm_status lbm_get_tuning(const lbm_ctx* c, lbm_tuning* t) {
     if (c->planned && c->has_interior) {
         t->ring_slots = c->i_ring;
         t->chunk_rows = c->i_chunk[0];
-        t->aligned = c->tune_aligned == 1 ? 1 : 0;
+        t->aligned = c->tune_aligned > 0 ? c->tune_aligned : 0;
         t->plan = 2;
     } else {
         t->ring_slots = c->tune_ring;

@@ -566,17 +566,21 @@ cudaError_t launch_batch_interior(int fmt, const BatchInteriorLaunch& L, int rin
     return cudaErrorInvalidValue;
 }
 
-void interior_strips(int fmt, int rx0, int rx1, bool aligned, int* strip_x0, int* strip_w, int* nstrips) {
+void interior_strips(int fmt, int rx0, int rx1, int aligned, int* strip_x0, int* strip_w, int* nstrips) {
     int W = 124, xg = rx0;  // 128 threads: the strip and its 2-column halo on each side
-    if (aligned) {
-        // the fewest strips of equal width on the grid of 32-byte sectors (8
-        // columns of a 4- or 8-byte plane, 16 of a 2-byte plane; column x sits
-        // at x + kPadCols of a plane row and rows start 256-byte aligned), so
-        // that no two CTAs store into one sector even when they run far apart
-        // in time
+    if (aligned == 1 || aligned == 2) {
+        // the fewest strips of equal width on a grid of 32-byte sectors
+        // (aligned 1: 8 columns of a 4- or 8-byte plane, 16 of a 2-byte
+        // plane), so that no two CTAs store into one sector even when they
+        // run far apart in time, or of 16-byte units (aligned 2: 2, 4 or 8
+        // columns, wider strips of 16-bit storage at the price of a shared
+        // sector at each strip boundary); column x sits at x + kPadCols of a
+        // plane row and rows start 256-byte aligned
         const bool half = fmt == kFmtF16 || fmt == kFmtBF16;
-        const int sec = half ? 16 : 8, wmax = half ? 112 : 120;
-        const int g0 = half ? -8 : 0;  // g0 + kPadCols is a multiple of the sector's columns
+        const int es = fmt == kFmtF64 ? 8 : (half ? 2 : 4);
+        const int sec = aligned == 1 ? (half ? 16 : 8) : 16 / es;
+        const int wmax = 124 / sec * sec;
+        const int g0 = ((-kPadCols) % sec + sec) % sec - sec;  // g0 + kPadCols is a multiple of sec
         auto fdiv = [](int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
         xg = g0 + fdiv(rx0 - g0, sec) * sec;
         const int span = rx1 - xg, n = (span + wmax - 1) / wmax;

@@ -31,11 +31,12 @@ int interior_occupancy(int fmt, int ring_slots);
 constexpr int kInteriorRing = 4;
 constexpr int kBatchRing = 4;
 // The strip grid of the interior kernel over columns [rx0, rx1): origin of
-// strip 0, output columns per strip, number of strips.  aligned: the fewest
-// strips of equal width (at most 120 columns, 112 for 16-bit storage) on
-// 32-byte sector boundaries (for CTAs of one body that may run in different
-// waves), else 124-column strips from rx0 (one wave).
-void interior_strips(int fmt, int rx0, int rx1, bool aligned, int* strip_x0, int* strip_w, int* nstrips);
+// strip 0, output columns per strip, number of strips.  aligned 1: the
+// fewest strips of equal width (at most 120 columns, 112 for 16-bit storage)
+// on 32-byte sector boundaries (for CTAs of one body that may run in
+// different waves); 2: the same on 16-byte boundaries (at most 124 columns,
+// 120 for 16-bit storage); otherwise 124-column strips from rx0 (one wave).
+void interior_strips(int fmt, int rx0, int rx1, int aligned, int* strip_x0, int* strip_w, int* nstrips);
 
 // One interior rectangle of a launch: its nodes [rect[0], rect[1]) x
 // [rect[2], rect[3]), the strip grid over its columns and the rows per tile.

@@ -139,24 +139,25 @@ def test_batch_argument_and_phase_errors():
 
 def test_batch_tuning_changes_the_split_not_the_result():
     """Every decomposition of a batch's interior tiles (ring depth, rows per
-    tile) gives bit-identical members; the batch autotuner returns one of its
-    candidates and leaves the members untouched; bad tunings are refused."""
+    tile, strip grid) gives bit-identical members; the batch autotuner
+    returns one of its candidates and leaves the members untouched; bad
+    tunings are refused."""
     members = _members()[:6]
     ref = []
     for prob, scheme in members:
         with lbm.Body(prob, storage="f32", scheme=scheme) as b:
             b.step(90)
             ref.append(_fields(b))
-    for ring, chunk in ((4, 0), (6, 8), (8, 40), (5, 256)):
+    for ring, chunk, aligned in ((4, 0, -1), (6, 8, 1), (8, 40, 0), (5, 256, 2), (4, 48, 0), (4, 64, 2)):
         bodies = [lbm.Body(prob, storage="f32", scheme=scheme) for prob, scheme in members]
         try:
-            with lbm.Batch(bodies, tuning=lbm.lbm_tuning(ring, chunk, 1)) as batch:
+            with lbm.Batch(bodies, tuning=lbm.lbm_tuning(ring, chunk, aligned)) as batch:
                 batch.step(90)
                 batch.sync()
             for k, b in enumerate(bodies):
                 got = _fields(b)
                 for key in ("u", "v", "r", "P"):
-                    assert np.array_equal(got[key], ref[k][key]), (ring, chunk, k, key)
+                    assert np.array_equal(got[key], ref[k][key]), (ring, chunk, aligned, k, key)
         finally:
             for b in bodies:
                 b.close()
@@ -167,10 +168,11 @@ def test_batch_tuning_changes_the_split_not_the_result():
         before = [b.read(lbm.LBM_FIELD_U)["u"] for b in bodies]
         best, ms = lbm.lbm_batch_autotune([b.ctx for b in bodies], 16)
         assert best.ring_slots in (4, 5, 6) and best.chunk_rows in (0, 32, 64, 128, 256) and 0 < ms < 10
+        assert best.aligned in (0, 1, 2)
         for b, u in zip(bodies, before):
             assert lbm.lbm_get_info(b.ctx)[0] == 3
             assert np.array_equal(b.read(lbm.LBM_FIELD_U)["u"], u)
-        for bad in (lbm.lbm_tuning(3, 0, 1), lbm.lbm_tuning(9, 0, 1), lbm.lbm_tuning(5, 7, 1)):
+        for bad in (lbm.lbm_tuning(3, 0, 1), lbm.lbm_tuning(9, 0, 1), lbm.lbm_tuning(5, 7, 1), lbm.lbm_tuning(4, 0, 3)):
             with pytest.raises(lbm.LbmError) as ei:
                 lbm.Batch(bodies, tuning=bad)
             assert ei.value.status == lbm.LBM_E_INVALID

@@ -243,7 +243,7 @@ def test_call_order_and_argument_errors():
     try:
         L = lbm.lib()
         assert L.lbm_step(ctx, 1) == lbm.LBM_E_STATE
-        for bad in ((0, 0, -1, 3), (0, 0, -1, -1), (3, 0, -1, 0), (0, 4, -1, 0), (0, 0, 2, 0)):
+        for bad in ((0, 0, -1, 3), (0, 0, -1, -1), (3, 0, -1, 0), (0, 4, -1, 0), (0, 0, 3, 0)):
             assert L.lbm_set_tuning(ctx, lbm.C.byref(lbm.lbm_tuning(*bad))) == lbm.LBM_E_INVALID, bad
         assert L.lbm_set_material(ctx, 0.3, -1.0, 1.0, 1.0, None) == lbm.LBM_E_INVALID
         assert L.lbm_set_material(ctx, 0.3, 0.3, 1.0, 2.5, None) == lbm.LBM_E_INVALID
@@ -287,7 +287,7 @@ def test_tuning_changes_the_split_not_the_result():
     prob, _ = CASES["clamped_96x50"]
     big = W.smooth_random(400, 300, W.clamped_free_edges(), seed=23, amp=0.01, vamp=0.004, lam=0.3, mu=0.3)
     wide = W.smooth_random(700, 90, W.all_periodic(), seed=29, amp=0.01, vamp=0.004, lam=0.3, mu=0.3)
-    tunings = ((4, 0, 0), (6, 32, 1), (8, 9, 0), (5, 256, 1), (7, 40, 0))
+    tunings = ((4, 0, 0), (6, 32, 1), (8, 9, 0), (5, 256, 1), (7, 40, 0), (4, 24, 2))
     for storage in ("f32", "f64", "f16"):
         for pr in (prob, big, wide):
             with lbm.Body(pr, storage=storage) as b:
