@@ -202,8 +202,11 @@ typedef struct {
                            storage, 1 otherwise) */
     int32_t plan;       /* 0: by size (default): a body of fewer than 2^17 nodes (3 x 2^17 in FP64)
                            runs as small tiles of the edge kernel only, a larger one as the
-                           interior kernel plus the edge bands; 1: edge tiles only; 2: the
-                           interior kernel wherever the body allows it */
+                           interior kernel plus the edge bands (a 3-node band each side of a
+                           periodic seam included); 1: edge tiles only; 2: the interior kernel
+                           wherever the body allows it, across periodic seams too (a launch
+                           after each step then copies the images of the nodes next to a
+                           seam) */
 } lbm_tuning;
 
 /* Sets the decomposition; only before the first lbm_step / lbm_read_fields /
@@ -305,9 +308,9 @@ LBM_API lbm_status lbm_destroy(lbm_ctx* ctx);
  * member with the interior kernel where the body allows it (plan 2 of
  * lbm_tuning, unless the member asked for plan 1), through the same
  * arithmetic as a single body: results are bit-identical to lbm_step on a
- * member that runs plan 2 (every body of 2^17 nodes or more does by
- * default); a smaller member stepped alone runs edge tiles only, which agree
- * with the interior kernel to rounding.
+ * member that runs plan 2; under the default plan a member stepped alone
+ * runs edge tiles only (fewer than 2^17 nodes) or gives its periodic seams
+ * edge bands, which agree with the interior kernel to rounding.
  */
 typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
 

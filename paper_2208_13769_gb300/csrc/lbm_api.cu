@@ -150,10 +150,23 @@ int64_t lbm::interior_nodes(const lbm_ctx* c) {
     return n;
 }
 
-void lbm::plan_rects(const lbm_ctx* c, bool edge_only, int irect[4][4], int* n_irect, int brect[12][4],
-                     int* nband) {
+void lbm::seam_box(const lbm_ctx* c, int box[4]) {
     const bool perx = c->bc[0].kind == kPeriodic, pery = c->bc[2].kind == kPeriodic;
-    const int bx = perx ? 3 : 2, by = pery ? 3 : 2;
+    box[0] = perx ? 0 : 2;
+    box[1] = perx ? c->nx : c->nx - 2;
+    box[2] = pery ? 0 : 2;
+    box[3] = pery ? c->ny : c->ny - 2;
+}
+
+void lbm::plan_rects(const lbm_ctx* c, bool edge_only, bool seams_inside, int irect[4][4], int* n_irect,
+                     int brect[12][4], int* nband) {
+    const bool perx = c->bc[0].kind == kPeriodic, pery = c->bc[2].kind == kPeriodic;
+    // a bounded edge keeps a 2-node band for the edge kernel's boundary
+    // rules; a periodic seam a 3-node band on each side (the interior
+    // kernel writes no images), unless the interior kernel runs across the
+    // seam, reading the images of the nodes beyond it, which the image
+    // launch refreshes after every step
+    const int bx = perx ? (seams_inside ? 0 : 3) : 2, by = pery ? (seams_inside ? 0 : 3) : 2;
     const int nx = c->nx, ny = c->ny;
     const int32_t* H = c->hole;
     const bool hole = H[0] < H[1];
@@ -205,16 +218,22 @@ void lbm::plan_rects(const lbm_ctx* c, bool edge_only, int irect[4][4], int* n_i
 }
 
 // The interior (nodes >= 2 from bounded edges and from a hole's faces, >= 3
-// from periodic seams) as up to 4 rectangles for the lean kernel; the bands
-// around the body and around the hole as tiles of the edge kernel; the
-// parameter table of both parities and the tile list go to the device.
+// from periodic seams, or across them) as up to 4 rectangles for the lean
+// kernel; the bands around the body and around the hole as tiles of the
+// edge kernel; the seam images; the parameter table of both parities and the
+// tile lists go to the device.
 static cudaError_t build_plan(lbm_ctx* c) {
     // edge tiles only for a body that the interior kernel's per-launch
     // latency floor would slow down (plan 0), or on request (plan 1)
     const int64_t nodes = int64_t(c->nx) * c->ny;
     const int64_t edge_only_below = c->fmt == kFmtF64 ? (int64_t(3) << 17) : (int64_t(1) << 17);
     const bool edge_only = c->tune_plan == 1 || (c->tune_plan == 0 && nodes < edge_only_below);
-    plan_rects(c, edge_only, c->irect, &c->n_irect, c->brect, &c->nband);
+    // periodic seams inside the interior kernel under plan 2 (as in a
+    // batch, whose one image launch serves every member); by size (plan 0)
+    // the seams keep their bands, whose edge launch runs beside the
+    // interior's instead of after it
+    const bool seams_inside = c->tune_plan == 2;
+    plan_rects(c, edge_only, seams_inside, c->irect, &c->n_irect, c->brect, &c->nband);
     const bool hole = c->hole[0] < c->hole[1];
     if (c->n_irect > 0) {
         c->i_ring = c->tune_ring ? c->tune_ring : kInteriorRing;
@@ -257,14 +276,34 @@ static cudaError_t build_plan(lbm_ctx* c) {
     for (int b = 0; b < c->nband; ++b) m += edge_tiles_of_rect(c->brect[b], 0, h + m, n - m, m == 0, kEdgeThreads);
     if (hole)
         for (int q = 0; q < c->n_irect; ++q) m += edge_tiles_of_rect(c->irect[q], 0, h + m, ni - m, false, kEdgeThreads);
+    // the images of the interior's nodes next to a periodic seam
+    const bool perx = c->bc[0].kind == kPeriodic, pery = c->bc[2].kind == kPeriodic;
+    int nimg = 0;
+    ImageTile* himg = nullptr;
+    if (c->has_interior && seams_inside && (perx || pery)) {
+        int box[4];
+        seam_box(c, box);
+        nimg = image_tiles_of_body(c->nx, c->ny, perx, pery, box, 0, nullptr, 0);
+        himg = new (std::nothrow) ImageTile[size_t(nimg)];
+        if (!himg) {
+            delete[] h;
+            return cudaErrorMemoryAllocation;
+        }
+        image_tiles_of_body(c->nx, c->ny, perx, pery, box, 0, himg, nimg);
+    }
     StepParams hp[2] = {make_params(c, 0), make_params(c, 1)};
     cudaError_t e = cudaMalloc(&c->dtiles, sizeof(EdgeTile) * size_t(ni));
     if (e == cudaSuccess) e = cudaMalloc(&c->dparams, sizeof(hp));
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->dtiles, h, sizeof(EdgeTile) * size_t(ni), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->dparams, hp, sizeof(hp), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // h is freed below
+    if (e == cudaSuccess && nimg > 0) e = cudaMalloc(&c->dimg, sizeof(ImageTile) * size_t(nimg));
+    if (e == cudaSuccess && nimg > 0)
+        e = cudaMemcpyAsync(c->dimg, himg, sizeof(ImageTile) * size_t(nimg), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // h and himg are freed below
     delete[] h;
+    delete[] himg;
     if (e != cudaSuccess) return e;
+    c->n_img = nimg;
     c->n_etiles = n;
     c->n_itiles = hole ? ni : 0;
     c->planned = true;
@@ -336,6 +375,11 @@ static cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int pa
         return launch_edge(c->fmt, L, int(ntiles), c->stream, 1, true, false);
     }
     if (!c->has_interior) return launch_band_part(c, parity, fields, c->stream);
+    if (c->n_etiles == 0) {  // a periodic body without bands: the interior, then its images
+        cudaError_t e = launch_interior_part(c, make_params(c, parity), fields);
+        if (e == cudaSuccess) e = launch_images(c->fmt, c->dparams + parity, c->dimg, c->n_img, c->stream);
+        return e;
+    }
     // interior first on the main stream, then the edge tiles on the side
     // stream: the small edge CTAs fill the room the interior CTAs leave
     cudaError_t e = cudaEventRecord(c->ev_fork, c->stream);
@@ -344,6 +388,7 @@ static cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int pa
     if (e == cudaSuccess) e = launch_band_part(c, parity, fields, c->side);
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    if (e == cudaSuccess) e = launch_images(c->fmt, c->dparams + parity, c->dimg, c->n_img, c->stream);
     return e;
 }
 
@@ -426,6 +471,7 @@ static void free_all(lbm_ctx* c) {
     cudaFree(c->readout);
     cudaFree(c->dparams);
     cudaFree(c->dtiles);
+    cudaFree(c->dimg);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->side) cudaStreamDestroy(c->side);
@@ -674,8 +720,9 @@ lbm_status lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double out[4]) {
     st = ctx_ensure_initialized(c);
     if (st != LBM_OK) return st;
     if (!c->planned) LBM_CUDA(c, build_plan(c));
-    // events e[2k] before step k's interior launch, e[2k+1] between its two
-    // launches, e[2k+2] after its band launch
+    // events e[2k] before step k's interior launch, e[2k+1] between it and
+    // the band launch, e[2k+2] after the band launch (and the image launch
+    // of a periodic body, timed with it)
     const int64_t nev = 2 * nsteps + 1;
     cudaEvent_t* ev = new (std::nothrow) cudaEvent_t[size_t(nev)];
     if (!ev) return LBM_E_OOM;
@@ -690,6 +737,7 @@ lbm_status lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double out[4]) {
         err = launch_interior_part(c, p, fields);
         if (err == cudaSuccess) err = cudaEventRecord(ev[2 * k + 1], c->stream);
         if (err == cudaSuccess) err = launch_band_part(c, c->parity, fields, c->stream);
+        if (err == cudaSuccess) err = launch_images(c->fmt, c->dparams + c->parity, c->dimg, c->n_img, c->stream);
         if (err == cudaSuccess) err = cudaEventRecord(ev[2 * k + 2], c->stream);
         if (err == cudaSuccess) {
             c->parity ^= 1;

@@ -48,11 +48,13 @@ struct lbm_batch {
     StepParams* dtab = nullptr;  // [2][n_entries]: entry q * n_entries + e at parity base_parity ^ q
     BatchItem* ditems = nullptr;  // interior tiles, longest first
     EdgeTile* dtiles = nullptr;   // edge tiles of every member
+    ImageTile* dimg = nullptr;    // seam images of the members with a periodic axis
     int32_t** dflagptr = nullptr;  // device: each member's status flag
     int32_t* dflagval = nullptr;   // device: the flags gathered by lbm_batch_sync
     std::vector<int32_t> hflag;    // host copy of dflagval
     int n_work = 0;               // interior tiles
     int n_edge = 0;               // edge tiles
+    int n_img = 0;                // image tiles
     int chunk_rows = 0;
     int ring = kBatchRing;
     int aligned = 1;  // strip grid of the interior tiles (interior_strips)
@@ -84,6 +86,7 @@ void batch_free(lbm_batch* b) {
     cudaFree(b->dtab);
     cudaFree(b->ditems);
     cudaFree(b->dtiles);
+    cudaFree(b->dimg);
     cudaFree(b->dflagptr);
     cudaFree(b->dflagval);
     if (b->ev_sync) cudaEventDestroy(b->ev_sync);
@@ -116,6 +119,7 @@ cudaError_t batch_launch(lbm_batch* b, int q, bool fields) {
     if (e == cudaSuccess) e = launch_edge(b->fmt, E, b->n_edge, b->side, 0, b->holed, false);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+    if (e == cudaSuccess) e = launch_images(b->fmt, tab, b->dimg, b->n_img, b->stream);
     return e;
 }
 
@@ -261,7 +265,7 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
     for (int i = 0; i < n; ++i) {
         const lbm_ctx* c = b->m[size_t(i)];
         Rects& r = mr[size_t(i)];
-        plan_rects(c, c->tune_plan == 1, r.irect, &r.n_irect, r.brect, &r.nband);
+        plan_rects(c, c->tune_plan == 1, true, r.irect, &r.n_irect, r.brect, &r.nband);
         for (int k = 0; k < r.n_irect; ++k)
             all_interior += int64_t(r.irect[k][1] - r.irect[k][0]) * (r.irect[k][3] - r.irect[k][2]);
         b->holed = b->holed || c->hole[0] < c->hole[1];
@@ -283,6 +287,7 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
     std::vector<StepParams> tab;
     std::vector<InteriorWork> work;
     std::vector<EdgeTile> tiles;
+    std::vector<ImageTile> imgs;
     std::vector<BatchItem> items;
     try {
         // parameter table: one entry per interior rectangle of each member
@@ -342,6 +347,17 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
                 edge_tiles_of_rect(mri.brect[r], e, tiles.data() + at, cnt, first, kEdgeThreads);
                 first = first && cnt == 0;
             }
+            // the images of its interior's nodes next to a periodic seam
+            const lbm_ctx* c = b->m[size_t(i)];
+            const bool perx = c->bc[0].kind == kPeriodic, pery = c->bc[2].kind == kPeriodic;
+            if (mri.n_irect > 0 && (perx || pery)) {
+                int box[4];
+                seam_box(c, box);
+                const int cnt = image_tiles_of_body(c->nx, c->ny, perx, pery, box, e, nullptr, 0);
+                const size_t at = imgs.size();
+                imgs.resize(at + size_t(cnt));
+                image_tiles_of_body(c->nx, c->ny, perx, pery, box, e, imgs.data() + at, cnt);
+            }
         }
         // longest tiles first: the short tiles of small bodies fill the tail
         // of the last wave
@@ -358,9 +374,11 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
         delete b;
         return LBM_E_OOM;
     }
-    if (items.size() > 0x7fffffff || tiles.size() > 0x7fffffff) e = cudaErrorInvalidValue;
+    if (items.size() > 0x7fffffff || tiles.size() > 0x7fffffff || imgs.size() > 0x7fffffff)
+        e = cudaErrorInvalidValue;
     b->n_work = int(work.size());
     b->n_edge = int(tiles.size());
+    b->n_img = int(imgs.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->dtab, sizeof(StepParams) * tab.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->dflagptr, sizeof(int32_t*) * size_t(n));
     if (e == cudaSuccess) e = cudaMalloc(&b->dflagval, sizeof(int32_t) * size_t(n));
@@ -382,6 +400,10 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
                             b->stream);
     if (e == cudaSuccess && !tiles.empty())
         e = cudaMemcpyAsync(b->dtiles, tiles.data(), sizeof(EdgeTile) * tiles.size(), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess && !imgs.empty()) e = cudaMalloc(&b->dimg, sizeof(ImageTile) * imgs.size());
+    if (e == cudaSuccess && !imgs.empty())
+        e = cudaMemcpyAsync(b->dimg, imgs.data(), sizeof(ImageTile) * imgs.size(), cudaMemcpyHostToDevice,
                             b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host tables die with this scope
     if (e != cudaSuccess) {

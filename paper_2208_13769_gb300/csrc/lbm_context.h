@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "lbm.h"
+#include "lbm_images.h"
 #include "lbm_kernels.h"
 
 namespace lbm {
@@ -107,6 +108,10 @@ struct lbm_ctx {
     // the interior rectangles (then after the band tiles in dtiles), so that
     // every face of the hole sees a tile as thick as its band
     int n_itiles = 0;
+    // images of the nodes next to a periodic seam that the interior kernel
+    // advances, copied after each step (lbm_images.h)
+    lbm::ImageTile* dimg = nullptr;
+    int n_img = 0;
 };
 
 namespace lbm {
@@ -129,7 +134,14 @@ int64_t interior_nodes(const lbm_ctx* c);
 // The rectangles of a step: the interior kernel's (n_irect, up to 4: a hole
 // splits the interior; none for a body too small for it) and the edge
 // tiles' (nband, up to 12).  edge_only: everything as edge tiles.
-void plan_rects(const lbm_ctx* c, bool edge_only, int irect[4][4], int* n_irect, int brect[12][4], int* nband);
+// seams_inside: the interior kernel also runs across periodic seams (their
+// images then come from an image launch after each step), else a 3-node
+// band on each side of a seam goes to the edge kernel.
+void plan_rects(const lbm_ctx* c, bool edge_only, bool seams_inside, int irect[4][4], int* n_irect,
+                int brect[12][4], int* nband);
+// The box of image sources of a body whose interior kernel runs across its
+// periodic seams: the whole axis where periodic, nodes 2 .. n - 3 where bounded.
+void seam_box(const lbm_ctx* c, int box[4]);
 // Plans the launches and runs the initialisation of Algorithm 1 once.
 lbm_status ctx_ensure_initialized(lbm_ctx* c);
 // Synchronises the context's stream and maps its device flag to a status.

@@ -467,3 +467,35 @@ def test_clamped_body_stability_horizon():
         with lbm.Body(literal, storage="f32", scheme=scheme) as b:
             b.step(horizon)
             assert b.read(lbm.LBM_FIELD_U, allow_unstable=True)["status"] == lbm.LBM_E_UNSTABLE, scheme
+
+
+@pytest.mark.auto_plan
+@pytest.mark.parametrize("layout", ["x_periodic", "y_periodic", "both_periodic"])
+def test_periodic_seams_as_bands_or_inside_the_interior_match_the_oracle(layout):
+    """A periodic body large enough for the interior kernel in FP64 too
+    (660 x 620):
+    under the default plan its seams keep 3-node bands of the edge kernel;
+    under plan 2 the interior kernel runs across them and a launch after
+    each step copies the nodes next to a seam into their images.  Both
+    against the oracle in FP64 and FP32; plan 2 bit-identical to the same
+    body in a batch."""
+    edges = {"x_periodic": [Pp, Pp, D0, N0], "y_periodic": [D0, N0, Pp, Pp], "both_periodic": W.all_periodic()}
+    prob = W.smooth_random(660, 620, edges[layout], seed=31, amp=0.01, vamp=0.004, lam=0.3, mu=0.3)
+    s = oracle.solver_from(prob, oracle.PREDICTOR)
+    s.step(60)
+    ref = s.read()
+    for storage, tol in (("f64", TOL["f64"]), ("f32", TOL["f32"])):
+        for plan in (0, 2):
+            with lbm.Body(prob, storage=storage, tuning=lbm.lbm_tuning(0, 0, -1, plan)) as b:
+                b.step(60)
+                got = b.read()
+                assert lbm.lbm_get_tuning(b.ctx).plan == 2  # the interior kernel runs
+            compare(ref, got, tol)
+    with lbm.Body(prob, storage="f32", tuning=lbm.lbm_tuning(0, 0, -1, 2)) as alone:
+        alone.step(60)
+        a = alone.read(lbm.LBM_FIELD_U | lbm.LBM_FIELD_V)
+    with lbm.Body(prob, storage="f32") as member:
+        with lbm.Batch([member]) as batch:
+            batch.step(60)
+        m = member.read(lbm.LBM_FIELD_U | lbm.LBM_FIELD_V)
+    assert np.array_equal(a["u"], m["u"]) and np.array_equal(a["v"], m["v"])
