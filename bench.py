@@ -62,13 +62,13 @@ def parse():
     ap.add_argument("--form-steps", type=int, default=500)
     ap.add_argument("--schemes", default="predictor,extrapolated",
                     help="other schemes timed on the same body, FP32 + compensated carry ('' to skip)")
-    ap.add_argument("--c3-steps", type=int, default=1000,
+    ap.add_argument("--c3-steps", type=int, default=5000,
                     help="steps of the 8192 x 8192 16-bit storage run (0 to skip)")
     ap.add_argument("--hole-steps", type=int, default=500,
                     help="steps of the 4096 x 4096 plate with a hole (0 to skip)")
     ap.add_argument("--batch", type=int, default=256,
                     help="bodies of the batched workload (seeded, sides 64..1024; 0 to skip)")
-    ap.add_argument("--batch-steps", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=2000)
     ap.add_argument("--solves", type=int, default=20,
                     help="repeated solves of the C1 and C2 workloads for p50 / p99 latency (0 to skip)")
     ap.add_argument("--serve", type=int, default=120,
@@ -682,9 +682,9 @@ def run_native(a):
     # solve latency: a solve creates the body from host arrays, initialises
     # it, runs its steps and reads u back to the host (host clock around
     # all of it); p50 / p99 over repeated solves of the 64 x 64 FP64 shear
-    # wave (1000 steps), the benchmark's clamped body in its format (2000 steps:
-    # the planned 5000 lie beyond its stable horizon) and the 256-body batch
-    # (256 steps; its members complete together)
+    # wave (1000 steps), the benchmark's clamped body in its format (5000
+    # steps) and the 256-body batch (2000 steps; its members complete
+    # together)
     solves = None
     if a.solves > 0 and world == 1:
         from paper_2208_13769_gb300 import workloads as W
@@ -719,17 +719,16 @@ def run_native(a):
                  1000, a.solves, 64 * 64),
                 ("c2_%dx%d_%s" % (a.nx, a.ny, a.storage),
                  lambda: [lbm.Body(c2, storage=a.storage, compensated=a.compensated, scheme=scheme_id(a.scheme),
-                                   stream=stream.cuda_stream, device=local, tuning=tuning)], 2000, a.solves,
+                                   stream=stream.cuda_stream, device=local, tuning=tuning)], 5000, a.solves,
                  a.nx * a.ny),
                 ("c4_256_bodies_f32", lambda: [lbm.Body(p, storage="f32", stream=stream.cuda_stream, device=local)
-                                               for p in c4.problems], 256, max(1, a.solves // 4),
+                                               for p in c4.problems], 2000, max(1, a.solves // 4),
                  sum(p.nx * p.ny for p in c4.problems))):
             one_solve(make, 8)  # warm: kernels loaded, graphs of this shape built once
             solves[name] = stats([one_solve(make, steps) for _ in range(n_solves)], nodes_per, steps)
 
     e2e = None
     if not a.no_e2e:
-        import dataclasses
 
         # inputs in pinned host memory before the clock starts; the upload,
         # the whole solve and the read-back of u into pinned memory inside it

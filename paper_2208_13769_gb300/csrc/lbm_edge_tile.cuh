@@ -47,7 +47,7 @@ struct Pops {
 // corner) carrying the traction (T0, T1) inv_len; Pbar* of Sec. 6 in the
 // wall's frame from the quasi-traction g = -T* + Q N and the tangential
 // entry of the populations' second moment.
-template <class TC>
+template <class TS, class TC>
 __device__ __forceinline__ TC abb_value(int i, TC fci, int sx, int sy, TC inv_len, TC T0, TC T1, TC r, TC pxx,
                                         TC pxy, TC pyy, TC q11, TC q12, TC q21, TC q22, TC inv_c2) {
     const TC N0 = TC(sx) * inv_len, N1 = TC(sy) * inv_len;
@@ -60,7 +60,7 @@ __device__ __forceinline__ TC abb_value(int i, TC fci, int sx, int sy, TC inv_le
     const TC sxx = pnn * N0 * N0 + TC(2) * pnt * N0 * t0 + ptt * t0 * t0;
     const TC syy = pnn * N1 * N1 + TC(2) * pnt * N1 * t1 + ptt * t1 * t1;
     const TC sxy = pnn * N0 * N1 + pnt * (N0 * t1 + t0 * N1) + ptt * t0 * t1;
-    return -fci + TC(2) * wgt<TC>(i) * eq_even<TC>(i, r, sxx, sxy, syy);
+    return -fci + wmul<TS>(TC(2) * wgt<TC>(i), eq_even<TC>(i, r, sxx, sxy, syy));
 }
 
 // Links of node (gx, gy) that leave the body through a bounded edge: the
@@ -94,7 +94,7 @@ __device__ __noinline__ void boundary_links(TS* fdst, Geo g, const StepParams& p
             }
             const TC inv_len = (sx != 0 && sy != 0) ? TC(0.70710678118654752440) : TC(1);
             const TC val =
-                abb_value<TC>(i, fc.v[i], sx, sy, inv_len, T0, T1, r, pxx, pxy, pyy, q11, q12, q21, q22, inv_c2);
+                abb_value<TS, TC>(i, fc.v[i], sx, sy, inv_len, T0, T1, r, pxx, pxy, pyy, q11, q12, q21, q22, inv_c2);
             const int oi = opp(i);
             store_img(fdst + oi * g.plane, g, dx, dy, Codec<TS, TC>::st(val, oi, p));
             continue;
@@ -119,7 +119,7 @@ __device__ __noinline__ void boundary_links(TS* fdst, Geo g, const StepParams& p
                 a0c = e->jh[0];
                 a1c = e->jh[1];
             }
-            val = fc.v[i] - TC(2) * wgt<TC>(i) * eq_odd<TC>(i, a0c, a1c);
+            val = fc.v[i] - wmul<TS>(TC(2) * wgt<TC>(i), eq_odd<TC>(i, a0c, a1c));
         } else {
             // Eq. (abbcon) with Pbar* of Sec. 6 in the wall-normal frame; a
             // corner link: N = (N1 + N2)/sqrt(2), T* = (T1 + T2)/sqrt(2)
@@ -134,7 +134,7 @@ __device__ __noinline__ void boundary_links(TS* fdst, Geo g, const StepParams& p
                 T0 += eb->T[0];
                 T1 += eb->T[1];
             }
-            val = abb_value<TC>(i, fc.v[i], sx, sy, inv_len, T0, T1, r, pxx, pxy, pyy, q11, q12, q21, q22, inv_c2);
+            val = abb_value<TS, TC>(i, fc.v[i], sx, sy, inv_len, T0, T1, r, pxx, pxy, pyy, q11, q12, q21, q22, inv_c2);
         }
         store_img(fdst + oi * g.plane, g, dx, dy, Codec<TS, TC>::st(val, oi, p));
     }
@@ -371,12 +371,12 @@ __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepP
         }
         const TC b0 = TC(3) * (k.omega * j0 + k.force_pref * sn0);
         const TC b1 = TC(3) * (k.omega * j1 + k.force_pref * sn1);
-        const TC ax = w1 * (k.omega * Ex), ay = w1 * (k.omega * Ey);
-        const TC ap = w5 * (k.omega * Ep), am = w5 * (k.omega * Em);
-        const TC bx = w1 * b0, by = w1 * b1;
-        const TC bp = w5 * (b0 + b1), bm = w5 * (b1 - b0);
+        const TC ax = wmul<TS>(w1, k.omega * Ex), ay = wmul<TS>(w1, k.omega * Ey);
+        const TC ap = wmul<TS>(w5, k.omega * Ep), am = wmul<TS>(w5, k.omega * Em);
+        const TC bx = wmul<TS>(w1, b0), by = wmul<TS>(w1, b1);
+        const TC bp = wmul<TS>(w5, b0 + b1), bm = wmul<TS>(w5, b1 - b0);
         TC fc[9];
-        fc[0] = k.one_m_omega * f[0] + w0 * (k.omega * E0);
+        fc[0] = k.one_m_omega * f[0] + wmul<TS>(w0, k.omega * E0);
         fc[1] = k.one_m_omega * f[1] + (ax + bx);
         fc[3] = k.one_m_omega * f[3] + (ax - bx);
         fc[2] = k.one_m_omega * f[2] + (ay + by);

@@ -354,12 +354,12 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeo
             const TC w0 = wgt<TC>(0), w1 = wgt<TC>(1), w5 = wgt<TC>(5);
             const TC b0 = TC(3) * (k.omega * j0 + k.force_pref * sn0);
             const TC b1 = TC(3) * (k.omega * j1 + k.force_pref * sn1);
-            const TC ax = w1 * (k.omega * Ex), ay = w1 * (k.omega * Ey);
-            const TC ap = w5 * (k.omega * Ep), am = w5 * (k.omega * Em);
-            const TC bx = w1 * b0, by = w1 * b1;
-            const TC bp = w5 * (b0 + b1), bm = w5 * (b1 - b0);
+            const TC ax = wmul<TS>(w1, k.omega * Ex), ay = wmul<TS>(w1, k.omega * Ey);
+            const TC ap = wmul<TS>(w5, k.omega * Ep), am = wmul<TS>(w5, k.omega * Em);
+            const TC bx = wmul<TS>(w1, b0), by = wmul<TS>(w1, b1);
+            const TC bp = wmul<TS>(w5, b0 + b1), bm = wmul<TS>(w5, b1 - b0);
             TC fc[9];
-            fc[0] = k.one_m_omega * f[0] + w0 * (k.omega * E0);
+            fc[0] = k.one_m_omega * f[0] + wmul<TS>(w0, k.omega * E0);
             fc[1] = k.one_m_omega * f[1] + (ax + bx);
             fc[3] = k.one_m_omega * f[3] + (ax - bx);
             fc[2] = k.one_m_omega * f[2] + (ay + by);
@@ -609,7 +609,7 @@ int interior_occupancy_t(int ring_slots) {
 int interior_occupancy(int fmt, int ring_slots) {
     switch (fmt) {
         case kFmtF64: return interior_occupancy_t<double, double, UPlain<double>, 128, 2, false>(ring_slots);
-        case kFmtF32: return interior_occupancy_t<float, float, UPlain<float>, 128, 6, true>(ring_slots);
+        case kFmtF32: return interior_occupancy_t<float, float, UPlain<float>, 128, 7, true>(ring_slots);
         case kFmtF32C: return interior_occupancy_t<float, float, UComp, 128, 4, false>(ring_slots);
         case kFmtF16: return interior_occupancy_t<__half, float, UComp, 128, 4, true>(ring_slots);
         default: return interior_occupancy_t<__nv_bfloat16, float, UComp, 128, 4, true>(ring_slots);
@@ -631,7 +631,7 @@ cudaError_t launch_interior(int fmt, const StepParams& p0, const InteriorRects& 
     if (!fields) p.fields = nullptr;
     switch (fmt) {
         case kFmtF64: return launch_interior_t<double, double, UPlain<double>, 128, 2, false>(p, R, s);
-        case kFmtF32: return launch_interior_t<float, float, UPlain<float>, 128, 6, true>(p, R, s);
+        case kFmtF32: return launch_interior_t<float, float, UPlain<float>, 128, 7, true>(p, R, s);
         case kFmtF32C: return launch_interior_t<float, float, UComp, 128, 4, false>(p, R, s);
         case kFmtF16: return launch_interior_t<__half, float, UComp, 128, 4, true>(p, R, s);
         case kFmtBF16: return launch_interior_t<__nv_bfloat16, float, UComp, 128, 4, true>(p, R, s);
