@@ -71,10 +71,14 @@ typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3 } lbm_storage
 typedef enum { LBM_UCARRY_NATIVE = 0, LBM_UCARRY_COMPENSATED = 1 } lbm_ucarry;
 
 /* Time level of the source 1S in the moment computation (Sec. 5):
- * EXPLICIT  -- Algorithm 1: the time-t source enters collision and moment.
+ * EXPLICIT  -- Algorithm 1: the time-t source enters collision and moment
+ *              (0: the value of a zeroed lbm_desc, and the Python binding's
+ *              default).
  * PREDICTOR -- the predictor-corrector the paper's footnote to Sec. 5 offers:
  *              1S(t+dt) evaluated from the explicitly predicted u*(t+dt)
- *              corrects j and u and is the next collision's source.  Default.
+ *              corrects j and u and is the next collision's source (stable
+ *              over more materials: Poisson ratio up to 0.40 in periodic and
+ *              Dirichlet bodies, where EXPLICIT needs lambda <= mu).
  * EXTRAPOLATED -- the variant Sec. 5 gives for an O(dt^3) error: 1S(t+dt)
  *              evaluated from the trapezoidal u(t+dt) of j extrapolated
  *              linearly from j(t - dt) and j(t) (j(-dt) = j(0)); as above it

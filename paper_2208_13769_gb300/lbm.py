@@ -345,7 +345,7 @@ def tuning_from_dict(d: dict) -> lbm_tuning:
 
 
 def autotune_cached(prob, storage: str = "f32", compensated: Optional[bool] = None,
-                    scheme: int = LBM_SCHEME_PREDICTOR, cache_path: Optional[str] = None, steps: int = 129,
+                    scheme: int = LBM_SCHEME_EXPLICIT, cache_path: Optional[str] = None, steps: int = 129,
                     stream: int = 0, device: int = 0) -> lbm_tuning:
     """The autotuner's choice for bodies of prob's size and edge kinds, from a
     JSON cache (keyed by storage, carry, scheme, size and edge kinds) when it
@@ -393,12 +393,14 @@ class Body:
 
     storage: "f64" | "f32" | "f16" | "bf16"; compensated: FP32-pair u-carry
     for "f32" (default True: a plain FP32 u loses Grad u to rounding once
-    |u| >> |H| dX); scheme: LBM_SCHEME_PREDICTOR (default), LBM_SCHEME_EXPLICIT
-    or LBM_SCHEME_EXTRAPOLATED (stable only for lambda = mu);
+    |u| >> |H| dX); scheme: LBM_SCHEME_EXPLICIT (default: Algorithm 1, the
+    time-t source in collision and moment), LBM_SCHEME_PREDICTOR (the
+    footnote's predictor-corrector, which Sec. 7's tension run needs) or
+    LBM_SCHEME_EXTRAPOLATED (stable only for lambda = mu);
     stream: an integer cudaStream_t handle (e.g. torch's stream.cuda_stream)."""
 
     def __init__(self, prob, storage: str = "f64", compensated: Optional[bool] = None,
-                 scheme: int = LBM_SCHEME_PREDICTOR, stream: int = 0, device: int = 0,
+                 scheme: int = LBM_SCHEME_EXPLICIT, stream: int = 0, device: int = 0,
                  f16_scale_log2: int = 0, tuning: Optional["lbm_tuning"] = None):
         self.prob = prob
         d = lbm_desc()

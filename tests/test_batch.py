@@ -98,7 +98,8 @@ def test_batch_member_matches_the_oracle():
     s.step(200)
     ref = s.read()
     s.close()
-    with lbm.Body(prob, storage="f64") as b, lbm.Body(other, storage="f64") as b2:
+    pr = lbm.LBM_SCHEME_PREDICTOR
+    with lbm.Body(prob, storage="f64", scheme=pr) as b, lbm.Body(other, storage="f64", scheme=pr) as b2:
         with lbm.Batch([b2, b]) as batch:
             batch.step(200)
         compare(ref, b.read(), 1e-12, keys=("u", "v", "P", "Pbar", "J", "sigma"))

@@ -82,6 +82,6 @@ def test_server_answers_every_request_when_one_cannot_be_created():
     assert recs[1].status == lbm.LBM_E_OOM
     for k in (0, 2, 3):
         assert recs[k].status == lbm.LBM_OK
-        with lbm.Body(reqs[k].problem, storage="f32") as alone:
+        with lbm.Body(reqs[k].problem, storage="f32", scheme=lbm.LBM_SCHEME_PREDICTOR) as alone:
             alone.step(reqs[k].steps)
             assert np.array_equal(srv.results[k], alone.read(lbm.LBM_FIELD_U)["u"])

@@ -210,10 +210,10 @@ def test_chunked_stepping_is_bitwise_identical():
 
 def test_diagnostics_match_oracle_sums():
     prob = CASES["clamped_96x50"][0]
-    s = oracle.solver_from(prob)
+    s = oracle.solver_from(prob, oracle.EXPLICIT)
     s.step(100)
     ref = s.read()
-    with lbm.Body(prob, storage="f64") as b:
+    with lbm.Body(prob, storage="f64", scheme=lbm.LBM_SCHEME_EXPLICIT) as b:
         b.step(100)
         d = b.diagnostics()
     j = prob.rho0 * ref["v"]
@@ -444,7 +444,8 @@ def test_edge_tiles_only_on_a_larger_body_match_the_oracle():
     s.step(100)
     ref = s.read()
     for storage, tol in (("f64", TOL["f64"]), ("f32", TOL["f32"])):
-        with lbm.Body(prob, storage=storage, tuning=lbm.lbm_tuning(0, 0, -1, 1)) as b:
+        with lbm.Body(prob, storage=storage, scheme=lbm.LBM_SCHEME_PREDICTOR,
+                      tuning=lbm.lbm_tuning(0, 0, -1, 1)) as b:
             b.step(100)
             got = b.read()
             assert lbm.lbm_get_tuning(b.ctx).plan == 1
@@ -485,12 +486,13 @@ def test_periodic_seams_as_bands_or_inside_the_interior_match_the_oracle(layout)
     body in a batch."""
     edges = {"x_periodic": [Pp, Pp, D0, N0], "y_periodic": [D0, N0, Pp, Pp], "both_periodic": W.all_periodic()}
     prob = W.smooth_random(660, 620, edges[layout], seed=31, amp=0.01, vamp=0.004, lam=0.3, mu=0.3)
-    s = oracle.solver_from(prob, oracle.PREDICTOR)
+    s = oracle.solver_from(prob, oracle.EXPLICIT)
     s.step(60)
     ref = s.read()
     for storage, tol in (("f64", TOL["f64"]), ("f32", TOL["f32"])):
         for plan in (0, 2):
-            with lbm.Body(prob, storage=storage, tuning=lbm.lbm_tuning(0, 0, -1, plan)) as b:
+            with lbm.Body(prob, storage=storage, scheme=lbm.LBM_SCHEME_EXPLICIT,
+                          tuning=lbm.lbm_tuning(0, 0, -1, plan)) as b:
                 b.step(60)
                 got = b.read()
                 assert lbm.lbm_get_tuning(b.ctx).plan == 2  # the interior kernel runs

@@ -38,7 +38,7 @@ def reference():
     """The clamped body (omega 1.9) at 512 x 256 after 500 steps, from the
     FP64 oracle."""
     prob = W.clamped_body(512, 256, nu=0.25, vmax=0.01)
-    s = oracle.solver_from(prob, oracle.PREDICTOR)
+    s = oracle.solver_from(prob, oracle.EXPLICIT)
     s.step(500)
     ref = s.read()
     s.close()

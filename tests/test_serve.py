@@ -31,7 +31,7 @@ def test_served_results_equal_solving_alone(storage):
     assert st["peak_hbm_bytes"] <= budget
     assert st["max_active"] < len(reqs)  # the budget made requests queue
     for i, q in enumerate(reqs):
-        with lbm.Body(q.problem, storage=storage) as b:
+        with lbm.Body(q.problem, storage=storage, scheme=be.scheme) as b:
             b.step(q.steps)
             u = b.read(lbm.LBM_FIELD_U, allow_unstable=True)["u"]
         # bit for bit (a request that went unstable has NaNs in the same places)
