@@ -151,10 +151,14 @@ LBM_API lbm_status lbm_set_boundary(lbm_ctx* ctx, int32_t edge, int32_t kind, co
  * LBM_E_STATE. */
 LBM_API lbm_status lbm_set_hole(lbm_ctx* ctx, const int32_t hole[4], const double traction[8]);
 
-/* Advances nsteps (>= 0) time steps: one fused stream-collide-constitutive
- * kernel launch per step on the context's stream (replayed as CUDA graphs for
- * long runs).  The observable fields (u, v, r) are captured at the last step.
- * Asynchronous.  Errors: LBM_E_STATE (material or boundaries unset),
+/* Advances nsteps (>= 0) time steps (Algorithm 1, one iteration each) on
+ * the context's stream, replayed as CUDA graphs of 64 steps for long runs.
+ * A step is the fused stream-collide-constitutive update in one launch of
+ * the interior kernel and one of the edge tiles on a side stream (or the
+ * edge tiles alone for a small body), plus, where the interior kernel runs
+ * across a periodic seam (lbm_tuning.plan 2), a launch copying the nodes
+ * next to the seam into their periodic images.  The observable fields (u,
+ * v, r) are captured at the last step.  Asynchronous.  Errors: LBM_E_STATE (material or boundaries unset),
  * LBM_E_INVALID (nsteps < 0), LBM_E_CUDA. */
 LBM_API lbm_status lbm_step(lbm_ctx* ctx, int64_t nsteps);
 

@@ -349,6 +349,18 @@ static cudaError_t launch_band_part(lbm_ctx* c, int parity, bool fields, cudaStr
     return launch_edge(c->fmt, L, c->n_etiles, st, 0, c->hole[0] < c->hole[1], c->scheme == LBM_SCHEME_EXTRAPOLATED);
 }
 
+// The edge-band tiles and the seam images of one step in one launch on the
+// context's stream.
+static cudaError_t launch_band_images_part(lbm_ctx* c, int parity, bool fields) {
+    EdgeLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.params = c->dparams + parity;
+    L.tiles = c->dtiles;
+    L.fields = fields ? 1 : 0;
+    return launch_edge_images(c->fmt, L, c->n_etiles, c->dimg, c->n_img, c->stream, c->hole[0] < c->hole[1],
+                              c->scheme == LBM_SCHEME_EXTRAPOLATED);
+}
+
 // Launches of one time step (mode 0) or the initialisation (mode 1).
 static cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int parity) {
     if (mode == 1 && c->n_itiles > 0) {  // a holed body: the plan's tiles
@@ -375,9 +387,11 @@ static cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int pa
         return launch_edge(c->fmt, L, int(ntiles), c->stream, 1, true, false);
     }
     if (!c->has_interior) return launch_band_part(c, parity, fields, c->stream);
-    if (c->n_etiles == 0) {  // a periodic body without bands: the interior, then its images
+    if (c->n_img > 0) {
+        // the interior across a periodic seam: then the band tiles and the
+        // seam images in one launch after it (the images copy what it wrote)
         cudaError_t e = launch_interior_part(c, make_params(c, parity), fields);
-        if (e == cudaSuccess) e = launch_images(c->fmt, c->dparams + parity, c->dimg, c->n_img, c->stream);
+        if (e == cudaSuccess) e = launch_band_images_part(c, parity, fields);
         return e;
     }
     // interior first on the main stream, then the edge tiles on the side
@@ -388,7 +402,6 @@ static cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int pa
     if (e == cudaSuccess) e = launch_band_part(c, parity, fields, c->side);
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
-    if (e == cudaSuccess) e = launch_images(c->fmt, c->dparams + parity, c->dimg, c->n_img, c->stream);
     return e;
 }
 
@@ -736,8 +749,9 @@ lbm_status lbm_profile_steps(lbm_ctx* c, int64_t nsteps, double out[4]) {
         const StepParams p = make_params(c, c->parity);
         err = launch_interior_part(c, p, fields);
         if (err == cudaSuccess) err = cudaEventRecord(ev[2 * k + 1], c->stream);
-        if (err == cudaSuccess) err = launch_band_part(c, c->parity, fields, c->stream);
-        if (err == cudaSuccess) err = launch_images(c->fmt, c->dparams + c->parity, c->dimg, c->n_img, c->stream);
+        if (err == cudaSuccess)
+            err = c->n_img > 0 ? launch_band_images_part(c, c->parity, fields)
+                               : launch_band_part(c, c->parity, fields, c->stream);
         if (err == cudaSuccess) err = cudaEventRecord(ev[2 * k + 2], c->stream);
         if (err == cudaSuccess) {
             c->parity ^= 1;

@@ -113,13 +113,21 @@ cudaError_t batch_launch(lbm_batch* b, int q, bool fields) {
     E.params = tab;
     E.tiles = b->dtiles;
     E.fields = fields ? 1 : 0;
+    if (b->n_img > 0) {
+        // members across periodic seams: the interior, then every member's
+        // edge tiles and seam images in one launch after it (the images copy
+        // what the interior launch wrote; the two launches barely overlapped
+        // anyway, six interior CTAs filling an SM's registers)
+        cudaError_t e = launch_batch_interior(b->fmt, I, b->ring, b->stream, nullptr);
+        if (e == cudaSuccess) e = launch_edge_images(b->fmt, E, b->n_edge, b->dimg, b->n_img, b->stream, b->holed, false);
+        return e;
+    }
     cudaError_t e = cudaEventRecord(b->ev_fork, b->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
     if (e == cudaSuccess) e = launch_batch_interior(b->fmt, I, b->ring, b->stream, nullptr);
     if (e == cudaSuccess) e = launch_edge(b->fmt, E, b->n_edge, b->side, 0, b->holed, false);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
-    if (e == cudaSuccess) e = launch_images(b->fmt, tab, b->dimg, b->n_img, b->stream);
     return e;
 }
 

@@ -17,6 +17,7 @@
 #include "lbm_device.cuh"
 #include "lbm_kernels.h"
 #include "lbm_edge_tile.cuh"
+#include "lbm_images.cuh"
 #include "lbm_pipeline.cuh"
 
 namespace lbm {
@@ -24,8 +25,16 @@ namespace lbm {
 static_assert(sizeof(StepParams) % 16 == 0, "StepParams is copied to shared memory in 16-byte words");
 
 template <class TS, class TC, class UT, int MODE, bool HOLE, bool XJ>
-__global__ void __launch_bounds__(kEdgeThreads, 3) edge_tile_kernel(const __grid_constant__ EdgeLaunch L) {
+__global__ void __launch_bounds__(kEdgeThreads, 3)
+    edge_tile_kernel(const __grid_constant__ EdgeLaunch L, const __grid_constant__ ImageLaunch I) {
     constexpr int N = kEdgeThreads;
+    static_assert(kImageThreads <= N, "an image tile fits an edge CTA");
+    if (I.tiles != nullptr && int(blockIdx.x) >= I.n_edge) {  // a seam-image CTA (uniform per CTA)
+        if (int(threadIdx.x) < kImageThreads)
+            image_copy<int(sizeof(TS)), int(sizeof(TC)), UT::planes>(L.params, I.tiles[blockIdx.x - I.n_edge],
+                                                                    int(threadIdx.x));
+        return;
+    }
     __shared__ __align__(16) StepParams sp;
     __shared__ EdgeNow<TC, UT> s_edge[5];
     __shared__ UT su[2 * N];                      // u*: [th][2 comps][tw]
@@ -60,31 +69,48 @@ __global__ void __launch_bounds__(kEdgeThreads, 3) edge_tile_kernel(const __grid
 
 // ---------------------------------------------------------------- launchers
 
+// ntiles edge tiles, then n_img image tiles (I.tiles, mode 0 only)
 template <class TS, class TC, class UT>
-cudaError_t launch_edge_t(const EdgeLaunch& L, int ntiles, cudaStream_t s, int mode, bool holed, bool xj) {
-    if (ntiles <= 0) return cudaSuccess;
+cudaError_t launch_edge_t(const EdgeLaunch& L, int ntiles, const ImageTile* img, int n_img, cudaStream_t s, int mode,
+                          bool holed, bool xj) {
+    if (mode != 0 || !img) n_img = 0;
+    const ImageLaunch I = {n_img > 0 ? img : nullptr, ntiles, 0};
+    const int64_t total = int64_t(ntiles) + n_img;
+    if (total <= 0) return cudaSuccess;
+    if (total > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    const int grid = int(total);
     // the initialisation runs once: one variant, which handles a hole and
     // reads the scheme
     if (mode == 1)
-        edge_tile_kernel<TS, TC, UT, 1, true, false><<<ntiles, kEdgeThreads, 0, s>>>(L);
+        edge_tile_kernel<TS, TC, UT, 1, true, false><<<grid, kEdgeThreads, 0, s>>>(L, I);
     else if (xj)
-        edge_tile_kernel<TS, TC, UT, 0, true, true><<<ntiles, kEdgeThreads, 0, s>>>(L);
+        edge_tile_kernel<TS, TC, UT, 0, true, true><<<grid, kEdgeThreads, 0, s>>>(L, I);
     else if (holed)
-        edge_tile_kernel<TS, TC, UT, 0, true, false><<<ntiles, kEdgeThreads, 0, s>>>(L);
+        edge_tile_kernel<TS, TC, UT, 0, true, false><<<grid, kEdgeThreads, 0, s>>>(L, I);
     else
-        edge_tile_kernel<TS, TC, UT, 0, false, false><<<ntiles, kEdgeThreads, 0, s>>>(L);
+        edge_tile_kernel<TS, TC, UT, 0, false, false><<<grid, kEdgeThreads, 0, s>>>(L, I);
     return cudaGetLastError();
 }
 
-cudaError_t launch_edge(int fmt, const EdgeLaunch& L, int ntiles, cudaStream_t s, int mode, bool holed, bool xj) {
+static cudaError_t launch_edge_fmt(int fmt, const EdgeLaunch& L, int ntiles, const ImageTile* img, int n_img,
+                                   cudaStream_t s, int mode, bool holed, bool xj) {
     switch (fmt) {
-        case kFmtF64: return launch_edge_t<double, double, UPlain<double>>(L, ntiles, s, mode, holed, xj);
-        case kFmtF32: return launch_edge_t<float, float, UPlain<float>>(L, ntiles, s, mode, holed, xj);
-        case kFmtF32C: return launch_edge_t<float, float, UComp>(L, ntiles, s, mode, holed, xj);
-        case kFmtF16: return launch_edge_t<__half, float, UComp>(L, ntiles, s, mode, holed, xj);
-        case kFmtBF16: return launch_edge_t<__nv_bfloat16, float, UComp>(L, ntiles, s, mode, holed, xj);
+        case kFmtF64: return launch_edge_t<double, double, UPlain<double>>(L, ntiles, img, n_img, s, mode, holed, xj);
+        case kFmtF32: return launch_edge_t<float, float, UPlain<float>>(L, ntiles, img, n_img, s, mode, holed, xj);
+        case kFmtF32C: return launch_edge_t<float, float, UComp>(L, ntiles, img, n_img, s, mode, holed, xj);
+        case kFmtF16: return launch_edge_t<__half, float, UComp>(L, ntiles, img, n_img, s, mode, holed, xj);
+        case kFmtBF16: return launch_edge_t<__nv_bfloat16, float, UComp>(L, ntiles, img, n_img, s, mode, holed, xj);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_edge(int fmt, const EdgeLaunch& L, int ntiles, cudaStream_t s, int mode, bool holed, bool xj) {
+    return launch_edge_fmt(fmt, L, ntiles, nullptr, 0, s, mode, holed, xj);
+}
+
+cudaError_t launch_edge_images(int fmt, const EdgeLaunch& L, int n_edge, const ImageTile* img, int n_img,
+                               cudaStream_t s, bool holed, bool xj) {
+    return launch_edge_fmt(fmt, L, n_edge, img, n_img, s, 0, holed, xj);
 }
 
 // Tiles of one rectangle for CTAs of nthreads threads.  A band at most 3

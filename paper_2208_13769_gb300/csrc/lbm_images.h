@@ -31,8 +31,23 @@ struct ImageTile {
 int image_tiles_of_body(int nx, int ny, bool perx, bool pery, const int rect[4], int inst, ImageTile* out,
                         int cap);
 
-// One launch over ntiles tiles (device list; params: the device table the
-// tiles index, whose f_dst / a_dst / s_dst are the state just written).
-cudaError_t launch_images(int fmt, const StepParams* params, const ImageTile* tiles, int ntiles, cudaStream_t s);
+// Image tiles appended to an edge launch: CTAs n_edge and on copy
+// tiles[blockIdx.x - n_edge] (tiles NULL: none).
+struct ImageLaunch {
+    const ImageTile* tiles;
+    int32_t n_edge;
+    int32_t pad;
+};
+
+struct EdgeLaunch;
+// A step's edge tiles (n_edge of them, as launch_edge with mode 0) and its
+// seam images (n_img tiles, a device list indexing the same parameter table
+// as the edge tiles, whose f_dst / a_dst / s_dst are the state being
+// written) in one launch, for a step whose interior kernel ran across a
+// periodic seam: it follows the interior launch on the same stream (the
+// images copy what the interior launch wrote), and the small CTAs of both
+// kinds share the SMs.
+cudaError_t launch_edge_images(int fmt, const EdgeLaunch& L, int n_edge, const ImageTile* img, int n_img,
+                               cudaStream_t s, bool holed, bool xj);
 
 }  // namespace lbm
