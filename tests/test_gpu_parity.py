@@ -272,6 +272,33 @@ def test_call_order_and_argument_errors():
         lbm.lbm_destroy(ctx)
 
 
+def test_size_limits_and_an_allocation_beyond_the_device():
+    """Sizes the layout cannot index are refused before any allocation (a
+    side above 2^30 nodes, a plane of 2^31 elements or more, a side below
+    3); a body that passes them but does not fit in device memory (40 000 x
+    40 000 nodes in FP64: about 400 GB) reports LBM_E_OOM and leaves the
+    device usable."""
+    L = lbm.lib()
+
+    def create(nx, ny, storage):
+        d = lbm.lbm_desc()
+        d.nx, d.ny, d.dX, d.storage = nx, ny, 1.0, storage
+        h = lbm.C.c_void_p()
+        st = L.lbm_create(lbm.C.byref(d), lbm.C.byref(h))
+        if h.value:
+            L.lbm_destroy(h)
+        return st, h.value
+
+    for nx, ny in (((1 << 30) + 1, 8), (8, (1 << 30) + 1), (50000, 50000), (2, 100), (100, 2)):
+        st, h = create(nx, ny, lbm.LBM_F32)
+        assert st == lbm.LBM_E_INVALID and not h, (nx, ny, st)
+    st, h = create(40000, 40000, lbm.LBM_F64)
+    assert st == lbm.LBM_E_OOM and not h, st
+    prob = CASES["clamped_96x50"][0]
+    ref, got = run_both(prob, 20, "f64")  # the device still computes
+    compare(ref, got, TOL["f64"])
+
+
 def test_bounded_wait_gives_up_and_the_context_survives():
     """The time-out path of the kernels' bounded mbarrier waits, run for real
     on a barrier that never completes: the wait returns, nothing faults, and
