@@ -3,8 +3,11 @@
 //
 // Each time step of a batch is two launches, as for a single body: the
 // interior tiles of every member (one CTA per tile, longest first) on the
-// batch's stream, and the edge tiles of every member on a side stream at the
-// same time, each CTA reading its member's parameters from a device table.
+// batch's stream, and the edge tiles of every member, each CTA reading its
+// member's parameters from a device table.  The edge launch runs on a side
+// stream at the same time, or, when some member's interior runs across a
+// periodic seam, after the interior launch with the seam-image copies
+// appended to it.
 // So small and uneven bodies share the GPU instead of each paying launches
 // per step, and chunks of 64 steps replay as one CUDA graph.  Every node of
 // every member goes through the same tile code and arithmetic as when the
@@ -99,7 +102,8 @@ void batch_free(lbm_batch* b) {
 // One batch time step from table parity q: the interior tiles on the batch's
 // stream and the edge tiles on the side stream, forked from and joined to
 // the batch's stream (the small edge CTAs fill the room the interior CTAs
-// leave).
+// leave), or, with seam images, the edge tiles and the images after the
+// interior on the batch's stream.
 cudaError_t batch_launch(lbm_batch* b, int q, bool fields) {
     const StepParams* tab = b->dtab + size_t(q) * size_t(b->n_entries);
     BatchInteriorLaunch I;

@@ -12,8 +12,8 @@ namespace lbm {
 // Along a periodic axis the 3 outer rows / columns of every state plane hold
 // copies of the nodes across the seam (lbm_params.h).  The edge kernel
 // writes the copies of the nodes it advances; where the interior kernel
-// advances the nodes next to a seam, an image launch after the step copies
-// them.  A tile is a box of image positions [x0, x1) x [y0, y1) of one
+// advances the nodes next to a seam, CTAs of the edge launch that follows
+// the interior launch copy them.  A tile is a box of image positions [x0, x1) x [y0, y1) of one
 // instance (entry of the parameter table), at most kImageThreads positions,
 // each copied from the node (x mod nx, y mod ny) in every plane of the
 // instance's destination state (populations, u-carry, source carry).
