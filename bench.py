@@ -50,14 +50,18 @@ def parse():
     ap.add_argument("--nx", type=int, default=4096)
     ap.add_argument("--ny", type=int, default=2048)
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16", "bf16"])
-    ap.add_argument("--native-ucarry", dest="compensated", action="store_false",
-                    help="plain FP32 displacement carry (default: compensated FP32 pair)")
+    ap.add_argument("--ucarry", default="lo16", choices=["pair", "lo16", "native"],
+                    help="FP32 displacement carry: compensated, its low word in 16 bits (default: 112 B per "
+                         "node update, the FP32 parity bounds hold), the compensated FP32 pair (120 B), or "
+                         "plain FP32")
+    ap.add_argument("--native-ucarry", dest="ucarry", action="store_const", const="native",
+                    help="plain FP32 displacement carry (same as --ucarry native)")
     ap.add_argument("--scheme", default="explicit", choices=["explicit", "predictor", "extrapolated"],
                     help="time level of 1S in the moment: Algorithm 1 (explicit), the footnote's "
                          "predictor-corrector, or the extrapolated j of Sec. 5")
     ap.add_argument("--nu", type=float, default=0.25)
     ap.add_argument("--vmax", type=float, default=0.01)
-    ap.add_argument("--forms", default="f32n,f16,bf16",
+    ap.add_argument("--forms", default="f32c,f32n,f16,bf16",
                     help="extra population formats timed on the same body ('' to skip)")
     ap.add_argument("--form-steps", type=int, default=500)
     ap.add_argument("--schemes", default="predictor,extrapolated",
@@ -107,8 +111,8 @@ def algorithmic_bytes(storage):
     """Bytes per node update that must cross HBM (9 populations and 4 carry
     values, each read and written once): FP64 208, FP32 104; 16-bit
     populations with an FP64-wide displacement carry and an FP32 source carry
-    84.  A form that moves more (the compensated FP32 carry: 120) is charged
-    these bytes, not its own."""
+    84.  A form that moves more (the compensated FP32 carry: 120, with its
+    low word in 16 bits: 112) is charged these bytes, not its own."""
     return {"f64": 208, "f32": 104, "f16": 84, "bf16": 84}[storage]
 
 
@@ -117,7 +121,7 @@ def config_of(a, prob):
         "workload": f"clamped neo-Hooke body {a.nx}x{a.ny} nodes, FP32 populations/arithmetic",
         "nx": a.nx, "ny": a.ny, "mu": prob.mu, "lambda": prob.lam, "nu": a.nu, "rho0": prob.rho0,
         "omega": prob.omega, "v_max": a.vmax, "edges": "x- clamped (Dirichlet), x+/y-/y+ traction-free",
-        "storage": a.storage, "u_carry": "compensated" if a.compensated else "native",
+        "storage": a.storage, "u_carry": UCARRY_LABEL[a.ucarry],
         "scheme": SCHEME_LABEL[a.scheme],
         "l2": "no flush: the state (two ping-pong copies, ~1 GB) is 8x the 129 MB L2",
     }
@@ -148,7 +152,15 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(storage, compensated, nodes):
+UCARRY_LABEL = {"pair": "compensated", "lo16": "compensated, 16-bit low word", "native": "native"}
+
+
+def comp_arg(ucarry):
+    """Body's `compensated` argument for a --ucarry choice."""
+    return {"pair": True, "lo16": "lo16", "native": False}[ucarry]
+
+
+def ncu_traffic(storage, ucarry, nodes):
     """DRAM bytes of one interior launch over `nodes` nodes, from the DRAM
     bytes per node of the committed ncu summary; None if absent or taken on
     other kernel sources."""
@@ -160,7 +172,7 @@ def ncu_traffic(storage, compensated, nodes):
         return None
     if d.get("source_hash") != kernel_source_hash():
         return None
-    key = storage + ("c" if compensated and storage == "f32" else "")
+    key = storage + ({"pair": "c", "lo16": "h"}.get(ucarry, "") if storage == "f32" else "")
     e = d.get("formats", {}).get(key)
     if not e:
         return None
@@ -394,14 +406,14 @@ def run_native(a):
         d = lbm.lbm_desc()
         d.nx, d.ny, d.dX = prob.nx, prob.ny, prob.dX
         d.storage = lbm.STORAGE[a.storage]
-        d.u_carry = lbm.LBM_UCARRY_COMPENSATED if a.compensated else lbm.LBM_UCARRY_NATIVE
+        d.u_carry = lbm.ucarry_of(comp_arg(a.ucarry))
         d.scheme = scheme_id(a.scheme)
         d.cuda_stream = stream.cuda_stream
         d.device = local
         t0 = time.perf_counter()
         tuning, tms = lbm.lbm_autotune(d, [e.kind for e in prob.edges], 129)
         tuning_info = dict(tuning.as_dict(), candidate_ms_per_step=tms, seconds=time.perf_counter() - t0)
-    body = lbm.Body(prob, storage=a.storage, compensated=a.compensated, scheme=scheme_id(a.scheme),
+    body = lbm.Body(prob, storage=a.storage, compensated=comp_arg(a.ucarry), scheme=scheme_id(a.scheme),
                     stream=stream.cuda_stream, device=local, tuning=tuning)
     _, moved_per_node = lbm.lbm_memory_info(body.ctx)
     bytes_per_node = algorithmic_bytes(a.storage)
@@ -434,7 +446,7 @@ def run_native(a):
     if has_interior:
         interior_ms = float(iprof[0])
         achieved = bytes_per_node * interior_nodes / (interior_ms * 1e-3) / 1e9
-        traffic = ncu_traffic(a.storage, a.compensated, interior_nodes)
+        traffic = ncu_traffic(a.storage, a.ucarry, interior_nodes)
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": "interior_step_kernel",
                 "algorithmic_bytes_per_node": bytes_per_node, "units_per_launch": interior_nodes,
@@ -469,7 +481,7 @@ def run_native(a):
             b64.step(a.warmup + a.form_steps)
             ref_u = b64.read(lbm.LBM_FIELD_U, allow_unstable=True)["u"]
     for f in [x for x in a.forms.split(",") if x]:
-        st, comp = {"f32c": ("f32", True), "f32n": ("f32", False)}.get(f, (f, False))
+        st, comp = {"f32c": ("f32", True), "f32n": ("f32", False), "f32h": ("f32", "lo16")}.get(f, (f, False))
         b = lbm.Body(prob, storage=st, compensated=comp, scheme=scheme_id(a.scheme), stream=stream.cuda_stream,
                      device=local)
         _, bpn = lbm.lbm_memory_info(b.ctx)
@@ -555,7 +567,7 @@ def run_native(a):
         from paper_2208_13769_gb300 import workloads as W
 
         plate = W.plate_with_hole(4096, T=0.02, t_off=math.inf)
-        b = lbm.Body(plate, storage=a.storage, compensated=a.compensated, stream=stream.cuda_stream, device=local)
+        b = lbm.Body(plate, storage=a.storage, compensated=comp_arg(a.ucarry), stream=stream.cuda_stream, device=local)
         _, pbpn = lbm.lbm_memory_info(b.ctx)
         b.step(a.warmup)
         s = time_steps(b, stream, a.hole_steps)
@@ -577,7 +589,7 @@ def run_native(a):
         spec = W.body_batch(a.batch)
         bnodes = sum(p.nx * p.ny for p in spec.problems)
         pred = lbm.LBM_SCHEME_PREDICTOR
-        bodies = [lbm.Body(p, storage=a.storage, compensated=a.compensated, scheme=pred,
+        bodies = [lbm.Body(p, storage=a.storage, compensated=comp_arg(a.ucarry), scheme=pred,
                            stream=stream.cuda_stream, device=local) for p in spec.problems]
         # the batch autotuner picks ring depth and rows per interior tile on
         # scratch copies of the members
@@ -726,7 +738,7 @@ def run_native(a):
                                                    stream=stream.cuda_stream, device=local)],
                  1000, a.solves, 64 * 64),
                 ("c2_%dx%d_%s" % (a.nx, a.ny, a.storage),
-                 lambda: [lbm.Body(c2, storage=a.storage, compensated=a.compensated, scheme=scheme_id(a.scheme),
+                 lambda: [lbm.Body(c2, storage=a.storage, compensated=comp_arg(a.ucarry), scheme=scheme_id(a.scheme),
                                    stream=stream.cuda_stream, device=local, tuning=tuning)], 5000, a.solves,
                  a.nx * a.ny),
                 ("c4_256_bodies_f32", lambda: [lbm.Body(p, storage="f32", scheme=lbm.LBM_SCHEME_PREDICTOR,
@@ -750,7 +762,7 @@ def run_native(a):
         pprob = dataclasses.replace(prob, u0=u0_h.numpy(), v0=v0_h.numpy(), make_initial=None)
         barrier()
         t0 = time.perf_counter()
-        b = lbm.Body(pprob, storage=a.storage, compensated=a.compensated, scheme=scheme_id(a.scheme),
+        b = lbm.Body(pprob, storage=a.storage, compensated=comp_arg(a.ucarry), scheme=scheme_id(a.scheme),
                      stream=stream.cuda_stream, device=local, tuning=tuning)
         b.step(a.steps)
         st, _ = lbm.lbm_read_fields(b.ctx, lbm.LBM_FIELD_U, u_h.numpy().reshape(-1), allow_unstable=True)

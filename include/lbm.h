@@ -66,9 +66,13 @@ typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3 } lbm_storage
 
 /* Displacement carry: NATIVE keeps u in the arithmetic type; COMPENSATED keeps
  * it as an unevaluated sum of two FP32 numbers (about 48 significant bits),
- * so that Grad u stays accurate when |u| is large.  F16/BF16 always use
- * COMPENSATED; F64 always uses FP64. */
-typedef enum { LBM_UCARRY_NATIVE = 0, LBM_UCARRY_COMPENSATED = 1 } lbm_ucarry;
+ * so that Grad u stays accurate when |u| is large; COMPENSATED16 keeps the
+ * same sum with the low word stored in 16 bits (FP16 of lo 2^k, k fixed per
+ * context from nx, ny and dX so that |u| up to 8 max(nx, ny) dX keeps about
+ * 35 significant bits; beyond that the low word saturates and u keeps FP32
+ * precision): 12 bytes per node for both components instead of 16.
+ * F16/BF16 always use COMPENSATED; F64 always uses FP64. */
+typedef enum { LBM_UCARRY_NATIVE = 0, LBM_UCARRY_COMPENSATED = 1, LBM_UCARRY_COMPENSATED16 = 2 } lbm_ucarry;
 
 /* Time level of the source 1S in the moment computation (Sec. 5):
  * EXPLICIT  -- Algorithm 1: the time-t source enters collision and moment

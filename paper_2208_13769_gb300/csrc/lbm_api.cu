@@ -23,7 +23,8 @@ size_t elem_size_storage(int fmt) {
     switch (fmt) {
         case kFmtF64: return 8;
         case kFmtF32:
-        case kFmtF32C: return 4;
+        case kFmtF32C:
+        case kFmtF32H: return 4;
         default: return 2;
     }
 }
@@ -31,8 +32,15 @@ size_t elem_size_compute(int fmt) { return fmt == kFmtF64 ? 8 : 4; }
 // planes of the source carry: the last source, or D and G of the
 // extrapolated scheme
 int source_planes(int scheme) { return scheme == LBM_SCHEME_EXTRAPOLATED ? 4 : 2; }
-size_t elem_size_ucarry(int fmt) { return fmt == kFmtF64 ? 8 : 4; }
-int ucarry_planes(int fmt) { return (fmt == kFmtF64 || fmt == kFmtF32) ? 1 : 2; }
+// bytes of the u-carry per node, both components (the layouts of
+// UPlain / UPair in lbm_device.cuh)
+size_t ucarry_bytes(int fmt) {
+    switch (fmt) {
+        case kFmtF32: return 8;
+        case kFmtF32H: return 12;
+        default: return 16;  // FP64, or a pair of FP32 words
+    }
+}
 
 }  // namespace
 
@@ -93,6 +101,8 @@ StepParams lbm::make_params(const lbm_ctx* c, int parity) {
         p.dec_scale[i] = float(dec);
         p.enc_scale[i] = float(1.0 / dec);
     }
+    p.lo_scale[0] = float(ldexp(1.0, c->lo_log2));
+    p.lo_scale[1] = float(ldexp(1.0, -c->lo_log2));
     for (int e = 0; e < 4; ++e) p.bc[e] = c->bc[e];
     // lattice constants in FP64, and rounded to FP32
     double* L = p.lat_d;
@@ -504,7 +514,9 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
     if (!d) return LBM_E_INVALID;
     if (d->nx < 3 || d->ny < 3 || !(d->dX > 0) || !isfinite(d->dX)) return LBM_E_INVALID;
     if (d->storage < LBM_F64 || d->storage > LBM_BF16) return LBM_E_INVALID;
-    if (d->u_carry != LBM_UCARRY_NATIVE && d->u_carry != LBM_UCARRY_COMPENSATED) return LBM_E_INVALID;
+    if (d->u_carry != LBM_UCARRY_NATIVE && d->u_carry != LBM_UCARRY_COMPENSATED &&
+        d->u_carry != LBM_UCARRY_COMPENSATED16)
+        return LBM_E_INVALID;
     if (d->scheme != LBM_SCHEME_EXPLICIT && d->scheme != LBM_SCHEME_PREDICTOR &&
         d->scheme != LBM_SCHEME_EXTRAPOLATED)
         return LBM_E_INVALID;
@@ -550,9 +562,19 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
     c->dX = d->dX;
     c->scheme = d->scheme;
     c->f16_scale_log2 = d->f16_scale_log2 ? d->f16_scale_log2 : 10;
+    {
+        // the 16-bit low words of the u-carry: |u| < 2^b = 8 max(nx, ny) dX
+        // rounded up keeps |lo| 2^k below 2^15 for k = 40 - b
+        int b = 0;
+        frexp(8.0 * double(std::max(d->nx, d->ny)) * d->dX, &b);
+        c->lo_log2 = std::min(100, std::max(-100, 40 - b));
+    }
     switch (d->storage) {
         case LBM_F64: c->fmt = kFmtF64; break;
-        case LBM_F32: c->fmt = d->u_carry == LBM_UCARRY_COMPENSATED ? kFmtF32C : kFmtF32; break;
+        case LBM_F32:
+            c->fmt = d->u_carry == LBM_UCARRY_COMPENSATED ? kFmtF32C
+                     : d->u_carry == LBM_UCARRY_COMPENSATED16 ? kFmtF32H : kFmtF32;
+            break;
         case LBM_F16: c->fmt = kFmtF16; break;
         default: c->fmt = kFmtBF16; break;
     }
@@ -575,7 +597,7 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
     }
 
     const size_t fbytes = size_t(9) * c->plane * elem_size_storage(c->fmt);
-    const size_t abytes = size_t(2 * ucarry_planes(c->fmt)) * c->plane * elem_size_ucarry(c->fmt);
+    const size_t abytes = ucarry_bytes(c->fmt) * c->plane;
     const size_t sbytes = size_t(source_planes(d->scheme)) * c->plane * elem_size_compute(c->fmt);
     const size_t fldbytes = size_t(5) * nodes * sizeof(double);
     const size_t ubytes = size_t(2) * nodes * sizeof(double);
@@ -791,7 +813,7 @@ lbm_status lbm_profile_interior(lbm_ctx* c, int64_t nlaunches, double out[2]) {
     // the state the next step reads, and the device flag, saved on the device
     const int q = c->parity;
     const size_t fb = size_t(9) * size_t(c->plane) * elem_size_storage(c->fmt);
-    const size_t ab = size_t(2 * ucarry_planes(c->fmt)) * size_t(c->plane) * elem_size_ucarry(c->fmt);
+    const size_t ab = ucarry_bytes(c->fmt) * size_t(c->plane);
     const size_t sb = size_t(source_planes(c->scheme)) * size_t(c->plane) * elem_size_compute(c->fmt);
     unsigned char* save = nullptr;
     cudaError_t err = cudaMalloc(&save, fb + ab + sb + sizeof(int32_t));
@@ -1008,11 +1030,12 @@ namespace {
 struct StateHeader {
     char magic[8];
     int32_t fmt, nx, ny, scheme;
+    int32_t lo_log2, pad;
     int64_t pitch, plane, steps;
     double dt;
     int64_t bytes;  // the whole state, header included
 };
-constexpr char kStateMagic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', '1'};
+constexpr char kStateMagic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', '2'};
 
 struct StateParts {
     size_t f, a, s, fields;
@@ -1021,7 +1044,7 @@ struct StateParts {
 StateParts state_parts(const lbm_ctx* c) {
     StateParts p;
     p.f = size_t(9) * size_t(c->plane) * elem_size_storage(c->fmt);
-    p.a = size_t(2 * ucarry_planes(c->fmt)) * size_t(c->plane) * elem_size_ucarry(c->fmt);
+    p.a = ucarry_bytes(c->fmt) * size_t(c->plane);
     p.s = size_t(source_planes(c->scheme)) * size_t(c->plane) * elem_size_compute(c->fmt);
     p.fields = size_t(5) * size_t(c->nx) * size_t(c->ny) * sizeof(double);
     return p;
@@ -1035,6 +1058,7 @@ StateHeader state_header(const lbm_ctx* c) {
     h.nx = c->nx;
     h.ny = c->ny;
     h.scheme = c->scheme;
+    h.lo_log2 = c->lo_log2;
     h.pitch = c->pitch;
     h.plane = c->plane;
     h.steps = c->steps;
@@ -1085,7 +1109,8 @@ lbm_status lbm_write_state(lbm_ctx* c, const void* in, int64_t in_len) {
     memcpy(&h, in, sizeof(h));
     const StateHeader mine = state_header(c);
     if (memcmp(h.magic, kStateMagic, sizeof(h.magic)) != 0 || h.fmt != mine.fmt || h.nx != mine.nx ||
-        h.ny != mine.ny || h.scheme != mine.scheme || h.pitch != mine.pitch || h.plane != mine.plane ||
+        h.ny != mine.ny || h.scheme != mine.scheme || h.lo_log2 != mine.lo_log2 || h.pitch != mine.pitch ||
+        h.plane != mine.plane ||
         h.dt != mine.dt || h.bytes != mine.bytes || in_len < h.bytes || h.steps < 0)
         return LBM_E_INVALID;
     DeviceGuard guard(c->device);
@@ -1135,7 +1160,7 @@ lbm_status lbm_memory_info(const lbm_ctx* c, int64_t* device_bytes, int64_t* byt
     if (device_bytes) *device_bytes = c->device_bytes;
     if (bytes_per_node_update) {
         const int64_t per = int64_t(9 * elem_size_storage(c->fmt)) +
-                            int64_t(2 * ucarry_planes(c->fmt) * elem_size_ucarry(c->fmt)) +
+                            int64_t(ucarry_bytes(c->fmt)) +
                             int64_t(source_planes(c->scheme) * elem_size_compute(c->fmt));
         *bytes_per_node_update = 2 * per;
     }

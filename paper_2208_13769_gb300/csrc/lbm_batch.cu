@@ -552,7 +552,8 @@ lbm_status lbm_batch_autotune(lbm_ctx* const* members, int32_t n, int64_t steps,
         d.ny = c->ny;
         d.dX = c->dX;
         d.storage = c->fmt == kFmtF64 ? LBM_F64 : (c->fmt == kFmtF16 ? LBM_F16 : (c->fmt == kFmtBF16 ? LBM_BF16 : LBM_F32));
-        d.u_carry = c->fmt == kFmtF32 ? LBM_UCARRY_NATIVE : LBM_UCARRY_COMPENSATED;
+        d.u_carry = c->fmt == kFmtF32 ? LBM_UCARRY_NATIVE
+                    : (c->fmt == kFmtF32H ? LBM_UCARRY_COMPENSATED16 : LBM_UCARRY_COMPENSATED);
         d.scheme = c->scheme;
         d.f16_scale_log2 = c->f16_scale_log2;
         d.cuda_stream = st;

@@ -53,6 +53,7 @@ struct lbm_ctx {
     int32_t nx = 0, ny = 0;
     double dX = 1.0;
     int32_t f16_scale_log2 = 10;
+    int32_t lo_log2 = 0;  // the u-carry's 16-bit low words hold lo 2^lo_log2 (kFmtF32H)
     // layout
     int64_t pitch = 0, plane = 0;
     // device memory

@@ -181,23 +181,58 @@ struct Codec<__nv_bfloat16, float> {
 };
 
 // ---------------------------------------------------------------- u-carry
-// Displacement number types.  Each provides: the element type and number of
-// planes per component in memory, construction from the planes of a row
-// segment, adding an increment (in the arithmetic type), renormalisation
-// before storing, differences (in the arithmetic type), the difference to an
-// FP64 value, and conversion to double.
+// Displacement number types.  Each provides: loading one component of a node
+// from the carry buffer and storing it back (the buffer's layout is the
+// type's own, below), construction from an FP64 value, adding an increment
+// (in the arithmetic type), renormalisation before storing, differences (in
+// the arithmetic type), the difference to an FP64 value, and conversion to
+// double.  A component's planes are reached through a view (pointers taken
+// once per kernel); store() of both components hands each stored word to
+// put(plane, value), which writes it at the node (and its periodic images,
+// in the edge kernel).
+
+// Layout of a carry buffer, for copies that move its words without
+// interpreting them (the seam images).
+enum CarryLayout : int {
+    kCarryOne = 0,    // one word of the arithmetic type per component: planes x, y
+    kCarryPair = 1,   // two FP32 words per component: planes x.hi, x.lo, y.hi, y.lo
+    kCarryPair16 = 2  // FP32 high word, 16-bit low word: x.hi, x.lo16, y.hi, y.lo16 (1.5 planes each)
+};
 
 template <class T>
 struct UPlain {  // u kept in T itself (FP64 or FP32)
-    using Elem = T;
-    static constexpr int planes = 1;
+    static constexpr int layout = kCarryOne;
     T v;
-    __device__ __forceinline__ static UPlain from_planes(const T* base, int e, int) { return UPlain{base[e]}; }
-    __device__ __forceinline__ static UPlain ld_global(const T* base, int64_t o, int64_t) { return UPlain{base[o]}; }
+    // a component's plane
+    template <class P>
+    struct ViewT {
+        P* w;
+    };
+    using View = ViewT<T>;
+    using CView = ViewT<const T>;
+    __device__ __forceinline__ static View view(void* a, int comp, int64_t plane) {
+        return View{static_cast<T*>(a) + comp * plane};
+    }
+    __device__ __forceinline__ static CView cview(const void* a, int comp, int64_t plane) {
+        return CView{static_cast<const T*>(a) + comp * plane};
+    }
+    // the stored words as loaded (decode() turns them into the value; a
+    // prefetch keeps them raw so that nothing waits for the load early)
+    using Raw = UPlain;
+    __device__ __forceinline__ static Raw load_raw(const CView& c, int64_t o, int64_t) { return UPlain{c.w[o]}; }
+    __device__ __forceinline__ static UPlain decode(const Raw& r, const StepParams&) { return r; }
+    __device__ __forceinline__ static UPlain load(const CView& c, int64_t o, int64_t plane, const StepParams& p) {
+        return decode(load_raw(c, o, plane), p);
+    }
+    template <class Put>
+    __device__ __forceinline__ static void store(const UPlain& x, const UPlain& y, const View& cx, const View& cy,
+                                                 int64_t, const StepParams&, Put&& put) {
+        put(cx.w, x.v);
+        put(cy.w, y.v);
+    }
     __device__ __forceinline__ static UPlain from_double(double d) { return UPlain{T(d)}; }
     __device__ __forceinline__ UPlain add(T d) const { return UPlain{v + d}; }
     __device__ __forceinline__ UPlain renorm() const { return *this; }
-    __device__ __forceinline__ T part(int) const { return v; }
     __device__ __forceinline__ T minus(const UPlain& o) const { return v - o.v; }
     __device__ __forceinline__ T minus_d(double d) const { return T(double(v) - d); }
     __device__ __forceinline__ double to_double() const { return double(v); }
@@ -206,30 +241,87 @@ struct UPlain {  // u kept in T itself (FP64 or FP32)
 // Unevaluated sum hi + lo of two floats ("double-float", about 48
 // significant bits).  Increments go into lo (lo stays small, so its rounding
 // is far below ulp(hi)); renorm() folds lo back with Knuth's two-sum before
-// the value is stored.  Stored as two planes per component: hi, then lo.
-struct UComp {
-    using Elem = float;
-    static constexpr int planes = 2;
+// the value is stored, leaving |lo| <= ulp(hi) / 2.
+// LO16 = false: lo stored as a float (16 bytes per node for both components).
+// LO16 = true: lo stored as FP16 of lo 2^k, k = StepParams::lo_log2 chosen per
+// body so that |lo| 2^k stays below 2^15 while |u| < 2^(40 - k); u keeps
+// about 35 significant bits in 12 bytes per node.  A larger |u| saturates the
+// low word (FP32 precision, no overflow).
+template <bool LO16>
+struct UPair {
+    static constexpr int layout = LO16 ? kCarryPair16 : kCarryPair;
     float hi, lo;
-    __device__ __forceinline__ static UComp from_planes(const float* base, int e, int seg) {
-        return UComp{base[e], base[seg + e]};
+    // a component's high-word plane; its low words follow in the next
+    // plane's worth of memory (plane floats, or the first half of it)
+    using Lo = typename std::conditional<LO16, __half, float>::type;
+    struct View {
+        float* hi;
+        Lo* lo;
+    };
+    struct CView {
+        const float* hi;
+    };
+    // first float of component comp: after 2 planes of floats per component,
+    // or after 1.5 (a multiple of 32 floats: plane is a multiple of 64)
+    __device__ __forceinline__ static int64_t comp_offset(int comp, int64_t plane) {
+        return LO16 ? comp * (plane + plane / 2) : comp * 2 * plane;
     }
-    __device__ __forceinline__ static UComp ld_global(const float* base, int64_t o, int64_t plane) {
-        return UComp{base[o], base[o + plane]};
+    __device__ __forceinline__ static View view(void* a, int comp, int64_t plane) {
+        float* h = static_cast<float*>(a) + comp_offset(comp, plane);
+        return View{h, reinterpret_cast<Lo*>(h + plane)};
     }
-    __device__ __forceinline__ static UComp from_double(double d) {
+    __device__ __forceinline__ static CView cview(const void* a, int comp, int64_t plane) {
+        return CView{static_cast<const float*>(a) + comp_offset(comp, plane)};
+    }
+    struct Raw {
+        float hi;
+        Lo lo;
+    };
+    __device__ __forceinline__ static Raw load_raw(const CView& c, int64_t o, int64_t plane) {
+        return Raw{c.hi[o], reinterpret_cast<const Lo*>(c.hi + plane)[o]};
+    }
+    __device__ __forceinline__ static UPair decode(const Raw& r, const StepParams& p) {
+        if constexpr (LO16)
+            return UPair{r.hi, __fmul_rn(__half2float(r.lo), p.lo_scale[1])};
+        else
+            return UPair{r.hi, r.lo};
+    }
+    __device__ __forceinline__ static UPair load(const CView& c, int64_t o, int64_t plane, const StepParams& p) {
+        return decode(load_raw(c, o, plane), p);
+    }
+    __device__ __forceinline__ Lo lo_word(const StepParams& p) const {
+        if constexpr (LO16) {
+            // round to nearest, finite values beyond the FP16 range clamped
+            // to +-65504 (cvt's satfinite)
+            unsigned short r;
+            asm("cvt.rn.satfinite.f16.f32 %0, %1;" : "=h"(r) : "f"(__fmul_rn(lo, p.lo_scale[0])));
+            return __ushort_as_half(r);
+        } else {
+            return lo;
+        }
+    }
+    // both components (the high words first: fewer registers live in the
+    // interior kernel than component by component)
+    template <class Put>
+    __device__ __forceinline__ static void store(const UPair& x, const UPair& y, const View& cx, const View& cy,
+                                                 int64_t, const StepParams& p, Put&& put) {
+        put(cx.hi, x.hi);
+        put(cy.hi, y.hi);
+        put(cx.lo, x.lo_word(p));
+        put(cy.lo, y.lo_word(p));
+    }
+    __device__ __forceinline__ static UPair from_double(double d) {
         const float h = __double2float_rn(d);
-        return UComp{h, __double2float_rn(d - double(h))};
+        return UPair{h, __double2float_rn(d - double(h))};
     }
-    __device__ __forceinline__ UComp add(float d) const { return UComp{hi, __fadd_rn(lo, d)}; }
-    __device__ __forceinline__ UComp renorm() const {
+    __device__ __forceinline__ UPair add(float d) const { return UPair{hi, __fadd_rn(lo, d)}; }
+    __device__ __forceinline__ UPair renorm() const {
         const float s = __fadd_rn(hi, lo);
         const float bb = __fsub_rn(s, hi);
         const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(lo, bb));
-        return UComp{s, e};
+        return UPair{s, e};
     }
-    __device__ __forceinline__ float part(int c) const { return c == 0 ? hi : lo; }
-    __device__ __forceinline__ float minus(const UComp& o) const {
+    __device__ __forceinline__ float minus(const UPair& o) const {
         return __fadd_rn(__fsub_rn(hi, o.hi), __fsub_rn(lo, o.lo));
     }
     __device__ __forceinline__ float minus_d(double d) const {
@@ -237,5 +329,7 @@ struct UComp {
     }
     __device__ __forceinline__ double to_double() const { return double(hi) + double(lo); }
 };
+using UComp = UPair<false>;
+using UCompH = UPair<true>;
 
 }  // namespace lbm

@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(kEdgeThreads, 3)
     static_assert(kImageThreads <= N, "an image tile fits an edge CTA");
     if (I.tiles != nullptr && int(blockIdx.x) >= I.n_edge) {  // a seam-image CTA (uniform per CTA)
         if (int(threadIdx.x) < kImageThreads)
-            image_copy<int(sizeof(TS)), int(sizeof(TC)), UT::planes>(L.params, I.tiles[blockIdx.x - I.n_edge],
+            image_copy<int(sizeof(TS)), int(sizeof(TC)), UT::layout>(L.params, I.tiles[blockIdx.x - I.n_edge],
                                                                     int(threadIdx.x));
         return;
     }
@@ -98,6 +98,7 @@ static cudaError_t launch_edge_fmt(int fmt, const EdgeLaunch& L, int ntiles, con
         case kFmtF64: return launch_edge_t<double, double, UPlain<double>>(L, ntiles, img, n_img, s, mode, holed, xj);
         case kFmtF32: return launch_edge_t<float, float, UPlain<float>>(L, ntiles, img, n_img, s, mode, holed, xj);
         case kFmtF32C: return launch_edge_t<float, float, UComp>(L, ntiles, img, n_img, s, mode, holed, xj);
+        case kFmtF32H: return launch_edge_t<float, float, UCompH>(L, ntiles, img, n_img, s, mode, holed, xj);
         case kFmtF16: return launch_edge_t<__half, float, UComp>(L, ntiles, img, n_img, s, mode, holed, xj);
         case kFmtBF16: return launch_edge_t<__nv_bfloat16, float, UComp>(L, ntiles, img, n_img, s, mode, holed, xj);
     }

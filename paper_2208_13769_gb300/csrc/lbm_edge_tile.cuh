@@ -153,8 +153,6 @@ __device__ __noinline__ void boundary_links(TS* fdst, Geo g, const StepParams& p
 template <class TS, class TC, class UT, int MODE, bool HOLE, bool XJ>
 __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepParams& p, bool want_fields, UT* su,
                                                TC* sq, TC* sinit, EdgeNow<TC, UT>* s_edge) {
-    using CT = typename UT::Elem;
-    constexpr int UP = UT::planes;
     const int t = threadIdx.x;
 
     // the collision of this launch is at t_now = n_now dt; the step counter
@@ -176,8 +174,10 @@ __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepP
     const int64_t pitch = g.pitch, plane = g.plane;
     const TS* __restrict__ fsrc = static_cast<const TS*>(p.f_src);
     TS* __restrict__ fdst = static_cast<TS*>(p.f_dst);
-    const CT* __restrict__ a_src = static_cast<const CT*>(p.a_src);
-    CT* __restrict__ a_dst = static_cast<CT*>(p.a_dst);
+    const void* __restrict__ a_src = p.a_src;
+    void* __restrict__ a_dst = p.a_dst;
+    const typename UT::CView as0 = UT::cview(a_src, 0, plane), as1 = UT::cview(a_src, 1, plane);
+    const typename UT::View ad0 = UT::view(a_dst, 0, plane), ad1 = UT::view(a_dst, 1, plane);
     const TC* __restrict__ s_src = static_cast<const TC*>(p.s_src);
     TC* __restrict__ s_dst = static_cast<TC*>(p.s_dst);
 
@@ -227,8 +227,8 @@ __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepP
 #pragma unroll
         for (int i = 0; i < 9; ++i)
             f[i] = Codec<TS, TC>::ld(fsrc[int64_t(i) * plane + o - ex(i) - int64_t(ey(i)) * pitch], i, p);
-        const UT A0 = UT::ld_global(a_src, o, plane);
-        const UT A1 = UT::ld_global(a_src + UP * plane, o, plane);
+        const UT A0 = UT::load(as0, o, plane, p);
+        const UT A1 = UT::load(as1, o, plane, p);
         if (inC) {
             so0 = s_src[o];
             so1 = s_src[o + plane];
@@ -425,11 +425,7 @@ __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepP
         const TC f0 = MODE == 1 ? TC(2) * ka0 : fo0, f1 = MODE == 1 ? TC(2) * ka1 : fo1;
         const UT A0 = xj ? ux.add(TC(4) * ka0 - f0).renorm() : ux.add(du0 + ka0).renorm();
         const UT A1 = xj ? uy.add(TC(4) * ka1 - f1).renorm() : uy.add(du1 + ka1).renorm();
-#pragma unroll
-        for (int c = 0; c < UP; ++c) {
-            put(a_dst + c * plane, A0.part(c));
-            put(a_dst + (UP + c) * plane, A1.part(c));
-        }
+        UT::store(A0, A1, ad0, ad1, plane, p, put);
         if (xj) {
             const TC d0 = MODE == 1 ? ka0 : so0, d1 = MODE == 1 ? ka1 : so1;
             put(s_dst, ka0);

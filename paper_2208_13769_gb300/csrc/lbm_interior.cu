@@ -90,10 +90,8 @@ __host__ __device__ constexpr size_t interior_row_bytes() {
 template <class TS, class TC, class UT, int NT, bool KEEP, bool XJ, bool UNROLL3, bool REV>
 __device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeom& tg, int bx, int by,
                                               double* fields) {
-    using CT = typename UT::Elem;
     const int W = tg.strip_w;
     constexpr int SEG = seg_elems<TS, NT>();
-    constexpr int UP = UT::planes;
     constexpr int ROW_BYTES = int(interior_row_bytes<TS, NT>());
     static_assert(ROW_BYTES % 16 == 0, "row size");
     constexpr int ALIGN_COLS = 16 / int(sizeof(TS));
@@ -132,8 +130,11 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeo
 
     const TS* __restrict__ fsrc = static_cast<const TS*>(p.f_src);
     TS* __restrict__ fdst = static_cast<TS*>(p.f_dst);
-    const CT* __restrict__ a_src = static_cast<const CT*>(p.a_src);
-    CT* __restrict__ a_dst = static_cast<CT*>(p.a_dst);
+    // the u-carry's planes, per component
+    const void* __restrict__ a_src = p.a_src;
+    void* __restrict__ a_dst = p.a_dst;
+    const typename UT::CView as0 = UT::cview(a_src, 0, plane), as1 = UT::cview(a_src, 1, plane);
+    const typename UT::View ad0 = UT::view(a_dst, 0, plane), ad1 = UT::view(a_dst, 1, plane);
     const TC* __restrict__ s_src = static_cast<const TC*>(p.s_src);
     TC* __restrict__ s_dst = static_cast<TC*>(p.s_dst);
 
@@ -206,11 +207,6 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeo
     TS* fd[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) fd[i] = fdst + int64_t(i) * plane;
-    const CT* as0 = a_src;
-    const CT* as1 = a_src + UP * plane;
-    CT* ad[2 * UP];
-#pragma unroll
-    for (int c = 0; c < 2 * UP; ++c) ad[c] = a_dst + int64_t(c) * plane;
     const TC* ss1 = s_src + plane;
     TC* sd1 = s_dst + plane;
     // the extrapolated scheme's F (planes 2, 3)
@@ -218,11 +214,11 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeo
     const TC* sf1 = s_src + 3 * plane;
 
     // carries prefetched one row ahead
-    UT an0, an1;
+    typename UT::Raw an0, an1;  // as stored: decoded where stage A uses them
     TC sn_old0 = TC(0), sn_old1 = TC(0), f_old0 = TC(0), f_old1 = TC(0);
     if (colA) {
-        an0 = UT::ld_global(as0, off_a, plane);
-        an1 = UT::ld_global(as1, off_a, plane);
+        an0 = UT::load_raw(as0, off_a, plane);
+        an1 = UT::load_raw(as1, off_a, plane);
     }
 
     bool bad = false;
@@ -259,17 +255,17 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeo
                 for (int i = 1; i < 9; ++i) gcur[i] = g[i];
             }
             if (XJ) {  // u* = u(t) + ku (3 jh(t) - jh(t - dt)) = E
-                su[(sA * 2) * NT + t] = an0;
-                su[(sA * 2 + 1) * NT + t] = an1;
+                su[(sA * 2) * NT + t] = UT::decode(an0, p);
+                su[(sA * 2 + 1) * NT + t] = UT::decode(an1, p);
             } else {
                 const TC m0 = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
                 const TC m1 = (g[2] - g[4]) + (g[5] - g[8]) + (g[6] - g[7]);
-                su[(sA * 2) * NT + t] = an0.add(k.ku * m0);
-                su[(sA * 2 + 1) * NT + t] = an1.add(k.ku * m1);
+                su[(sA * 2) * NT + t] = UT::decode(an0, p).add(k.ku * m0);
+                su[(sA * 2 + 1) * NT + t] = UT::decode(an1, p).add(k.ku * m1);
             }
             if (q + 1 < niter) {
-                an0 = UT::ld_global(as0, off_a + dpitch, plane);
-                an1 = UT::ld_global(as1, off_a + dpitch, plane);
+                an0 = UT::load_raw(as0, off_a + dpitch, plane);
+                an1 = UT::load_raw(as1, off_a + dpitch, plane);
             }
         }
         __syncthreads();
@@ -390,11 +386,8 @@ __device__ __forceinline__ bool interior_tile(const StepParams& p, const TileGeo
             const TC ka1 = XJ ? k.ku * j1 : k.ku * (j1 + TC(0.5) * sn1);
             const UT A0 = XJ ? ux.add(TC(4) * ka0 - fo0).renorm() : ux.add(du0 + ka0).renorm();
             const UT A1 = XJ ? uy.add(TC(4) * ka1 - fo1).renorm() : uy.add(du1 + ka1).renorm();
-#pragma unroll
-            for (int c = 0; c < UP; ++c) {
-                ad[c][o] = A0.part(c);
-                ad[UP + c][o] = A1.part(c);
-            }
+            auto put = [o](auto* base, auto v) { base[o] = v; };
+            UT::store(A0, A1, ad0, ad1, plane, p, put);
             if (XJ) {
                 s_dst[o] = ka0;
                 sd1[o] = ka1;
@@ -587,6 +580,8 @@ cudaError_t launch_batch_interior(int fmt, const BatchInteriorLaunch& L, int rin
             return launch_batch_interior_t<float, float, UPlain<float>, NT, 6, true>(L, ring_slots, s, resident);
         case kFmtF32C:
             return launch_batch_interior_t<float, float, UComp, NT, 6, false>(L, ring_slots, s, resident);
+        case kFmtF32H:
+            return launch_batch_interior_t<float, float, UCompH, NT, 6, false>(L, ring_slots, s, resident);
         case kFmtF16:
             return launch_batch_interior_t<__half, float, UComp, NT, 6, true>(L, ring_slots, s, resident);
         case kFmtBF16:
@@ -640,6 +635,7 @@ int interior_occupancy(int fmt, int ring_slots) {
         case kFmtF64: return interior_occupancy_t<double, double, UPlain<double>, 128, 2, false>(ring_slots);
         case kFmtF32: return interior_occupancy_t<float, float, UPlain<float>, 128, 7, true>(ring_slots);
         case kFmtF32C: return interior_occupancy_t<float, float, UComp, 128, 4, false>(ring_slots);
+        case kFmtF32H: return interior_occupancy_t<float, float, UCompH, 128, 4, false>(ring_slots);
         case kFmtF16: return interior_occupancy_t<__half, float, UComp, 128, 4, true>(ring_slots);
         default: return interior_occupancy_t<__nv_bfloat16, float, UComp, 128, 4, true>(ring_slots);
     }
@@ -650,6 +646,7 @@ size_t interior_smem(int fmt, int ring_slots) {
         case kFmtF64: return interior_smem_bytes<double, double, UPlain<double>, 128>(ring_slots);
         case kFmtF32: return interior_smem_bytes<float, float, UPlain<float>, 128>(ring_slots);
         case kFmtF32C: return interior_smem_bytes<float, float, UComp, 128>(ring_slots);
+        case kFmtF32H: return interior_smem_bytes<float, float, UCompH, 128>(ring_slots);
         case kFmtF16: return interior_smem_bytes<__half, float, UComp, 128>(ring_slots);
         default: return interior_smem_bytes<__nv_bfloat16, float, UComp, 128>(ring_slots);
     }
@@ -662,6 +659,7 @@ cudaError_t launch_interior(int fmt, const StepParams& p0, const InteriorRects& 
         case kFmtF64: return launch_interior_t<double, double, UPlain<double>, 128, 2, false>(p, R, s);
         case kFmtF32: return launch_interior_t<float, float, UPlain<float>, 128, 7, true>(p, R, s);
         case kFmtF32C: return launch_interior_t<float, float, UComp, 128, 4, false>(p, R, s);
+        case kFmtF32H: return launch_interior_t<float, float, UCompH, 128, 4, false>(p, R, s);
         case kFmtF16: return launch_interior_t<__half, float, UComp, 128, 4, true>(p, R, s);
         case kFmtBF16: return launch_interior_t<__nv_bfloat16, float, UComp, 128, 4, true>(p, R, s);
     }

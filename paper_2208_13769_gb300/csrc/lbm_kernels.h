@@ -13,7 +13,8 @@ enum Format : int {
     kFmtF32 = 1,   // FP32 / FP32 / FP32
     kFmtF32C = 2,  // FP32 / FP32 / compensated FP32 pair
     kFmtF16 = 3,   // FP16 / FP32 / compensated FP32 pair
-    kFmtBF16 = 4   // BF16 / FP32 / compensated FP32 pair
+    kFmtBF16 = 4,  // BF16 / FP32 / compensated FP32 pair
+    kFmtF32H = 5   // FP32 / FP32 / FP32 + 16-bit low word (UCompH)
 };
 
 

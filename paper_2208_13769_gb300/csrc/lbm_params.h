@@ -46,7 +46,7 @@ struct StepParams {
 
     const void* f_src;  // 9 planes of f^col(t_n), storage type
     void* f_dst;        // 9 planes of f^col(t_n+1)
-    const void* a_src;  // u-carry A: 2 comps x (1 or 2) planes
+    const void* a_src;  // u-carry A: 2 components, in the layout of the format's carry type
     void* a_dst;
     const void* s_src;  // source carry 1S: 2 planes, arithmetic type
     void* s_dst;
@@ -62,6 +62,8 @@ struct StepParams {
     double body[2];
     float enc_scale[9];  // 16-bit storage: 1 / (w_i 2^-s)
     float dec_scale[9];  // w_i 2^-s
+    float lo_scale[2];   // u-carry with 16-bit low words: 2^k and 2^-k (UCompH)
+    float pad3[2];
     EdgeBC bc[4];
     // lattice constants, computed once on the host in FP64 (kLat* indices);
     // lat_f holds the same values rounded to FP32

@@ -13,7 +13,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 import threading
-from typing import Optional
+from typing import Optional, Union
 
 import numpy as np
 
@@ -21,7 +21,19 @@ from . import build as _build
 
 LBM_OK, LBM_E_INVALID, LBM_E_OOM, LBM_E_CUDA, LBM_E_UNSTABLE, LBM_E_TIMEOUT, LBM_E_STATE = range(7)
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = range(4)
-LBM_UCARRY_NATIVE, LBM_UCARRY_COMPENSATED = 0, 1
+LBM_UCARRY_NATIVE, LBM_UCARRY_COMPENSATED, LBM_UCARRY_COMPENSATED16 = 0, 1, 2
+
+
+def ucarry_of(compensated) -> int:
+    """The lbm_ucarry value of a Body's `compensated` argument: None or True
+    (FP32 pair), False (plain), "lo16" (FP32 high word + 16-bit low word)."""
+    if compensated is None or compensated is True:
+        return LBM_UCARRY_COMPENSATED
+    if compensated is False:
+        return LBM_UCARRY_NATIVE
+    if compensated == "lo16":
+        return LBM_UCARRY_COMPENSATED16
+    raise ValueError(f"compensated: None, True, False or 'lo16', not {compensated!r}")
 LBM_SCHEME_EXPLICIT, LBM_SCHEME_PREDICTOR, LBM_SCHEME_EXTRAPOLATED = 0, 1, 2
 LBM_PERIODIC, LBM_DIRICHLET, LBM_NEUMANN = 0, 1, 2
 LBM_FIELD_U, LBM_FIELD_V, LBM_FIELD_P, LBM_FIELD_PBAR, LBM_FIELD_R, LBM_FIELD_SIGMA, LBM_FIELD_J = (
@@ -344,7 +356,7 @@ def tuning_from_dict(d: dict) -> lbm_tuning:
     return lbm_tuning(int(d["ring_slots"]), int(d["chunk_rows"]), int(d["aligned"]), int(d.get("plan", 0)))
 
 
-def autotune_cached(prob, storage: str = "f32", compensated: Optional[bool] = None,
+def autotune_cached(prob, storage: str = "f32", compensated: Optional[Union[bool, str]] = None,
                     scheme: int = LBM_SCHEME_EXPLICIT, cache_path: Optional[str] = None, steps: int = 129,
                     stream: int = 0, device: int = 0) -> lbm_tuning:
     """The autotuner's choice for bodies of prob's size and edge kinds, from a
@@ -352,9 +364,9 @@ def autotune_cached(prob, storage: str = "f32", compensated: Optional[bool] = No
     holds one, else measured now and stored."""
     import json
 
-    comp = True if compensated is None else compensated
+    uc = ucarry_of(compensated)
     kinds = [e.kind for e in prob.edges]
-    key = f"{storage}:{int(comp)}:{scheme}:{prob.nx}x{prob.ny}:{''.join(str(k) for k in kinds)}:p"
+    key = f"{storage}:{uc}:{scheme}:{prob.nx}x{prob.ny}:{''.join(str(k) for k in kinds)}:p"
     cache = {}
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as fh:
@@ -364,7 +376,7 @@ def autotune_cached(prob, storage: str = "f32", compensated: Optional[bool] = No
     d = lbm_desc()
     d.nx, d.ny, d.dX = prob.nx, prob.ny, prob.dX
     d.storage = STORAGE[storage]
-    d.u_carry = LBM_UCARRY_COMPENSATED if comp else LBM_UCARRY_NATIVE
+    d.u_carry = uc
     d.scheme = scheme
     d.cuda_stream = stream or None
     d.device = device
@@ -393,22 +405,21 @@ class Body:
 
     storage: "f64" | "f32" | "f16" | "bf16"; compensated: FP32-pair u-carry
     for "f32" (default True: a plain FP32 u loses Grad u to rounding once
-    |u| >> |H| dX); scheme: LBM_SCHEME_EXPLICIT (default: Algorithm 1, the
+    |u| >> |H| dX; "lo16": the pair with its low word in 16 bits, 12 instead
+    of 16 bytes per node, about 35 significant bits); scheme: LBM_SCHEME_EXPLICIT (default: Algorithm 1, the
     time-t source in collision and moment), LBM_SCHEME_PREDICTOR (the
     footnote's predictor-corrector, which Sec. 7's tension run needs) or
     LBM_SCHEME_EXTRAPOLATED (stable only for lambda = mu);
     stream: an integer cudaStream_t handle (e.g. torch's stream.cuda_stream)."""
 
-    def __init__(self, prob, storage: str = "f64", compensated: Optional[bool] = None,
+    def __init__(self, prob, storage: str = "f64", compensated: Optional[Union[bool, str]] = None,
                  scheme: int = LBM_SCHEME_EXPLICIT, stream: int = 0, device: int = 0,
                  f16_scale_log2: int = 0, tuning: Optional["lbm_tuning"] = None):
         self.prob = prob
         d = lbm_desc()
         d.nx, d.ny, d.dX = prob.nx, prob.ny, prob.dX
         d.storage = STORAGE[storage]
-        if compensated is None:
-            compensated = True
-        d.u_carry = LBM_UCARRY_COMPENSATED if compensated else LBM_UCARRY_NATIVE
+        d.u_carry = ucarry_of(compensated)
         d.scheme = scheme
         d.f16_scale_log2 = f16_scale_log2
         u0, v0 = prob.initial() if hasattr(prob, "initial") else (prob.u0, prob.v0)

@@ -351,8 +351,9 @@ def benchmark_body_runs():
     """The benchmark's body (4096 x 2048 clamped, Algorithm 1's explicit
     moment, omega 1.9) in the benchmark's launch configuration (one-wave
     interior, edge tiles on the side stream, a captured 64-step graph) after
-    70 steps: the FP64 oracle, the FP32 path (compensated carry) and the FP64
-    path on the same inputs."""
+    70 steps: the FP64 oracle, the FP32 path (compensated carry), the FP32
+    path with the carry's low word in 16 bits and the FP64 path on the same
+    inputs."""
     prob = W.clamped_body(4096, 2048, nu=0.25, vmax=0.01)
     s = oracle.solver_from(prob, oracle.EXPLICIT)
     s.step(70)
@@ -361,10 +362,13 @@ def benchmark_body_runs():
     with lbm.Body(prob, storage="f32", compensated=True, scheme=lbm.LBM_SCHEME_EXPLICIT) as b:
         b.step(70)
         got32 = b.read()
+    with lbm.Body(prob, storage="f32", compensated="lo16", scheme=lbm.LBM_SCHEME_EXPLICIT) as b:
+        b.step(70)
+        got32h = b.read()
     with lbm.Body(prob, storage="f64", scheme=lbm.LBM_SCHEME_EXPLICIT) as b:
         b.step(70)
         got64 = b.read()
-    return prob, ref, got32, got64
+    return prob, ref, {"pair": got32, "lo16": got32h}, got64
 
 
 def _bands(nx, ny, w=3):
@@ -383,24 +387,27 @@ def test_benchmark_body_at_full_size_against_the_oracle(benchmark_body_runs):
     nodes and a whole-field norm would hide an error confined to them, the
     largest error in each edge band and corner, relative to the largest
     value of the field, within the same tolerances."""
-    prob, ref, got32, got64 = benchmark_body_runs
-    compare(ref, got32, TOL["f32"], keys=("u", "v"))
+    prob, ref, got32s, got64 = benchmark_body_runs
+    for got32 in got32s.values():
+        compare(ref, got32, TOL["f32"], keys=("u", "v"))
     compare(ref, got64, TOL["f64"], keys=("u", "v", "J"))
     for name, (ys, xs) in _bands(prob.nx, prob.ny).items():
         for k in ("u", "v"):
             scale = np.abs(ref[k]).max()
             e64 = np.abs(got64[k][ys, xs] - ref[k][ys, xs]).max() / scale
-            e32 = np.abs(got32[k][ys, xs] - ref[k][ys, xs]).max() / scale
-            assert e64 <= TOL["f64"] and e32 <= TOL["f32"], (name, k, e64, e32)
+            assert e64 <= TOL["f64"], (name, k, e64)
+            for form, got32 in got32s.items():
+                e32 = np.abs(got32[k][ys, xs] - ref[k][ys, xs]).max() / scale
+                assert e32 <= TOL["f32"], (form, name, k, e32)
 
 
 @pytest.mark.xfail(reason="known miss at this size: P comes from differences of u, and |u| / (|Grad u| dX) is "
                           "about 4e3 after 70 steps, so the rounding of u weighs that much more in P "
                           "(measured FP64 3.2e-12, FP32 2.1e-5)", strict=False)
 def test_benchmark_body_stress_at_full_size_within_the_stated_tolerances(benchmark_body_runs):
-    prob, ref, got32, got64 = benchmark_body_runs
+    prob, ref, got32s, got64 = benchmark_body_runs
     compare(ref, got64, TOL["f64"], keys=("P", "Pbar"))
-    compare(ref, got32, TOL["f32"], keys=("P",))
+    compare(ref, got32s["pair"], TOL["f32"], keys=("P",))
 
 
 def test_benchmark_body_stress_at_full_size_within_its_rounding_floor(benchmark_body_runs):
@@ -414,7 +421,7 @@ def test_benchmark_body_stress_at_full_size_within_its_rounding_floor(benchmark_
     eps_32 |v| sqrt(n) dt / |u|, times kappa in P (here |v| / |u| ~ 1 / t).
     These are floors, not tolerances: P meets the stated 1e-12 / 1e-5 on the
     smaller parity bodies."""
-    prob, ref, got32, got64 = benchmark_body_runs
+    prob, ref, got32s, got64 = benchmark_body_runs
     H = np.stack([np.gradient(ref["u"][:, :, a], prob.dX, axis=ax) for a in range(2) for ax in (1, 0)])
     kappa = np.sqrt((ref["u"] ** 2).mean()) / (np.sqrt((H ** 2).mean()) * prob.dX)
     n, dt = 70, oracle.solver_from(prob).dt
@@ -423,7 +430,8 @@ def test_benchmark_body_stress_at_full_size_within_its_rounding_floor(benchmark_
     floor32 = np.finfo(np.float32).eps * kappa * prob.dX * vu * np.sqrt(n) * dt
     assert 1e3 < kappa < 1e5, kappa
     assert rel_l2(got64["P"], ref["P"]) <= floor64, (rel_l2(got64["P"], ref["P"]), floor64)
-    assert rel_l2(got32["P"], ref["P"]) <= floor32, (rel_l2(got32["P"], ref["P"]), floor32)
+    for form, got32 in got32s.items():
+        assert rel_l2(got32["P"], ref["P"]) <= floor32, (form, rel_l2(got32["P"], ref["P"]), floor32)
 
 
 AUTO_CASES = ["clamped_96x50", "periodic_100x70", "x_periodic_y_walls_70x37", "ragged_33x13_mixed",
