@@ -274,15 +274,17 @@ def run_reference(a):
     if rank != 0:
         return 0
     prob = workload(a)
-    steps = a.cpu_steps or auto_cpu_steps(prob)
+    # K timed samples and W untimed warm-up samples of the same size, the
+    # whole run held to about two minutes of oracle time
+    k = max(1, a.steps)
+    warm = max(0, a.warmup)
+    steps = a.cpu_steps or auto_cpu_steps(prob, budget_s=min(12.0, max(0.5, 120.0 / (k + warm))))
     vals = []
-    # W warm-up samples of one time step each (at most 20: a few seconds)
-    warm = max(1, min(a.warmup, 20)) if a.warmup > 0 else 0
     for _ in range(warm):
-        oracle_sample(prob, 1)
+        oracle_sample(prob, steps)
     t_all = 0.0
     cores = 1
-    for _ in range(max(1, min(a.steps, 3))):
+    for _ in range(k):
         v, dt, cores = oracle_sample(prob, steps)
         vals.append(v)
         t_all += dt
@@ -290,7 +292,7 @@ def run_reference(a):
     sample = f"{steps} time steps of the full {a.nx}x{a.ny} body per timed repetition, {len(vals)} repetitions"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": a.gpus,
-        "steps": len(vals), "warmup": warm, "ms_per_step": 1e3 * prob.nodes / (value * 1e6),
+        "steps": k, "warmup": warm, "ms_per_step": 1e3 * prob.nodes / (value * 1e6),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_of(a, prob),
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
