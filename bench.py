@@ -179,6 +179,88 @@ def ncu_traffic(storage, ucarry, nodes):
     return e["dram_bytes_per_node"] * nodes
 
 
+class NvmlClockSampler:
+    """SM clock and clock-event reasons read through NVML (the driver's
+    libnvidia-ml, by ctypes) every millisecond from a host thread, so that a
+    timed region of a few milliseconds still holds samples.  Reads only."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, device):
+        import ctypes
+        import threading
+
+        self.ct = ctypes
+        self.threading = threading
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.handle = ctypes.c_void_p()
+        bus = None
+        try:
+            import torch
+
+            pr = torch.cuda.get_device_properties(device)
+            bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0".encode()
+        except Exception:
+            bus = None
+        rc = 1
+        if bus is not None:
+            rc = self.lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(self.handle))
+        if rc != 0:
+            rc = self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(device), ctypes.byref(self.handle))
+        if rc != 0:
+            raise OSError("no NVML handle for the device")
+        self.reason_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint(0)
+        self.max_mhz = float(mx.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.handle, 1, ctypes.byref(mx)) == 0 \
+            and mx.value else None
+        self.samples = []
+        self.stop_flag = False
+        self.thread = None
+
+    def sample(self):
+        ct = self.ct
+        clk, rs = ct.c_uint(0), ct.c_ulonglong(0)
+        if self.lib.nvmlDeviceGetClockInfo(self.handle, 1, ct.byref(clk)) != 0:  # NVML_CLOCK_SM
+            return
+        if self.reason_fn(self.handle, ct.byref(rs)) != 0:
+            return
+        self.samples.append((float(clk.value), int(rs.value)))
+
+    def start(self):
+        def run():
+            while not self.stop_flag:
+                self.sample()
+                time.sleep(0.001)
+
+        self.sample()
+        self.thread = self.threading.Thread(target=run, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        self.stop_flag = True
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        self.sample()
+        if not self.samples:
+            return None
+        reasons = sorted({nm for _, r in self.samples for bit, nm in self.REASONS.items() if r & bit})
+        sm = [c for c, _ in self.samples]
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": self.max_mhz or max(sm), "reasons": reasons,
+                "samples": len(sm), "source": "NVML, every 1 ms during the timed region"}
+
+
+def clock_sampler(device):
+    """NVML where the driver's library loads, else nvidia-smi."""
+    try:
+        return NvmlClockSampler(device)
+    except Exception:
+        return ClockSampler(device)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -421,7 +503,7 @@ def run_native(a):
     bytes_per_node = algorithmic_bytes(a.storage)
     body.step(a.warmup)
     body.read(lbm.LBM_FIELD_U, allow_unstable=True)
-    clocks = ClockSampler(local)
+    clocks = clock_sampler(local)
     barrier()
     clocks.start()
     secs = time_steps(body, stream, a.steps)

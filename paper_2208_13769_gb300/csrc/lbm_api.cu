@@ -168,6 +168,12 @@ void lbm::seam_box(const lbm_ctx* c, int box[4]) {
     box[3] = pery ? c->ny : c->ny - 2;
 }
 
+unsigned lbm::bounded_sides(const lbm_ctx* c, const int rect[4]) {
+    const bool perx = c->bc[0].kind == kPeriodic, pery = c->bc[2].kind == kPeriodic;
+    return (!perx && rect[0] == 0 ? 1u : 0u) | (!perx && rect[1] == c->nx ? 2u : 0u) |
+           (!pery && rect[2] == 0 ? 4u : 0u) | (!pery && rect[3] == c->ny ? 8u : 0u);
+}
+
 void lbm::plan_rects(const lbm_ctx* c, bool edge_only, bool seams_inside, int irect[4][4], int* n_irect,
                      int brect[12][4], int* nband) {
     const bool perx = c->bc[0].kind == kPeriodic, pery = c->bc[2].kind == kPeriodic;
@@ -276,16 +282,20 @@ static cudaError_t build_plan(lbm_ctx* c) {
     }
     c->has_interior = c->n_irect > 0;  // a hole may leave the bands only
     int n = 0;
-    for (int b = 0; b < c->nband; ++b) n += edge_tiles_of_rect(c->brect[b], 0, nullptr, 0, false, kEdgeThreads);
+    for (int b = 0; b < c->nband; ++b)
+        n += edge_tiles_of_rect(c->brect[b], 0, nullptr, 0, false, kEdgeThreads, bounded_sides(c, c->brect[b]));
     int ni = n;  // the initialisation's tiles: with a hole, the interior rectangles' too
     if (hole)
-        for (int q = 0; q < c->n_irect; ++q) ni += edge_tiles_of_rect(c->irect[q], 0, nullptr, 0, false, kEdgeThreads);
+        for (int q = 0; q < c->n_irect; ++q)
+            ni += edge_tiles_of_rect(c->irect[q], 0, nullptr, 0, false, kEdgeThreads, 0);
     EdgeTile* h = new (std::nothrow) EdgeTile[size_t(ni)];
     if (!h) return cudaErrorMemoryAllocation;
     int m = 0;
-    for (int b = 0; b < c->nband; ++b) m += edge_tiles_of_rect(c->brect[b], 0, h + m, n - m, m == 0, kEdgeThreads);
+    for (int b = 0; b < c->nband; ++b)
+        m += edge_tiles_of_rect(c->brect[b], 0, h + m, n - m, m == 0, kEdgeThreads, bounded_sides(c, c->brect[b]));
     if (hole)
-        for (int q = 0; q < c->n_irect; ++q) m += edge_tiles_of_rect(c->irect[q], 0, h + m, ni - m, false, kEdgeThreads);
+        for (int q = 0; q < c->n_irect; ++q)
+            m += edge_tiles_of_rect(c->irect[q], 0, h + m, ni - m, false, kEdgeThreads, 0);
     // the images of the interior's nodes next to a periodic seam
     const bool perx = c->bc[0].kind == kPeriodic, pery = c->bc[2].kind == kPeriodic;
     int nimg = 0;

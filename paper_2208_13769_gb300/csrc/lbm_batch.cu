@@ -353,10 +353,11 @@ lbm_status lbm_batch_create_tuned(lbm_ctx* const* members, int32_t n, void* cuda
             bool first = true;
             const int e = first_entry[size_t(i)];
             for (int r = 0; r < mri.nband; ++r) {
-                const int cnt = edge_tiles_of_rect(mri.brect[r], e, nullptr, 0, false, kEdgeThreads);
+                const unsigned bs = bounded_sides(b->m[size_t(i)], mri.brect[r]);
+                const int cnt = edge_tiles_of_rect(mri.brect[r], e, nullptr, 0, false, kEdgeThreads, bs);
                 const size_t at = tiles.size();
                 tiles.resize(at + size_t(cnt));
-                edge_tiles_of_rect(mri.brect[r], e, tiles.data() + at, cnt, first, kEdgeThreads);
+                edge_tiles_of_rect(mri.brect[r], e, tiles.data() + at, cnt, first, kEdgeThreads, bs);
                 first = first && cnt == 0;
             }
             // the images of its interior's nodes next to a periodic seam

@@ -140,6 +140,9 @@ int64_t interior_nodes(const lbm_ctx* c);
 // band on each side of a seam goes to the edge kernel.
 void plan_rects(const lbm_ctx* c, bool edge_only, bool seams_inside, int irect[4][4], int* n_irect,
                 int brect[12][4], int* nband);
+// The sides of rect on a bounded edge of the body (bit 0: x low, 1: x high,
+// 2: y low, 3: y high), for edge_tiles_of_rect.
+unsigned bounded_sides(const lbm_ctx* c, const int rect[4]);
 // The box of image sources of a body whose interior kernel runs across its
 // periodic seams: the whole axis where periodic, nodes 2 .. n - 3 where bounded.
 void seam_box(const lbm_ctx* c, int box[4]);

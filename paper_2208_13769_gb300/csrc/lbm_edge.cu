@@ -55,6 +55,8 @@ __global__ void __launch_bounds__(kEdgeThreads, 3)
         tile.y1 = min(L.rect[3], tile.y0 + oh);
         tile.tw = 32;
         tile.th = uint8_t(N / 32);
+        tile.hx = 2;
+        tile.hy = 2;
         tile.lead = b == 0;
     }
     {
@@ -116,30 +118,39 @@ cudaError_t launch_edge_images(int fmt, const EdgeLaunch& L, int n_edge, const I
 
 // Tiles of one rectangle for CTAs of nthreads threads.  A band at most 3
 // nodes thick gets tiles exactly as thick (th = thickness + 4 rows of
-// threads, tw = nthreads / th columns), so few threads compute halo only; a
-// larger rectangle gets wide tiles (32 x 8 threads for 256, 16 x 8 for 128).
-// Every tile has the full extent min(rectangle, tile) along both axes (the
-// last one of a row or column is shifted back, recomputing its neighbour's
-// nodes bit for bit), so each output node on a bounded edge (bodies and
-// bands are at least 2 nodes thick) finds the Q of its two inward
-// neighbours, which stage B computes for the output nodes and their 1-node
-// ring, inside the tile.  Returns the number of tiles (written to out, at
-// most cap, when out is not NULL).
-int edge_tiles_of_rect(const int rect[4], int inst, EdgeTile* out, int cap, bool lead_first, int nthreads) {
+// threads, 2 fewer for each side on a bounded edge of the body, where the
+// halo would lie outside it; tw = nthreads / th columns), so few threads
+// compute halo only; a larger rectangle gets wide tiles (32 x 8 threads for
+// 256, 16 x 8 for 128).  Every tile has the full extent min(rectangle, tile)
+// along both axes (the last one of a row or column is shifted back,
+// recomputing its neighbour's nodes bit for bit), so each output node on a
+// bounded edge (bodies and bands are at least 2 nodes thick) finds the Q of
+// its two inward neighbours, which stage B computes for the output nodes and
+// their 1-node ring, inside the tile.  Returns the number of tiles (written
+// to out, at most cap, when out is not NULL).
+int edge_tiles_of_rect(const int rect[4], int inst, EdgeTile* out, int cap, bool lead_first, int nthreads,
+                       unsigned bounded) {
     const int w = rect[1] - rect[0], h = rect[3] - rect[2];
     if (w <= 0 || h <= 0 || nthreads < 128) return 0;
-    int tw, th;
+    int tw, th, hx = 2, hy = 2, ow, oh;
     if (h <= 3) {
-        th = h + 4;
-        tw = nthreads / th;
+        hy = (bounded & 4) ? 0 : 2;
+        th = h + hy + ((bounded & 8) ? 0 : 2);
+        tw = nthreads / th < 255 ? nthreads / th : 255;
+        ow = tw - 4;
+        oh = h;
     } else if (w <= 3) {
-        tw = w + 4;
-        th = nthreads / tw;
+        hx = (bounded & 1) ? 0 : 2;
+        tw = w + hx + ((bounded & 2) ? 0 : 2);
+        th = nthreads / tw < 255 ? nthreads / tw : 255;
+        ow = w;
+        oh = th - 4;
     } else {
         th = 8;
         tw = nthreads / th >= 32 ? 32 : nthreads / th;
+        ow = tw - 4;
+        oh = th - 4;
     }
-    const int ow = tw - 4, oh = th - 4;
     int n = 0;
     for (int y = rect[2]; y < rect[3]; y += oh)
         for (int x = rect[0]; x < rect[1]; x += ow) {
@@ -154,6 +165,8 @@ int edge_tiles_of_rect(const int rect[4], int inst, EdgeTile* out, int cap, bool
                 e.y1 = ys + oh < rect[3] ? ys + oh : rect[3];
                 e.tw = uint8_t(tw);
                 e.th = uint8_t(th);
+                e.hx = uint8_t(hx);
+                e.hy = uint8_t(hy);
                 e.lead = int16_t(lead_first && n == 0);
             }
             ++n;

@@ -186,7 +186,8 @@ __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepP
     const int tw = tile.tw, th = tile.th;
     const int tx = t % tw, ty = t / tw;  // ty >= th: an idle thread
     const int nxo = tile.x1 - tile.x0, nyo = tile.y1 - tile.y0;  // output extent
-    const int gxr = tile.x0 - 2 + tx, gyr = tile.y0 - 2 + ty;
+    const int hx = tile.hx, hy = tile.hy;  // halo before the output nodes
+    const int gxr = tile.x0 - hx + tx, gyr = tile.y0 - hy + ty;
     const bool okx = g.perx ? (gxr >= -2 && gxr < nx + 2) : (gxr >= 0 && gxr < nx);
     const bool oky = g.pery ? (gyr >= -2 && gyr < ny + 2) : (gyr >= 0 && gyr < ny);
     const int gx = g.perx ? wrap_coord(gxr, nx) : gxr;
@@ -197,8 +198,8 @@ __device__ __forceinline__ void edge_tile_body(const EdgeTile& tile, const StepP
     const bool holed = HOLE && p.hole[0] < p.hole[1];  // the body has a hole (uniform)
     const bool removed = holed && in_hole(p.hole, gx, gy);
     const bool inA = okx && oky && ty < th && !removed;
-    const bool inB = inA && tx >= 1 && tx <= nxo + 2 && ty >= 1 && ty <= nyo + 2;
-    const bool inC = tx >= 2 && tx < nxo + 2 && ty >= 2 && ty < nyo + 2 && !removed;
+    const bool inB = inA && tx >= hx - 1 && tx <= hx + nxo && ty >= hy - 1 && ty <= hy + nyo;
+    const bool inC = tx >= hx && tx < hx + nxo && ty >= hy && ty < hy + nyo && !removed;
     // a removed neighbour along an axis is a face of the hole: a bounded edge
     // for the ghost rules
     const bool hxl = holed && in_hole(p.hole, gx - 1, gy), hxh = holed && in_hole(p.hole, gx + 1, gy);

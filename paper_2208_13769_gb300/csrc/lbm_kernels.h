@@ -78,8 +78,9 @@ cudaError_t launch_batch_interior(int fmt, const BatchInteriorLaunch& L, int rin
                                   int* resident);
 
 // The edge kernel (lbm_edge.cu): small 2-D tiles with every boundary rule.
-// A tile's threads cover its output nodes and a 2-node halo: tw x th nodes
-// (tw x th <= kEdgeThreads), (tw - 4) x (th - 4) of them output.
+// A tile's threads cover its output nodes and a 2-node halo, except beyond a
+// side that lies on a bounded edge of the body, where there are no nodes:
+// tw x th nodes (tw x th <= kEdgeThreads), from (x0 - hx, y0 - hy).
 constexpr int kEdgeThreads = 256;
 
 struct EdgeTile {
@@ -87,6 +88,7 @@ struct EdgeTile {
     int32_t x0, y0;  // first output node
     int32_t x1, y1;  // one past the last output node
     uint8_t tw, th;  // threads along x and y
+    uint8_t hx, hy;  // halo nodes before the first output node (2, or 0 on a bounded edge)
     int16_t lead;    // this tile advances the instance's step counter
 };
 
@@ -104,8 +106,11 @@ struct EdgeLaunch {
 cudaError_t launch_edge(int fmt, const EdgeLaunch& L, int ntiles, cudaStream_t s, int mode, bool holed, bool xj);
 
 // Tiles of one band rectangle for CTAs of `nthreads` threads (kEdgeThreads
-// for the edge kernel); count only when out is NULL.
-int edge_tiles_of_rect(const int rect[4], int inst, EdgeTile* out, int cap, bool lead_first, int nthreads);
+// for the edge kernel); count only when out is NULL.  bounded: the sides of
+// rect that lie on a bounded edge of the body (bit 0: x low, 1: x high,
+// 2: y low, 3: y high), beyond which a band's tiles need no halo.
+int edge_tiles_of_rect(const int rect[4], int inst, EdgeTile* out, int cap, bool lead_first, int nthreads,
+                       unsigned bounded);
 
 // Read-out parameters: stresses from the FP64 displacement field.
 struct ReadoutParams {
