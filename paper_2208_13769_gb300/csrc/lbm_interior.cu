@@ -513,9 +513,15 @@ __global__ void __launch_bounds__(NT, MINB) batch_interior_kernel(const __grid_c
     }
     __syncthreads();
     const TileGeom tg = {{sp.rect[0], sp.rect[1], sp.rect[2], sp.rect[3]}, sp.strip_x0, sp.strip_w, sp.chunk_rows};
-    // (one walk direction: a batch's chunks of a strip run in different
-    // waves, and the second path would spill at this register cap)
-    interior_tile<TS, TC, UT, NT, true, false, UNROLL3, false>(sp, tg, it.a, it.b, L.fields ? sp.fields : nullptr);
+    // chunks of odd index walk up their rows, as in the single-body kernel:
+    // the list holds a member's chunks row by row, so the chunks on either
+    // side of a boundary run at about the same time and read its halo rows
+    // together (not the unrolled row loop, whose second copy would cost more
+    // than the L2 hits give)
+    if (!UNROLL3 && (it.b & 1))
+        interior_tile<TS, TC, UT, NT, true, false, UNROLL3, true>(sp, tg, it.a, it.b, L.fields ? sp.fields : nullptr);
+    else
+        interior_tile<TS, TC, UT, NT, true, false, UNROLL3, false>(sp, tg, it.a, it.b, L.fields ? sp.fields : nullptr);
 }
 
 template <class TS, class TC, class UT, int NT>
