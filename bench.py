@@ -616,7 +616,9 @@ def run_native(a):
     # its displacement error against the FP64 path on the same inputs (the
     # full field and the stride-16 downsample, 512 x 512 points); the FP64
     # path stands in for the oracle, which this size would keep busy for an
-    # hour; the body stays inside the method's stable horizon
+    # hour; at the default 5000 steps the body stays inside the method's
+    # stable horizon (at the planned 20 000 it does not: the runs report
+    # LBM_E_UNSTABLE and the errors are not finite)
     c3 = None
     if a.c3_steps > 0 and world == 1:
         from paper_2208_13769_gb300 import workloads as W
