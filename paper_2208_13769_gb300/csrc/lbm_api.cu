@@ -401,8 +401,8 @@ static cudaError_t launch_step_kernels(lbm_ctx* c, int mode, bool fields, int pa
         L.rect[1] = c->nx;
         L.rect[2] = 0;
         L.rect[3] = c->ny;
-        L.rtiles_x = (c->nx + 27) / 28;
-        const int64_t ntiles = int64_t(L.rtiles_x) * ((c->ny + 3) / 4);
+        L.rtiles_x = (c->nx + kInitOutW - 1) / kInitOutW;
+        const int64_t ntiles = int64_t(L.rtiles_x) * ((c->ny + kInitOutH - 1) / kInitOutH);
         if (ntiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
         return launch_edge(c->fmt, L, int(ntiles), c->stream, 1, true, false);
     }

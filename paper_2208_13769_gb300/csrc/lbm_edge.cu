@@ -44,17 +44,17 @@ __global__ void __launch_bounds__(kEdgeThreads, 3)
     EdgeTile tile;
     if (L.tiles != nullptr) {
         tile = L.tiles[blockIdx.x];
-    } else {  // implicit grid of wide tiles over L.rect (last tiles shifted back)
+    } else {  // implicit grid of square tiles over L.rect (last tiles shifted back)
         const int b = int(blockIdx.x);
         const int bx = b % L.rtiles_x, by = b / L.rtiles_x;
-        constexpr int ow = 32 - 4, oh = N / 32 - 4;
+        constexpr int ow = kInitOutW, oh = kInitOutH;
         tile.inst = 0;
         tile.x0 = max(L.rect[0], min(L.rect[0] + bx * ow, L.rect[1] - ow));
         tile.x1 = min(L.rect[1], tile.x0 + ow);
         tile.y0 = max(L.rect[2], min(L.rect[2] + by * oh, L.rect[3] - oh));
         tile.y1 = min(L.rect[3], tile.y0 + oh);
-        tile.tw = 32;
-        tile.th = uint8_t(N / 32);
+        tile.tw = kInitTileW;
+        tile.th = uint8_t(N / kInitTileW);
         tile.hx = 2;
         tile.hy = 2;
         tile.lead = b == 0;
