@@ -632,16 +632,19 @@ lbm_status lbm_create(const lbm_desc* d, lbm_ctx** out) {
         return err == cudaErrorMemoryAllocation ? LBM_E_OOM : LBM_E_CUDA;
     }
     c->device_bytes = int64_t(2 * (fbytes + abytes + sbytes) + fldbytes + (d->u0 ? ubytes : 0) + (d->v0 ? ubytes : 0));
+    // the state is cleared on the side stream while the initial fields are
+    // uploaded on the main one (the copy engines and the SMs work at once)
     for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
-        err = cudaMemsetAsync(c->f[k], 0, fbytes, c->stream);
-        if (err == cudaSuccess) err = cudaMemsetAsync(c->a[k], 0, abytes, c->stream);
-        if (err == cudaSuccess) err = cudaMemsetAsync(c->s[k], 0, sbytes, c->stream);
+        err = cudaMemsetAsync(c->f[k], 0, fbytes, c->side);
+        if (err == cudaSuccess) err = cudaMemsetAsync(c->a[k], 0, abytes, c->side);
+        if (err == cudaSuccess) err = cudaMemsetAsync(c->s[k], 0, sbytes, c->side);
     }
-    if (err == cudaSuccess) err = cudaMemsetAsync(c->fields, 0, fldbytes, c->stream);
-    if (err == cudaSuccess) err = cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->stream);
-    if (err == cudaSuccess) err = cudaMemsetAsync(c->counter, 0, 2 * sizeof(int64_t), c->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(c->fields, 0, fldbytes, c->side);
+    if (err == cudaSuccess) err = cudaMemsetAsync(c->flag, 0, sizeof(int32_t), c->side);
+    if (err == cudaSuccess) err = cudaMemsetAsync(c->counter, 0, 2 * sizeof(int64_t), c->side);
     if (err == cudaSuccess && d->u0) err = cudaMemcpyAsync(c->u0, d->u0, ubytes, cudaMemcpyHostToDevice, c->stream);
     if (err == cudaSuccess && d->v0) err = cudaMemcpyAsync(c->v0, d->v0, ubytes, cudaMemcpyHostToDevice, c->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(c->side);
     if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
     if (err != cudaSuccess) {
         free_all(c);
