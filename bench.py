@@ -315,15 +315,27 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- oracle (CPU)
 
-def oracle_sample(prob, steps):
-    """Times the FP64 CPU oracle as it stands on `steps` steps of prob."""
+ORACLE_SCHEME = {"explicit": "EXPLICIT", "predictor": "PREDICTOR", "extrapolated": "EXTRAPOLATED"}
+
+
+def oracle_solver(prob, scheme):
+    """The FP64 CPU oracle on prob with the benchmark's scheme."""
     import oracle
 
-    s = oracle.solver_from(prob)
+    return oracle.solver_from(prob, getattr(oracle, ORACLE_SCHEME[scheme]))
+
+
+def oracle_sample(prob, steps, scheme="explicit", solver=None):
+    """Times the FP64 CPU oracle as it stands on `steps` steps of prob: on
+    `solver`, which goes on from its current state, or on a new one."""
+    import oracle
+
+    s = solver if solver is not None else oracle_solver(prob, scheme)
     t0 = time.perf_counter()
     s.step(steps)
     dt = time.perf_counter() - t0
-    s.close()
+    if solver is None:
+        s.close()
     return prob.nodes * steps / dt / 1e6, dt, oracle.threads()
 
 
@@ -334,7 +346,7 @@ def oracle_single_thread(a, steps):
     env = dict(os.environ, OMP_NUM_THREADS="1")
     cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", "1", "--warmup", "0",
            "--cpu-steps", str(steps), "--nx", str(a.nx), "--ny", str(a.ny), "--nu", str(a.nu),
-           "--vmax", str(a.vmax)]
+           "--vmax", str(a.vmax), "--scheme", a.scheme]
     try:
         r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600, check=True)
         line = json.loads(r.stdout.strip().splitlines()[-1])
@@ -344,8 +356,8 @@ def oracle_single_thread(a, steps):
         return {"value": None, "error": str(exc)[:200]}
 
 
-def auto_cpu_steps(prob, budget_s=12.0):
-    mlups, dt, _ = oracle_sample(prob, 1)
+def auto_cpu_steps(prob, budget_s=12.0, scheme="explicit", solver=None):
+    mlups, dt, _ = oracle_sample(prob, 1, scheme, solver)
     per = prob.nodes / (mlups * 1e6)
     return max(1, min(200, int(budget_s / max(per, 1e-9))))
 
@@ -355,20 +367,23 @@ def run_reference(a):
     if rank != 0:
         return 0
     prob = workload(a)
-    # K timed samples and W untimed warm-up samples of the same size, the
-    # whole run held to about two minutes of oracle time
+    # one oracle body, timed over W untimed and then K timed samples of the
+    # same number of time steps, the whole run held to about two minutes of
+    # oracle time (the body stays well inside its stable horizon)
     k = max(1, a.steps)
     warm = max(0, a.warmup)
-    steps = a.cpu_steps or auto_cpu_steps(prob, budget_s=min(12.0, max(0.5, 120.0 / (k + warm))))
+    solver = oracle_solver(prob, a.scheme)
+    steps = a.cpu_steps or auto_cpu_steps(prob, min(12.0, max(0.5, 120.0 / (k + warm))), a.scheme, solver)
     vals = []
     for _ in range(warm):
-        oracle_sample(prob, steps)
+        oracle_sample(prob, steps, a.scheme, solver)
     t_all = 0.0
     cores = 1
     for _ in range(k):
-        v, dt, cores = oracle_sample(prob, steps)
+        v, dt, cores = oracle_sample(prob, steps, a.scheme, solver)
         vals.append(v)
         t_all += dt
+    solver.close()
     value = statistics.median(vals)
     sample = f"{steps} time steps of the full {a.nx}x{a.ny} body per timed repetition, {len(vals)} repetitions"
     line = {
@@ -864,8 +879,8 @@ def run_native(a):
 
     cpu = None
     if rank == 0 and not a.no_cpu:
-        steps = a.cpu_steps or auto_cpu_steps(prob)
-        v, dt, cores = oracle_sample(prob, steps)
+        steps = a.cpu_steps or auto_cpu_steps(prob, scheme=a.scheme)
+        v, dt, cores = oracle_sample(prob, steps, a.scheme)
         cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": f"{steps} time steps of the full {a.nx}x{a.ny} body ({dt:.1f} s, FP64 oracle)",
                "single_thread": oracle_single_thread(a, max(1, steps // max(1, cores)))}
