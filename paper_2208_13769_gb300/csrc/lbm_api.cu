@@ -10,6 +10,7 @@
 
 #include "lbm.h"
 #include "lbm_context.h"
+#include "lbm_init_grid.h"
 #include "lbm_kernels.h"
 
 using namespace lbm;

@@ -18,6 +18,7 @@
 #include "lbm_kernels.h"
 #include "lbm_edge_tile.cuh"
 #include "lbm_images.cuh"
+#include "lbm_init_grid.h"
 #include "lbm_pipeline.cuh"
 
 namespace lbm {

@@ -82,11 +82,6 @@ cudaError_t launch_batch_interior(int fmt, const BatchInteriorLaunch& L, int rin
 // side that lies on a bounded edge of the body, where there are no nodes:
 // tw x th nodes (tw x th <= kEdgeThreads), from (x0 - hx, y0 - hy).
 constexpr int kEdgeThreads = 256;
-// The initialisation's implicit grid over the whole body: tiles of
-// kInitTileW x (kEdgeThreads / kInitTileW) threads, 12 x 12 output nodes
-// (144 of 256 threads, against 112 for 32 x 8).
-constexpr int kInitTileW = 16;
-constexpr int kInitOutW = kInitTileW - 4, kInitOutH = kEdgeThreads / kInitTileW - 4;
 
 struct EdgeTile {
     int32_t inst;    // entry of the parameter table
